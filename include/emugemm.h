@@ -1,0 +1,327 @@
+/*
+ * emugemm.h -- C ABI of the GB300 (sm_103a) emulated-GEMM library.
+ *
+ * The library computes C = alpha * A * B + beta * C for FP64, FP32 and
+ * complex128 matrices on the INT8 tensor cores, with the two Ozaki schemes
+ * of the EmuGEMM paper (Lu, Maeder, Luisier, Ziogas):
+ *
+ *   Scheme I  (Sec. II-C-1, Eqs. 1-3; fused kernel of Algorithm 1, Sec. III)
+ *     Each row of A and each column of B is scaled by a power of two to its
+ *     maximum exponent and cut into p INT8 slices (signed leading slice,
+ *     unsigned tails, beta = 8 bits each).  All p(p+1)/2 slice products with
+ *     i + j < p are formed exactly in INT32 and combined by the shift-reduce
+ *     of Eq. (3).  Here the shift-reduce is exact: the partial sums are
+ *     combined as integers and rounded once to binary64.
+ *
+ *   Scheme II (Sec. II-C-2, Eqs. 4-8; fused kernel of Sec. IV-A)
+ *     A and B are scaled to integers, reduced modulo N pairwise-coprime
+ *     moduli m_l <= 256 (256, 255, 253, 251, ...), multiplied with one INT8
+ *     GEMM per modulus, reduced modulo m_l and reconstructed by the Chinese
+ *     Remainder Theorem (Eq. 8), all inside one kernel.  Complex input uses
+ *     the 3M method (Eq. 16).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Pointers named A, B, C, X, or ending in _dev are DEVICE pointers on the
+ *    handle's device.  They are owned by the caller; the library reads or
+ *    writes them only inside the stream-ordered work it enqueues and never
+ *    keeps them after the call returns.  Pointers ending in _host are host
+ *    pointers, read or written before the call returns.
+ *  - layout (EMU_ROW_MAJOR / EMU_COL_MAJOR) applies to A, B and C together.
+ *    Row-major: element (i, j) of an r x c matrix X with leading dimension
+ *    ldx is X[i * ldx + j], ldx >= c.  Column-major: X[i + j * ldx],
+ *    ldx >= r.  A is m x k, B is k x n, C is m x n.
+ *  - Complex matrices are arrays of interleaved (re, im) doubles
+ *    (cuDoubleComplex layout); leading dimensions count complex elements.
+ *    alpha and beta of emu_zgemm are host arrays {re, im}.
+ *  - beta == 0 means C is not read (NaN in C is ignored).
+ *  - All work is enqueued on `stream` (0 = legacy default stream) and the
+ *    call returns without synchronising.  Errors visible on the host are
+ *    returned at once and nothing is enqueued.  Errors found on the device
+ *    (non-finite input, a bounded wait that timed out) are recorded in the
+ *    handle's device status word; emu_get_status synchronises the stream
+ *    and returns them.  When the status word reports an error the contents
+ *    of C are unspecified.  No kernel traps.
+ *  - A handle owns workspace and is not thread safe: calls that share a
+ *    handle must be ordered (same stream, or synchronised by the caller).
+ *  - m, n or k equal to 0 is valid: with k == 0 the product is zero and
+ *    C = beta * C (alpha ignored); with m == 0 or n == 0 nothing is done.
+ */
+#ifndef EMUGEMM_H
+#define EMUGEMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct emu_handle_s *emu_handle_t;
+typedef void *emu_stream_t; /* a cudaStream_t */
+
+typedef enum { EMU_ROW_MAJOR = 0, EMU_COL_MAJOR = 1 } emu_layout_t;
+
+typedef enum { EMU_SCHEME_I = 1, EMU_SCHEME_II = 2 } emu_scheme_t;
+
+typedef enum {
+  EMU_OK = 0,
+  EMU_ERR_INVALID_ARG = 1, /* bad pointer, size, leading dimension or enum */
+  EMU_ERR_UNSUPPORTED = 2, /* p / N / k outside the supported range        */
+  EMU_ERR_NONFINITE = 3,   /* an input held NaN or +-inf (device-detected) */
+  EMU_ERR_CUDA = 4,        /* a CUDA runtime or driver call failed         */
+  EMU_ERR_ALLOC = 5,       /* device memory could not be allocated         */
+  EMU_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up           */
+  EMU_ERR_TOL_NOT_MET = 7  /* auto precision: tolerance not met at p_max   */
+} emu_status_t;
+
+/* Supported ranges. */
+#define EMU_P_MIN 1          /* Scheme I slices                         */
+#define EMU_P_MAX 12
+#define EMU_NM_MIN 1         /* Scheme II moduli                        */
+#define EMU_NM_MAX 20
+#define EMU_K_MAX_II 131071  /* Scheme II: |products| <= 2^14, INT32 exact */
+
+/* ------------------------------------------------------------------ */
+/* Handle, status, workspace                                           */
+/* ------------------------------------------------------------------ */
+
+/* Create a handle bound to CUDA device `device` (made current inside every
+ * call).  Allocates a small device status word.  Errors: EMU_ERR_CUDA,
+ * EMU_ERR_ALLOC, EMU_ERR_INVALID_ARG (h == NULL). */
+emu_status_t emu_create(emu_handle_t *h, int device);
+
+/* Destroy a handle: synchronises its device, frees library-owned workspace,
+ * cached graphs and the status word.  NULL is accepted. */
+emu_status_t emu_destroy(emu_handle_t h);
+
+/* Synchronise `stream`, read and clear the device status word.  Returns
+ * EMU_OK, EMU_ERR_NONFINITE, EMU_ERR_TIMEOUT or EMU_ERR_CUDA. */
+emu_status_t emu_get_status(emu_handle_t h, emu_stream_t stream);
+
+/* Human-readable name of a status code (static string). */
+const char *emu_status_string(emu_status_t s);
+
+/* Bytes of device workspace one call needs (is_complex selects the 3M
+ * Scheme II layout: three residue sets per operand). */
+emu_status_t emu_workspace_size(emu_scheme_t scheme, int64_t m, int64_t n, int64_t k, int p_or_nm,
+                                int is_complex, size_t *bytes_host);
+
+/* Give the handle a caller-owned workspace (device pointer, 256-byte
+ * aligned).  Calls that need more than `bytes` return EMU_ERR_ALLOC instead
+ * of allocating.  Passing NULL returns to library-owned workspace, which is
+ * grown with cudaMallocAsync on the call's stream when needed. */
+emu_status_t emu_set_workspace(emu_handle_t h, void *workspace_dev, size_t bytes);
+
+/* ------------------------------------------------------------------ */
+/* Emulated GEMM                                                       */
+/* ------------------------------------------------------------------ */
+
+/* FP64 C = alpha*A*B + beta*C.  scheme = EMU_SCHEME_I with p_or_nm = p in
+ * [EMU_P_MIN, EMU_P_MAX] slices, or EMU_SCHEME_II with p_or_nm = N in
+ * [EMU_NM_MIN, EMU_NM_MAX] moduli (k <= EMU_K_MAX_II).  Sec. II-C. */
+emu_status_t emu_dgemm(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k,
+                       double alpha, const double *A, int64_t lda, const double *B, int64_t ldb,
+                       double beta, double *C, int64_t ldc, emu_scheme_t scheme, int p_or_nm,
+                       emu_stream_t stream);
+
+/* FP32 C = alpha*A*B + beta*C.  The inputs are widened to binary64 exactly,
+ * the method runs as in emu_dgemm, and each result is rounded once more to
+ * binary32 (the paper's SGEMM emulation, Sec. III-B, "FP32 or FP64 output"). */
+emu_status_t emu_sgemm(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k,
+                       float alpha, const float *A, int64_t lda, const float *B, int64_t ldb,
+                       float beta, float *C, int64_t ldc, emu_scheme_t scheme, int p_or_nm,
+                       emu_stream_t stream);
+
+/* complex128 C = alpha*A*B + beta*C by Scheme II with the 3M method
+ * (Sec. IV-B, Eq. 16): per modulus T1 = Re*Re, T2 = Im*Im, T3 = Sum*Sum,
+ * Re(C') = T1 - T2, Im(C') = T3 - T1 - T2 (mod m_l), one CRT per part.
+ * One power-of-two scale per row of A / column of B covers both parts.
+ * scheme must be EMU_SCHEME_II (EMU_SCHEME_I returns EMU_ERR_UNSUPPORTED). */
+emu_status_t emu_zgemm(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k,
+                       const double *alpha_host, const double *A, int64_t lda, const double *B,
+                       int64_t ldb, const double *beta_host, double *C, int64_t ldc,
+                       emu_scheme_t scheme, int nm, emu_stream_t stream);
+
+/* ------------------------------------------------------------------ */
+/* Steps of the path, exported for verification and ablation           */
+/* ------------------------------------------------------------------ */
+
+/* Layout of the split outputs (Eq. 11, "interleaved" layout): an operand
+ * with `rows` reduction vectors of length k becomes an int8 matrix of
+ * emu_split_rows(rows) rows and emu_split_cols_I(k, p) columns, row-major,
+ * K contiguous.  Row r, K-chunk c (32 wide), slice t occupies bytes
+ * [(c*p + t)*32, (c*p + t)*32 + 32).  Slice 0 is two's-complement signed,
+ * slices t >= 1 are unsigned bytes.  Rows >= `rows` and K >= k are zero.
+ * emu_split_rows rounds up to a multiple of 128, emu_split_cols_I(k, p) is
+ * p * (k rounded up to 32).  Scheme II uses planes: plane l (modulus m_l) is
+ * a matrix of emu_split_rows(rows) x emu_split_cols_II(k) int8 symmetric
+ * residues, emu_split_cols_II(k) = k rounded up to 128. */
+int64_t emu_split_rows(int64_t rows);
+int64_t emu_split_cols_I(int64_t k, int p);
+int64_t emu_split_cols_II(int64_t k);
+
+/* Scheme I split of one operand (Eq. 1 + Eq. 11).  operand = 0: the rows
+ * of the m x k matrix X (the A operand); operand = 1: the columns of the
+ * k x n matrix X (the B operand).  `rows` is m or n.  Writes the
+ * interleaved slices to hat_dev (emu_split_rows(rows) * emu_split_cols_I(k,
+ * p) bytes) and the exponents E (smallest E with max |x| < 2^E, 0 for a zero
+ * vector) to exp_dev (int32[rows]).  Non-finite input sets the status word. */
+emu_status_t emu_split_I(emu_handle_t h, emu_layout_t layout, int operand, int64_t rows, int64_t k,
+                         const double *X, int64_t ldx, int p, int8_t *hat_dev, int32_t *exp_dev,
+                         emu_stream_t stream);
+
+/* Scheme II split of one operand (Eq. 5): residues of trunc(x * 2^(b - E))
+ * for the first nm moduli, b = emu_scale_bits_II(nm, k_total, 0).  Writes
+ * nm planes to res_dev (nm * emu_split_rows(rows) * emu_split_cols_II(k)
+ * bytes) and exponents to exp_dev.  k_total is the K of the product whose
+ * scaling is wanted (normally k). */
+emu_status_t emu_split_II(emu_handle_t h, emu_layout_t layout, int operand, int64_t rows, int64_t k,
+                          int64_t k_total, const double *X, int64_t ldx, int nm, int8_t *res_dev,
+                          int32_t *exp_dev, emu_stream_t stream);
+
+/* Unfused ("naive") Scheme I: the exact INT32 partials C_s of Eq. (2),
+ * s = 0..p-1, written to Cs_dev as p row-major m x n int32 matrices
+ * (Cs_dev[(s*m + i)*n + j]).  Requires k <= emu_chunk_len_I(p) so that every
+ * C_s fits in INT32; A, B and layout as in emu_dgemm.  This is the INT32
+ * round trip that the fused kernel avoids (Eq. 9); it shares the fused
+ * kernel's main loop. */
+emu_status_t emu_partials_I(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k,
+                            const double *A, int64_t lda, const double *B, int64_t ldb, int p,
+                            int32_t *Cs_dev, emu_stream_t stream);
+
+/* Paper-design Scheme II output (Sec. IV-A): per-modulus INT8 residues
+ * C'_l = (A'_l B'_l) mod m_l in [0, m_l), as nm row-major m x n uint8
+ * matrices (R_dev[(l*m + i)*n + j]).  The CRT is left to the caller. */
+emu_status_t emu_residues_II(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k,
+                             const double *A, int64_t lda, const double *B, int64_t ldb, int nm,
+                             uint8_t *R_dev, emu_stream_t stream);
+
+/* Method constants computed by the library's host code. */
+int64_t emu_chunk_len_I(int p);              /* K_c: INT32-exact K range of Eq. (2) */
+int emu_moduli(int nm, int32_t *mods_host); /* first nm moduli; returns count      */
+int emu_scale_bits_II(int nm, int64_t k, int is_complex); /* Scheme II exponent b    */
+
+/* ------------------------------------------------------------------ */
+/* Grouped (batched) emulated DGEMM                                    */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+  int64_t m, n, k;
+  double alpha, beta;
+  const double *A; /* device */
+  int64_t lda;
+  const double *B; /* device */
+  int64_t ldb;
+  double *C; /* device */
+  int64_t ldc;
+} emu_gemm_desc_t;
+
+/* `count` independent Scheme I products with p slices (row-major, the
+ * descriptors are host memory).  One grouped split launch and one
+ * persistent grouped GEMM launch over a (problem, tile) work list ordered
+ * longest-first; the launch sequence is captured once into a CUDA graph and
+ * replayed while the descriptors stay identical.  Tile shapes come from the
+ * autotuner cache (emu_tune_grouped) or a default.  The paper has no
+ * batched interface; the tile model follows Table I. */
+emu_status_t emu_dgemm_grouped(emu_handle_t h, int count, const emu_gemm_desc_t *descs_host, int p,
+                               emu_stream_t stream);
+
+/* Same products, one emu_dgemm call per problem (the launch-loop baseline). */
+emu_status_t emu_dgemm_grouped_loop(emu_handle_t h, int count, const emu_gemm_desc_t *descs_host,
+                                    int p, emu_stream_t stream);
+
+/* Autotune the grouped tile configuration for this problem list: times the
+ * candidate configurations (Table I: tile M/N and pipeline depth) on the
+ * given data and stores the fastest per shape bucket in the handle; writes
+ * the chosen configuration index per bucket to the cache file `path` if
+ * non-NULL.  Returns the number of configurations timed in *timed_host. */
+emu_status_t emu_tune_grouped(emu_handle_t h, int count, const emu_gemm_desc_t *descs_host, int p,
+                              const char *path, int *timed_host, emu_stream_t stream);
+
+/* Load a tuning cache written by emu_tune_grouped. */
+emu_status_t emu_load_tuning(emu_handle_t h, const char *path);
+
+/* ------------------------------------------------------------------ */
+/* Learned slice-count selector                                        */
+/* ------------------------------------------------------------------ */
+
+/* MLP 66 -> 64 -> 64 -> 8 (ReLU, softmax over p = 3..10), FP32, 8968
+ * parameters in the packed order W1[64][66], b1[64], W2[64][64], b2[64],
+ * W3[8][64], b3[8].  The paper has no selector (it lacks automatic dynamic
+ * precision, Sec. VII); this is the library's own. */
+#define EMU_SEL_IN 66
+#define EMU_SEL_HID 64
+#define EMU_SEL_OUT 8
+#define EMU_SEL_P0 3
+#define EMU_SEL_NPARAM 8968
+
+/* Features of one product (device output float[66]): 32-bin histogram of
+ * E_i - e(a_ij) (exponent deficit of each element of A against its row
+ * maximum, bins 0..30 and >= 31, zeros in bin 31) normalised to sum 1, the
+ * same for the columns of B, log2(k)/16 and -log10(tol)/16.  A, B device,
+ * layout as emu_dgemm; at most `sample` rows of A and columns of B are read
+ * (evenly spaced; 0 = all). */
+emu_status_t emu_sel_features(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k,
+                              const double *A, int64_t lda, const double *B, int64_t ldb, double tol,
+                              int64_t sample, float *feat_dev, emu_stream_t stream);
+
+/* Forward pass for `batch` feature rows X_dev[batch][66] -> probabilities
+ * P_dev[batch][8]; params_dev holds the packed parameters.  When act_dev is
+ * non-NULL the hidden activations (batch x 128 floats) are saved for the
+ * backward pass. */
+emu_status_t emu_sel_forward(emu_handle_t h, int64_t batch, const float *params_dev,
+                             const float *X_dev, float *P_dev, float *act_dev, emu_stream_t stream);
+
+/* Backward pass of the mean cross-entropy loss against integer labels
+ * y_dev[batch] in [0, 8): writes dL/dparams to grad_dev (8968 floats,
+ * overwritten) and the loss to loss_dev (one float). */
+emu_status_t emu_sel_backward(emu_handle_t h, int64_t batch, const float *params_dev,
+                              const float *X_dev, const float *act_dev, const float *P_dev,
+                              const int32_t *y_dev, float *grad_dev, float *loss_dev,
+                              emu_stream_t stream);
+
+/* One Adam step (step >= 1) over the 8968 parameters; m_dev and v_dev are
+ * the moment buffers (zero-initialised by the caller). */
+emu_status_t emu_sel_adam(emu_handle_t h, float *params_dev, const float *grad_dev, float *m_dev,
+                          float *v_dev, int step, float lr, float beta1, float beta2, float eps,
+                          emu_stream_t stream);
+
+/* Install trained parameters (host array of 8968 floats) in the handle. */
+emu_status_t emu_sel_load(emu_handle_t h, const float *params_host);
+
+/* Double-double reference of sampled output entries (the selector's judge):
+ * for the `count` (i, j) pairs in idx_dev (int32 pairs), ref_dev receives
+ * (hi, lo) of sum_h a_ih b_hj computed with error-free transformations in
+ * FP64, and absab_dev receives sum_h |a_ih||b_hj|. */
+emu_status_t emu_probe_dd(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k,
+                          const double *A, int64_t lda, const double *B, int64_t ldb, int count,
+                          const int32_t *idx_dev, double *ref_dev, double *absab_dev,
+                          emu_stream_t stream);
+
+/* Auto precision: C = alpha*A*B + beta*C with the smallest p the selector
+ * predicts for max_ij |C - AB|_ij / (|A||B|)_ij <= tol.  The prediction is
+ * checked on `probe` sampled entries against emu_probe_dd; on a miss p is
+ * raised (to max(p+1, the bound-based p)) and the product recomputed, up to
+ * EMU_P_MAX.  Without loaded selector weights the bound-based p is used.
+ * Synchronises `stream` (the probe result decides the next step); *p_used
+ * receives the p of the returned result.  beta must be 0 (C is overwritten
+ * on a retry).  Returns EMU_ERR_TOL_NOT_MET if even EMU_P_MAX misses. */
+emu_status_t emu_dgemm_auto(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k,
+                            double alpha, const double *A, int64_t lda, const double *B,
+                            int64_t ldb, double *C, int64_t ldc, double tol, int probe,
+                            int *p_used_host, emu_stream_t stream);
+
+/* Bound-based slice count for tolerance tol from the exponent statistics
+ * (host): smallest p in [3, 10] whose worst-case truncation bound
+ * 2^(-8p+3) * 2^(spread) * k meets tol, where spread is the largest exponent
+ * deficit seen in the sampled rows/columns.  Written to *p_host. */
+emu_status_t emu_bound_p(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k,
+                         const double *A, int64_t lda, const double *B, int64_t ldb, double tol,
+                         int *p_host, emu_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EMUGEMM_H */

@@ -1,0 +1,53 @@
+// emu_handle.h -- the library handle and host-side planning helpers shared
+// by the C ABI translation units.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/emugemm.h"
+
+struct emu_handle_s {
+  int device = 0;
+  int num_sms = 0;
+  int* status = nullptr;  // device status word (bit flags, see emu_device.cuh)
+  void* ws = nullptr;     // workspace
+  size_t ws_bytes = 0;
+  bool ws_user = false;   // caller-owned workspace
+  void* grouped = nullptr;   // grouped-GEMM plan cache (grouped.cu)
+  void* selector = nullptr;  // selector state (select.cu)
+};
+
+namespace emu {
+
+// Byte offsets of one call's workspace regions.
+struct Plan {
+  int64_t rows_a, rows_b, cols;
+  size_t off_maxA, off_maxB, off_EA, off_FB, off_hatA, off_hatB, bytes;
+};
+Plan plan_I(int64_t m, int64_t n, int64_t k, int p);
+Plan plan_II(int64_t m, int64_t n, int64_t k, int nm, int nsets);
+
+// Row-major view of a product (see normalize in api.cu).
+struct View {
+  int64_t M, N;
+  const void* A;
+  int64_t ldA;
+  bool a_kcontig;
+  const void* B;
+  int64_t ldB;
+  bool b_kcontig;
+};
+void normalize(emu_layout_t layout, int64_t m, int64_t n, const void* A, int64_t lda, const void* B,
+               int64_t ldb, View* v);
+bool check_lds(emu_layout_t layout, int64_t m, int64_t n, int64_t k, int64_t lda, int64_t ldb, int64_t ldc);
+
+emu_status_t handle_workspace(emu_handle_s* h, size_t bytes, cudaStream_t st, uint8_t** out);
+void handle_release_extras(emu_handle_s* h);
+
+template <typename T>
+emu_status_t run_scheme_I(emu_handle_s* h, const View& v, int64_t k, int p, double alpha, double beta,
+                          void* C, int64_t ldc, int out_mode, int32_t* partials, cudaStream_t st,
+                          uint8_t* ws_override);
+
+}  // namespace emu

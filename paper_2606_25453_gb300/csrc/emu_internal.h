@@ -1,0 +1,105 @@
+// emu_internal.h -- declarations shared by the library's translation units
+// (host launchers, layout helpers, method tables passed to kernels).
+#pragma once
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "emu_device.cuh"
+
+namespace emu {
+
+constexpr int kMaxModuli = 20;  // Scheme II moduli supported
+constexpr int kPow2TabLen = 128; // 2^e mod m for e < 128 (a' < 2^b, b < 128)
+constexpr int kCrtLimbs = 5;     // P < 2^160 for up to 20 moduli
+constexpr int kSplitRowAlign = 128;
+
+// Layout of split outputs (see the C ABI header).
+inline int64_t split_rows(int64_t rows) { return (rows + kSplitRowAlign - 1) / kSplitRowAlign * kSplitRowAlign; }
+inline int64_t split_cols_I(int64_t k, int p) { return (k + 31) / 32 * 32 * p; }
+inline int64_t split_cols_II(int64_t k) { return (k + 127) / 128 * 128; }
+
+// Scheme II tables, passed by value to kernels.
+struct ModTables {
+  uint32_t mods[kMaxModuli];
+  uint32_t two32mod[kMaxModuli];                 // 2^32 mod m_l
+  uint8_t pow2mod[kMaxModuli][kPow2TabLen];      // 2^e mod m_l
+};
+
+// CRT tables of Eq. (8) for a given number of moduli.
+struct CrtTables {
+  uint32_t w[kMaxModuli][kCrtLimbs];  // (P/m_l) * q_l, little-endian 32-bit limbs
+  uint32_t P[kCrtLimbs];
+  uint32_t Phalf[kCrtLimbs];          // floor(P/2)
+  double invP;                        // 1/P rounded (quotient estimate only)
+  int nm;
+};
+
+// Host-side method constants (api.cu).
+int host_moduli(int nm, int32_t* out);
+int64_t host_chunk_len_I(int p);
+int host_scale_bits_II(int nm, int64_t k, int is_complex);
+void host_mod_tables(int nm, ModTables* t);
+void host_crt_tables(int nm, CrtTables* t);
+
+// ---------------------------------------------------------------- launchers
+template <typename T>
+void launch_scan(const T* X, int64_t ld, bool kcontig, int64_t rows, int64_t k, int cw,
+                 unsigned long long* maxbits, int* status, cudaStream_t st);
+template <typename T>
+void launch_split_I(const T* X, int64_t ld, bool kcontig, int64_t rows, int64_t k, int p,
+                    const unsigned long long* maxbits, int8_t* hat, int32_t* E, cudaStream_t st);
+template <typename T>
+void launch_split_II(const T* X, int64_t ld, bool kcontig, int64_t rows, int64_t k, int nm, int b,
+                     int cw, const ModTables& tabs, const unsigned long long* maxbits, int8_t* res,
+                     int32_t* E, cudaStream_t st);
+
+// Output modes of the Scheme I kernel.
+enum GemmOut : int { OUT_F64 = 0, OUT_F32 = 1, OUT_PARTIALS = 2 };
+
+struct GemmIArgs {
+  const CUtensorMap* descA;  // host copies, passed to the kernel by value
+  const CUtensorMap* descB;
+  int M, N;
+  int nk32;     // number of 32-wide K-chunks
+  int kc32;     // fold interval in K-chunks (K_c / 32)
+  const int32_t* EA;
+  const int32_t* FB;
+  double alpha, beta;
+  void* C;
+  int64_t ldc;
+  int32_t* partials;
+  int* status;
+  int num_sms;
+};
+cudaError_t launch_gemm_I(int p, int out_mode, const GemmIArgs& a, cudaStream_t st);
+
+// Scheme II kernel modes.
+enum GemmIIOut : int { II_F64 = 0, II_F32 = 1, II_RESIDUES = 2, II_Z3M = 3 };
+
+struct GemmIIArgs {
+  const CUtensorMap* descA;
+  const CUtensorMap* descB;
+  int M, N;
+  int nk32;
+  int rowsA_pad, rowsB_pad;  // plane heights in the stacked residue matrices
+  int nm;
+  int escale;                 // -2b
+  const int32_t* EA;
+  const int32_t* FB;
+  double alpha_re, alpha_im, beta_re, beta_im;
+  void* C;
+  int64_t ldc;
+  uint8_t* residues;
+  int* status;
+  int num_sms;
+};
+cudaError_t launch_gemm_II(int out_mode, const GemmIIArgs& a, const ModTables& mt,
+                           const CrtTables& ct, cudaStream_t st);
+
+// Tensor map for a row-major int8 matrix [rows][cols] read in boxes of
+// 32 bytes x box_rows with 32-byte swizzling.
+bool make_tmap_i8(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows,
+                  uint32_t box_rows);
+
+}  // namespace emu

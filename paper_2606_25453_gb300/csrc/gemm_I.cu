@@ -1,0 +1,295 @@
+// gemm_I.cu -- fused Scheme I kernel (Algorithm 1, Sec. III-B).
+//
+// One persistent CTA per SM walks the output tiles.  A producer warp streams
+// the interleaved slices (Eq. 11) of A-hat and B-hat into a multi-stage
+// shared-memory ring with TMA (one 32-byte-wide box per slice, 32-byte
+// swizzle, completion on an mbarrier).  Eight consumer warps each own a
+// 16 x 16 output patch and, per 32-wide K-chunk, load all p A-slice
+// fragments with ldmatrix, then stream the B slices and issue the triangular
+// schedule of Eq. (2): acc[i+j] += A'_i B'_j for i + j < p, p(p+1) INT8
+// mma.sync per chunk (signed leading / unsigned tail variants).  The p INT32
+// accumulators live in registers (the GB300 INT8 path is the warp-level
+// mma.sync, so this is the paper's register-resident regime).
+//
+// Every K_c elements (the INT32-exact range of Eq. 2) the accumulators are
+// drained into an exact 128-bit integer S = sum_s C_s 256^(p-1-s).  The
+// epilogue rounds S once to binary64 (shift-reduce of Eq. 3 without any
+// rounding beyond the final one), applies 2^(E_i + F_j - 14 - 8(p-1)) and
+// the BLAS update, and stores C.  No partial product reaches global memory
+// (OUT_PARTIALS, the unfused ablation, writes the INT32 C_s instead).
+#include "emu_internal.h"
+
+namespace emu {
+
+namespace {
+
+constexpr int kBM = 64, kBN = 32;
+constexpr int kCW = 8;                 // consumer warps (4 along M x 2 along N)
+constexpr int kThreads = (kCW + 1) * 32;
+constexpr int kBlkA = kBM * 32, kBlkB = kBN * 32;
+
+template <int P>
+struct CfgI {
+  static constexpr int kStageBytes = P * (kBlkA + kBlkB);
+  static constexpr int kRaw = 163840 / kStageBytes;
+  static constexpr int kStages = kRaw < 2 ? 2 : (kRaw > 8 ? 8 : kRaw);
+  static constexpr int kSmem = kStages * kStageBytes + 1024 + 2 * kStages * 8 + 64;
+};
+
+struct KParamsI {
+  CUtensorMap tA;
+  CUtensorMap tB;
+  int M, N, nk32, kc32, tiles_m, tiles_n;
+  const int32_t* EA;
+  const int32_t* FB;
+  int escale;
+  double alpha, beta;
+  void* C;
+  int64_t ldc;
+  int32_t* partials;
+  int* status;
+};
+
+__device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, int& tm, int& tn) {
+  constexpr int G = 8;  // group of tile rows for L2 reuse
+  int per_group = G * tiles_n;
+  int g = tile / per_group;
+  int first = g * G;
+  int gsz = tiles_m - first < G ? tiles_m - first : G;
+  int in = tile - g * per_group;
+  tm = first + in % gsz;
+  tn = in / gsz;
+}
+
+template <int I, int J>
+__device__ __forceinline__ void mma_slice(int32_t* d, const uint32_t* a, const uint32_t* b) {
+  mma_i8<I == 0, J == 0>(d, a, b);
+}
+
+// acc[s] += A'_i B'_j for all i + j = s < P, for one B slice j (static).
+template <int P, int J, int I = 0>
+struct TriRow {
+  __device__ __forceinline__ static void run(int32_t (*acc)[2][4], const uint32_t (*af)[4],
+                                             const uint32_t* bf) {
+    if constexpr (I + J < P) {
+      mma_slice<I, J>(acc[I + J][0], af[I], bf);
+      mma_slice<I, J>(acc[I + J][1], af[I], bf + 2);
+      TriRow<P, J, I + 1>::run(acc, af, bf);
+    }
+  }
+};
+
+template <int P, int J = 0>
+struct TriAll {
+  __device__ __forceinline__ static void run(int32_t (*acc)[2][4], const uint32_t (*af)[4],
+                                             uint32_t sB, uint32_t b_off) {
+    if constexpr (J < P) {
+      uint32_t bf[4];
+      ldsm_x4(sB + J * kBlkB + b_off, bf[0], bf[1], bf[2], bf[3]);
+      TriRow<P, J>::run(acc, af, bf);
+      TriAll<P, J + 1>::run(acc, af, sB, b_off);
+    }
+  }
+};
+
+template <int P>
+__device__ __forceinline__ void fold(int32_t (*acc)[2][4], __int128 (*S)[4]) {
+#pragma unroll
+  for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      __int128 t = acc[0][nt][q];
+#pragma unroll
+      for (int s = 1; s < P; ++s) t = t * 256 + acc[s][nt][q];
+      S[nt][q] += t;
+#pragma unroll
+      for (int s = 0; s < P; ++s) acc[s][nt][q] = 0;
+    }
+}
+
+template <int P, int OUT>
+__global__ void __launch_bounds__(kThreads, 1) gemm_I_kernel(const __grid_constant__ KParamsI kp) {
+  using Cfg = CfgI<P>;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* smem = smem_raw + (base - raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + Cfg::kStages * Cfg::kStageBytes);
+  uint64_t* empty = full + Cfg::kStages;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < Cfg::kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kCW);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  const int ntiles = kp.tiles_m * kp.tiles_n;
+
+  if (warp == kCW) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      tma_prefetch_desc(&kp.tA);
+      tma_prefetch_desc(&kp.tB);
+      uint32_t it = 0;
+      for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        int tm, tn;
+        tile_coords(tile, kp.tiles_m, kp.tiles_n, tm, tn);
+        for (int kk = 0; kk < kp.nk32; ++kk, ++it) {
+          const uint32_t stage = it % Cfg::kStages;
+          const uint32_t par = (it / Cfg::kStages) & 1u;
+          if (it >= static_cast<uint32_t>(Cfg::kStages) && !mbar_wait_bounded(&empty[stage], par ^ 1u)) {
+            set_status(kp.status, ST_TIMEOUT);
+            return;
+          }
+          mbar_arrive_expect_tx(&full[stage], Cfg::kStageBytes);
+          uint8_t* sA = smem + stage * Cfg::kStageBytes;
+          uint8_t* sB = sA + P * kBlkA;
+#pragma unroll
+          for (int t = 0; t < P; ++t)
+            tma_load_2d(sA + t * kBlkA, &kp.tA, &full[stage], (kk * P + t) * 32, tm * kBM);
+#pragma unroll
+          for (int t = 0; t < P; ++t)
+            tma_load_2d(sB + t * kBlkB, &kp.tB, &full[stage], (kk * P + t) * 32, tn * kBN);
+        }
+      }
+    }
+    return;
+  }
+
+  // -------------------------------------------------------------- consumers
+  const int wm = warp >> 1, wn = warp & 1;
+  const uint32_t a_off = swz32(wm * 16 + (lane & 15), lane >> 4);
+  const uint32_t b_off = swz32(wn * 16 + (lane & 7) + ((lane >> 4) << 3), (lane >> 3) & 1);
+  uint32_t it = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int tm, tn;
+    tile_coords(tile, kp.tiles_m, kp.tiles_n, tm, tn);
+    int32_t acc[P][2][4];
+    __int128 S[2][4];
+#pragma unroll
+    for (int s = 0; s < P; ++s)
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[s][nt][q] = 0;
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) S[nt][q] = 0;
+
+    int since_fold = 0;
+    for (int kk = 0; kk < kp.nk32; ++kk, ++it) {
+      const uint32_t stage = it % Cfg::kStages;
+      const uint32_t par = (it / Cfg::kStages) & 1u;
+      if (!mbar_wait_bounded(&full[stage], par)) {
+        set_status(kp.status, ST_TIMEOUT);
+        return;
+      }
+      const uint32_t sA = base + stage * Cfg::kStageBytes;
+      const uint32_t sB = sA + P * kBlkA;
+      uint32_t af[P][4];
+#pragma unroll
+      for (int i = 0; i < P; ++i) ldsm_x4(sA + i * kBlkA + a_off, af[i][0], af[i][1], af[i][2], af[i][3]);
+      TriAll<P>::run(acc, af, sB, b_off);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[stage]);
+      if (OUT != OUT_PARTIALS && ++since_fold == kp.kc32) {
+        fold<P>(acc, S);
+        since_fold = 0;
+      }
+    }
+
+    const int row0 = tm * kBM + wm * 16 + (lane >> 2);
+    const int col0 = tn * kBN + wn * 16 + (lane & 3) * 2;
+    if (OUT == OUT_PARTIALS) {
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          int row = row0 + (q >> 1) * 8, col = col0 + nt * 8 + (q & 1);
+          if (row < kp.M && col < kp.N) {
+#pragma unroll
+            for (int s = 0; s < P; ++s)
+              kp.partials[(static_cast<int64_t>(s) * kp.M + row) * kp.N + col] = acc[s][nt][q];
+          }
+        }
+      continue;
+    }
+    fold<P>(acc, S);
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int row = row0 + (q >> 1) * 8, col = col0 + nt * 8 + (q & 1);
+        if (row < kp.M && col < kp.N) {
+          double d = i128_to_double_rn(S[nt][q]);
+          double r = scale2(d, kp.EA[row] + kp.FB[col] + kp.escale);
+          if (OUT == OUT_F64) {
+            double* cp = static_cast<double*>(kp.C) + static_cast<int64_t>(row) * kp.ldc + col;
+            *cp = blas_update(kp.alpha, r, kp.beta, kp.beta != 0.0 ? *cp : 0.0);
+          } else {
+            float* cp = static_cast<float*>(kp.C) + static_cast<int64_t>(row) * kp.ldc + col;
+            *cp = static_cast<float>(
+                blas_update(kp.alpha, r, kp.beta, kp.beta != 0.0 ? static_cast<double>(*cp) : 0.0));
+          }
+        }
+      }
+  }
+}
+
+template <int P, int OUT>
+cudaError_t launch_p(const GemmIArgs& a, cudaStream_t st) {
+  using Cfg = CfgI<P>;
+  cudaError_t e = cudaFuncSetAttribute(gemm_I_kernel<P, OUT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
+  if (e != cudaSuccess) return e;
+  KParamsI kp;
+  kp.tA = *a.descA;
+  kp.tB = *a.descB;
+  kp.M = a.M;
+  kp.N = a.N;
+  kp.nk32 = a.nk32;
+  kp.kc32 = a.kc32;
+  kp.tiles_m = (a.M + kBM - 1) / kBM;
+  kp.tiles_n = (a.N + kBN - 1) / kBN;
+  kp.EA = a.EA;
+  kp.FB = a.FB;
+  kp.escale = -14 - 8 * (P - 1);
+  kp.alpha = a.alpha;
+  kp.beta = a.beta;
+  kp.C = a.C;
+  kp.ldc = a.ldc;
+  kp.partials = a.partials;
+  kp.status = a.status;
+  int ntiles = kp.tiles_m * kp.tiles_n;
+  if (ntiles == 0) return cudaSuccess;
+  int grid = ntiles < a.num_sms ? ntiles : a.num_sms;
+  gemm_I_kernel<P, OUT><<<grid, kThreads, Cfg::kSmem, st>>>(kp);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int gemm_I_tile_m() { return kBM; }
+int gemm_I_tile_n() { return kBN; }
+
+cudaError_t launch_gemm_I(int p, int out_mode, const GemmIArgs& a, cudaStream_t st) {
+#define EMU_P(PP)                                                        \
+  case PP:                                                               \
+    if (out_mode == OUT_F64) return launch_p<PP, OUT_F64>(a, st);        \
+    if (out_mode == OUT_F32) return launch_p<PP, OUT_F32>(a, st);        \
+    return launch_p<PP, OUT_PARTIALS>(a, st);
+  switch (p) {
+    EMU_P(1) EMU_P(2) EMU_P(3) EMU_P(4) EMU_P(5) EMU_P(6)
+    EMU_P(7) EMU_P(8) EMU_P(9) EMU_P(10) EMU_P(11) EMU_P(12)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef EMU_P
+}
+
+}  // namespace emu

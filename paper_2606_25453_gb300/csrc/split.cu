@@ -1,0 +1,376 @@
+// split.cu -- exponent scan and slice / residue packing (HBM-bound steps).
+//
+// Scan (Eq. 1 scale vectors; Scheme II scaling): for every reduction vector
+// of an operand (row of A, column of B) the largest |x| is found by an
+// unsigned max over the IEEE-754 bit patterns with the sign cleared (which
+// orders finite magnitudes), so the scan does no floating-point arithmetic.
+// Non-finite values have bit patterns >= 0x7FF0... and set the status word.
+//
+// Split I (Eq. 1, layout Eq. 11): x = trunc(a * 2^(8p-1-E)) taken exactly
+// from the bits of a; the p bytes of the 8p-bit two's complement of x are
+// the slices (leading slice signed, tails unsigned), written interleaved:
+// row r, K-chunk c (32 wide), slice t at bytes [(c*p+t)*32, +32).
+//
+// Split II (Eq. 5): a' = trunc(a * 2^(b-E)), symmetric residues modulo the
+// moduli, one plane per modulus; complex input also writes the residues of
+// a'_re + a'_im for the 3M product (Eq. 16).
+#include "emu_internal.h"
+
+namespace emu {
+
+// ------------------------------------------------------------------ loads
+template <typename T>
+__device__ __forceinline__ uint64_t load_absbits(const T* p);
+template <>
+__device__ __forceinline__ uint64_t load_absbits<double>(const double* p) {
+  return dbits(__ldg(p)) & 0x7FFFFFFFFFFFFFFFull;
+}
+template <>
+__device__ __forceinline__ uint64_t load_absbits<float>(const float* p) {
+  return dbits(static_cast<double>(__ldg(p))) & 0x7FFFFFFFFFFFFFFFull;  // exact widening
+}
+template <typename T>
+__device__ __forceinline__ uint64_t load_bits(const T* p);
+template <>
+__device__ __forceinline__ uint64_t load_bits<double>(const double* p) {
+  return dbits(__ldg(p));
+}
+template <>
+__device__ __forceinline__ uint64_t load_bits<float>(const float* p) {
+  return dbits(static_cast<double>(__ldg(p)));
+}
+
+// ------------------------------------------------------------------ scan
+// Vector r, element h of operand X: kcontig -> X[(r*ld + h)*cw + part],
+// else X[(h*ld + r)*cw + part]; cw = 2 for complex (both parts scanned).
+template <typename T, bool KCONTIG>
+__global__ void scan_kernel(const T* __restrict__ X, int64_t ld, int64_t rows, int64_t k, int cw,
+                            unsigned long long* __restrict__ maxbits, int* status) {
+  if (KCONTIG) {
+    // one warp per (row, K segment of 32*64 elements)
+    int lane = threadIdx.x & 31;
+    int64_t r = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= rows) return;
+    int64_t len = k * cw;
+    int64_t seg = 2048;
+    int64_t h0 = static_cast<int64_t>(blockIdx.y) * seg;
+    int64_t h1 = h0 + seg < len ? h0 + seg : len;
+    const T* row = X + r * ld * cw;
+    uint64_t mx = 0;
+    for (int64_t h = h0 + lane; h < h1; h += 32) {
+      uint64_t v = load_absbits(row + h);
+      mx = v > mx ? v : mx;
+    }
+    for (int o = 16; o; o >>= 1) {
+      uint64_t w = __shfl_xor_sync(0xffffffffu, mx, o);
+      mx = w > mx ? w : mx;
+    }
+    if (lane == 0 && h0 < h1) {
+      atomicMax(maxbits + r, static_cast<unsigned long long>(mx));
+      if (mx >= 0x7FF0000000000000ull) set_status(status, ST_NONFINITE);
+    }
+  } else {
+    // block 32 x 8: lanes over vectors (coalesced), 8 row-groups over K
+    int64_t r = static_cast<int64_t>(blockIdx.x) * 32 + threadIdx.x;
+    int64_t seg = 256;
+    int64_t h0 = static_cast<int64_t>(blockIdx.y) * seg;
+    int64_t h1 = h0 + seg < k ? h0 + seg : k;
+    uint64_t mx = 0;
+    if (r < rows) {
+      for (int64_t h = h0 + threadIdx.y; h < h1; h += blockDim.y) {
+        const T* p = X + (h * ld + r) * cw;
+        uint64_t v = load_absbits(p);
+        mx = v > mx ? v : mx;
+        if (cw == 2) {
+          uint64_t w = load_absbits(p + 1);
+          mx = w > mx ? w : mx;
+        }
+      }
+    }
+    __shared__ uint64_t red[8][32];
+    red[threadIdx.y][threadIdx.x] = mx;
+    __syncthreads();
+    if (threadIdx.y == 0 && r < rows) {
+      for (int q = 1; q < blockDim.y; ++q) mx = red[q][threadIdx.x] > mx ? red[q][threadIdx.x] : mx;
+      if (h0 < h1) {
+        atomicMax(maxbits + r, static_cast<unsigned long long>(mx));
+        if (mx >= 0x7FF0000000000000ull) set_status(status, ST_NONFINITE);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ split I
+// Bytes of the 8P-bit two's complement of x = sign * (mag << lsh).
+template <int P>
+struct Digits {
+  uint32_t d[P];
+};
+template <int P>
+__device__ __forceinline__ void slice_digits(uint64_t bits, int E, uint32_t* out) {
+  ScaledInt s = scaled_trunc_bits(bits, 8 * P - 1 - E);
+  bool neg = (bits >> 63) != 0;
+  if (P <= 8) {
+    uint64_t v = s.lsh < 64 ? (s.mag << s.lsh) : 0ull;  // < 2^(8P-1) <= 2^63
+    if (neg) v = ~v + 1ull;
+#pragma unroll
+    for (int t = 0; t < P; ++t) out[t] = static_cast<uint32_t>((v >> (8 * (P - 1 - t))) & 0xFFu);
+  } else {
+    unsigned __int128 v = s.lsh < 128 ? (static_cast<unsigned __int128>(s.mag) << s.lsh)
+                                      : static_cast<unsigned __int128>(0);
+    if (neg) v = ~v + static_cast<unsigned __int128>(1);
+#pragma unroll
+    for (int t = 0; t < P; ++t) out[t] = static_cast<uint32_t>((v >> (8 * (P - 1 - t))) & 0xFFu);
+  }
+}
+
+__device__ __forceinline__ int exp_from_maxbits(const unsigned long long* maxbits, int64_t r,
+                                                int64_t rows) {
+  if (r >= rows) return 0;
+  uint64_t mb = maxbits[r];
+  if (mb >= 0x7FF0000000000000ull) return 0;  // non-finite: flagged by the scan
+  return frexp_exp_bits(mb);
+}
+
+// K-contiguous source: one warp per (row, 32-wide K-chunk); lane = h % 32.
+template <typename T, int P>
+__global__ void split_I_kcontig(const T* __restrict__ X, int64_t ld, int64_t rows, int64_t k,
+                                int64_t rows_pad, int64_t nchunks,
+                                const unsigned long long* __restrict__ maxbits,
+                                int8_t* __restrict__ hat, int32_t* __restrict__ E_out) {
+  int lane = threadIdx.x & 31;
+  int64_t w = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (w >= rows_pad * nchunks) return;
+  int64_t r = w / nchunks, c = w % nchunks;
+  int64_t h = c * 32 + lane;
+  int E = exp_from_maxbits(maxbits, r, rows);
+  uint32_t dg[P];
+  if (r < rows && h < k) {
+    slice_digits<P>(load_bits(X + r * ld + h), E, dg);
+  } else {
+#pragma unroll
+    for (int t = 0; t < P; ++t) dg[t] = 0;
+  }
+  uint8_t* row = reinterpret_cast<uint8_t*>(hat) + r * (nchunks * 32 * P);
+#pragma unroll
+  for (int t = 0; t < P; ++t) row[(c * P + t) * 32 + lane] = static_cast<uint8_t>(dg[t]);
+  if (c == 0 && lane == 0 && r < rows && E_out) E_out[r] = E;
+}
+
+// K-strided source (element (r, h) at X[h*ld + r]): one thread per
+// (vector r, K-chunk c), lanes over consecutive r (coalesced reads); each
+// thread assembles 32 bytes per slice and writes them as two 16-byte stores.
+template <typename T, int P>
+__global__ void split_I_kstrided(const T* __restrict__ X, int64_t ld, int64_t rows, int64_t k,
+                                 int64_t rows_pad, int64_t nchunks,
+                                 const unsigned long long* __restrict__ maxbits,
+                                 int8_t* __restrict__ hat, int32_t* __restrict__ E_out) {
+  int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  int64_t c = blockIdx.y;
+  if (r >= rows_pad) return;
+  int E = exp_from_maxbits(maxbits, r, rows);
+  uint32_t word[P][8];
+#pragma unroll
+  for (int t = 0; t < P; ++t)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) word[t][q] = 0;
+#pragma unroll 1
+  for (int wq = 0; wq < 8; ++wq) {
+    uint32_t cur[P];
+#pragma unroll
+    for (int t = 0; t < P; ++t) cur[t] = 0;
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq) {
+      int64_t h = c * 32 + wq * 4 + qq;
+      uint32_t dg[P];
+      if (r < rows && h < k) {
+        slice_digits<P>(load_bits(X + h * ld + r), E, dg);
+      } else {
+#pragma unroll
+        for (int t = 0; t < P; ++t) dg[t] = 0;
+      }
+#pragma unroll
+      for (int t = 0; t < P; ++t) cur[t] |= dg[t] << (8 * qq);
+    }
+    // place the finished 4-byte word at position wq (static register indices)
+#pragma unroll
+    for (int t = 0; t < P; ++t) {
+#pragma unroll
+      for (int z = 0; z < 8; ++z) word[t][z] = (wq == z) ? cur[t] : word[t][z];
+    }
+  }
+  uint8_t* row = reinterpret_cast<uint8_t*>(hat) + r * (nchunks * 32 * P);
+#pragma unroll
+  for (int t = 0; t < P; ++t) {
+    uint4* dst = reinterpret_cast<uint4*>(row + (c * P + t) * 32);
+    dst[0] = make_uint4(word[t][0], word[t][1], word[t][2], word[t][3]);
+    dst[1] = make_uint4(word[t][4], word[t][5], word[t][6], word[t][7]);
+  }
+  if (c == 0 && r < rows && E_out) E_out[r] = E;
+}
+
+// ------------------------------------------------------------------ split II
+// Residue of x = sign * (mag << lsh) modulo m, in [0, m); mag < 2^53 is
+// reduced in two 32-bit pieces, 2^lsh mod m comes from the table.
+__device__ __forceinline__ uint32_t mod_scaled(uint64_t mag, int lsh, bool neg, uint32_t m,
+                                               uint32_t two32m, const uint8_t* pow2tab_m) {
+  uint32_t hi = static_cast<uint32_t>(mag >> 32), lo = static_cast<uint32_t>(mag);
+  uint32_t r = ((hi % m) * two32m + lo % m) % m;
+  if (lsh) {
+    uint32_t f = lsh < kPow2TabLen ? pow2tab_m[lsh] : 0u;  // lsh < b < 128 by construction
+    r = (r * f) % m;
+  }
+  if (neg && r) r = m - r;
+  return r;
+}
+
+__device__ __forceinline__ int8_t sym_res(uint32_t r, uint32_t m) {
+  int v = static_cast<int>(r);
+  if (v > static_cast<int>((m - 1) / 2)) v -= static_cast<int>(m);
+  return static_cast<int8_t>(v);
+}
+
+// One thread per element of a (rows_pad x kpad) plane.  cw = 1 real, 2
+// complex (writes 3 residue sets: re, im, re+im).  Planes: set q, modulus l
+// at res + ((q*nm + l)*rows_pad + r)*kpad + h.
+template <typename T, bool KCONTIG>
+__global__ void split_II_kernel(const T* __restrict__ X, int64_t ld, int64_t rows, int64_t k,
+                                int64_t rows_pad, int64_t kpad, int nm, int b, int cw,
+                                const __grid_constant__ ModTables mt,
+                                const unsigned long long* __restrict__ maxbits,
+                                int8_t* __restrict__ res, int32_t* __restrict__ E_out) {
+  __shared__ uint8_t tab[kMaxModuli][kPow2TabLen];
+  __shared__ uint32_t mods[kMaxModuli], two32[kMaxModuli];
+  for (int i = threadIdx.x; i < nm * kPow2TabLen; i += blockDim.x)
+    tab[i / kPow2TabLen][i % kPow2TabLen] = mt.pow2mod[i / kPow2TabLen][i % kPow2TabLen];
+  for (int i = threadIdx.x; i < nm; i += blockDim.x) {
+    mods[i] = mt.mods[i];
+    two32[i] = mt.two32mod[i];
+  }
+  __syncthreads();
+  int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  int64_t r, h;
+  if (KCONTIG) {
+    r = idx / kpad;
+    h = idx % kpad;
+  } else {  // consecutive threads over r for coalesced strided reads
+    h = idx / rows_pad;
+    r = idx % rows_pad;
+  }
+  if (r >= rows_pad || h >= kpad) return;
+  int E = exp_from_maxbits(maxbits, r, rows);
+  bool valid = r < rows && h < k;
+  int64_t plane = rows_pad * kpad;
+  int64_t off = r * kpad + h;
+  if (cw == 1) {
+    uint64_t bits = 0;
+    if (valid) bits = load_bits(KCONTIG ? X + r * ld + h : X + h * ld + r);
+    ScaledInt s = scaled_trunc_bits(bits, b - E);
+    bool neg = (bits >> 63) != 0;
+    for (int l = 0; l < nm; ++l) {
+      uint32_t m = mods[l];
+      uint32_t rr = valid ? mod_scaled(s.mag, s.lsh, neg, m, two32[l], tab[l]) : 0u;
+      res[l * plane + off] = sym_res(rr, m);
+    }
+  } else {
+    uint64_t br = 0, bi = 0;
+    if (valid) {
+      const T* p = KCONTIG ? X + (r * ld + h) * 2 : X + (h * ld + r) * 2;
+      br = load_bits(p);
+      bi = load_bits(p + 1);
+    }
+    ScaledInt sr = scaled_trunc_bits(br, b - E), si = scaled_trunc_bits(bi, b - E);
+    bool nr = (br >> 63) != 0, ni = (bi >> 63) != 0;
+    for (int l = 0; l < nm; ++l) {
+      uint32_t m = mods[l];
+      uint32_t rr = valid ? mod_scaled(sr.mag, sr.lsh, nr, m, two32[l], tab[l]) : 0u;
+      uint32_t ri = valid ? mod_scaled(si.mag, si.lsh, ni, m, two32[l], tab[l]) : 0u;
+      uint32_t rs = (rr + ri) % m;
+      res[(0 * nm + l) * plane + off] = sym_res(rr, m);
+      res[(1 * nm + l) * plane + off] = sym_res(ri, m);
+      res[(2 * nm + l) * plane + off] = sym_res(rs, m);
+    }
+  }
+  if (h == 0 && r < rows && E_out) E_out[r] = E;
+}
+
+// ------------------------------------------------------------------ launchers
+template <typename T>
+void launch_scan(const T* X, int64_t ld, bool kcontig, int64_t rows, int64_t k, int cw,
+                 unsigned long long* maxbits, int* status, cudaStream_t st) {
+  cudaMemsetAsync(maxbits, 0, sizeof(unsigned long long) * (rows > 0 ? rows : 1), st);
+  if (rows == 0 || k == 0) return;
+  if (kcontig) {
+    int64_t len = k * cw;
+    dim3 grid(static_cast<unsigned>((rows + 7) / 8), static_cast<unsigned>((len + 2047) / 2048));
+    scan_kernel<T, true><<<grid, 256, 0, st>>>(X, ld, rows, k, cw, maxbits, status);
+  } else {
+    dim3 grid(static_cast<unsigned>((rows + 31) / 32), static_cast<unsigned>((k + 255) / 256));
+    scan_kernel<T, false><<<grid, dim3(32, 8), 0, st>>>(X, ld, rows, k, cw, maxbits, status);
+  }
+}
+template void launch_scan<double>(const double*, int64_t, bool, int64_t, int64_t, int,
+                                  unsigned long long*, int*, cudaStream_t);
+template void launch_scan<float>(const float*, int64_t, bool, int64_t, int64_t, int,
+                                 unsigned long long*, int*, cudaStream_t);
+
+template <typename T, int P>
+static void launch_split_I_p(const T* X, int64_t ld, bool kcontig, int64_t rows, int64_t k,
+                             const unsigned long long* maxbits, int8_t* hat, int32_t* E,
+                             cudaStream_t st) {
+  int64_t rows_pad = split_rows(rows), nchunks = split_cols_I(k, 1) / 32;
+  if (rows_pad == 0 || nchunks == 0) return;
+  if (kcontig) {
+    int64_t warps = rows_pad * nchunks;
+    int64_t blocks = (warps + 7) / 8;
+    split_I_kcontig<T, P><<<static_cast<unsigned>(blocks), 256, 0, st>>>(X, ld, rows, k, rows_pad,
+                                                                         nchunks, maxbits, hat, E);
+  } else {
+    dim3 grid(static_cast<unsigned>((rows_pad + 127) / 128), static_cast<unsigned>(nchunks));
+    split_I_kstrided<T, P><<<grid, 128, 0, st>>>(X, ld, rows, k, rows_pad, nchunks, maxbits, hat, E);
+  }
+}
+
+template <typename T>
+void launch_split_I(const T* X, int64_t ld, bool kcontig, int64_t rows, int64_t k, int p,
+                    const unsigned long long* maxbits, int8_t* hat, int32_t* E, cudaStream_t st) {
+  switch (p) {
+#define EMU_CASE(PP) \
+  case PP:           \
+    launch_split_I_p<T, PP>(X, ld, kcontig, rows, k, maxbits, hat, E, st); \
+    break;
+    EMU_CASE(1) EMU_CASE(2) EMU_CASE(3) EMU_CASE(4) EMU_CASE(5) EMU_CASE(6)
+    EMU_CASE(7) EMU_CASE(8) EMU_CASE(9) EMU_CASE(10) EMU_CASE(11) EMU_CASE(12)
+#undef EMU_CASE
+    default:
+      break;
+  }
+}
+template void launch_split_I<double>(const double*, int64_t, bool, int64_t, int64_t, int,
+                                     const unsigned long long*, int8_t*, int32_t*, cudaStream_t);
+template void launch_split_I<float>(const float*, int64_t, bool, int64_t, int64_t, int,
+                                    const unsigned long long*, int8_t*, int32_t*, cudaStream_t);
+
+template <typename T>
+void launch_split_II(const T* X, int64_t ld, bool kcontig, int64_t rows, int64_t k, int nm, int b,
+                     int cw, const ModTables& tabs, const unsigned long long* maxbits, int8_t* res,
+                     int32_t* E, cudaStream_t st) {
+  int64_t rows_pad = split_rows(rows), kpad = split_cols_II(k);
+  int64_t total = rows_pad * kpad;
+  if (total == 0) return;
+  int64_t blocks = (total + 255) / 256;
+  if (kcontig)
+    split_II_kernel<T, true><<<static_cast<unsigned>(blocks), 256, 0, st>>>(
+        X, ld, rows, k, rows_pad, kpad, nm, b, cw, tabs, maxbits, res, E);
+  else
+    split_II_kernel<T, false><<<static_cast<unsigned>(blocks), 256, 0, st>>>(
+        X, ld, rows, k, rows_pad, kpad, nm, b, cw, tabs, maxbits, res, E);
+}
+template void launch_split_II<double>(const double*, int64_t, bool, int64_t, int64_t, int, int, int,
+                                      const ModTables&, const unsigned long long*, int8_t*, int32_t*,
+                                      cudaStream_t);
+template void launch_split_II<float>(const float*, int64_t, bool, int64_t, int64_t, int, int, int,
+                                     const ModTables&, const unsigned long long*, int8_t*, int32_t*,
+                                     cudaStream_t);
+
+}  // namespace emu
