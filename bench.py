@@ -1,0 +1,366 @@
+"""Benchmark: emulated FP64 GEMM on the INT8 tensor cores of one GB300.
+
+Workload (one "step"): Scheme I emulated DGEMM C = A @ B, M = N = K = 8192,
+row-major float64, A and B drawn by the paper's test-matrix generator
+(Eq. 19) with phi = 0.5, p = 8 INT8 slices: exponent scan, split into
+interleaved slices, fused INT8 GEMM with the exact shift-reduce epilogue.
+Inputs (512 MiB each) are larger than L2 (129 MB), so no L2 flush is needed.
+
+Printed: one JSON line with the effective FP64 TFLOP/s (2 M N K / t), the
+INT8 tensor rate and its fraction of the measured INT8 peak, the roofline
+of the fused GEMM kernel, an end-to-end number through host buffers, cuBLAS
+DGEMM on the same GPU at its own accuracy, the error of both against a
+double-double reference on sampled entries, the CPU oracle baseline, and the
+SM clocks seen during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 run under torch.distributed.run: every rank computes its own
+independent product (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "emulated FP64 TFLOP/s (Scheme I DGEMM on INT8 tensor cores)"
+UNIT = "TFLOP/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--p", type=int, default=8)
+    ap.add_argument("--phi", type=float, default=0.5)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--cpu-rows", type=int, default=16, help="rows of C in the CPU oracle sample")
+    ap.add_argument("--no-extras", action="store_true", help="skip cuBLAS / accuracy / CPU legs")
+    return ap.parse_args()
+
+
+def config(args, world):
+    return {"workload": "Scheme I emulated DGEMM M=N=K=%d phi=%g p=%d (Eq. 19 generator, seed %d)"
+                        % (args.n, args.phi, args.p, args.seed),
+            "m": args.n, "n": args.n, "k": args.n, "p": args.p, "phi": args.phi, "layout": "row-major",
+            "scheme": "I", "l2": "inputs larger than L2 (2 x %d MiB), no flush" % (8 * args.n * args.n >> 20),
+            "parallelism": "replicas" if world == 1 else "dp%d independent products" % world}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+def file_sha(path):
+    with open(path, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()
+
+
+def load_traffic(p, n):
+    """DRAM bytes per launch of the fused GEMM from the committed ncu summary,
+    only if the kernel source is unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", "gemm_I_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+        src = os.path.join(ROOT, "paper_2606_25453_gb300", "csrc", "gemm_I.cu")
+        if d.get("gemm_I_cu_sha256") != file_sha(src):
+            return None
+        ent = d.get("per_launch", {}).get("p%d_n%d" % (p, n))
+        return ent
+    except Exception:
+        return None
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path))
+    except Exception:
+        return {}
+
+
+def oracle_cpu_sample(args, A, B, rows):
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.emu_I(A[rows], B, args.p)
+    dt = time.perf_counter() - t0
+    return dt, oracle.num_threads()
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args, rank, world):
+    """The CPU oracle as it stands, on a bounded sample of the workload per step."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    A, B = synth.gemm_pair(args.n, args.n, args.n, args.phi, args.seed)
+    rows = list(range(max(1, args.cpu_rows // 4)))
+    for _ in range(args.warmup):
+        oracle.emu_I(A[rows[:1]], B, args.p)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.emu_I(A[rows], B, args.p)
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    v = 2.0 * len(rows) * args.n * args.n / t / 1e12
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config(args, world),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": "%d rows of C (all %d columns, K = %d) per step" % (len(rows), args.n, args.n)},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2606_25453_gb300 as emu
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    n, p = args.n, args.p
+    A, B = synth.gemm_pair(n, n, n, args.phi, args.seed + 17 * rank)
+    Ad = torch.from_numpy(A).to(dev)
+    Bd = torch.from_numpy(B).to(dev)
+    Cd = torch.empty((n, n), dtype=torch.float64, device=dev)
+    h = emu.Handle(local_rank)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        emu.check(emu.emu_dgemm(h.h, emu.EMU_ROW_MAJOR, n, n, n, 1.0, Ad.data_ptr(), n, Bd.data_ptr(), n, 0.0,
+                                Cd.data_ptr(), n, emu.EMU_SCHEME_I, p, stream.cuda_stream), "emu_dgemm")
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if h.status() != 0:
+        raise RuntimeError("device status %d after warm-up" % h.status())
+
+    # ---------------- timed region: inputs resident in HBM
+    h.trace(True)
+    h.trace_read()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    tr = h.trace_read()
+    h.trace(False)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    flops = 2.0 * n * n * n
+    value = world * flops * args.steps / (ms * 1e-3) / 1e12
+    int8_ops = float(p * (p + 1)) * n * n * n
+    status = h.status()
+
+    # ---------------- end to end through host buffers (pinned), copies timed
+    A_pin = torch.from_numpy(A).pin_memory()
+    B_pin = torch.from_numpy(B).pin_memory()
+    C_pin = torch.empty((n, n), dtype=torch.float64).pin_memory()
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e2.record(stream)
+    for _ in range(args.steps):
+        Ad.copy_(A_pin, non_blocking=True)
+        Bd.copy_(B_pin, non_blocking=True)
+        step()
+        C_pin.copy_(Cd, non_blocking=True)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e2.elapsed_time(e3)
+    if dist:
+        t = torch.tensor([ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    e2e_value = world * flops * args.steps / (ms_e2e * 1e-3) / 1e12
+
+    extras = {}
+    int8_peak = None
+    if rank == 0 and not args.no_extras:
+        # measured dense INT8 peak on this GPU: cuBLASLt INT8 GEMM 8192^3 (best of 5)
+        a8 = torch.randint(-128, 127, (8192, 8192), dtype=torch.int8, device=dev)
+        b8 = torch.randint(-128, 127, (8192, 8192), dtype=torch.int8, device=dev).t().contiguous().t()
+        torch._int_mm(a8, b8)
+        best = 1e30
+        for _ in range(5):
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            torch._int_mm(a8, b8)
+            s1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, s0.elapsed_time(s1))
+        int8_peak = 2.0 * 8192 ** 3 / (best * 1e-3) / 1e12
+        del a8, b8
+        # cuBLAS DGEMM (native FP64) on the same inputs
+        ref = Ad @ Bd
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(2):
+            ref = Ad @ Bd
+        s1.record(stream)
+        torch.cuda.synchronize()
+        cublas_tflops = 2 * flops / (s0.elapsed_time(s1) * 1e-3) / 1e12
+        # accuracy on sampled entries against the double-double reference
+        import oracle
+        oracle.build()
+        rng = np.random.Generator(np.random.PCG64(1234))
+        ri = np.sort(rng.choice(n, 8, replace=False))
+        ci = np.sort(rng.choice(n, 64, replace=False))
+        hi, lo = oracle.dd_gemm(A[ri], B[:, ci])
+        den = np.abs(A[ri]) @ np.abs(B[:, ci])
+        ours_s = Cd[ri][:, ci].cpu().numpy()
+        cub_s = ref[ri][:, ci].cpu().numpy()
+        err_ours = float(np.max(np.abs((ours_s - hi) - lo) / den))
+        err_cub = float(np.max(np.abs((cub_s - hi) - lo) / den))
+        extras = {"cublas_dgemm_tflops": cublas_tflops, "speedup_vs_cublas_dgemm": value / world / cublas_tflops,
+                  "err_max_rel_absAB": err_ours, "err_cublas_dgemm": err_cub,
+                  "err_bound_4k_u": 4 * n * 2.0 ** -53, "err_sample": "8 x 64 entries vs double-double"}
+        del ref
+        # CPU oracle baseline on a bounded sample of rows
+        rows = list(range(args.cpu_rows))
+        dt, cores = oracle_cpu_sample(args, A, B, rows)
+        extras["cpu_baseline"] = {"value": 2.0 * len(rows) * n * n / dt / 1e12, "unit": UNIT, "cores": cores,
+                                  "kind": "oracle",
+                                  "sample": "%d rows of C (all %d columns, K = %d), %.1f s" % (len(rows), n, n, dt)}
+
+    if rank == 0:
+        gemm_ms = tr["ms_gemm"] / max(tr["gemm_launches"], 1)
+        achieved = int8_ops / (gemm_ms * 1e-3) / 1e12
+        peak = int8_peak
+        traffic = load_traffic(p, n)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int8->int32 (f64 in/out)", "data": "synthetic",
+                "config": config(args, world),
+                "int8_tops": int8_ops * args.steps * world / (ms * 1e-3) / 1e12,
+                "int8_frac_of_peak": (int8_ops * args.steps / (ms * 1e-3) / 1e12 / peak) if peak else None,
+                "roofline": {"bound": "tensor", "kernel": "gemm_I_kernel<%d>" % p, "achieved": achieved,
+                             "peak": peak, "unit": UNIT, "frac": (achieved / peak) if peak else None,
+                             "traffic": traffic,
+                             "ops": "INT8 ops p(p+1) M N K (multiply+add = 2)",
+                             "peak_source": "measured live: cuBLASLt INT8 GEMM 8192^3 on this GPU"},
+                "phase_ms_per_step": {k2: tr[k2] / args.steps for k2 in ("ms_scan", "ms_split", "ms_gemm")},
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * n * n,
+                        "d2h_bytes_per_step": 8 * n * n},
+                "gpu_launches": tr["kernel_launches"],
+                "clocks": clk.summary(),
+                "device_status": status,
+                "measured_peaks_file": {k2: measured_peaks().get(k2) for k2 in ("hbm_gbs", "bf16_tflops")}}
+        if "cpu_baseline" in extras:
+            line["cpu_baseline"] = extras.pop("cpu_baseline")
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    h.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

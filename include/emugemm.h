@@ -113,6 +113,17 @@ emu_status_t emu_workspace_size(emu_scheme_t scheme, int64_t m, int64_t n, int64
  * grown with cudaMallocAsync on the call's stream when needed. */
 emu_status_t emu_set_workspace(emu_handle_t h, void *workspace_dev, size_t bytes);
 
+/* Tracing: when enabled, every call records CUDA events on its stream around
+ * each kernel phase (exponent scan, split, fused GEMM, other) and counts the
+ * kernels it launches.  emu_trace_read synchronises the recorded events and
+ * returns the accumulated device milliseconds per phase (ms_host[4]: scan,
+ * split, gemm, other), the number of fused-GEMM launches and of all kernel
+ * launches since the last read, then clears the counters.  Not available
+ * while a stream is being captured into a CUDA graph. */
+emu_status_t emu_trace_enable(emu_handle_t h, int enable);
+emu_status_t emu_trace_read(emu_handle_t h, double *ms_host, int64_t *gemm_launches_host,
+                            int64_t *kernel_launches_host);
+
 /* ------------------------------------------------------------------ */
 /* Emulated GEMM                                                       */
 /* ------------------------------------------------------------------ */

@@ -60,6 +60,8 @@ _SIGS = {
     "emu_chunk_len_I": (_i64, [_i32]),
     "emu_moduli": (_i32, [_i32, _vp]),
     "emu_scale_bits_II": (_i32, [_i32, _i64, _i32]),
+    "emu_trace_enable": (_i32, [_vp, _i32]),
+    "emu_trace_read": (_i32, [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -106,6 +108,16 @@ class Handle:
 
     def status(self, stream=None) -> int:
         return int(emu_get_status(self.h, _stream_ptr(stream)))
+
+    def trace(self, enable: bool = True) -> None:
+        check(emu_trace_enable(self.h, int(enable)), "emu_trace_enable")
+
+    def trace_read(self) -> dict:
+        ms = (_dbl * 4)()
+        g, k = _i64(), _i64()
+        check(emu_trace_read(self.h, ms, ctypes.byref(g), ctypes.byref(k)), "emu_trace_read")
+        return {"ms_scan": ms[0], "ms_split": ms[1], "ms_gemm": ms[2], "ms_other": ms[3],
+                "gemm_launches": g.value, "kernel_launches": k.value}
 
 
 _default = {}

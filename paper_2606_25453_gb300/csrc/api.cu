@@ -430,10 +430,14 @@ emu_status_t run_scheme_I(emu_handle_s* h, const View& v, int64_t k, int p, doub
   auto* hatB = reinterpret_cast<int8_t*>(ws + pl.off_hatB);
   const T* A = static_cast<const T*>(v.A);
   const T* B = static_cast<const T*>(v.B);
+  trace_begin(h, PH_SCAN, st);
   launch_scan<T>(A, v.ldA, v.a_kcontig, v.M, k, 1, maxA, h->status, st);
   launch_scan<T>(B, v.ldB, v.b_kcontig, v.N, k, 1, maxB, h->status, st);
+  trace_end(h, PH_SCAN, st, 2);
+  trace_begin(h, PH_SPLIT, st);
   launch_split_I<T>(A, v.ldA, v.a_kcontig, v.M, k, p, maxA, hatA, EA, st);
   launch_split_I<T>(B, v.ldB, v.b_kcontig, v.N, k, p, maxB, hatB, FB, st);
+  trace_end(h, PH_SPLIT, st, 2);
   CUtensorMap ta, tb;
   if (!make_tmap_i8(&ta, hatA, static_cast<uint64_t>(pl.cols), static_cast<uint64_t>(pl.rows_a), 64) ||
       !make_tmap_i8(&tb, hatB, static_cast<uint64_t>(pl.cols), static_cast<uint64_t>(pl.rows_b), 32))
@@ -454,7 +458,10 @@ emu_status_t run_scheme_I(emu_handle_s* h, const View& v, int64_t k, int p, doub
   a.partials = partials;
   a.status = h->status;
   a.num_sms = h->num_sms;
-  return cuda_err(launch_gemm_I(p, out_mode, a, st));
+  trace_begin(h, PH_GEMM, st);
+  cudaError_t e = launch_gemm_I(p, out_mode, a, st);
+  trace_end(h, PH_GEMM, st, 1);
+  return cuda_err(e);
 }
 template emu_status_t run_scheme_I<double>(emu_handle_s*, const View&, int64_t, int, double, double,
                                            void*, int64_t, int, int32_t*, cudaStream_t, uint8_t*);
@@ -483,10 +490,14 @@ emu_status_t run_scheme_II(emu_handle_s* h, const View& v, int64_t k, int nm, in
   host_mod_tables(nm, &mt);
   CrtTables ct;
   host_crt_tables(nm, &ct);
+  trace_begin(h, PH_SCAN, st);
   launch_scan<T>(A, v.ldA, v.a_kcontig, v.M, k, cw, maxA, h->status, st);
   launch_scan<T>(B, v.ldB, v.b_kcontig, v.N, k, cw, maxB, h->status, st);
+  trace_end(h, PH_SCAN, st, 2);
+  trace_begin(h, PH_SPLIT, st);
   launch_split_II<T>(A, v.ldA, v.a_kcontig, v.M, k, nm, b, cw, mt, maxA, resA, EA, st);
   launch_split_II<T>(B, v.ldB, v.b_kcontig, v.N, k, nm, b, cw, mt, maxB, resB, FB, st);
+  trace_end(h, PH_SPLIT, st, 2);
   CUtensorMap ta, tb;
   if (!make_tmap_i8(&ta, resA, static_cast<uint64_t>(pl.cols),
                     static_cast<uint64_t>(pl.rows_a) * nm * nsets, 64) ||
@@ -514,7 +525,10 @@ emu_status_t run_scheme_II(emu_handle_s* h, const View& v, int64_t k, int nm, in
   a.residues = residues;
   a.status = h->status;
   a.num_sms = h->num_sms;
-  return cuda_err(launch_gemm_II(out_mode, a, mt, ct, st));
+  trace_begin(h, PH_GEMM, st);
+  cudaError_t e = launch_gemm_II(out_mode, a, mt, ct, st);
+  trace_end(h, PH_GEMM, st, 1);
+  return cuda_err(e);
 }
 
 template <typename T>

@@ -16,6 +16,7 @@ struct emu_handle_s {
   bool ws_user = false;   // caller-owned workspace
   void* grouped = nullptr;   // grouped-GEMM plan cache (grouped.cu)
   void* selector = nullptr;  // selector state (select.cu)
+  void* trace = nullptr;     // per-phase timing state (trace.cu), null when off
 };
 
 namespace emu {
@@ -43,6 +44,12 @@ void normalize(emu_layout_t layout, int64_t m, int64_t n, const void* A, int64_t
 bool check_lds(emu_layout_t layout, int64_t m, int64_t n, int64_t k, int64_t lda, int64_t ldb, int64_t ldc);
 
 emu_status_t handle_workspace(emu_handle_s* h, size_t bytes, cudaStream_t st, uint8_t** out);
+
+// Tracing phases and hooks (no-ops unless tracing is enabled).
+enum TracePhase : int { PH_SCAN = 0, PH_SPLIT = 1, PH_GEMM = 2, PH_OTHER = 3 };
+void trace_begin(emu_handle_s* h, int phase, cudaStream_t st);
+void trace_end(emu_handle_s* h, int phase, cudaStream_t st, int kernels);
+void trace_release(emu_handle_s* h);
 void handle_release_extras(emu_handle_s* h);
 
 template <typename T>

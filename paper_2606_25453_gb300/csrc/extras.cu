@@ -7,5 +7,6 @@ void selector_release(emu_handle_s* h);
 void handle_release_extras(emu_handle_s* h) {
   grouped_release(h);
   selector_release(h);
+  trace_release(h);
 }
 }  // namespace emu
