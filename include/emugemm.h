@@ -154,6 +154,35 @@ emu_status_t emu_zgemm(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n
                        int64_t ldb, const double *beta_host, double *C, int64_t ldc,
                        emu_scheme_t scheme, int nm, emu_stream_t stream);
 
+/* Allocation-free Scheme I DGEMM.  The paper has no counterpart: this entry
+ * point exists for callers that may not allocate device memory while they
+ * run -- programs that reserve all device memory up front in their own pool,
+ * latency-critical code that cannot afford the implicit synchronisation of
+ * cudaMalloc / cudaFree, and plugins whose host forbids allocation.  It
+ * computes exactly what emu_dgemm(..., EMU_SCHEME_I, p, stream) computes (the
+ * same kernels, bit-identical results) without a handle, and calls no
+ * cudaMalloc, cudaFree or other allocating routine: its scratch is a fixed
+ * file-scope device array of EMU_NOALLOC_SCRATCH_BYTES that every GPU which
+ * loads the library holds until the process exits.
+ *  - Runs on the current CUDA device.  The first call on a device looks up
+ *    the array's device address (cudaGetSymbolAddress); make that first call
+ *    before any stream capture on that device.
+ *  - Products whose workspace (emu_workspace_size for Scheme I) exceeds
+ *    EMU_NOALLOC_SCRATCH_BYTES - 256 are rejected with EMU_ERR_UNSUPPORTED
+ *    (e.g. m = n = k = 2048 fits for p <= 7).
+ *  - All calls share the array and it keeps the last call's contents; each
+ *    call clears what must start at zero.  Calls whose work overlaps on the
+ *    GPU (unordered streams) race on the array and give wrong results.
+ *  - status_dev (device int, optional): device-detected errors are OR-ed
+ *    into it as bit flags (1 = non-finite input, 2 = a bounded wait timed
+ *    out); the caller zeroes it and reads it after synchronising.  NULL
+ *    discards them.
+ *  - Arguments, layouts and return codes otherwise as emu_dgemm. */
+#define EMU_NOALLOC_SCRATCH_BYTES (64ll << 20)
+emu_status_t emu_dgemm_noalloc(emu_layout_t layout, int64_t m, int64_t n, int64_t k, double alpha,
+                               const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
+                               double *C, int64_t ldc, int p, int *status_dev, emu_stream_t stream);
+
 /* ------------------------------------------------------------------ */
 /* Steps of the path, exported for verification and ablation           */
 /* ------------------------------------------------------------------ */

@@ -60,6 +60,8 @@ _SIGS = {
     "emu_chunk_len_I": (_i64, [_i32]),
     "emu_moduli": (_i32, [_i32, _vp]),
     "emu_scale_bits_II": (_i32, [_i32, _i64, _i32]),
+    "emu_dgemm_noalloc": (_i32, [_i32, _i64, _i64, _i64, _dbl, _vp, _i64, _vp, _i64, _dbl, _vp, _i64, _i32, _vp,
+                                 _vp]),
     "emu_trace_enable": (_i32, [_vp, _i32]),
     "emu_trace_read": (_i32, [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
 }
