@@ -37,6 +37,13 @@ lib = ctypes.CDLL(_LIB_PATH)
 
 _i64, _i32, _dbl, _flt, _vp, _sz = (ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_float,
                                     ctypes.c_void_p, ctypes.c_size_t)
+class GemmDesc(ctypes.Structure):
+    """emu_gemm_desc_t: one row-major product of a grouped call."""
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64), ("alpha", ctypes.c_double),
+                ("beta", ctypes.c_double), ("A", ctypes.c_void_p), ("lda", ctypes.c_int64), ("B", ctypes.c_void_p),
+                ("ldb", ctypes.c_int64), ("C", ctypes.c_void_p), ("ldc", ctypes.c_int64)]
+
+
 _SIGS = {
     "emu_create": (_i32, [ctypes.POINTER(_vp), _i32]),
     "emu_destroy": (_i32, [_vp]),
@@ -62,6 +69,11 @@ _SIGS = {
     "emu_scale_bits_II": (_i32, [_i32, _i64, _i32]),
     "emu_dgemm_noalloc": (_i32, [_i32, _i64, _i64, _i64, _dbl, _vp, _i64, _vp, _i64, _dbl, _vp, _i64, _i32, _vp,
                                  _vp]),
+    "emu_dgemm_grouped": (_i32, [_vp, _i32, ctypes.POINTER(GemmDesc), _i32, _vp]),
+    "emu_dgemm_grouped_loop": (_i32, [_vp, _i32, ctypes.POINTER(GemmDesc), _i32, _vp]),
+    "emu_tune_grouped": (_i32, [_vp, _i32, ctypes.POINTER(GemmDesc), _i32, ctypes.c_char_p, ctypes.POINTER(_i32),
+                                _vp]),
+    "emu_load_tuning": (_i32, [_vp, ctypes.c_char_p]),
     "emu_trace_enable": (_i32, [_vp, _i32]),
     "emu_trace_read": (_i32, [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
 }
@@ -268,3 +280,32 @@ def residues_II(A, B, nm: int, handle=None, stream=None):
     check(emu_residues_II(h.h, EMU_ROW_MAJOR, m, n, k, _ptr(A), A.stride(0), _ptr(B), B.stride(0), nm,
                           _ptr(out), _stream_ptr(stream)), "emu_residues_II")
     return out
+
+
+def grouped_descs(As, Bs, Cs, alphas=None, betas=None):
+    """Array of GemmDesc for lists of row-major float64 CUDA tensors."""
+    cnt = len(As)
+    arr = (GemmDesc * cnt)()
+    for i, (A, B, C) in enumerate(zip(As, Bs, Cs)):
+        m, k = A.shape
+        n = B.shape[1]
+        arr[i] = GemmDesc(m, n, k, 1.0 if alphas is None else alphas[i], 0.0 if betas is None else betas[i],
+                          A.data_ptr(), max(A.stride(0), k, 1), B.data_ptr(), max(B.stride(0), n, 1), C.data_ptr(),
+                          max(C.stride(0), n, 1))
+    return arr
+
+
+def dgemm_grouped(descs, p: int = 6, handle=None, stream=None, loop: bool = False):
+    """Run emu_dgemm_grouped (one graph-captured persistent launch) or, with
+    loop=True, emu_dgemm_grouped_loop (one emu_dgemm per product)."""
+    h = handle or default_handle(0)
+    fn = emu_dgemm_grouped_loop if loop else emu_dgemm_grouped
+    check(fn(h.h, len(descs), descs, p, _stream_ptr(stream)), fn.__name__)
+
+
+def tune_grouped(descs, p: int = 6, path: str | None = None, handle=None, stream=None) -> int:
+    h = handle or default_handle(0)
+    timed = _i32()
+    check(emu_tune_grouped(h.h, len(descs), descs, p, None if path is None else path.encode(), ctypes.byref(timed),
+                           _stream_ptr(stream)), "emu_tune_grouped")
+    return timed.value

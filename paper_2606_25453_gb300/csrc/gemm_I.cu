@@ -18,6 +18,7 @@
 // the BLAS update, and stores C.  No partial product reaches global memory
 // (OUT_PARTIALS, the unfused ablation, writes the INT32 C_s instead).
 #include "emu_internal.h"
+#include "gemm_I_core.cuh"
 
 namespace emu {
 
@@ -59,52 +60,6 @@ __device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, 
   int in = tile - g * per_group;
   tm = first + in % gsz;
   tn = in / gsz;
-}
-
-template <int I, int J>
-__device__ __forceinline__ void mma_slice(int32_t* d, const uint32_t* a, const uint32_t* b) {
-  mma_i8<I == 0, J == 0>(d, a, b);
-}
-
-// acc[s] += A'_i B'_j for all i + j = s < P, for one B slice j (static).
-template <int P, int J, int I = 0>
-struct TriRow {
-  __device__ __forceinline__ static void run(int32_t (*acc)[2][4], const uint32_t (*af)[4],
-                                             const uint32_t* bf) {
-    if constexpr (I + J < P) {
-      mma_slice<I, J>(acc[I + J][0], af[I], bf);
-      mma_slice<I, J>(acc[I + J][1], af[I], bf + 2);
-      TriRow<P, J, I + 1>::run(acc, af, bf);
-    }
-  }
-};
-
-template <int P, int J = 0>
-struct TriAll {
-  __device__ __forceinline__ static void run(int32_t (*acc)[2][4], const uint32_t (*af)[4],
-                                             uint32_t sB, uint32_t b_off) {
-    if constexpr (J < P) {
-      uint32_t bf[4];
-      ldsm_x4(sB + J * kBlkB + b_off, bf[0], bf[1], bf[2], bf[3]);
-      TriRow<P, J>::run(acc, af, bf);
-      TriAll<P, J + 1>::run(acc, af, sB, b_off);
-    }
-  }
-};
-
-template <int P>
-__device__ __forceinline__ void fold(int32_t (*acc)[2][4], __int128 (*S)[4]) {
-#pragma unroll
-  for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      __int128 t = acc[0][nt][q];
-#pragma unroll
-      for (int s = 1; s < P; ++s) t = t * 256 + acc[s][nt][q];
-      S[nt][q] += t;
-#pragma unroll
-      for (int s = 0; s < P; ++s) acc[s][nt][q] = 0;
-    }
 }
 
 template <int P, int OUT>
@@ -194,7 +149,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_I_kernel(const __grid_consta
       uint32_t af[P][4];
 #pragma unroll
       for (int i = 0; i < P; ++i) ldsm_x4(sA + i * kBlkA + a_off, af[i][0], af[i][1], af[i][2], af[i][3]);
-      TriAll<P>::run(acc, af, sB, b_off);
+      TriAll<P, kBlkB>::run(acc, af, sB, b_off);
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[stage]);
       if (OUT != OUT_PARTIALS && ++since_fold == kp.kc32) {

@@ -1,7 +1,764 @@
-// grouped.cu -- grouped (batched) Scheme I products.
-#include "emu_internal.h"
+// grouped.cu -- many independent Scheme I products in one persistent launch.
+//
+// The paper has no batched interface; this follows its tile model (Table I):
+// the products' output tiles form one work list, balanced over the CTAs by a
+// longest-processing-time assignment (tile cost = number of K chunks), and
+// one persistent kernel walks each CTA's list.  The exponent scan and the
+// split of all operands are one launch each.  The launch sequence (memset,
+// scan, split, GEMM) is captured once into a CUDA graph and replayed while
+// the product descriptors stay identical.  The tile shape (BM x BN, warps of
+// 16 x 16) is chosen per shape bucket by a timing autotuner.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <queue>
+#include <sstream>
+#include <string>
+#include <vector>
+
 #include "emu_handle.h"
+#include "emu_internal.h"
+#include "gemm_I_core.cuh"
 
 namespace emu {
-void grouped_release(emu_handle_s* h) { (void)h; }
+
+namespace {
+
+struct GProb {
+  const double* A;
+  const double* B;
+  double* C;
+  int64_t lda, ldb, ldc;
+  int M, N, K, nk32;
+  double alpha, beta;
+  unsigned long long* maxA;
+  unsigned long long* maxB;
+  int32_t* EA;
+  int32_t* FB;
+  int8_t* hatA;
+  int8_t* hatB;
+  int64_t rows_a, rows_b, nchunks;
+};
+
+// index of the problem owning block `blk` in a prefix array start[0..count]
+__device__ __forceinline__ int find_prob(const int* start, int count, int blk) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (start[mid] <= blk) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------- scan
+// Blocks [0, startA[count]) scan rows of A (one warp per row, K segments of
+// 2048); the rest scan columns of B (32 columns x 8 K-lanes, segments of 256).
+__global__ void grouped_scan_kernel(const GProb* __restrict__ probs, int count, const int* __restrict__ startA,
+                                    const int* __restrict__ startB, int* status) {
+  int blk = blockIdx.x;
+  const int totA = startA[count];
+  if (blk < totA) {
+    int pi = find_prob(startA, count, blk);
+    const GProb& pr = probs[pi];
+    int local = blk - startA[pi];
+    int kseg = (pr.K + 2047) / 2048;
+    int rb = local / kseg, ks = local % kseg;
+    int lane = threadIdx.x & 31;
+    int r = rb * 8 + (threadIdx.x >> 5);
+    if (r >= pr.M) return;
+    int h0 = ks * 2048, h1 = min(h0 + 2048, pr.K);
+    const double* row = pr.A + static_cast<int64_t>(r) * pr.lda;
+    uint64_t mx = 0;
+    for (int h = h0 + lane; h < h1; h += 32) {
+      uint64_t v = dbits(__ldg(row + h)) & 0x7FFFFFFFFFFFFFFFull;
+      mx = v > mx ? v : mx;
+    }
+    for (int o = 16; o; o >>= 1) {
+      uint64_t w = __shfl_xor_sync(0xffffffffu, mx, o);
+      mx = w > mx ? w : mx;
+    }
+    if (lane == 0 && h0 < h1) {
+      atomicMax(pr.maxA + r, static_cast<unsigned long long>(mx));
+      if (mx >= 0x7FF0000000000000ull) set_status(status, ST_NONFINITE);
+    }
+    return;
+  }
+  blk -= totA;
+  int pi = find_prob(startB, count, blk);
+  const GProb& pr = probs[pi];
+  int local = blk - startB[pi];
+  int kseg = (pr.K + 255) / 256;
+  int cb = local / kseg, ks = local % kseg;
+  int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  int c = cb * 32 + tx;
+  int h0 = ks * 256, h1 = min(h0 + 256, pr.K);
+  uint64_t mx = 0;
+  if (c < pr.N) {
+    for (int h = h0 + ty; h < h1; h += 8) {
+      uint64_t v = dbits(__ldg(pr.B + static_cast<int64_t>(h) * pr.ldb + c)) & 0x7FFFFFFFFFFFFFFFull;
+      mx = v > mx ? v : mx;
+    }
+  }
+  __shared__ uint64_t red[8][32];
+  red[ty][tx] = mx;
+  __syncthreads();
+  if (ty == 0 && c < pr.N && h0 < h1) {
+    for (int q = 1; q < 8; ++q) mx = red[q][tx] > mx ? red[q][tx] : mx;
+    atomicMax(pr.maxB + c, static_cast<unsigned long long>(mx));
+    if (mx >= 0x7FF0000000000000ull) set_status(status, ST_NONFINITE);
+  }
+}
+
+// ---------------------------------------------------------------- split
+template <int P>
+__device__ __forceinline__ void digits_of(uint64_t bits, int E, uint32_t* out) {
+  ScaledInt s = scaled_trunc_bits(bits, 8 * P - 1 - E);
+  bool neg = (bits >> 63) != 0;
+  if (P <= 8) {
+    uint64_t v = s.lsh < 64 ? (s.mag << s.lsh) : 0ull;
+    if (neg) v = ~v + 1ull;
+#pragma unroll
+    for (int t = 0; t < P; ++t) out[t] = static_cast<uint32_t>((v >> (8 * (P - 1 - t))) & 0xFFu);
+  } else {
+    unsigned __int128 v = s.lsh < 128 ? (static_cast<unsigned __int128>(s.mag) << s.lsh)
+                                      : static_cast<unsigned __int128>(0);
+    if (neg) v = ~v + static_cast<unsigned __int128>(1);
+#pragma unroll
+    for (int t = 0; t < P; ++t) out[t] = static_cast<uint32_t>((v >> (8 * (P - 1 - t))) & 0xFFu);
+  }
+}
+
+__device__ __forceinline__ int exp_of(const unsigned long long* mb, int r, int rows) {
+  if (r >= rows) return 0;
+  uint64_t v = mb[r];
+  return v >= 0x7FF0000000000000ull ? 0 : frexp_exp_bits(v);
+}
+
+// Blocks [0, startA[count]): A rows, one warp per (row, 32-wide chunk).
+// The rest: B columns, one thread per (column, chunk), 32 bytes per slice.
+template <int P>
+__global__ void grouped_split_kernel(const GProb* __restrict__ probs, int count, const int* __restrict__ startA,
+                                     const int* __restrict__ startB) {
+  int blk = blockIdx.x;
+  const int totA = startA[count];
+  if (blk < totA) {
+    int pi = find_prob(startA, count, blk);
+    const GProb& pr = probs[pi];
+    int64_t w = static_cast<int64_t>(blk - startA[pi]) * 8 + (threadIdx.x >> 5);
+    if (w >= pr.rows_a * pr.nchunks) return;
+    int lane = threadIdx.x & 31;
+    int r = static_cast<int>(w / pr.nchunks);
+    int c = static_cast<int>(w % pr.nchunks);
+    int h = c * 32 + lane;
+    int E = exp_of(pr.maxA, r, pr.M);
+    uint32_t dg[P];
+    if (r < pr.M && h < pr.K) {
+      digits_of<P>(dbits(__ldg(pr.A + static_cast<int64_t>(r) * pr.lda + h)), E, dg);
+    } else {
+#pragma unroll
+      for (int t = 0; t < P; ++t) dg[t] = 0;
+    }
+    uint8_t* row = reinterpret_cast<uint8_t*>(pr.hatA) + static_cast<int64_t>(r) * pr.nchunks * 32 * P;
+#pragma unroll
+    for (int t = 0; t < P; ++t) row[(c * P + t) * 32 + lane] = static_cast<uint8_t>(dg[t]);
+    if (c == 0 && lane == 0 && r < pr.M) pr.EA[r] = E;
+    return;
+  }
+  blk -= totA;
+  int pi = find_prob(startB, count, blk);
+  const GProb& pr = probs[pi];
+  int local = blk - startB[pi];
+  int rblocks = static_cast<int>((pr.rows_b + 255) / 256);
+  int c = local / rblocks;
+  int r = (local % rblocks) * 256 + threadIdx.x;
+  if (r >= pr.rows_b) return;
+  int E = exp_of(pr.maxB, r, pr.N);
+  uint32_t word[P][8];
+#pragma unroll
+  for (int t = 0; t < P; ++t)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) word[t][q] = 0;
+#pragma unroll 1
+  for (int wq = 0; wq < 8; ++wq) {
+    uint32_t cur[P];
+#pragma unroll
+    for (int t = 0; t < P; ++t) cur[t] = 0;
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq) {
+      int h = c * 32 + wq * 4 + qq;
+      uint32_t dg[P];
+      if (r < pr.N && h < pr.K) {
+        digits_of<P>(dbits(__ldg(pr.B + static_cast<int64_t>(h) * pr.ldb + r)), E, dg);
+      } else {
+#pragma unroll
+        for (int t = 0; t < P; ++t) dg[t] = 0;
+      }
+#pragma unroll
+      for (int t = 0; t < P; ++t) cur[t] |= dg[t] << (8 * qq);
+    }
+#pragma unroll
+    for (int t = 0; t < P; ++t)
+#pragma unroll
+      for (int z = 0; z < 8; ++z) word[t][z] = (wq == z) ? cur[t] : word[t][z];
+  }
+  uint8_t* row = reinterpret_cast<uint8_t*>(pr.hatB) + static_cast<int64_t>(r) * pr.nchunks * 32 * P;
+#pragma unroll
+  for (int t = 0; t < P; ++t) {
+    uint4* dst = reinterpret_cast<uint4*>(row + (c * P + t) * 32);
+    dst[0] = make_uint4(word[t][0], word[t][1], word[t][2], word[t][3]);
+    dst[1] = make_uint4(word[t][4], word[t][5], word[t][6], word[t][7]);
+  }
+  if (c == 0 && r < pr.N) pr.FB[r] = E;
+}
+
+// ---------------------------------------------------------------- GEMM
+template <int P, int BM, int BN>
+struct CfgG {
+  static constexpr int kWM = BM / 16, kWN = BN / 16, kCW = kWM * kWN;
+  static constexpr int kThreads = (kCW + 1) * 32;
+  static constexpr int kBlkA = BM * 32, kBlkB = BN * 32;
+  static constexpr int kStageBytes = P * (kBlkA + kBlkB);
+  static constexpr int kBudget = kCW >= 8 ? 163840 : 98304;  // 4-warp tiles run 2 CTAs per SM
+  static constexpr int kRaw = kBudget / kStageBytes;
+  static constexpr int kStages = kRaw < 2 ? 2 : (kRaw > 8 ? 8 : kRaw);
+  static constexpr int kSmem = kStages * kStageBytes + 1024 + 2 * kStages * 8 + 64;
+  static constexpr int kOcc = kCW >= 8 ? 1 : 2;
+};
+
+template <int P, int BM, int BN>
+__global__ void __launch_bounds__(CfgG<P, BM, BN>::kThreads, CfgG<P, BM, BN>::kOcc)
+    gemm_I_grouped_kernel(const GProb* __restrict__ probs, const CUtensorMap* __restrict__ maps,
+                          const int4* __restrict__ tiles, const int* __restrict__ cta_ptr, int kc32, int escale,
+                          int* status) {
+  using Cfg = CfgG<P, BM, BN>;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* smem = smem_raw + (base - raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + Cfg::kStages * Cfg::kStageBytes);
+  uint64_t* empty = full + Cfg::kStages;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < Cfg::kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], Cfg::kCW);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const int t0 = cta_ptr[blockIdx.x], t1 = cta_ptr[blockIdx.x + 1];
+
+  if (warp == Cfg::kCW) {
+    if (lane == 0) {
+      uint32_t it = 0;
+      for (int t = t0; t < t1; ++t) {
+        const int4 tl = tiles[t];
+        const CUtensorMap* dA = maps + 2 * tl.x;
+        const CUtensorMap* dB = dA + 1;
+        const int nk32 = probs[tl.x].nk32;
+        for (int kk = 0; kk < nk32; ++kk, ++it) {
+          const uint32_t stage = it % Cfg::kStages;
+          const uint32_t par = (it / Cfg::kStages) & 1u;
+          if (it >= static_cast<uint32_t>(Cfg::kStages) && !mbar_wait_bounded(&empty[stage], par ^ 1u)) {
+            set_status(status, ST_TIMEOUT);
+            return;
+          }
+          mbar_arrive_expect_tx(&full[stage], Cfg::kStageBytes);
+          uint8_t* sA = smem + stage * Cfg::kStageBytes;
+          uint8_t* sB = sA + P * Cfg::kBlkA;
+#pragma unroll
+          for (int q = 0; q < P; ++q) tma_load_2d(sA + q * Cfg::kBlkA, dA, &full[stage], (kk * P + q) * 32, tl.y * BM);
+#pragma unroll
+          for (int q = 0; q < P; ++q) tma_load_2d(sB + q * Cfg::kBlkB, dB, &full[stage], (kk * P + q) * 32, tl.z * BN);
+        }
+      }
+    }
+    return;
+  }
+
+  const int wm = warp / Cfg::kWN, wn = warp % Cfg::kWN;
+  const uint32_t a_off = swz32(wm * 16 + (lane & 15), lane >> 4);
+  const uint32_t b_off = swz32(wn * 16 + (lane & 7) + ((lane >> 4) << 3), (lane >> 3) & 1);
+  uint32_t it = 0;
+  for (int t = t0; t < t1; ++t) {
+    const int4 tl = tiles[t];
+    const GProb& pr = probs[tl.x];
+    int32_t acc[P][2][4];
+    __int128 S[2][4];
+#pragma unroll
+    for (int s = 0; s < P; ++s)
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[s][nt][q] = 0;
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) S[nt][q] = 0;
+    int since = 0;
+    const int nk32 = pr.nk32;
+    for (int kk = 0; kk < nk32; ++kk, ++it) {
+      const uint32_t stage = it % Cfg::kStages;
+      const uint32_t par = (it / Cfg::kStages) & 1u;
+      if (!mbar_wait_bounded(&full[stage], par)) {
+        set_status(status, ST_TIMEOUT);
+        return;
+      }
+      const uint32_t sA = base + stage * Cfg::kStageBytes;
+      const uint32_t sB = sA + P * Cfg::kBlkA;
+      uint32_t af[P][4];
+#pragma unroll
+      for (int i = 0; i < P; ++i) ldsm_x4(sA + i * Cfg::kBlkA + a_off, af[i][0], af[i][1], af[i][2], af[i][3]);
+      TriAll<P, Cfg::kBlkB>::run(acc, af, sB, b_off);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[stage]);
+      if (++since == kc32) {
+        fold<P>(acc, S);
+        since = 0;
+      }
+    }
+    fold<P>(acc, S);
+    const int row0 = tl.y * BM + wm * 16 + (lane >> 2);
+    const int col0 = tl.z * BN + wn * 16 + (lane & 3) * 2;
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int row = row0 + (q >> 1) * 8, col = col0 + nt * 8 + (q & 1);
+        if (row < pr.M && col < pr.N) {
+          double d = i128_to_double_rn(S[nt][q]);
+          double r = scale2(d, pr.EA[row] + pr.FB[col] + escale);
+          double* cp = pr.C + static_cast<int64_t>(row) * pr.ldc + col;
+          *cp = blas_update(pr.alpha, r, pr.beta, pr.beta != 0.0 ? *cp : 0.0);
+        }
+      }
+  }
+}
+
+// ---------------------------------------------------------------- host plan
+constexpr int kNumCfg = 3;
+constexpr int kCfgBM[kNumCfg] = {64, 32, 32};
+constexpr int kCfgBN[kNumCfg] = {32, 32, 64};
+
+struct GroupPlan {
+  std::vector<emu_gemm_desc_t> descs;
+  int p = 0, cfg = 0, grid = 0, count = 0;
+  void* dev = nullptr;  // one device buffer: probs, maps, tiles, cta_ptr, starts, workspace
+  size_t dev_bytes = 0;
+  GProb* d_probs = nullptr;
+  CUtensorMap* d_maps = nullptr;
+  int4* d_tiles = nullptr;
+  int* d_cta = nullptr;
+  int* d_startA_scan = nullptr;
+  int* d_startB_scan = nullptr;
+  int* d_startA_split = nullptr;
+  int* d_startB_split = nullptr;
+  unsigned long long* d_max = nullptr;
+  size_t max_bytes = 0;
+  int scan_blocks = 0, split_blocks = 0;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+};
+
+struct GroupState {
+  GroupPlan* plan = nullptr;
+  std::map<std::string, int> tuned;  // shape bucket -> configuration index
+  cudaStream_t capture = nullptr;
+};
+
+void free_plan(GroupPlan* pl) {
+  if (!pl) return;
+  if (pl->exec) cudaGraphExecDestroy(pl->exec);
+  if (pl->graph) cudaGraphDestroy(pl->graph);
+  if (pl->dev) cudaFree(pl->dev);
+  delete pl;
+}
+
+GroupState* state_of(emu_handle_s* h) {
+  if (!h->grouped) h->grouped = new GroupState();
+  return static_cast<GroupState*>(h->grouped);
+}
+
+bool same_descs(const std::vector<emu_gemm_desc_t>& a, const emu_gemm_desc_t* b, int count) {
+  if (static_cast<int>(a.size()) != count) return false;
+  return std::memcmp(a.data(), b, sizeof(emu_gemm_desc_t) * count) == 0;
+}
+
+// Shape bucket of a product list: p, and log2 buckets of the median output
+// side and of the median K.
+std::string bucket_of(int count, const emu_gemm_desc_t* d, int p) {
+  std::vector<double> side, kk;
+  for (int i = 0; i < count; ++i) {
+    side.push_back(std::sqrt(static_cast<double>(d[i].m) * static_cast<double>(d[i].n)));
+    kk.push_back(static_cast<double>(d[i].k));
+  }
+  std::nth_element(side.begin(), side.begin() + count / 2, side.end());
+  std::nth_element(kk.begin(), kk.begin() + count / 2, kk.end());
+  char buf[64];
+  std::snprintf(buf, sizeof(buf), "p%d_mn%d_k%d", p, static_cast<int>(std::floor(std::log2(side[count / 2] + 1))),
+                static_cast<int>(std::floor(std::log2(kk[count / 2] + 1))));
+  return buf;
+}
+
+template <int P, int BM, int BN>
+cudaError_t launch_gemm_grouped(const GroupPlan& pl, int* status, cudaStream_t st, bool attrs_only) {
+  using Cfg = CfgG<P, BM, BN>;
+  if (attrs_only)
+    return cudaFuncSetAttribute(gemm_I_grouped_kernel<P, BM, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                Cfg::kSmem);
+  gemm_I_grouped_kernel<P, BM, BN><<<pl.grid, Cfg::kThreads, Cfg::kSmem, st>>>(
+      pl.d_probs, pl.d_maps, pl.d_tiles, pl.d_cta, static_cast<int>(host_chunk_len_I(P) / 32), -14 - 8 * (P - 1),
+      status);
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_by_cfg(const GroupPlan& pl, int* status, cudaStream_t st, bool attrs_only) {
+  switch (pl.cfg) {
+    case 0: return launch_gemm_grouped<P, 64, 32>(pl, status, st, attrs_only);
+    case 1: return launch_gemm_grouped<P, 32, 32>(pl, status, st, attrs_only);
+    default: return launch_gemm_grouped<P, 32, 64>(pl, status, st, attrs_only);
+  }
+}
+
+// Set the dynamic shared memory limit of the plan's GEMM instantiation
+// (done before capture: it is not stream work).
+cudaError_t prepare_attrs(const GroupPlan& pl) {
+  switch (pl.p) {
+#define EMU_GA(PP) case PP: return launch_by_cfg<PP>(pl, nullptr, nullptr, true);
+    EMU_GA(1) EMU_GA(2) EMU_GA(3) EMU_GA(4) EMU_GA(5) EMU_GA(6)
+    EMU_GA(7) EMU_GA(8) EMU_GA(9) EMU_GA(10) EMU_GA(11) EMU_GA(12)
+#undef EMU_GA
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int occupancy_of(int cfg) { return (kCfgBM[cfg] / 16) * (kCfgBN[cfg] / 16) >= 8 ? 1 : 2; }
+
+cudaError_t launch_group(const GroupPlan& pl, int* status, cudaStream_t st) {
+  cudaMemsetAsync(pl.d_max, 0, pl.max_bytes, st);
+  if (pl.scan_blocks)
+    grouped_scan_kernel<<<pl.scan_blocks, 256, 0, st>>>(pl.d_probs, pl.count, pl.d_startA_scan, pl.d_startB_scan,
+                                                         status);
+  if (pl.split_blocks) {
+    switch (pl.p) {
+#define EMU_GS(PP) \
+  case PP: grouped_split_kernel<PP><<<pl.split_blocks, 256, 0, st>>>(pl.d_probs, pl.count, pl.d_startA_split, pl.d_startB_split); break;
+      EMU_GS(1) EMU_GS(2) EMU_GS(3) EMU_GS(4) EMU_GS(5) EMU_GS(6)
+      EMU_GS(7) EMU_GS(8) EMU_GS(9) EMU_GS(10) EMU_GS(11) EMU_GS(12)
+#undef EMU_GS
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  switch (pl.p) {
+#define EMU_GG(PP) case PP: return launch_by_cfg<PP>(pl, status, st, false);
+    EMU_GG(1) EMU_GG(2) EMU_GG(3) EMU_GG(4) EMU_GG(5) EMU_GG(6)
+    EMU_GG(7) EMU_GG(8) EMU_GG(9) EMU_GG(10) EMU_GG(11) EMU_GG(12)
+#undef EMU_GG
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+static size_t al256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+// Build a plan: device tables, workspace, tensor maps, LPT tile lists.
+emu_status_t build_plan(emu_handle_s* h, int count, const emu_gemm_desc_t* d, int p, int cfg, GroupPlan** out) {
+  auto* pl = new GroupPlan();
+  pl->descs.assign(d, d + count);
+  pl->p = p;
+  pl->cfg = cfg;
+  pl->count = count;
+  const int BM = kCfgBM[cfg], BN = kCfgBN[cfg];
+  pl->grid = h->num_sms * occupancy_of(cfg);
+
+  // sizes
+  std::vector<GProb> probs(count);
+  size_t off = 0;
+  size_t o_probs = off; off += al256(sizeof(GProb) * count);
+  size_t o_maps = off; off += al256(sizeof(CUtensorMap) * 2 * count);
+  // tile list
+  std::vector<int4> tiles;
+  for (int i = 0; i < count; ++i) {
+    int tm = static_cast<int>((d[i].m + BM - 1) / BM), tn = static_cast<int>((d[i].n + BN - 1) / BN);
+    for (int a = 0; a < tm; ++a)
+      for (int b = 0; b < tn; ++b) tiles.push_back(make_int4(i, a, b, 0));
+  }
+  // longest-processing-time assignment to grid slots (cost = K chunks)
+  std::stable_sort(tiles.begin(), tiles.end(), [&](const int4& x, const int4& y) { return d[x.x].k > d[y.x].k; });
+  int grid = pl->grid;
+  if (static_cast<int>(tiles.size()) < grid) grid = std::max<int>(1, static_cast<int>(tiles.size()));
+  pl->grid = grid;
+  std::vector<std::vector<int4>> per(grid);
+  using Slot = std::pair<int64_t, int>;
+  std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> heap;
+  for (int g = 0; g < grid; ++g) heap.push({0, g});
+  for (const int4& t : tiles) {
+    Slot s = heap.top();
+    heap.pop();
+    per[s.second].push_back(t);
+    s.first += (d[t.x].k + 31) / 32;
+    heap.push(s);
+  }
+  std::vector<int4> flat;
+  std::vector<int> cta(grid + 1, 0);
+  for (int g = 0; g < grid; ++g) {
+    cta[g] = static_cast<int>(flat.size());
+    flat.insert(flat.end(), per[g].begin(), per[g].end());
+  }
+  cta[grid] = static_cast<int>(flat.size());
+  size_t o_tiles = off; off += al256(sizeof(int4) * std::max<size_t>(flat.size(), 1));
+  size_t o_cta = off; off += al256(sizeof(int) * (grid + 1));
+  // block prefix arrays
+  std::vector<int> sA(count + 1), sB(count + 1), pA(count + 1), pB(count + 1);
+  sA[0] = sB[0] = pA[0] = pB[0] = 0;
+  for (int i = 0; i < count; ++i) {
+    int64_t M = d[i].m, N = d[i].n, K = d[i].k;
+    int64_t rows_a = split_rows(M), rows_b = split_rows(N), nch = (K + 31) / 32;
+    sA[i + 1] = sA[i] + static_cast<int>(((M + 7) / 8) * ((K + 2047) / 2048));
+    sB[i + 1] = sB[i] + static_cast<int>(((N + 31) / 32) * ((K + 255) / 256));
+    pA[i + 1] = pA[i] + static_cast<int>((rows_a * nch + 7) / 8);
+    pB[i + 1] = pB[i] + static_cast<int>(((rows_b + 255) / 256) * nch);
+  }
+  size_t o_starts = off; off += al256(sizeof(int) * 4 * (count + 1));
+  // per-problem workspace
+  size_t o_max = off;
+  size_t max_bytes = 0;
+  for (int i = 0; i < count; ++i) max_bytes += al256(8 * std::max<int64_t>(d[i].m, 1)) + al256(8 * std::max<int64_t>(d[i].n, 1));
+  off += max_bytes;
+  std::vector<size_t> o_ws(count);
+  for (int i = 0; i < count; ++i) {
+    Plan w = plan_I(d[i].m, d[i].n, d[i].k, p);
+    o_ws[i] = off;
+    off += al256(w.bytes);
+  }
+  pl->dev_bytes = off;
+  if (cudaMalloc(&pl->dev, off) != cudaSuccess) {
+    cudaGetLastError();
+    delete pl;
+    return EMU_ERR_ALLOC;
+  }
+  uint8_t* base = static_cast<uint8_t*>(pl->dev);
+  pl->d_probs = reinterpret_cast<GProb*>(base + o_probs);
+  pl->d_maps = reinterpret_cast<CUtensorMap*>(base + o_maps);
+  pl->d_tiles = reinterpret_cast<int4*>(base + o_tiles);
+  pl->d_cta = reinterpret_cast<int*>(base + o_cta);
+  int* starts = reinterpret_cast<int*>(base + o_starts);
+  pl->d_startA_scan = starts;
+  pl->d_startB_scan = starts + (count + 1);
+  pl->d_startA_split = starts + 2 * (count + 1);
+  pl->d_startB_split = starts + 3 * (count + 1);
+  pl->d_max = reinterpret_cast<unsigned long long*>(base + o_max);
+  pl->max_bytes = max_bytes;
+  pl->scan_blocks = sA[count] + sB[count];
+  pl->split_blocks = pA[count] + pB[count];
+  std::vector<CUtensorMap> maps(2 * count);
+  size_t moff = 0;
+  for (int i = 0; i < count; ++i) {
+    GProb& g = probs[i];
+    g.A = d[i].A;
+    g.B = d[i].B;
+    g.C = d[i].C;
+    g.lda = d[i].lda;
+    g.ldb = d[i].ldb;
+    g.ldc = d[i].ldc;
+    g.M = static_cast<int>(d[i].m);
+    g.N = static_cast<int>(d[i].n);
+    g.K = static_cast<int>(d[i].k);
+    g.nk32 = static_cast<int>((d[i].k + 31) / 32);
+    g.alpha = d[i].alpha;
+    g.beta = d[i].beta;
+    g.maxA = reinterpret_cast<unsigned long long*>(base + o_max + moff);
+    moff += al256(8 * std::max<int64_t>(d[i].m, 1));
+    g.maxB = reinterpret_cast<unsigned long long*>(base + o_max + moff);
+    moff += al256(8 * std::max<int64_t>(d[i].n, 1));
+    Plan w = plan_I(d[i].m, d[i].n, d[i].k, p);
+    uint8_t* ws = base + o_ws[i];
+    g.EA = reinterpret_cast<int32_t*>(ws + w.off_EA);
+    g.FB = reinterpret_cast<int32_t*>(ws + w.off_FB);
+    g.hatA = reinterpret_cast<int8_t*>(ws + w.off_hatA);
+    g.hatB = reinterpret_cast<int8_t*>(ws + w.off_hatB);
+    g.rows_a = w.rows_a;
+    g.rows_b = w.rows_b;
+    g.nchunks = (d[i].k + 31) / 32;
+    if (!make_tmap_i8(&maps[2 * i], g.hatA, static_cast<uint64_t>(w.cols), static_cast<uint64_t>(w.rows_a), BM) ||
+        !make_tmap_i8(&maps[2 * i + 1], g.hatB, static_cast<uint64_t>(w.cols), static_cast<uint64_t>(w.rows_b), BN)) {
+      free_plan(pl);
+      return EMU_ERR_CUDA;
+    }
+  }
+  std::vector<int> st4;
+  st4.insert(st4.end(), sA.begin(), sA.end());
+  st4.insert(st4.end(), sB.begin(), sB.end());
+  st4.insert(st4.end(), pA.begin(), pA.end());
+  st4.insert(st4.end(), pB.begin(), pB.end());
+  bool ok = cudaMemcpy(pl->d_probs, probs.data(), sizeof(GProb) * count, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(pl->d_maps, maps.data(), sizeof(CUtensorMap) * 2 * count, cudaMemcpyHostToDevice) == cudaSuccess &&
+            (flat.empty() || cudaMemcpy(pl->d_tiles, flat.data(), sizeof(int4) * flat.size(), cudaMemcpyHostToDevice) == cudaSuccess) &&
+            cudaMemcpy(pl->d_cta, cta.data(), sizeof(int) * (grid + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(starts, st4.data(), sizeof(int) * st4.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+  if (!ok) {
+    free_plan(pl);
+    return EMU_ERR_CUDA;
+  }
+  *out = pl;
+  return EMU_OK;
+}
+
+// Capture the plan's launch sequence into a graph (on a private stream).
+emu_status_t capture_plan(emu_handle_s* h, GroupState* gs, GroupPlan* pl) {
+  if (!gs->capture && cudaStreamCreateWithFlags(&gs->capture, cudaStreamNonBlocking) != cudaSuccess)
+    return EMU_ERR_CUDA;
+  if (prepare_attrs(*pl) != cudaSuccess) return EMU_ERR_CUDA;
+  if (cudaStreamBeginCapture(gs->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return EMU_ERR_CUDA;
+  cudaError_t le = launch_group(*pl, h->status, gs->capture);
+  cudaError_t ce = cudaStreamEndCapture(gs->capture, &pl->graph);
+  if (le != cudaSuccess || ce != cudaSuccess) {
+    cudaGetLastError();
+    return EMU_ERR_CUDA;
+  }
+  if (cudaGraphInstantiate(&pl->exec, pl->graph, 0) != cudaSuccess) return EMU_ERR_CUDA;
+  return EMU_OK;
+}
+
+emu_status_t validate(emu_handle_s* h, int count, const emu_gemm_desc_t* d, int p) {
+  if (!h || count < 0 || (count > 0 && !d)) return EMU_ERR_INVALID_ARG;
+  if (p < EMU_P_MIN || p > EMU_P_MAX) return EMU_ERR_UNSUPPORTED;
+  for (int i = 0; i < count; ++i) {
+    if (d[i].m < 1 || d[i].n < 1 || d[i].k < 1) return EMU_ERR_INVALID_ARG;
+    if (d[i].m > (1 << 24) || d[i].n > (1 << 24) || d[i].k > (1 << 24)) return EMU_ERR_UNSUPPORTED;
+    if (!d[i].A || !d[i].B || !d[i].C) return EMU_ERR_INVALID_ARG;
+    if (!check_lds(EMU_ROW_MAJOR, d[i].m, d[i].n, d[i].k, d[i].lda, d[i].ldb, d[i].ldc)) return EMU_ERR_INVALID_ARG;
+  }
+  return EMU_OK;
+}
+
+// Run (building and capturing if the product list changed) with a given cfg.
+emu_status_t run_group(emu_handle_s* h, int count, const emu_gemm_desc_t* d, int p, int cfg, cudaStream_t st) {
+  GroupState* gs = state_of(h);
+  GroupPlan* pl = gs->plan;
+  if (!pl || pl->p != p || pl->cfg != cfg || !same_descs(pl->descs, d, count)) {
+    if (pl) {
+      cudaDeviceSynchronize();
+      free_plan(pl);
+      gs->plan = nullptr;
+    }
+    emu_status_t s = build_plan(h, count, d, p, cfg, &pl);
+    if (s != EMU_OK) return s;
+    s = capture_plan(h, gs, pl);
+    if (s != EMU_OK) {
+      free_plan(pl);
+      return s;
+    }
+    gs->plan = pl;
+  }
+  trace_begin(h, PH_GEMM, st);
+  cudaError_t e = cudaGraphLaunch(pl->exec, st);
+  trace_end(h, PH_GEMM, st, 3);
+  return e == cudaSuccess ? EMU_OK : EMU_ERR_CUDA;
+}
+
+}  // namespace
+
+void grouped_release(emu_handle_s* h) {
+  if (!h->grouped) return;
+  auto* gs = static_cast<GroupState*>(h->grouped);
+  free_plan(gs->plan);
+  if (gs->capture) cudaStreamDestroy(gs->capture);
+  delete gs;
+  h->grouped = nullptr;
+}
+
 }  // namespace emu
+
+using namespace emu;
+
+extern "C" {
+
+emu_status_t emu_dgemm_grouped(emu_handle_t h, int count, const emu_gemm_desc_t* descs, int p, emu_stream_t stream) {
+  emu_status_t s = validate(h, count, descs, p);
+  if (s != EMU_OK || count == 0) return s;
+  cudaSetDevice(h->device);
+  GroupState* gs = state_of(h);
+  int cfg = 0;
+  auto it = gs->tuned.find(bucket_of(count, descs, p));
+  if (it != gs->tuned.end()) cfg = it->second;
+  return run_group(h, count, descs, p, cfg, static_cast<cudaStream_t>(stream));
+}
+
+emu_status_t emu_dgemm_grouped_loop(emu_handle_t h, int count, const emu_gemm_desc_t* d, int p, emu_stream_t stream) {
+  emu_status_t s = validate(h, count, d, p);
+  if (s != EMU_OK) return s;
+  for (int i = 0; i < count; ++i) {
+    s = emu_dgemm(h, EMU_ROW_MAJOR, d[i].m, d[i].n, d[i].k, d[i].alpha, d[i].A, d[i].lda, d[i].B, d[i].ldb,
+                  d[i].beta, d[i].C, d[i].ldc, EMU_SCHEME_I, p, stream);
+    if (s != EMU_OK) return s;
+  }
+  return EMU_OK;
+}
+
+emu_status_t emu_tune_grouped(emu_handle_t h, int count, const emu_gemm_desc_t* d, int p, const char* path,
+                              int* timed, emu_stream_t stream) {
+  emu_status_t s = validate(h, count, d, p);
+  if (s != EMU_OK || count == 0) return s;
+  cudaSetDevice(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int best_cfg = 0, n_timed = 0;
+  for (int cfg = 0; cfg < kNumCfg; ++cfg) {
+    s = run_group(h, count, d, p, cfg, st);  // builds, captures and warms up
+    if (s != EMU_OK) break;
+    run_group(h, count, d, p, cfg, st);
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 3; ++r) run_group(h, count, d, p, cfg, st);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ++n_timed;
+    if (ms < best) {
+      best = ms;
+      best_cfg = cfg;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != EMU_OK) return s;
+  GroupState* gs = state_of(h);
+  gs->tuned[bucket_of(count, d, p)] = best_cfg;
+  if (timed) *timed = n_timed;
+  if (path) {
+    std::ofstream f(path);
+    if (!f) return EMU_ERR_INVALID_ARG;
+    f << "{\n";
+    size_t i = 0;
+    for (auto& kv : gs->tuned)
+      f << "  \"" << kv.first << "\": " << kv.second << (++i < gs->tuned.size() ? ",\n" : "\n");
+    f << "}\n";
+  }
+  return EMU_OK;
+}
+
+emu_status_t emu_load_tuning(emu_handle_t h, const char* path) {
+  if (!h || !path) return EMU_ERR_INVALID_ARG;
+  std::ifstream f(path);
+  if (!f) return EMU_ERR_INVALID_ARG;
+  GroupState* gs = state_of(h);
+  std::string line;
+  while (std::getline(f, line)) {
+    size_t q1 = line.find('"'), q2 = line.find('"', q1 + 1), c = line.find(':', q2 + 1);
+    if (q1 == std::string::npos || q2 == std::string::npos || c == std::string::npos) continue;
+    int v = std::atoi(line.c_str() + c + 1);
+    if (v < 0 || v >= kNumCfg) return EMU_ERR_INVALID_ARG;
+    gs->tuned[line.substr(q1 + 1, q2 - q1 - 1)] = v;
+  }
+  return EMU_OK;
+}
+
+}  // extern "C"
