@@ -297,9 +297,10 @@ emu_status_t emu_load_tuning(emu_handle_t h, const char *path);
 #define EMU_SEL_NPARAM 8968
 
 /* Features of one product (device output float[66]): 32-bin histogram of
- * E_i - e(a_ij) (exponent deficit of each element of A against its row
- * maximum, bins 0..30 and >= 31, zeros in bin 31) normalised to sum 1, the
- * same for the columns of B, log2(k)/16 and -log10(tol)/16.  A, B device,
+ * d = E_i - e(a_ij) (exponent deficit of each element of A against its row
+ * maximum, e = frexp exponent) in bins of 3 exponents, bin = min(d/3, 31),
+ * zeros in bin 31, normalised to sum 1; the same for the columns of B;
+ * log2(k)/16 and -log10(tol)/16.  A, B device,
  * layout as emu_dgemm; at most `sample` rows of A and columns of B are read
  * (evenly spaced; 0 = all). */
 emu_status_t emu_sel_features(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k,
@@ -339,14 +340,17 @@ emu_status_t emu_probe_dd(emu_handle_t h, emu_layout_t layout, int64_t m, int64_
                           const int32_t *idx_dev, double *ref_dev, double *absab_dev,
                           emu_stream_t stream);
 
-/* Auto precision: C = alpha*A*B + beta*C with the smallest p the selector
- * predicts for max_ij |C - AB|_ij / (|A||B|)_ij <= tol.  The prediction is
- * checked on `probe` sampled entries against emu_probe_dd; on a miss p is
- * raised (to max(p+1, the bound-based p)) and the product recomputed, up to
- * EMU_P_MAX.  Without loaded selector weights the bound-based p is used.
- * Synchronises `stream` (the probe result decides the next step); *p_used
- * receives the p of the returned result.  beta must be 0 (C is overwritten
- * on a retry).  Returns EMU_ERR_TOL_NOT_MET if even EMU_P_MAX misses. */
+/* Auto precision: C = alpha*A*B with the smallest p the selector predicts
+ * for max_ij |C - AB|_ij / (|A||B|)_ij <= tol: the smallest class whose
+ * cumulative predicted probability reaches 0.8, and EMU_P_MAX for the
+ * open-ended top class "10 or more".  The result is checked on `probe`
+ * sampled entries against emu_probe_dd; on a miss p is raised to
+ * max(p + 1, the bound-based p), then to EMU_P_MAX, and the product is
+ * recomputed.  Without loaded selector weights the bound-based p is used.
+ * Synchronises `stream` (the probe decides the next step); *p_used receives
+ * the p of the returned result.  There is no beta: C is overwritten.
+ * Returns EMU_ERR_TOL_NOT_MET (C holds the EMU_P_MAX result) if even
+ * EMU_P_MAX misses on the probed entries. */
 emu_status_t emu_dgemm_auto(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k,
                             double alpha, const double *A, int64_t lda, const double *B,
                             int64_t ldb, double *C, int64_t ldc, double tol, int probe,
@@ -354,8 +358,9 @@ emu_status_t emu_dgemm_auto(emu_handle_t h, emu_layout_t layout, int64_t m, int6
 
 /* Bound-based slice count for tolerance tol from the exponent statistics
  * (host): smallest p in [3, 10] whose worst-case truncation bound
- * 2^(-8p+3) * 2^(spread) * k meets tol, where spread is the largest exponent
- * deficit seen in the sampled rows/columns.  Written to *p_host. */
+ * 2^(-8p+3) * 2^(spread) * k meets tol, where spread is the upper edge of the
+ * largest exponent-deficit bin seen in 64 sampled rows/columns (10 if none
+ * does).  Written to *p_host. */
 emu_status_t emu_bound_p(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k,
                          const double *A, int64_t lda, const double *B, int64_t ldb, double tol,
                          int *p_host, emu_stream_t stream);

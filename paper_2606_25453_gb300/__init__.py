@@ -74,6 +74,15 @@ _SIGS = {
     "emu_tune_grouped": (_i32, [_vp, _i32, ctypes.POINTER(GemmDesc), _i32, ctypes.c_char_p, ctypes.POINTER(_i32),
                                 _vp]),
     "emu_load_tuning": (_i32, [_vp, ctypes.c_char_p]),
+    "emu_sel_features": (_i32, [_vp, _i32, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _dbl, _i64, _vp, _vp]),
+    "emu_sel_forward": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp, _vp]),
+    "emu_sel_backward": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "emu_sel_adam": (_i32, [_vp, _vp, _vp, _vp, _vp, _i32, _flt, _flt, _flt, _flt, _vp]),
+    "emu_sel_load": (_i32, [_vp, ctypes.POINTER(_flt)]),
+    "emu_probe_dd": (_i32, [_vp, _i32, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _i32, _vp, _vp, _vp, _vp]),
+    "emu_dgemm_auto": (_i32, [_vp, _i32, _i64, _i64, _i64, _dbl, _vp, _i64, _vp, _i64, _vp, _i64, _dbl, _i32,
+                              ctypes.POINTER(_i32), _vp]),
+    "emu_bound_p": (_i32, [_vp, _i32, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _dbl, ctypes.POINTER(_i32), _vp]),
     "emu_trace_enable": (_i32, [_vp, _i32]),
     "emu_trace_read": (_i32, [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
 }
@@ -309,3 +318,20 @@ def tune_grouped(descs, p: int = 6, path: str | None = None, handle=None, stream
     check(emu_tune_grouped(h.h, len(descs), descs, p, None if path is None else path.encode(), ctypes.byref(timed),
                            _stream_ptr(stream)), "emu_tune_grouped")
     return timed.value
+
+
+def dgemm_auto(A, B, tol: float, alpha: float = 1.0, probe: int = 64, handle=None, stream=None):
+    """C = alpha*A@B with the p chosen by the selector (or the bound if no
+    weights are loaded), checked on `probe` sampled entries; returns (C, p)."""
+    import torch
+    m, k = A.shape
+    n = B.shape[1]
+    C = torch.empty((m, n), dtype=torch.float64, device=A.device)
+    layout, lda, ldb, ldc = _layout_of(A, B, C)
+    h = handle or default_handle(A.device.index or 0)
+    p = _i32()
+    code = emu_dgemm_auto(h.h, layout, m, n, k, alpha, _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc, tol, probe,
+                          ctypes.byref(p), _stream_ptr(stream))
+    if code not in (0, 7):
+        check(code, "emu_dgemm_auto")
+    return C, p.value, code

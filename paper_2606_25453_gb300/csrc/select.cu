@@ -1,7 +1,496 @@
-// select.cu -- learned slice-count selector.
-#include "emu_internal.h"
+// select.cu -- learned slice-count selector for Scheme I (auto precision).
+//
+// The paper picks p by hand and notes that it lacks an automatic precision
+// choice (Sec. VII).  This file adds one: per-product features (exponent
+// deficit histograms of sampled rows of A and columns of B, log2 k and the
+// requested tolerance), a 66-64-64-8 MLP with hand-written FP32 forward,
+// backward and Adam kernels, a double-double probe of sampled output entries
+// that judges a prediction, and emu_dgemm_auto, which escalates p when the
+// probe finds the tolerance missed.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
 #include "emu_handle.h"
+#include "emu_internal.h"
 
 namespace emu {
-void selector_release(emu_handle_s* h) { (void)h; }
+
+namespace {
+
+constexpr int kIn = EMU_SEL_IN, kHid = EMU_SEL_HID, kOut = EMU_SEL_OUT;
+constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kHid * kIn, kOffW2 = kOffB1 + kHid, kOffB2 = kOffW2 + kHid * kHid,
+              kOffW3 = kOffB2 + kHid, kOffB3 = kOffW3 + kOut * kHid, kNParam = kOffB3 + kOut;
+static_assert(kNParam == EMU_SEL_NPARAM, "parameter count");
+
+struct SelState {
+  float* params = nullptr;  // device, loaded weights
+  bool loaded = false;
+};
+SelState* sel_of(emu_handle_s* h) {
+  if (!h->selector) h->selector = new SelState();
+  return static_cast<SelState*>(h->selector);
+}
+
+// ---------------------------------------------------------------- features
+// Exponent of |x| from its bits: frexp exponent (E with |x| in [2^(E-1), 2^E)).
+__device__ __forceinline__ int exp_bits(uint64_t ab) { return frexp_exp_bits(ab); }
+
+// One block per sampled vector: 32-bin histogram of the exponent deficit
+// d = E_vec - e(x) in bins of 3 exponents (bin = min(d / 3, 31); x == 0 ->
+// bin 31), added to hist (uint32[32]).
+__global__ void feat_hist_kernel(const double* __restrict__ X, int64_t ld, bool kcontig, int64_t rows, int64_t k,
+                                 int64_t stride, const unsigned long long* __restrict__ maxbits,
+                                 unsigned int* __restrict__ hist) {
+  __shared__ unsigned int sh[32];
+  if (threadIdx.x < 32) sh[threadIdx.x] = 0;
+  __syncthreads();
+  int64_t r = static_cast<int64_t>(blockIdx.x) * stride;
+  if (r < rows) {
+    uint64_t mb = maxbits[r];
+    int E = mb >= 0x7FF0000000000000ull ? 0 : exp_bits(mb);
+    for (int64_t h = threadIdx.x; h < k; h += blockDim.x) {
+      uint64_t ab = dbits(__ldg(kcontig ? X + r * ld + h : X + h * ld + r)) & 0x7FFFFFFFFFFFFFFFull;
+      int bin = 31;
+      if (ab != 0 && ab < 0x7FF0000000000000ull) {
+        int d = E - exp_bits(ab);
+        bin = d < 0 ? 0 : (d / 3 > 31 ? 31 : d / 3);
+      }
+      atomicAdd(&sh[bin], 1u);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 32 && sh[threadIdx.x]) atomicAdd(&hist[threadIdx.x], sh[threadIdx.x]);
+}
+
+__global__ void feat_finalize_kernel(const unsigned int* __restrict__ hist, double log2k, double ltol,
+                                     float* __restrict__ feat) {
+  int t = threadIdx.x;
+  __shared__ float tot[2];
+  if (t < 2) {
+    unsigned int s = 0;
+    for (int i = 0; i < 32; ++i) s += hist[t * 32 + i];
+    tot[t] = s ? static_cast<float>(s) : 1.0f;
+  }
+  __syncthreads();
+  if (t < 64) feat[t] = static_cast<float>(hist[t]) / tot[t / 32];
+  if (t == 64) feat[64] = static_cast<float>(log2k / 16.0);
+  if (t == 65) feat[65] = static_cast<float>(ltol / 16.0);
+}
+
+// ---------------------------------------------------------------- MLP
+// One block of 64 threads per sample.  act (optional): [h1 | h2] per sample.
+__global__ void mlp_forward_kernel(const float* __restrict__ prm, const float* __restrict__ X, int64_t batch,
+                                   float* __restrict__ P, float* __restrict__ act) {
+  __shared__ float x[kIn], h1[kHid], h2[kHid], z[kOut];
+  const int64_t b = blockIdx.x;
+  const int j = threadIdx.x;
+  if (b >= batch) return;
+  for (int i = j; i < kIn; i += blockDim.x) x[i] = X[b * kIn + i];
+  __syncthreads();
+  float s = prm[kOffB1 + j];
+  for (int i = 0; i < kIn; ++i) s = fmaf(prm[kOffW1 + j * kIn + i], x[i], s);
+  h1[j] = s > 0.f ? s : 0.f;
+  __syncthreads();
+  s = prm[kOffB2 + j];
+  for (int i = 0; i < kHid; ++i) s = fmaf(prm[kOffW2 + j * kHid + i], h1[i], s);
+  h2[j] = s > 0.f ? s : 0.f;
+  __syncthreads();
+  if (j < kOut) {
+    float t = prm[kOffB3 + j];
+    for (int i = 0; i < kHid; ++i) t = fmaf(prm[kOffW3 + j * kHid + i], h2[i], t);
+    z[j] = t;
+  }
+  __syncthreads();
+  if (j < kOut) {
+    float mx = z[0];
+    for (int o = 1; o < kOut; ++o) mx = fmaxf(mx, z[o]);
+    float den = 0.f;
+    for (int o = 0; o < kOut; ++o) den += expf(z[o] - mx);
+    P[b * kOut + j] = expf(z[j] - mx) / den;
+  }
+  if (act) {
+    act[b * 2 * kHid + j] = h1[j];
+    act[b * 2 * kHid + kHid + j] = h2[j];
+  }
+}
+
+// Mean cross-entropy backward.  Each block takes `per` samples, accumulates
+// the parameter gradient in shared memory and adds it to grad once.
+__global__ void mlp_backward_kernel(const float* __restrict__ prm, const float* __restrict__ X,
+                                    const float* __restrict__ act, const float* __restrict__ P,
+                                    const int32_t* __restrict__ y, int64_t batch, int per, float* __restrict__ grad,
+                                    float* __restrict__ loss) {
+  extern __shared__ float g[];  // kNParam floats
+  __shared__ float dz[kOut], dh2[kHid], dh1[kHid];
+  const int j = threadIdx.x;  // 64 threads
+  for (int i = j; i < kNParam; i += blockDim.x) g[i] = 0.f;
+  __syncthreads();
+  const float inv = 1.0f / static_cast<float>(batch);
+  float lsum = 0.f;
+  for (int q = 0; q < per; ++q) {
+    int64_t b = static_cast<int64_t>(blockIdx.x) * per + q;
+    if (b >= batch) break;
+    const float* x = X + b * kIn;
+    const float* h1 = act + b * 2 * kHid;
+    const float* h2 = h1 + kHid;
+    const int lab = y[b];
+    if (j < kOut) dz[j] = (P[b * kOut + j] - (j == lab ? 1.f : 0.f)) * inv;
+    if (j == 0) lsum += -logf(fmaxf(P[b * kOut + lab], 1e-30f));
+    __syncthreads();
+    // layer 3
+    for (int o = 0; o < kOut; ++o) g[kOffW3 + o * kHid + j] += dz[o] * h2[j];
+    if (j < kOut) g[kOffB3 + j] += dz[j];
+    float s = 0.f;
+    for (int o = 0; o < kOut; ++o) s = fmaf(prm[kOffW3 + o * kHid + j], dz[o], s);
+    dh2[j] = h2[j] > 0.f ? s : 0.f;
+    __syncthreads();
+    // layer 2 (thread j owns row j of W2)
+    for (int i = 0; i < kHid; ++i) g[kOffW2 + j * kHid + i] += dh2[j] * h1[i];
+    g[kOffB2 + j] += dh2[j];
+    s = 0.f;
+    for (int o = 0; o < kHid; ++o) s = fmaf(prm[kOffW2 + o * kHid + j], dh2[o], s);
+    dh1[j] = h1[j] > 0.f ? s : 0.f;
+    __syncthreads();
+    // layer 1 (thread j owns row j of W1)
+    for (int i = 0; i < kIn; ++i) g[kOffW1 + j * kIn + i] += dh1[j] * x[i];
+    g[kOffB1 + j] += dh1[j];
+    __syncthreads();
+  }
+  for (int i = j; i < kNParam; i += blockDim.x)
+    if (g[i] != 0.f) atomicAdd(&grad[i], g[i]);
+  if (j == 0 && lsum != 0.f) atomicAdd(loss, lsum * inv);
+}
+
+__global__ void adam_kernel(float* __restrict__ prm, const float* __restrict__ grad, float* __restrict__ m,
+                            float* __restrict__ v, int n, float lr, float b1, float b2, float eps, float c1, float c2) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float gi = grad[i];
+  float mi = b1 * m[i] + (1.f - b1) * gi;
+  float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  prm[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// ---------------------------------------------------------------- probe
+struct DD {
+  double hi, lo;
+};
+__device__ __forceinline__ DD dd_add(DD a, DD b) {
+  double s = __dadd_rn(a.hi, b.hi);
+  double z = __dsub_rn(s, a.hi);
+  double e = __dadd_rn(__dsub_rn(a.hi, __dsub_rn(s, z)), __dsub_rn(b.hi, z));
+  e = __dadd_rn(e, __dadd_rn(a.lo, b.lo));
+  double t = __dadd_rn(s, e);
+  return {t, __dsub_rn(e, __dsub_rn(t, s))};
+}
+
+// One warp per sampled entry (i, j): compensated dot product (TwoProduct by
+// fma, TwoSum accumulation) per lane, lanes combined by double-double adds.
+__global__ void probe_dd_kernel(const double* __restrict__ A, int64_t lda, bool a_kcontig, const double* __restrict__ B,
+                                int64_t ldb, bool b_kcontig, int64_t k, int count, const int32_t* __restrict__ idx,
+                                double* __restrict__ ref, double* __restrict__ absab) {
+  int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= count) return;
+  int64_t i = idx[2 * w], j = idx[2 * w + 1];
+  DD acc{0.0, 0.0};
+  double ab = 0.0;
+  for (int64_t h = lane; h < k; h += 32) {
+    double a = a_kcontig ? A[i * lda + h] : A[h * lda + i];
+    double b = b_kcontig ? B[j * ldb + h] : B[h * ldb + j];
+    double p = __dmul_rn(a, b);
+    double e = __fma_rn(a, b, -p);
+    acc = dd_add(acc, DD{p, e});
+    ab = __fma_rn(fabs(a), fabs(b), ab);
+  }
+  for (int o = 16; o; o >>= 1) {
+    DD other{__shfl_xor_sync(0xffffffffu, acc.hi, o), __shfl_xor_sync(0xffffffffu, acc.lo, o)};
+    acc = dd_add(acc, other);
+    ab = __dadd_rn(ab, __shfl_xor_sync(0xffffffffu, ab, o));
+  }
+  if (lane == 0) {
+    ref[2 * w] = acc.hi;
+    ref[2 * w + 1] = acc.lo;
+    absab[w] = ab;
+  }
+}
+
+__global__ void gather_kernel(const double* __restrict__ C, int64_t ldc, int count, const int32_t* __restrict__ idx,
+                              double* __restrict__ out) {
+  int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w < count) out[w] = C[static_cast<int64_t>(idx[2 * w]) * ldc + idx[2 * w + 1]];
+}
+
+}  // namespace
+
+void selector_release(emu_handle_s* h) {
+  auto* s = static_cast<SelState*>(h->selector);
+  if (!s) return;
+  if (s->params) cudaFree(s->params);
+  delete s;
+  h->selector = nullptr;
+}
+
 }  // namespace emu
+
+using namespace emu;
+
+namespace {
+
+// Features of one product into feat (device float[66]); needs 8*(m+n)+256
+// bytes of scratch (maxbits + histogram).
+emu_status_t features_impl(emu_handle_s* h, const View& v, int64_t k, double tol, int64_t sample, float* feat,
+                           uint8_t* scratch, cudaStream_t st) {
+  auto* maxA = reinterpret_cast<unsigned long long*>(scratch);
+  auto* maxB = maxA + v.M;
+  auto* hist = reinterpret_cast<unsigned int*>(maxB + v.N);
+  launch_scan<double>(static_cast<const double*>(v.A), v.ldA, v.a_kcontig, v.M, k, 1, maxA, h->status, st);
+  launch_scan<double>(static_cast<const double*>(v.B), v.ldB, v.b_kcontig, v.N, k, 1, maxB, h->status, st);
+  cudaMemsetAsync(hist, 0, 64 * sizeof(unsigned int), st);
+  int64_t sa = sample > 0 ? std::max<int64_t>(1, v.M / sample) : 1;
+  int64_t sb = sample > 0 ? std::max<int64_t>(1, v.N / sample) : 1;
+  int64_t na = (v.M + sa - 1) / sa, nb = (v.N + sb - 1) / sb;
+  if (sample > 0) {
+    na = std::min<int64_t>(na, sample);
+    nb = std::min<int64_t>(nb, sample);
+  }
+  feat_hist_kernel<<<static_cast<unsigned>(na), 256, 0, st>>>(static_cast<const double*>(v.A), v.ldA, v.a_kcontig, v.M,
+                                                               k, sa, maxA, hist);
+  feat_hist_kernel<<<static_cast<unsigned>(nb), 256, 0, st>>>(static_cast<const double*>(v.B), v.ldB, v.b_kcontig, v.N,
+                                                               k, sb, maxB, hist + 32);
+  feat_finalize_kernel<<<1, 96, 0, st>>>(hist, std::log2(static_cast<double>(k)), -std::log10(tol), feat);
+  return cudaGetLastError() == cudaSuccess ? EMU_OK : EMU_ERR_CUDA;
+}
+
+size_t feat_scratch(const View& v) { return 8 * static_cast<size_t>(v.M + v.N) + 512; }
+
+bool valid_layout(emu_layout_t l) { return l == EMU_ROW_MAJOR || l == EMU_COL_MAJOR; }
+
+// Bound-based p: smallest p in [3, 10] with 2^(-8p+3) * 2^spread * k <= tol,
+// spread = the upper edge of the largest exponent-deficit bin seen.
+int bound_p_from_hist(const float* f, int64_t k, double tol) {
+  int spread = 0;
+  for (int i = 0; i < 64; ++i)
+    if (f[i] > 0.f) spread = std::max(spread, 3 * (i % 32) + 2);
+  for (int p = 3; p <= 10; ++p)
+    if (std::ldexp(1.0, -8 * p + 3 + spread) * static_cast<double>(k) <= tol) return p;
+  return 10;
+}
+
+}  // namespace
+
+extern "C" {
+
+emu_status_t emu_sel_features(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k, const double* A,
+                              int64_t lda, const double* B, int64_t ldb, double tol, int64_t sample, float* feat,
+                              emu_stream_t stream) {
+  if (!h || !feat || !A || !B || m < 1 || n < 1 || k < 1 || !(tol > 0.0) || !valid_layout(layout))
+    return EMU_ERR_INVALID_ARG;
+  if (!check_lds(layout, m, n, k, lda, ldb, layout == EMU_ROW_MAJOR ? n : m)) return EMU_ERR_INVALID_ARG;
+  cudaSetDevice(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  View v;
+  normalize(layout, m, n, A, lda, B, ldb, &v);
+  uint8_t* ws = nullptr;
+  emu_status_t s = handle_workspace(h, feat_scratch(v), st, &ws);
+  if (s != EMU_OK) return s;
+  return features_impl(h, v, k, tol, sample, feat, ws, st);
+}
+
+emu_status_t emu_sel_forward(emu_handle_t h, int64_t batch, const float* prm, const float* X, float* P, float* act,
+                             emu_stream_t stream) {
+  if (!h || !prm || !X || !P || batch < 0) return EMU_ERR_INVALID_ARG;
+  if (batch == 0) return EMU_OK;
+  if (batch > INT32_MAX) return EMU_ERR_UNSUPPORTED;
+  cudaSetDevice(h->device);
+  mlp_forward_kernel<<<static_cast<unsigned>(batch), kHid, 0, static_cast<cudaStream_t>(stream)>>>(prm, X, batch, P,
+                                                                                                    act);
+  return cudaGetLastError() == cudaSuccess ? EMU_OK : EMU_ERR_CUDA;
+}
+
+emu_status_t emu_sel_backward(emu_handle_t h, int64_t batch, const float* prm, const float* X, const float* act,
+                              const float* P, const int32_t* y, float* grad, float* loss, emu_stream_t stream) {
+  if (!h || !prm || !X || !act || !P || !y || !grad || !loss || batch < 1) return EMU_ERR_INVALID_ARG;
+  cudaSetDevice(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int per = 32;
+  const int smem = kNParam * static_cast<int>(sizeof(float));
+  if (cudaFuncSetAttribute(mlp_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    return EMU_ERR_CUDA;
+  cudaMemsetAsync(grad, 0, sizeof(float) * kNParam, st);
+  cudaMemsetAsync(loss, 0, sizeof(float), st);
+  unsigned blocks = static_cast<unsigned>((batch + per - 1) / per);
+  mlp_backward_kernel<<<blocks, kHid, smem, st>>>(prm, X, act, P, y, batch, per, grad, loss);
+  return cudaGetLastError() == cudaSuccess ? EMU_OK : EMU_ERR_CUDA;
+}
+
+emu_status_t emu_sel_adam(emu_handle_t h, float* prm, const float* grad, float* m, float* v, int step, float lr,
+                          float b1, float b2, float eps, emu_stream_t stream) {
+  if (!h || !prm || !grad || !m || !v || step < 1) return EMU_ERR_INVALID_ARG;
+  cudaSetDevice(h->device);
+  float c1 = 1.f - std::pow(b1, static_cast<float>(step)), c2 = 1.f - std::pow(b2, static_cast<float>(step));
+  adam_kernel<<<(kNParam + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(prm, grad, m, v, kNParam, lr, b1,
+                                                                                      b2, eps, c1, c2);
+  return cudaGetLastError() == cudaSuccess ? EMU_OK : EMU_ERR_CUDA;
+}
+
+emu_status_t emu_sel_load(emu_handle_t h, const float* params) {
+  if (!h || !params) return EMU_ERR_INVALID_ARG;
+  cudaSetDevice(h->device);
+  SelState* s = sel_of(h);
+  if (!s->params && cudaMalloc(&s->params, sizeof(float) * kNParam) != cudaSuccess) return EMU_ERR_ALLOC;
+  if (cudaMemcpy(s->params, params, sizeof(float) * kNParam, cudaMemcpyHostToDevice) != cudaSuccess)
+    return EMU_ERR_CUDA;
+  s->loaded = true;
+  return EMU_OK;
+}
+
+emu_status_t emu_probe_dd(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k, const double* A,
+                          int64_t lda, const double* B, int64_t ldb, int count, const int32_t* idx, double* ref,
+                          double* absab, emu_stream_t stream) {
+  if (!h || !A || !B || !idx || !ref || !absab || count < 0 || m < 1 || n < 1 || k < 1 || !valid_layout(layout))
+    return EMU_ERR_INVALID_ARG;
+  if (!check_lds(layout, m, n, k, lda, ldb, layout == EMU_ROW_MAJOR ? n : m)) return EMU_ERR_INVALID_ARG;
+  if (count == 0) return EMU_OK;
+  cudaSetDevice(h->device);
+  // entries are given in the caller's (i, j) of C; the kernel reads A rows
+  // and B columns directly in the caller's layout
+  bool a_k = layout == EMU_ROW_MAJOR, b_k = layout != EMU_ROW_MAJOR;
+  probe_dd_kernel<<<(count * 32 + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      A, lda, a_k, B, ldb, b_k, k, count, idx, ref, absab);
+  return cudaGetLastError() == cudaSuccess ? EMU_OK : EMU_ERR_CUDA;
+}
+
+emu_status_t emu_bound_p(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k, const double* A,
+                         int64_t lda, const double* B, int64_t ldb, double tol, int* p_out, emu_stream_t stream) {
+  if (!p_out) return EMU_ERR_INVALID_ARG;
+  float* feat = nullptr;
+  if (!h) return EMU_ERR_INVALID_ARG;
+  cudaSetDevice(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // features into the tail of the workspace region
+  View v;
+  if (!valid_layout(layout) || m < 1 || n < 1 || k < 1 || !A || !B || !(tol > 0.0)) return EMU_ERR_INVALID_ARG;
+  normalize(layout, m, n, A, lda, B, ldb, &v);
+  uint8_t* ws = nullptr;
+  size_t need = feat_scratch(v) + 512;
+  emu_status_t s = handle_workspace(h, need, st, &ws);
+  if (s != EMU_OK) return s;
+  feat = reinterpret_cast<float*>(ws + feat_scratch(v));
+  s = features_impl(h, v, k, tol, 64, feat, ws, st);
+  if (s != EMU_OK) return s;
+  float f[kIn];
+  if (cudaMemcpyAsync(f, feat, sizeof(f), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return EMU_ERR_CUDA;
+  *p_out = bound_p_from_hist(f, k, tol);
+  return EMU_OK;
+}
+
+emu_status_t emu_dgemm_auto(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k, double alpha,
+                            const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc,
+                            double tol, int probe, int* p_used, emu_stream_t stream) {
+  if (!h || !p_used || !A || !B || !C || m < 1 || n < 1 || k < 1 || !(tol > 0.0) || probe < 0 || !valid_layout(layout))
+    return EMU_ERR_INVALID_ARG;
+  if (!check_lds(layout, m, n, k, lda, ldb, ldc)) return EMU_ERR_INVALID_ARG;
+  cudaSetDevice(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  SelState* ss = sel_of(h);
+  View v;
+  normalize(layout, m, n, A, lda, B, ldb, &v);
+  // small device scratch of the selector (features, probabilities, probe)
+  const int pc = std::max(probe, 1);
+  size_t need = feat_scratch(v) + 1024 + static_cast<size_t>(pc) * (8 + 16 + 8 + 8) + 256;
+  uint8_t* ws = nullptr;
+  emu_status_t s = handle_workspace(h, need, st, &ws);
+  if (s != EMU_OK) return s;
+  float* feat = reinterpret_cast<float*>(ws + feat_scratch(v));
+  float* prob = feat + 128;
+  s = features_impl(h, v, k, tol, 64, feat, ws, st);
+  if (s != EMU_OK) return s;
+  float f[kIn], pr[kOut];
+  if (ss->loaded) mlp_forward_kernel<<<1, kHid, 0, st>>>(ss->params, feat, 1, prob, nullptr);
+  if (cudaMemcpyAsync(f, feat, sizeof(f), cudaMemcpyDeviceToHost, st) != cudaSuccess) return EMU_ERR_CUDA;
+  if (ss->loaded && cudaMemcpyAsync(pr, prob, sizeof(pr), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return EMU_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return EMU_ERR_CUDA;
+  const int pb = bound_p_from_hist(f, k, tol);
+  int p = pb;
+  if (ss->loaded) {  // smallest class whose cumulative predicted probability reaches 0.8
+    float c = 0.f;
+    int cls = kOut - 1;
+    for (int o = 0; o < kOut; ++o) {
+      c += pr[o];
+      if (c >= 0.8f) {
+        cls = o;
+        break;
+      }
+    }
+    // the top class is open-ended ("10 or more"): go to the largest p at once
+    p = cls == kOut - 1 ? EMU_P_MAX : EMU_SEL_P0 + cls;
+  }
+  // probe entries: a deterministic spread over C (caller's coordinates)
+  std::vector<int32_t> idx(2 * static_cast<size_t>(probe));
+  uint64_t x = 0x9E3779B97F4A7C15ull ^ static_cast<uint64_t>(m * 1315423911u + n * 2654435761u + k);
+  for (int q = 0; q < probe; ++q) {
+    x ^= x << 13;
+    x ^= x >> 7;
+    x ^= x << 17;
+    idx[2 * q] = static_cast<int32_t>(x % static_cast<uint64_t>(m));
+    x ^= x << 13;
+    x ^= x >> 7;
+    x ^= x << 17;
+    idx[2 * q + 1] = static_cast<int32_t>(x % static_cast<uint64_t>(n));
+  }
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    s = emu_dgemm(h, layout, m, n, k, alpha, A, lda, B, ldb, 0.0, C, ldc, EMU_SCHEME_I, p, stream);
+    if (s != EMU_OK) return s;
+    *p_used = p;
+    if (probe == 0) return EMU_OK;
+    // workspace may have moved inside emu_dgemm: re-fetch the selector scratch
+    s = handle_workspace(h, need, st, &ws);
+    if (s != EMU_OK) return s;
+    auto* d_idx = reinterpret_cast<int32_t*>(ws + feat_scratch(v) + 1024);
+    auto* d_ref = reinterpret_cast<double*>(ws + feat_scratch(v) + 1024 + 8 * static_cast<size_t>(pc));
+    auto* d_ab = d_ref + 2 * pc;
+    auto* d_c = d_ab + pc;
+    if (cudaMemcpyAsync(d_idx, idx.data(), sizeof(int32_t) * idx.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return EMU_ERR_CUDA;
+    s = emu_probe_dd(h, layout, m, n, k, A, lda, B, ldb, probe, d_idx, d_ref, d_ab, stream);
+    if (s != EMU_OK) return s;
+    if (layout == EMU_ROW_MAJOR) {
+      gather_kernel<<<(probe + 127) / 128, 128, 0, st>>>(C, ldc, probe, d_idx, d_c);
+    } else {  // column-major C: element (i, j) at C[i + j*ldc] = row-major view with (j, i)
+      std::vector<int32_t> sw(idx.size());
+      for (int q = 0; q < probe; ++q) {
+        sw[2 * q] = idx[2 * q + 1];
+        sw[2 * q + 1] = idx[2 * q];
+      }
+      auto* d_sw = reinterpret_cast<int32_t*>(d_c + pc);
+      cudaMemcpyAsync(d_sw, sw.data(), sizeof(int32_t) * sw.size(), cudaMemcpyHostToDevice, st);
+      gather_kernel<<<(probe + 127) / 128, 128, 0, st>>>(C, ldc, probe, d_sw, d_c);
+    }
+    std::vector<double> ref(2 * static_cast<size_t>(probe)), ab(probe), cv(probe);
+    cudaMemcpyAsync(ref.data(), d_ref, sizeof(double) * ref.size(), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(ab.data(), d_ab, sizeof(double) * ab.size(), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(cv.data(), d_c, sizeof(double) * cv.size(), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return EMU_ERR_CUDA;
+    double worst = 0.0;
+    for (int q = 0; q < probe; ++q) {
+      double d = std::fabs((cv[q] / alpha - ref[2 * q]) - ref[2 * q + 1]);
+      double e = ab[q] > 0.0 ? d / ab[q] : (d > 0.0 ? INFINITY : 0.0);
+      worst = std::max(worst, e);
+    }
+    if (worst <= tol) return EMU_OK;
+    if (p >= EMU_P_MAX) return EMU_ERR_TOL_NOT_MET;
+    // a miss at the top class goes straight to the largest p
+    p = (attempt == 0 && p < EMU_SEL_P0 + kOut - 1) ? std::max(p + 1, pb) : EMU_P_MAX;
+    p = std::min(p, EMU_P_MAX);
+  }
+  return EMU_ERR_TOL_NOT_MET;
+}
+
+}  // extern "C"
