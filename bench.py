@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-rows", type=int, default=16, help="rows of C in the CPU oracle sample")
     ap.add_argument("--no-extras", action="store_true", help="skip cuBLAS / accuracy / CPU legs")
+    ap.add_argument("--suite", default=None, help="write the secondary measurements (all paths) to this JSONL file")
     return ap.parse_args()
 
 
@@ -351,8 +352,147 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------ suite
+def run_suite(path, args):
+    """Secondary measurements: every path of the library on one GPU, one JSON
+    object per point (device-resident inputs, CUDA-event timing, 1 warm-up +
+    3 timed calls, error on 8 x 64 sampled entries vs double-double)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    import paper_2606_25453_gb300 as emu
+    oracle.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    h = emu.Handle(0)
+    out = open(path, "w")
+
+    def emit(d):
+        out.write(json.dumps(d) + "\n")
+        out.flush()
+        print(json.dumps(d), flush=True)
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    rng = np.random.Generator(np.random.PCG64(99))
+
+    def sampled_err(A, B, C, complex_=False):
+        ri = np.sort(rng.choice(A.shape[0], 8, replace=False))
+        ci = np.sort(rng.choice(B.shape[1], 64, replace=False))
+        if complex_:
+            hi, lo = oracle.dd_zgemm(A[ri], B[:, ci])
+        else:
+            hi, lo = oracle.dd_gemm(A[ri], B[:, ci])
+        return oracle.err_metric(C[ri][:, ci], (hi, lo), A[ri], B[:, ci])
+
+    cache = {}
+
+    def pair(n, phi, dtype=np.float64):
+        key = (n, phi, dtype)
+        if key not in cache:
+            cache.clear()
+            A, B = synth.gemm_pair(n, n, n, phi, 7)
+            if dtype is np.float32:
+                A, B = A.astype(np.float32), B.astype(np.float32)
+            cache[key] = (A, B, torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev))
+        return cache[key]
+
+    # cuBLAS references on this GPU
+    for n in (4096, 8192):
+        A, B, Ad, Bd = pair(n, 0.5)
+        ms = timed(lambda: Ad @ Bd, reps=2)
+        C = (Ad @ Bd).cpu().numpy()
+        emit({"path": "cublas_dgemm", "n": n, "tflops": 2 * n ** 3 / ms / 1e9, "ms": ms, "err": sampled_err(A, B, C)})
+        Af, Bf = Ad.float(), Bd.float()
+        ms = timed(lambda: Af @ Bf)
+        emit({"path": "cublas_sgemm", "n": n, "tflops": 2 * n ** 3 / ms / 1e9, "ms": ms})
+    # Scheme I DGEMM: p sweep, phi sweep
+    for n in (4096, 8192):
+        for phi in (0.5, 2.0, 4.0):
+            A, B, Ad, Bd = pair(n, phi)
+            Cd = torch.empty((n, n), dtype=torch.float64, device=dev)
+            for p in range(4, 13) if phi == 4.0 else range(4, 9):
+                ms = timed(lambda: emu.dgemm(Ad, Bd, Cd, scheme="I", p=p, handle=h))
+                emit({"path": "emu_dgemm_I", "n": n, "phi": phi, "p": p, "tflops": 2 * n ** 3 / ms / 1e9,
+                      "int8_tops": p * (p + 1) * n ** 3 / ms / 1e9, "ms": ms,
+                      "err": sampled_err(A, B, Cd.cpu().numpy())})
+    n = 16384
+    A, B = synth.gemm_pair(n, n, n, 0.5, 7)
+    Ad, Bd = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+    Cd = torch.empty((n, n), dtype=torch.float64, device=dev)
+    for p in (7, 8):
+        ms = timed(lambda: emu.dgemm(Ad, Bd, Cd, scheme="I", p=p, handle=h), reps=1)
+        emit({"path": "emu_dgemm_I", "n": n, "phi": 0.5, "p": p, "tflops": 2 * n ** 3 / ms / 1e9,
+              "int8_tops": p * (p + 1) * n ** 3 / ms / 1e9, "ms": ms, "err": sampled_err(A, B, Cd.cpu().numpy())})
+    del Ad, Bd, Cd
+    # Scheme I SGEMM
+    for p in (3, 4):
+        A, B, Ad, Bd = pair(8192, 0.5, np.float32)
+        Cd = torch.empty((8192, 8192), dtype=torch.float32, device=dev)
+        ms = timed(lambda: emu.sgemm(Ad, Bd, Cd, scheme="I", p=p, handle=h))
+        emit({"path": "emu_sgemm_I", "n": 8192, "phi": 0.5, "p": p, "tflops": 2 * 8192 ** 3 / ms / 1e9,
+              "int8_tops": p * (p + 1) * 8192 ** 3 / ms / 1e9, "ms": ms,
+              "err": sampled_err(A.astype(np.float64), B.astype(np.float64), Cd.cpu().numpy().astype(np.float64))})
+    # Scheme II DGEMM
+    for phi in (0.5, 4.0):
+        A, B, Ad, Bd = pair(8192, phi)
+        Cd = torch.empty((8192, 8192), dtype=torch.float64, device=dev)
+        for nm in (12, 14, 16, 18, 20):
+            ms = timed(lambda: emu.dgemm(Ad, Bd, Cd, scheme="II", p=nm, handle=h))
+            emit({"path": "emu_dgemm_II", "n": 8192, "phi": phi, "nm": nm, "tflops": 2 * 8192 ** 3 / ms / 1e9,
+                  "int8_tops": 2 * nm * 8192 ** 3 / ms / 1e9, "ms": ms, "err": sampled_err(A, B, Cd.cpu().numpy())})
+    cache.clear()
+    # ZGEMM 3M vs cuBLAS ZGEMM
+    n = 8192
+    A, B = synth.gemm_pair_complex(n, n, n, 1.0, 7)
+    Ad, Bd = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+    ms = timed(lambda: Ad @ Bd, reps=1)
+    emit({"path": "cublas_zgemm", "n": n, "tflops_8mnk": 8 * n ** 3 / ms / 1e9, "ms": ms,
+          "err": sampled_err(A, B, (Ad @ Bd).cpu().numpy(), True)})
+    Cd = torch.empty((n, n), dtype=torch.complex128, device=dev)
+    for nm in (12, 16, 20):
+        ms = timed(lambda: emu.zgemm(Ad, Bd, Cd, nm=nm, handle=h), reps=1)
+        emit({"path": "emu_zgemm_3m", "n": n, "phi": 1.0, "nm": nm, "tflops_8mnk": 8 * n ** 3 / ms / 1e9,
+              "tflops_2mnk": 2 * n ** 3 / ms / 1e9, "int8_tops": 6 * nm * n ** 3 / ms / 1e9, "ms": ms,
+              "err": sampled_err(A, B, Cd.cpu().numpy(), True)})
+    del Ad, Bd, Cd
+    # grouped: 512 uneven products, graph vs per-product loop
+    shapes = synth.grouped_shapes(512, 0)
+    As, Bs, Cs = [], [], []
+    for i, (m, nn, k) in enumerate(shapes):
+        A, B = synth.gemm_pair(m, nn, k, 1.0, 5000 + i)
+        As.append(torch.from_numpy(A).to(dev))
+        Bs.append(torch.from_numpy(B).to(dev))
+        Cs.append(torch.empty((m, nn), dtype=torch.float64, device=dev))
+    d = emu.grouped_descs(As, Bs, Cs)
+    flops = sum(2 * m * nn * k for m, nn, k in shapes)
+    ms_default = timed(lambda: emu.dgemm_grouped(d, 6, handle=h), reps=5)
+    ncfg = emu.tune_grouped(d, 6, handle=h)
+    ms_tuned = timed(lambda: emu.dgemm_grouped(d, 6, handle=h), reps=5)
+    ms_loop = timed(lambda: emu.dgemm_grouped(d, 6, handle=h, loop=True), reps=2)
+    emit({"path": "emu_dgemm_grouped", "count": 512, "p": 6, "ms_graph_default_tile": ms_default,
+          "ms_graph_tuned": ms_tuned, "configs_timed": ncfg, "ms_loop": ms_loop,
+          "tflops_graph": flops / ms_tuned / 1e9, "tflops_loop": flops / ms_loop / 1e9,
+          "int8_tops_graph": 21 * flops / ms_tuned / 1e9, "speedup_graph_vs_loop": ms_loop / ms_tuned})
+    out.close()
+    h.close()
+
+
 def main():
     args = parse()
+    if args.suite:
+        run_suite(args.suite, args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
