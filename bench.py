@@ -142,6 +142,21 @@ def load_traffic(p, n):
         return None
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """Largest value of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_tflops(world: int, flops_per_rank_step: float, steps: int, ms_max: float) -> float:
+    """Whole-job throughput: all ranks' work divided by the slowest rank's time."""
+    return world * flops_per_rank_step * steps / (ms_max * 1e-3) / 1e12
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -236,13 +251,10 @@ def run_ours(args, rank, world, local_rank):
     ms = e0.elapsed_time(e1)
     tr = h.trace_read()
     h.trace(False)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     ms_step = ms / args.steps
     flops = 2.0 * n * n * n
-    value = world * flops * args.steps / (ms * 1e-3) / 1e12
+    value = aggregate_tflops(world, flops, args.steps, ms)
     int8_ops = float(p * (p + 1)) * n * n * n
     status = h.status()
 
@@ -263,12 +275,8 @@ def run_ours(args, rank, world, local_rank):
         C_pin.copy_(Cd, non_blocking=True)
     e3.record(stream)
     torch.cuda.synchronize()
-    ms_e2e = e2.elapsed_time(e3)
-    if dist:
-        t = torch.tensor([ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
-    e2e_value = world * flops * args.steps / (ms_e2e * 1e-3) / 1e12
+    ms_e2e = max_over_ranks(e2.elapsed_time(e3), dist, dev)
+    e2e_value = aggregate_tflops(world, flops, args.steps, ms_e2e)
 
     extras = {}
     int8_peak = None

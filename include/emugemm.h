@@ -99,6 +99,16 @@ emu_status_t emu_destroy(emu_handle_t h);
  * EMU_OK, EMU_ERR_NONFINITE, EMU_ERR_TIMEOUT or EMU_ERR_CUDA. */
 emu_status_t emu_get_status(emu_handle_t h, emu_stream_t stream);
 
+/* Failure-path self-test: launches one block whose mbarrier wait can never
+ * be satisfied (nothing arrives on it).  The wait is bounded exactly like the
+ * waits of the GEMM kernels, here by limit_cycles (clamped to [1e3, 2e9]
+ * clock cycles); when it gives up the kernel records EMU_ERR_TIMEOUT in the
+ * status word and returns, leaving the context usable.  emu_get_status then
+ * reports EMU_ERR_TIMEOUT.  (The library's own waits give up after ~1 s.)
+ * Host-side fault injection: with the environment variable EMU_FAULT=alloc
+ * every library-owned workspace allocation fails with EMU_ERR_ALLOC. */
+emu_status_t emu_selftest_wait(emu_handle_t h, int64_t limit_cycles, emu_stream_t stream);
+
 /* Human-readable name of a status code (static string). */
 const char *emu_status_string(emu_status_t s);
 

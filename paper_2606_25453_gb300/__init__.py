@@ -49,6 +49,7 @@ _SIGS = {
     "emu_destroy": (_i32, [_vp]),
     "emu_get_status": (_i32, [_vp, _vp]),
     "emu_status_string": (ctypes.c_char_p, [_i32]),
+    "emu_selftest_wait": (_i32, [_vp, _i64, _vp]),
     "emu_workspace_size": (_i32, [_i32, _i64, _i64, _i64, _i32, _i32, ctypes.POINTER(_sz)]),
     "emu_set_workspace": (_i32, [_vp, _vp, _sz]),
     "emu_dgemm": (_i32, [_vp, _i32, _i64, _i64, _i64, _dbl, _vp, _i64, _vp, _i64, _dbl, _vp, _i64, _i32,

@@ -4,6 +4,7 @@
 // the exported intermediate steps.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -218,6 +219,18 @@ __global__ void scale_z_kernel(double* C, int64_t ldc, int64_t m, int64_t n, dou
   p[1] = __fma_rn(br, ci, __dmul_rn(bi, cr));
 }
 
+// One warp waits on an mbarrier that nothing arrives on; the bounded wait
+// gives up after `limit` cycles and records the timeout.
+__global__ void selftest_wait_kernel(int* status, long long limit) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0, limit)) set_status(status, ST_TIMEOUT);
+}
+
 }  // namespace emu
 
 using namespace emu;
@@ -226,8 +239,19 @@ using namespace emu;
 static emu_status_t cuda_err(cudaError_t e) { return e == cudaSuccess ? EMU_OK : EMU_ERR_CUDA; }
 
 namespace emu {
+// EMU_FAULT=alloc: host-side fault injection for the allocation failure path.
+static bool fault_alloc() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = std::getenv("EMU_FAULT");
+    v = (e && std::strcmp(e, "alloc") == 0) ? 1 : 0;
+  }
+  return v == 1;
+}
+
 emu_status_t handle_workspace(emu_handle_s* h, size_t bytes, cudaStream_t st, uint8_t** out) {
   if (bytes == 0) bytes = 256;
+  if (!h->ws_user && bytes > h->ws_bytes && fault_alloc()) return EMU_ERR_ALLOC;
   if (h->ws_user) {
     if (bytes > h->ws_bytes) return EMU_ERR_ALLOC;
     *out = static_cast<uint8_t*>(h->ws);
@@ -302,6 +326,14 @@ emu_status_t emu_get_status(emu_handle_t h, emu_stream_t stream) {
   if (v & ST_TIMEOUT) return EMU_ERR_TIMEOUT;
   if (v & ST_NONFINITE) return EMU_ERR_NONFINITE;
   return EMU_OK;
+}
+
+emu_status_t emu_selftest_wait(emu_handle_t h, int64_t limit_cycles, emu_stream_t stream) {
+  if (!h) return EMU_ERR_INVALID_ARG;
+  cudaSetDevice(h->device);
+  long long lim = limit_cycles < 1000 ? 1000 : (limit_cycles > 2000000000LL ? 2000000000LL : limit_cycles);
+  selftest_wait_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(h->status, lim);
+  return cuda_err(cudaGetLastError());
 }
 
 const char* emu_status_string(emu_status_t s) {

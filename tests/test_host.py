@@ -1,0 +1,97 @@
+"""Host-side checks that need no GPU: the library loads and exports every
+entry point declared in include/emugemm.h, its method constants agree with
+the oracle's independent derivations, argument validation, and the
+multi-rank aggregation of bench.py over a 2-rank gloo process group."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "emugemm.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2606_25453_gb300 as emu
+    return emu
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(emu_[A-Za-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 35
+    missing = [n for n in names if not hasattr(lib.lib, n)]
+    assert not missing, missing
+
+
+def test_constants_match_oracle(lib, orc):
+    for p in range(1, 13):
+        assert lib.emu_chunk_len_I(p) == orc.chunk_len_I(p)
+    assert lib.moduli(20) == orc.moduli(20)
+    for nm in (1, 5, 12, 16, 20):
+        for k in (1, 100, 4096, 8192, 131071):
+            for c in (0, 1):
+                assert lib.emu_scale_bits_II(nm, k, c) == orc.scale_bits_II(nm, k, bool(c))
+
+
+def test_split_layout_sizes(lib):
+    assert lib.emu_split_rows(1) == 128 and lib.emu_split_rows(129) == 256
+    assert lib.emu_split_cols_I(33, 3) == 64 * 3
+    assert lib.emu_split_cols_II(129) == 256
+
+
+def test_argument_validation_without_gpu(lib):
+    sz = ctypes.c_size_t()
+    assert lib.emu_workspace_size(1, 100, 100, 100, 8, 0, ctypes.byref(sz)) == 0 and sz.value > 2 * 100 * 800
+    assert lib.emu_workspace_size(1, 10, 10, 10, 13, 0, ctypes.byref(sz)) == 2
+    assert lib.emu_workspace_size(2, 10, 10, 10, 21, 0, ctypes.byref(sz)) == 2
+    assert lib.emu_workspace_size(3, 10, 10, 10, 5, 0, ctypes.byref(sz)) == 1
+    assert lib.emu_dgemm(None, 0, 4, 4, 4, 1.0, None, 4, None, 4, 0.0, None, 4, 1, 3, None) == 1
+    assert lib.emu_status_string(6) == b"EMU_ERR_TIMEOUT"
+    # column-major leading dimensions must cover the rows
+    assert lib.emu_dgemm_noalloc(1, 8, 8, 8, 1.0, 1, 4, 1, 8, 0.0, 1, 8, 4, None, None) == 1
+
+
+def test_create_without_gpu_reports_cuda_error(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    assert lib.emu_create(ctypes.byref(h), 0) == 4  # EMU_ERR_CUDA
+
+
+def _rank_main(rank, world, port, out):
+    import torch.distributed as dist
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ms = 100.0 + 50.0 * rank  # the slower rank decides
+    mx = bench.max_over_ranks(ms, dist, "cpu")
+    val = bench.aggregate_tflops(world, 2.0 * 8192 ** 3, 5, mx)
+    out[rank] = (mx, val)
+    dist.destroy_process_group()
+
+
+def test_multirank_aggregation_gloo():
+    import socket
+    import torch.multiprocessing as mp
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.spawn(_rank_main, args=(2, port, out), nprocs=2, join=True)
+    assert out[0][0] == out[1][0] == 150.0
+    expect = 2 * 2.0 * 8192 ** 3 * 5 / 0.150 / 1e12
+    assert abs(out[0][1] - expect) < 1e-9 * expect
