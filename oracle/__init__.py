@@ -10,7 +10,9 @@ Conventions: matrices are numpy float64 (complex: complex128), row-major, and
 the functions take ``A`` (m x k) and ``B`` (k x n) as mathematical matrices;
 the wrapper passes ``B.T`` to the C code, whose column operand is stored as
 rows.  Paper references: Scheme I -- Sec. II-C-1, Eqs. (1)-(3), (11);
-Scheme II -- Sec. II-C-2, Eqs. (4)-(8); 3M -- Sec. IV-B, Eq. (16).
+Scheme II -- Sec. II-C-2, Eqs. (4)-(8); 3M -- Sec. IV-B, Eq. (16); Scheme I
+on FP8 (E4M3) slices -- the FP8 formulation Sec. VII names as future work,
+on the layout of Sec. III-A (reading R7 in emu_oracle.c).
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests
 (exact rationals / Python big integers / closed forms); none is unpinned.
@@ -71,6 +73,9 @@ def _load():
                 "orc_emu_II": (i32, [i64, i64, i64, i32, dbl, vp, vp, dbl, vp, vp, i32]),
                 "orc_modprod_Z3M": (None, [i64, i64, i64, i32, vp, vp, vp, vp, vp, vp, vp, vp]),
                 "orc_emu_Z3M": (i32, [i64, i64, i64, i32, dbl, dbl, vp, vp, dbl, dbl, vp]),
+                "orc_split_F8": (None, [i64, i64, vp, vp, i32, vp]),
+                "orc_chunk_len_F8": (i64, [i32]),
+                "orc_emu_F8": (i32, [i64, i64, i64, i32, dbl, vp, vp, dbl, vp, vp, i32]),
                 "orc_dd_gemm": (None, [i64, i64, i64, vp, vp, vp, vp]),
                 "orc_dd_zgemm": (None, [i64, i64, i64, vp, vp, vp, vp]),
             }
@@ -173,6 +178,40 @@ def emu_I(A, B, p: int, alpha: float = 1.0, beta: float = 0.0, C=None, out_f32: 
         Cf = np.zeros(1, dtype=np.float32)
     rc = _load().orc_emu_I(m, n, k, p, float(alpha), _p(A), _p(Bt), float(beta), _p(Cd), _p(Cf),
                            int(out_f32))
+    if rc:
+        raise ValueError("non-finite input")
+    return Cf if out_f32 else Cd
+
+
+# ---------------------------------------------------------------- Scheme I, FP8 slices
+def chunk_len_F8(p: int) -> int:
+    """K_c over which FP32 accumulation of E4M3 slice products stays exact."""
+    return int(_load().orc_chunk_len_F8(p))
+
+
+def split_F8_rows(X, p: int, E=None) -> np.ndarray:
+    """Balanced base-32 digits of the rows of X (reading R7): int16 [p, rows, k]."""
+    X = _f64(X)
+    if E is None:
+        E = row_exponents(X)
+    E = np.ascontiguousarray(E, dtype=np.int32)
+    D = np.zeros((p,) + X.shape, dtype=np.int16)
+    _load().orc_split_F8(X.shape[0], X.shape[1], _p(X), _p(E), p, _p(D))
+    return D
+
+
+def emu_F8(A, B, p: int, alpha: float = 1.0, beta: float = 0.0, C=None, out_f32: bool = False) -> np.ndarray:
+    """Scheme I with E4M3 slices (beta = 5): C = alpha*A@B + beta*C."""
+    A, Bt = _f64(A), _f64(np.asarray(B).T)
+    m, k = A.shape
+    n = Bt.shape[0]
+    if out_f32:
+        Cf = np.zeros((m, n), dtype=np.float32) if C is None else np.array(C, dtype=np.float32, order="C")
+        Cd = np.zeros(1)
+    else:
+        Cd = np.zeros((m, n)) if C is None else np.array(C, dtype=np.float64, order="C")
+        Cf = np.zeros(1, dtype=np.float32)
+    rc = _load().orc_emu_F8(m, n, k, p, float(alpha), _p(A), _p(Bt), float(beta), _p(Cd), _p(Cf), int(out_f32))
     if rc:
         raise ValueError("non-finite input")
     return Cf if out_f32 else Cd

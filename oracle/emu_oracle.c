@@ -51,6 +51,14 @@
  *       binary64 (nearest, ties to even), then scaled by a power of two.
  *   R6  BLAS update: beta == 0 -> C = alpha * r (C not read), else
  *       C = fma(alpha, r, beta * C).
+ *   R7  Scheme I on FP8 (E4M3) slices -- the FP8 formulation the paper names
+ *       as future work (Sec. VII) on the same interleaved layout (Sec. III-A
+ *       notes the layout is agnostic to the slice type): beta = 5,
+ *       x = trunc(a * 2^(5p-1-E)), balanced base-32 digits (d_t in [-16, 15]
+ *       for t >= 1, d_0 in [-16, 16]), all exactly representable in E4M3, so
+ *       every slice product is exact and FP32 sums of them are exact while
+ *       |sum| <= 2^24.  Result: RN(S) * 2^(E_i + F_j - 8 - 5(p-1)) with
+ *       S = sum_s 32^(p-1-s) C_s exact.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -750,4 +758,77 @@ void orc_dd_zgemm(int64_t m, int64_t n, int64_t k, const double *A, const double
       lo[2 * (i * n + j) + 1] = c - (t - s);
       hi[2 * (i * n + j) + 1] = t;
     }
+}
+
+/* ------------------------------------------------------------------ */
+/* Scheme I on FP8 (E4M3) slices (reading R7)                          */
+/* ------------------------------------------------------------------ */
+
+/* Balanced base-32 digits of x = trunc(a * 2^(5p-1-E)): from the lowest
+ * digit up, d = x mod 32 taken in [-16, 15], x = (x - d) / 32; the remaining
+ * x is the leading digit.  D: p x rows x k int16. */
+void orc_split_F8(int64_t rows, int64_t k, const double *X, const int32_t *E, int p, int16_t *D) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < rows; ++i)
+    for (int64_t h = 0; h < k; ++h) {
+      i128 x = scaled_trunc(X[i * k + h], 5 * p - 1 - E[i]);
+      for (int t = p - 1; t >= 1; --t) {
+        int r = (int)(x % 32);
+        if (r < 0) r += 32;
+        if (r >= 16) r -= 32;
+        D[((int64_t)t * rows + i) * k + h] = (int16_t)r;
+        x = (x - r) / 32;
+      }
+      D[i * k + h] = (int16_t)x;
+    }
+}
+
+/* K_c for FP32-exact accumulation: every |d_i d_j| <= 256, so |C_s| grows by
+ * at most (s+1)*256 per unit of K; largest multiple of 256 keeping all
+ * partial sums within 2^24. */
+int64_t orc_chunk_len_F8(int p) {
+  int64_t worst = (int64_t)p * 256;
+  int64_t lim = ((int64_t)1 << 24) / worst;
+  return (lim / 256) * 256;
+}
+
+/* Full emulated product with E4M3 slices (reading R7), as orc_emu_I. */
+int orc_emu_F8(int64_t m, int64_t n, int64_t k, int p, double alpha, const double *A, const double *Bt,
+               double beta, double *C, float *Cf, int out_f32) {
+  int32_t *E = malloc(sizeof(int32_t) * (m > 0 ? m : 1));
+  int32_t *F = malloc(sizeof(int32_t) * (n > 0 ? n : 1));
+  int16_t *DA = malloc(sizeof(int16_t) * (size_t)(p * m * k > 0 ? p * m * k : 1));
+  int16_t *DB = malloc(sizeof(int16_t) * (size_t)(p * n * k > 0 ? p * n * k : 1));
+  int rc = 0;
+  if (orc_row_exponents(m, k, A, E) || orc_row_exponents(n, k, Bt, F)) {
+    rc = -1;
+    goto out;
+  }
+  orc_split_F8(m, k, A, E, p, DA);
+  orc_split_F8(n, k, Bt, F, p, DB);
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int64_t i = 0; i < m; ++i)
+    for (int64_t j = 0; j < n; ++j) {
+      i128 S = 0;
+      for (int s = 0; s < p; ++s) {
+        int64_t Cs = 0;
+        for (int t = 0; t <= s; ++t) {
+          const int16_t *a = DA + ((int64_t)t * m + i) * k;
+          const int16_t *b = DB + ((int64_t)(s - t) * n + j) * k;
+          for (int64_t h = 0; h < k; ++h) Cs += (int64_t)a[h] * (int64_t)b[h];
+        }
+        S += (i128)Cs << (5 * (p - 1 - s));
+      }
+      double r = ldexp(i128_to_double(S), E[i] + F[j] - 8 - 5 * (p - 1));
+      if (out_f32)
+        Cf[i * n + j] = (float)blas_update(alpha, r, beta, beta == 0.0 ? 0.0 : (double)Cf[i * n + j]);
+      else
+        C[i * n + j] = blas_update(alpha, r, beta, beta == 0.0 ? 0.0 : C[i * n + j]);
+    }
+out:
+  free(E);
+  free(F);
+  free(DA);
+  free(DB);
+  return rc;
 }
