@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--p", type=int, default=8)
     ap.add_argument("--phi", type=float, default=0.5)
+    ap.add_argument("--scheme", default="I", choices=["I", "I_F8", "II"],
+                    help="I: INT8 slices; I_F8: E4M3 slices on the FP8 tensor path; II: CRT (p = moduli)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-rows", type=int, default=16, help="rows of C in the CPU oracle sample")
     ap.add_argument("--no-extras", action="store_true", help="skip cuBLAS / accuracy / CPU legs")
@@ -56,11 +58,20 @@ def parse():
     return ap.parse_args()
 
 
+SCHEME_NAME = {"I": "Scheme I", "I_F8": "Scheme I on E4M3 slices", "II": "Scheme II"}
+
+
+def ops_per_mnk(scheme, p):
+    """Tensor ops per M*N*K of one product: the triangle p(p+1) or 2 N_m."""
+    return 2 * p if scheme == "II" else p * (p + 1)
+
+
 def config(args, world):
-    return {"workload": "Scheme I emulated DGEMM M=N=K=%d phi=%g p=%d (Eq. 19 generator, seed %d)"
-                        % (args.n, args.phi, args.p, args.seed),
+    return {"workload": "%s emulated DGEMM M=N=K=%d phi=%g %s=%d (Eq. 19 generator, seed %d)"
+                        % (SCHEME_NAME[args.scheme], args.n, args.phi, "N" if args.scheme == "II" else "p", args.p,
+                           args.seed),
             "m": args.n, "n": args.n, "k": args.n, "p": args.p, "phi": args.phi, "layout": "row-major",
-            "scheme": "I", "l2": "inputs larger than L2 (2 x %d MiB), no flush" % (8 * args.n * args.n >> 20),
+            "scheme": args.scheme, "l2": "inputs larger than L2 (2 x %d MiB), no flush" % (8 * args.n * args.n >> 20),
             "parallelism": "replicas" if world == 1 else "dp%d independent products" % world}
 
 
@@ -222,10 +233,11 @@ def run_ours(args, rank, world, local_rank):
     Cd = torch.empty((n, n), dtype=torch.float64, device=dev)
     h = emu.Handle(local_rank)
     stream = torch.cuda.current_stream(dev)
+    scheme_code = {"I": emu.EMU_SCHEME_I, "I_F8": emu.EMU_SCHEME_I_F8, "II": emu.EMU_SCHEME_II}[args.scheme]
 
     def step():
         emu.check(emu.emu_dgemm(h.h, emu.EMU_ROW_MAJOR, n, n, n, 1.0, Ad.data_ptr(), n, Bd.data_ptr(), n, 0.0,
-                                Cd.data_ptr(), n, emu.EMU_SCHEME_I, p, stream.cuda_stream), "emu_dgemm")
+                                Cd.data_ptr(), n, scheme_code, p, stream.cuda_stream), "emu_dgemm")
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -255,7 +267,7 @@ def run_ours(args, rank, world, local_rank):
     ms_step = ms / args.steps
     flops = 2.0 * n * n * n
     value = aggregate_tflops(world, flops, args.steps, ms)
-    int8_ops = float(p * (p + 1)) * n * n * n
+    int8_ops = float(ops_per_mnk(args.scheme, p)) * n * n * n
     status = h.status()
 
     # ---------------- end to end through host buffers (pinned), copies timed
@@ -331,19 +343,27 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0:
         gemm_ms = tr["ms_gemm"] / max(tr["gemm_launches"], 1)
         achieved = int8_ops / (gemm_ms * 1e-3) / 1e12
-        peak = int8_peak
-        traffic = load_traffic(p, n)
+        peak, peak_src = int8_peak, "measured live: cuBLASLt INT8 GEMM 8192^3 on this GPU"
+        if args.scheme == "I_F8":
+            bf16 = measured_peaks().get("bf16_tflops")
+            peak = 2.0 * bf16 if bf16 else 2.0 * 1900.0
+            peak_src = ("FP8 dense peak = measured bf16 %s x nominal FP8/bf16 ratio 2 (4.5 / 2.25 PFLOP/s)"
+                        % ("(MEASURED_PEAKS.json)" if bf16 else "(fallback 1.9 PFLOP/s)"))
+        traffic = load_traffic(p, n) if args.scheme == "I" else None
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int8->int32 (f64 in/out)", "data": "synthetic",
                 "config": config(args, world),
                 "int8_tops": int8_ops * args.steps * world / (ms * 1e-3) / 1e12,
-                "int8_frac_of_peak": (int8_ops * args.steps / (ms * 1e-3) / 1e12 / peak) if peak else None,
-                "roofline": {"bound": "tensor", "kernel": "gemm_I_kernel<%d>" % p, "achieved": achieved,
+                "int8_frac_of_peak": (int8_ops * args.steps / (ms * 1e-3) / 1e12 / int8_peak) if int8_peak else None,
+                "roofline": {"bound": "tensor",
+                             "kernel": ("gemm_II_kernel" if args.scheme == "II" else
+                                        "gemm_I_kernel<%d, F8=%d>" % (p, args.scheme == "I_F8")),
+                             "achieved": achieved,
                              "peak": peak, "unit": UNIT, "frac": (achieved / peak) if peak else None,
                              "traffic": traffic,
                              "ops": "INT8 ops p(p+1) M N K (multiply+add = 2)",
-                             "peak_source": "measured live: cuBLASLt INT8 GEMM 8192^3 on this GPU"},
+                             "peak_source": peak_src},
                 "phase_ms_per_step": {k2: tr[k2] / args.steps for k2 in ("ms_scan", "ms_split", "ms_gemm")},
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * n * n,
                         "d2h_bytes_per_step": 8 * n * n},

@@ -62,7 +62,12 @@ typedef void *emu_stream_t; /* a cudaStream_t */
 
 typedef enum { EMU_ROW_MAJOR = 0, EMU_COL_MAJOR = 1 } emu_layout_t;
 
-typedef enum { EMU_SCHEME_I = 1, EMU_SCHEME_II = 2 } emu_scheme_t;
+/* EMU_SCHEME_I_F8: Scheme I on the FP8 tensor cores -- the paper's
+ * interleaved layout and fused triangular kernel with E4M3 slices (beta = 5,
+ * balanced base-32 digits, all products exact, FP32 accumulation kept exact
+ * by draining every K_c), the FP8 formulation Sec. VII names as future work.
+ * p_or_nm is the number of E4M3 slices (5 bits each: p = 11 gives 54 bits). */
+typedef enum { EMU_SCHEME_I = 1, EMU_SCHEME_II = 2, EMU_SCHEME_I_F8 = 3 } emu_scheme_t;
 
 typedef enum {
   EMU_OK = 0,
@@ -138,9 +143,10 @@ emu_status_t emu_trace_read(emu_handle_t h, double *ms_host, int64_t *gemm_launc
 /* Emulated GEMM                                                       */
 /* ------------------------------------------------------------------ */
 
-/* FP64 C = alpha*A*B + beta*C.  scheme = EMU_SCHEME_I with p_or_nm = p in
- * [EMU_P_MIN, EMU_P_MAX] slices, or EMU_SCHEME_II with p_or_nm = N in
- * [EMU_NM_MIN, EMU_NM_MAX] moduli (k <= EMU_K_MAX_II).  Sec. II-C. */
+/* FP64 C = alpha*A*B + beta*C.  scheme = EMU_SCHEME_I or EMU_SCHEME_I_F8
+ * with p_or_nm = p in [EMU_P_MIN, EMU_P_MAX] slices, or EMU_SCHEME_II with
+ * p_or_nm = N in [EMU_NM_MIN, EMU_NM_MAX] moduli (k <= EMU_K_MAX_II).
+ * Sec. II-C. */
 emu_status_t emu_dgemm(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k,
                        double alpha, const double *A, int64_t lda, const double *B, int64_t ldb,
                        double beta, double *C, int64_t ldc, emu_scheme_t scheme, int p_or_nm,
@@ -221,6 +227,12 @@ emu_status_t emu_split_I(emu_handle_t h, emu_layout_t layout, int operand, int64
                          const double *X, int64_t ldx, int p, int8_t *hat_dev, int32_t *exp_dev,
                          emu_stream_t stream);
 
+/* As emu_split_I for EMU_SCHEME_I_F8: the same interleaved layout holding
+ * E4M3 bytes of the balanced base-32 digits of x = trunc(x * 2^(5p-1-E)). */
+emu_status_t emu_split_F8(emu_handle_t h, emu_layout_t layout, int operand, int64_t rows, int64_t k,
+                          const double *X, int64_t ldx, int p, int8_t *hat_dev, int32_t *exp_dev,
+                          emu_stream_t stream);
+
 /* Scheme II split of one operand (Eq. 5): residues of trunc(x * 2^(b - E))
  * for the first nm moduli, b = emu_scale_bits_II(nm, k_total, 0).  Writes
  * nm planes to res_dev (nm * emu_split_rows(rows) * emu_split_cols_II(k)
@@ -240,6 +252,13 @@ emu_status_t emu_partials_I(emu_handle_t h, emu_layout_t layout, int64_t m, int6
                             const double *A, int64_t lda, const double *B, int64_t ldb, int p,
                             int32_t *Cs_dev, emu_stream_t stream);
 
+/* As emu_partials_I for EMU_SCHEME_I_F8: the FP32 accumulators of the E4M3
+ * triangle converted to int32 (exact), p row-major m x n matrices;
+ * k <= emu_chunk_len_F8(p). */
+emu_status_t emu_partials_F8(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k,
+                             const double *A, int64_t lda, const double *B, int64_t ldb, int p,
+                             int32_t *Cs_dev, emu_stream_t stream);
+
 /* Paper-design Scheme II output (Sec. IV-A): per-modulus INT8 residues
  * C'_l = (A'_l B'_l) mod m_l in [0, m_l), as nm row-major m x n uint8
  * matrices (R_dev[(l*m + i)*n + j]).  The CRT is left to the caller. */
@@ -249,6 +268,7 @@ emu_status_t emu_residues_II(emu_handle_t h, emu_layout_t layout, int64_t m, int
 
 /* Method constants computed by the library's host code. */
 int64_t emu_chunk_len_I(int p);              /* K_c: INT32-exact K range of Eq. (2) */
+int64_t emu_chunk_len_F8(int p);             /* K_c: FP32-exact K range, E4M3 slices */
 int emu_moduli(int nm, int32_t *mods_host); /* first nm moduli; returns count      */
 int emu_scale_bits_II(int nm, int64_t k, int is_complex); /* Scheme II exponent b    */
 

@@ -200,6 +200,20 @@ def split_F8_rows(X, p: int, E=None) -> np.ndarray:
     return D
 
 
+def partials_F8(A, B, p: int, kc: int | None = None) -> np.ndarray:
+    """Exact chunked triangle partials of the E4M3 digits: int64 [nchunks, p, m, n]."""
+    A, Bt = _f64(A), _f64(np.asarray(B).T)
+    m, k = A.shape
+    n = Bt.shape[0]
+    kc = chunk_len_F8(p) if kc is None else kc
+    DA = split_F8_rows(A, p)
+    DB = split_F8_rows(Bt, p)
+    nch = -(-k // kc) if k else 0
+    out = np.zeros((nch, p, m, n), dtype=np.int64)
+    _load().orc_partials_I(m, n, k, p, kc, _p(DA), _p(DB), _p(out))
+    return out
+
+
 def emu_F8(A, B, p: int, alpha: float = 1.0, beta: float = 0.0, C=None, out_f32: bool = False) -> np.ndarray:
     """Scheme I with E4M3 slices (beta = 5): C = alpha*A@B + beta*C."""
     A, Bt = _f64(A), _f64(np.asarray(B).T)

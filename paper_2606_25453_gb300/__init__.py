@@ -16,7 +16,7 @@ from . import build as _build_mod
 _LIB_PATH = _build_mod.LIB
 
 EMU_ROW_MAJOR, EMU_COL_MAJOR = 0, 1
-EMU_SCHEME_I, EMU_SCHEME_II = 1, 2
+EMU_SCHEME_I, EMU_SCHEME_II, EMU_SCHEME_I_F8 = 1, 2, 3
 STATUS = {0: "EMU_OK", 1: "EMU_ERR_INVALID_ARG", 2: "EMU_ERR_UNSUPPORTED", 3: "EMU_ERR_NONFINITE",
           4: "EMU_ERR_CUDA", 5: "EMU_ERR_ALLOC", 6: "EMU_ERR_TIMEOUT", 7: "EMU_ERR_TOL_NOT_MET"}
 EMU_P_MAX, EMU_NM_MAX, EMU_K_MAX_II = 12, 20, 131071
@@ -62,10 +62,13 @@ _SIGS = {
     "emu_split_cols_I": (_i64, [_i64, _i32]),
     "emu_split_cols_II": (_i64, [_i64]),
     "emu_split_I": (_i32, [_vp, _i32, _i32, _i64, _i64, _vp, _i64, _i32, _vp, _vp, _vp]),
+    "emu_split_F8": (_i32, [_vp, _i32, _i32, _i64, _i64, _vp, _i64, _i32, _vp, _vp, _vp]),
     "emu_split_II": (_i32, [_vp, _i32, _i32, _i64, _i64, _i64, _vp, _i64, _i32, _vp, _vp, _vp]),
     "emu_partials_I": (_i32, [_vp, _i32, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _i32, _vp, _vp]),
     "emu_residues_II": (_i32, [_vp, _i32, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _i32, _vp, _vp]),
     "emu_chunk_len_I": (_i64, [_i32]),
+    "emu_chunk_len_F8": (_i64, [_i32]),
+    "emu_partials_F8": (_i32, [_vp, _i32, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _i32, _vp, _vp]),
     "emu_moduli": (_i32, [_i32, _vp]),
     "emu_scale_bits_II": (_i32, [_i32, _i64, _i32]),
     "emu_dgemm_noalloc": (_i32, [_i32, _i64, _i64, _i64, _dbl, _vp, _i64, _vp, _i64, _dbl, _vp, _i64, _i32, _vp,
@@ -158,7 +161,9 @@ def _scheme(s) -> int:
         return EMU_SCHEME_I
     if s in (2, "II", "ii", EMU_SCHEME_II):
         return EMU_SCHEME_II
-    raise ValueError("scheme must be 'I' or 'II'")
+    if s in (3, "I_F8", "F8", "f8", EMU_SCHEME_I_F8):
+        return EMU_SCHEME_I_F8
+    raise ValueError("scheme must be 'I', 'II' or 'I_F8'")
 
 
 def _layout_of(A, B, C):
@@ -233,9 +238,10 @@ def moduli(nm: int) -> list[int]:
     return [int(out[i]) for i in range(got)]
 
 
-def split_I(X, p: int, operand: int = 0, handle=None, stream=None):
+def split_I(X, p: int, operand: int = 0, handle=None, stream=None, f8: bool = False):
     """Scheme I split of A's rows (operand 0, X is m x k) or B's columns
-    (operand 1, X is k x n); returns (hat int8 tensor, exponents int32)."""
+    (operand 1, X is k x n); returns (hat int8 tensor, exponents int32).
+    f8=True: E4M3 slices (emu_split_F8)."""
     import torch
     if operand == 0:
         rows, k = X.shape
@@ -246,8 +252,9 @@ def split_I(X, p: int, operand: int = 0, handle=None, stream=None):
     hat = torch.empty((emu_split_rows(rows), emu_split_cols_I(k, p)), dtype=torch.int8, device=X.device)
     E = torch.empty((max(rows, 1),), dtype=torch.int32, device=X.device)
     h = handle or default_handle(X.device.index or 0)
-    check(emu_split_I(h.h, layout, operand, rows, k, _ptr(X), max(ldx, 1), p, _ptr(hat), _ptr(E),
-                      _stream_ptr(stream)), "emu_split_I")
+    fn = emu_split_F8 if f8 else emu_split_I
+    check(fn(h.h, layout, operand, rows, k, _ptr(X), max(ldx, 1), p, _ptr(hat), _ptr(E), _stream_ptr(stream)),
+          fn.__name__)
     return hat, E[:rows]
 
 
@@ -268,15 +275,17 @@ def split_II(X, nm: int, k_total: int | None = None, operand: int = 0, handle=No
     return res, E[:rows]
 
 
-def partials_I(A, B, p: int, handle=None, stream=None):
-    """Unfused Scheme I: int32 tensor [p, m, n] of the exact partials C_s."""
+def partials_I(A, B, p: int, handle=None, stream=None, f8: bool = False):
+    """Unfused Scheme I: int32 tensor [p, m, n] of the exact partials C_s
+    (f8=True: the E4M3 engine's FP32 accumulators, converted exactly)."""
     import torch
     m, k = A.shape
     n = B.shape[1]
     out = torch.empty((p, m, n), dtype=torch.int32, device=A.device)
     h = handle or default_handle(A.device.index or 0)
-    check(emu_partials_I(h.h, EMU_ROW_MAJOR, m, n, k, _ptr(A), A.stride(0), _ptr(B), B.stride(0), p,
-                         _ptr(out), _stream_ptr(stream)), "emu_partials_I")
+    fn = emu_partials_F8 if f8 else emu_partials_I
+    check(fn(h.h, EMU_ROW_MAJOR, m, n, k, _ptr(A), A.stride(0), _ptr(B), B.stride(0), p, _ptr(out),
+             _stream_ptr(stream)), fn.__name__)
     return out
 
 

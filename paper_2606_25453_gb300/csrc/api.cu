@@ -2,6 +2,7 @@
 // method constants, tensor maps, and the launch sequences of the hot path
 // (scan -> split -> fused GEMM) for emu_dgemm / emu_sgemm / emu_zgemm and
 // the exported intermediate steps.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -60,6 +61,16 @@ int64_t host_chunk_len_I(int p) {
     worst = -lo > worst ? -lo : worst;
   }
   int64_t lim = 2147483647LL / worst;
+  return lim - lim % 256;
+}
+
+// K_c for the E4M3 engine: every |d_i d_j| <= 16 * 16, so C_s grows by at
+// most (s+1) * 256 per unit of K; largest multiple of 256 keeping every FP32
+// partial sum within 2^24 (where FP32 holds all integers exactly).
+int64_t host_chunk_len_F8(int p) {
+  int64_t worst = 0;
+  for (int s = 0; s < p; ++s) worst = std::max<int64_t>(worst, static_cast<int64_t>(s + 1) * 16 * 16);
+  int64_t lim = (int64_t{1} << 24) / worst;
   return lim - lim % 256;
 }
 
@@ -354,6 +365,7 @@ int64_t emu_split_rows(int64_t rows) { return split_rows(rows); }
 int64_t emu_split_cols_I(int64_t k, int p) { return split_cols_I(k, p); }
 int64_t emu_split_cols_II(int64_t k) { return split_cols_II(k); }
 int64_t emu_chunk_len_I(int p) { return p >= 1 ? host_chunk_len_I(p) : 0; }
+int64_t emu_chunk_len_F8(int p) { return p >= 1 ? host_chunk_len_F8(p) : 0; }
 int emu_moduli(int nm, int32_t* mods) { return mods ? host_moduli(nm, mods) : 0; }
 int emu_scale_bits_II(int nm, int64_t k, int is_complex) { return host_scale_bits_II(nm, k, is_complex); }
 
@@ -447,7 +459,7 @@ bool check_lds(emu_layout_t layout, int64_t m, int64_t n, int64_t k, int64_t lda
 template <typename T>
 emu_status_t run_scheme_I(emu_handle_s* h, const View& v, int64_t k, int p, double alpha, double beta,
                           void* C, int64_t ldc, int out_mode, int32_t* partials, cudaStream_t st,
-                          uint8_t* ws_override) {
+                          uint8_t* ws_override, bool f8) {
   Plan pl = plan_I(v.M, v.N, k, p);
   uint8_t* ws = ws_override;
   if (!ws) {
@@ -467,8 +479,8 @@ emu_status_t run_scheme_I(emu_handle_s* h, const View& v, int64_t k, int p, doub
   launch_scan<T>(B, v.ldB, v.b_kcontig, v.N, k, 1, maxB, h->status, st);
   trace_end(h, PH_SCAN, st, 2);
   trace_begin(h, PH_SPLIT, st);
-  launch_split_I<T>(A, v.ldA, v.a_kcontig, v.M, k, p, maxA, hatA, EA, st);
-  launch_split_I<T>(B, v.ldB, v.b_kcontig, v.N, k, p, maxB, hatB, FB, st);
+  launch_split_I<T>(A, v.ldA, v.a_kcontig, v.M, k, p, maxA, hatA, EA, st, f8);
+  launch_split_I<T>(B, v.ldB, v.b_kcontig, v.N, k, p, maxB, hatB, FB, st, f8);
   trace_end(h, PH_SPLIT, st, 2);
   CUtensorMap ta, tb;
   if (!make_tmap_i8(&ta, hatA, static_cast<uint64_t>(pl.cols), static_cast<uint64_t>(pl.rows_a), 64) ||
@@ -480,7 +492,7 @@ emu_status_t run_scheme_I(emu_handle_s* h, const View& v, int64_t k, int p, doub
   a.M = static_cast<int>(v.M);
   a.N = static_cast<int>(v.N);
   a.nk32 = static_cast<int>((k + 31) / 32);
-  a.kc32 = static_cast<int>(host_chunk_len_I(p) / 32);
+  a.kc32 = static_cast<int>((f8 ? host_chunk_len_F8(p) : host_chunk_len_I(p)) / 32);
   a.EA = EA;
   a.FB = FB;
   a.alpha = alpha;
@@ -491,14 +503,14 @@ emu_status_t run_scheme_I(emu_handle_s* h, const View& v, int64_t k, int p, doub
   a.status = h->status;
   a.num_sms = h->num_sms;
   trace_begin(h, PH_GEMM, st);
-  cudaError_t e = launch_gemm_I(p, out_mode, a, st);
+  cudaError_t e = launch_gemm_I(p, out_mode, a, st, f8);
   trace_end(h, PH_GEMM, st, 1);
   return cuda_err(e);
 }
 template emu_status_t run_scheme_I<double>(emu_handle_s*, const View&, int64_t, int, double, double,
-                                           void*, int64_t, int, int32_t*, cudaStream_t, uint8_t*);
+                                           void*, int64_t, int, int32_t*, cudaStream_t, uint8_t*, bool);
 template emu_status_t run_scheme_I<float>(emu_handle_s*, const View&, int64_t, int, double, double,
-                                          void*, int64_t, int, int32_t*, cudaStream_t, uint8_t*);
+                                          void*, int64_t, int, int32_t*, cudaStream_t, uint8_t*, bool);
 
 template <typename T>
 emu_status_t run_scheme_II(emu_handle_s* h, const View& v, int64_t k, int nm, int cw, double ar,
@@ -578,7 +590,7 @@ extern "C" {
 emu_status_t emu_workspace_size(emu_scheme_t scheme, int64_t m, int64_t n, int64_t k, int p_or_nm,
                                 int is_complex, size_t* bytes) {
   if (!bytes || m < 0 || n < 0 || k < 0) return EMU_ERR_INVALID_ARG;
-  if (scheme == EMU_SCHEME_I) {
+  if (scheme == EMU_SCHEME_I || scheme == EMU_SCHEME_I_F8) {
     if (p_or_nm < EMU_P_MIN || p_or_nm > EMU_P_MAX || is_complex) return EMU_ERR_UNSUPPORTED;
     *bytes = plan_I(m, n, k, p_or_nm).bytes;
     return EMU_OK;
@@ -603,7 +615,7 @@ static emu_status_t gemm_common(emu_handle_t h, emu_layout_t layout, int64_t m, 
   if (!check_lds(layout, m, n, k, lda, ldb, ldc)) return EMU_ERR_INVALID_ARG;
   if (m > 0 && n > 0 && !C) return EMU_ERR_INVALID_ARG;
   if (m > 0 && n > 0 && k > 0 && (!A || !B)) return EMU_ERR_INVALID_ARG;
-  if (scheme == EMU_SCHEME_I) {
+  if (scheme == EMU_SCHEME_I || scheme == EMU_SCHEME_I_F8) {
     if (p_or_nm < EMU_P_MIN || p_or_nm > EMU_P_MAX) return EMU_ERR_UNSUPPORTED;
   } else if (scheme == EMU_SCHEME_II) {
     if (p_or_nm < EMU_NM_MIN || p_or_nm > EMU_NM_MAX) return EMU_ERR_UNSUPPORTED;
@@ -631,9 +643,9 @@ static emu_status_t real_gemm(emu_handle_t h, emu_layout_t layout, int64_t m, in
     return cuda_err(cudaGetLastError());
   }
   const int out = sizeof(T) == 8 ? 0 : 1;
-  if (scheme == EMU_SCHEME_I)
+  if (scheme == EMU_SCHEME_I || scheme == EMU_SCHEME_I_F8)
     return run_scheme_I<T>(h, v, k, p_or_nm, alpha, beta, C, ldc, out == 0 ? OUT_F64 : OUT_F32, nullptr,
-                           st, nullptr);
+                           st, nullptr, scheme == EMU_SCHEME_I_F8);
   return run_scheme_II<T>(h, v, k, p_or_nm, 1, alpha, 0.0, beta, 0.0, C, ldc, out == 0 ? II_F64 : II_F32,
                           nullptr, st);
 }
@@ -674,8 +686,25 @@ emu_status_t emu_zgemm(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n
 }
 
 // ---------------------------------------------------------------- steps
+static emu_status_t split_slices(emu_handle_t h, emu_layout_t layout, int operand, int64_t rows, int64_t k,
+                                 const double* X, int64_t ldx, int p, int8_t* hat, int32_t* E, emu_stream_t stream,
+                                 bool f8);
+
 emu_status_t emu_split_I(emu_handle_t h, emu_layout_t layout, int operand, int64_t rows, int64_t k,
                          const double* X, int64_t ldx, int p, int8_t* hat, int32_t* E, emu_stream_t stream) {
+  return split_slices(h, layout, operand, rows, k, X, ldx, p, hat, E, stream, false);
+}
+
+emu_status_t emu_split_F8(emu_handle_t h, emu_layout_t layout, int operand, int64_t rows, int64_t k,
+                          const double* X, int64_t ldx, int p, int8_t* hat, int32_t* E, emu_stream_t stream) {
+  return split_slices(h, layout, operand, rows, k, X, ldx, p, hat, E, stream, true);
+}
+
+}  // extern "C"
+
+static emu_status_t split_slices(emu_handle_t h, emu_layout_t layout, int operand, int64_t rows, int64_t k,
+                                 const double* X, int64_t ldx, int p, int8_t* hat, int32_t* E, emu_stream_t stream,
+                                 bool f8) {
   if (!h || !hat || !E || rows < 0 || k < 0 || (operand != 0 && operand != 1)) return EMU_ERR_INVALID_ARG;
   if (layout != EMU_ROW_MAJOR && layout != EMU_COL_MAJOR) return EMU_ERR_INVALID_ARG;
   if (p < EMU_P_MIN || p > EMU_P_MAX) return EMU_ERR_UNSUPPORTED;
@@ -690,9 +719,11 @@ emu_status_t emu_split_I(emu_handle_t h, emu_layout_t layout, int operand, int64
   if (s != EMU_OK) return s;
   auto* mx = reinterpret_cast<unsigned long long*>(ws);
   launch_scan<double>(X, ldx, kcontig, rows, k, 1, mx, h->status, st);
-  launch_split_I<double>(X, ldx, kcontig, rows, k, p, mx, hat, E, st);
+  launch_split_I<double>(X, ldx, kcontig, rows, k, p, mx, hat, E, st, f8);
   return cuda_err(cudaGetLastError());
 }
+
+extern "C" {
 
 emu_status_t emu_split_II(emu_handle_t h, emu_layout_t layout, int operand, int64_t rows, int64_t k,
                           int64_t k_total, const double* X, int64_t ldx, int nm, int8_t* res, int32_t* E,
@@ -730,6 +761,22 @@ emu_status_t emu_partials_I(emu_handle_t h, emu_layout_t layout, int64_t m, int6
   if (v.M == 0 || v.N == 0) return EMU_OK;
   if (k == 0) return cuda_err(cudaMemsetAsync(Cs, 0, sizeof(int32_t) * p * v.M * v.N, st));
   return run_scheme_I<double>(h, v, k, p, 1.0, 0.0, nullptr, 0, OUT_PARTIALS, Cs, st, nullptr);
+}
+
+emu_status_t emu_partials_F8(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k,
+                             const double* A, int64_t lda, const double* B, int64_t ldb, int p, int32_t* Cs,
+                             emu_stream_t stream) {
+  emu_status_t s = gemm_common(h, layout, m, n, k, A, lda, B, ldb, Cs, layout == EMU_ROW_MAJOR ? n : m,
+                               EMU_SCHEME_I_F8, p);
+  if (s != EMU_OK) return s;
+  if (k > host_chunk_len_F8(p)) return EMU_ERR_UNSUPPORTED;
+  if (layout != EMU_ROW_MAJOR) return EMU_ERR_UNSUPPORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  View v;
+  normalize(layout, m, n, A, lda, B, ldb, &v);
+  if (v.M == 0 || v.N == 0) return EMU_OK;
+  if (k == 0) return cuda_err(cudaMemsetAsync(Cs, 0, sizeof(int32_t) * p * v.M * v.N, st));
+  return run_scheme_I<double>(h, v, k, p, 1.0, 0.0, nullptr, 0, OUT_PARTIALS, Cs, st, nullptr, true);
 }
 
 emu_status_t emu_residues_II(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k,

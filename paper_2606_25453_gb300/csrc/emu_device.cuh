@@ -110,6 +110,26 @@ EMU_MMA_I8(false, true, "u8", "s8")
 EMU_MMA_I8(false, false, "u8", "u8")
 #undef EMU_MMA_I8
 
+// D = A*B + D, m16n8k32, E4M3 x E4M3 -> FP32.  The library only feeds it
+// integers |d| <= 16 and keeps every partial sum within 2^24, where FP32
+// accumulation is exact.
+__device__ __forceinline__ void mma_e4m3(float* d, const uint32_t* a, const uint32_t* b) {
+  asm volatile("mma.sync.aligned.m16n8k32.row.col.f32.e4m3.e4m3.f32"
+               " {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+               : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+               : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// E4M3 byte of an integer v with |v| <= 16 (exact): sign, exponent
+// floor(log2 |v|) + 7, three mantissa bits.
+__device__ __forceinline__ uint32_t e4m3_of_int(int v) {
+  uint32_t a = static_cast<uint32_t>(v < 0 ? -v : v);
+  if (a == 0) return 0u;
+  int e = 31 - __clz(static_cast<int>(a));
+  uint32_t mant = ((a << 3) >> e) & 7u;
+  return (v < 0 ? 0x80u : 0u) | (static_cast<uint32_t>(e + 7) << 3) | mant;
+}
+
 // Byte offset inside a [rows][32 B] block written by TMA with 32-byte
 // swizzling: the 16-byte half `chunk` of row `row` is stored at
 // chunk ^ ((row >> 2) & 1).

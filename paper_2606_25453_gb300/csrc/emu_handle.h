@@ -55,6 +55,6 @@ void handle_release_extras(emu_handle_s* h);
 template <typename T>
 emu_status_t run_scheme_I(emu_handle_s* h, const View& v, int64_t k, int p, double alpha, double beta,
                           void* C, int64_t ldc, int out_mode, int32_t* partials, cudaStream_t st,
-                          uint8_t* ws_override);
+                          uint8_t* ws_override, bool f8 = false);
 
 }  // namespace emu

@@ -38,6 +38,7 @@ struct CrtTables {
 // Host-side method constants (api.cu).
 int host_moduli(int nm, int32_t* out);
 int64_t host_chunk_len_I(int p);
+int64_t host_chunk_len_F8(int p);
 int host_scale_bits_II(int nm, int64_t k, int is_complex);
 void host_mod_tables(int nm, ModTables* t);
 void host_crt_tables(int nm, CrtTables* t);
@@ -48,7 +49,8 @@ void launch_scan(const T* X, int64_t ld, bool kcontig, int64_t rows, int64_t k, 
                  unsigned long long* maxbits, int* status, cudaStream_t st);
 template <typename T>
 void launch_split_I(const T* X, int64_t ld, bool kcontig, int64_t rows, int64_t k, int p,
-                    const unsigned long long* maxbits, int8_t* hat, int32_t* E, cudaStream_t st);
+                    const unsigned long long* maxbits, int8_t* hat, int32_t* E, cudaStream_t st,
+                    bool f8 = false);
 template <typename T>
 void launch_split_II(const T* X, int64_t ld, bool kcontig, int64_t rows, int64_t k, int nm, int b,
                      int cw, const ModTables& tabs, const unsigned long long* maxbits, int8_t* res,
@@ -72,7 +74,7 @@ struct GemmIArgs {
   int* status;
   int num_sms;
 };
-cudaError_t launch_gemm_I(int p, int out_mode, const GemmIArgs& a, cudaStream_t st);
+cudaError_t launch_gemm_I(int p, int out_mode, const GemmIArgs& a, cudaStream_t st, bool f8 = false);
 
 // Scheme II kernel modes.
 enum GemmIIOut : int { II_F64 = 0, II_F32 = 1, II_RESIDUES = 2, II_Z3M = 3 };

@@ -1,9 +1,9 @@
 // gemm_I.cu -- fused Scheme I kernel (Algorithm 1, Sec. III-B).
 //
-// One persistent CTA per SM walks the output tiles.  A producer warp streams
-// the interleaved slices (Eq. 11) of A-hat and B-hat into a multi-stage
+// One persistent CTA per SM walks the output tiles.  A producer streams the
+// interleaved slices (Eq. 11) of A-hat and B-hat into a multi-stage
 // shared-memory ring with TMA (one 32-byte-wide box per slice, 32-byte
-// swizzle, completion on an mbarrier).  Eight consumer warps each own a
+// swizzle, completion on an mbarrier).  Eight math warps each own a
 // 16 x 16 output patch and, per 32-wide K-chunk, load all p A-slice
 // fragments with ldmatrix, then stream the B slices and issue the triangular
 // schedule of Eq. (2): acc[i+j] += A'_i B'_j for i + j < p, p(p+1) INT8
@@ -17,6 +17,10 @@
 // rounding beyond the final one), applies 2^(E_i + F_j - 14 - 8(p-1)) and
 // the BLAS update, and stores C.  No partial product reaches global memory
 // (OUT_PARTIALS, the unfused ablation, writes the INT32 C_s instead).
+//
+// The same kernel runs the E4M3 engine (F8): slices are balanced base-32
+// digits in E4M3 bytes, the MMA is the FP8 mma.sync with FP32 accumulators
+// (exact below 2^24, drained every K_c of that engine), beta = 5.
 #include "emu_internal.h"
 #include "gemm_I_core.cuh"
 
@@ -25,8 +29,13 @@ namespace emu {
 namespace {
 
 constexpr int kBM = 64, kBN = 32;
-constexpr int kCW = 8;                 // consumer warps (4 along M x 2 along N)
-constexpr int kThreads = (kCW + 1) * 32;
+constexpr int kCW = 8;  // math warps (4 along M x 2 along N)
+// INT8 engine: a ninth, dedicated producer warp issues the TMA loads (the
+// INT8 kernels fit in 168 registers, the limit with 3 warps on one SM
+// sub-partition).  E4M3 engine: no ninth warp -- thread 0 issues the loads
+// kStages - 1 iterations ahead -- so each thread may use 255 registers.
+template <bool F8>
+constexpr int threads_of() { return F8 ? kCW * 32 : (kCW + 1) * 32; }
 constexpr int kBlkA = kBM * 32, kBlkB = kBN * 32;
 
 template <int P>
@@ -62,9 +71,28 @@ __device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, 
   tn = in / gsz;
 }
 
-template <int P, int OUT>
-__global__ void __launch_bounds__(kThreads, 1) gemm_I_kernel(const __grid_constant__ KParamsI kp) {
+// Issue the TMA loads of pipeline iteration j (tile of this CTA, K-chunk).
+template <int P>
+__device__ __forceinline__ void issue_loads(const KParamsI& kp, uint8_t* smem, uint64_t* full, uint32_t j) {
   using Cfg = CfgI<P>;
+  const uint32_t stage = j % Cfg::kStages;
+  const int tile = blockIdx.x + static_cast<int>(j / kp.nk32) * gridDim.x;
+  const int kk = static_cast<int>(j % kp.nk32);
+  int tm, tn;
+  tile_coords(tile, kp.tiles_m, kp.tiles_n, tm, tn);
+  mbar_arrive_expect_tx(&full[stage], Cfg::kStageBytes);
+  uint8_t* sA = smem + stage * Cfg::kStageBytes;
+  uint8_t* sB = sA + P * kBlkA;
+#pragma unroll
+  for (int t = 0; t < P; ++t) tma_load_2d(sA + t * kBlkA, &kp.tA, &full[stage], (kk * P + t) * 32, tm * kBM);
+#pragma unroll
+  for (int t = 0; t < P; ++t) tma_load_2d(sB + t * kBlkB, &kp.tB, &full[stage], (kk * P + t) * 32, tn * kBN);
+}
+
+template <int P, int OUT, bool F8>
+__global__ void __launch_bounds__(threads_of<F8>(), 1) gemm_I_kernel(const __grid_constant__ KParamsI kp) {
+  using Cfg = CfgI<P>;
+  using Acc = typename Engine<F8>::Acc;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -83,39 +111,32 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_I_kernel(const __grid_consta
   __syncthreads();
 
   const int ntiles = kp.tiles_m * kp.tiles_n;
-
-  if (warp == kCW) {
-    // ------------------------------------------------------------ producer
-    if (lane == 0) {
-      tma_prefetch_desc(&kp.tA);
-      tma_prefetch_desc(&kp.tB);
-      uint32_t it = 0;
-      for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        int tm, tn;
-        tile_coords(tile, kp.tiles_m, kp.tiles_n, tm, tn);
-        for (int kk = 0; kk < kp.nk32; ++kk, ++it) {
-          const uint32_t stage = it % Cfg::kStages;
-          const uint32_t par = (it / Cfg::kStages) & 1u;
-          if (it >= static_cast<uint32_t>(Cfg::kStages) && !mbar_wait_bounded(&empty[stage], par ^ 1u)) {
+  const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - static_cast<int>(blockIdx.x)) / gridDim.x + 1 : 0;
+  const uint32_t total = static_cast<uint32_t>(my_tiles) * static_cast<uint32_t>(kp.nk32);
+  if constexpr (!F8) {
+    if (warp == kCW) {  // dedicated producer warp
+      if (lane == 0) {
+        tma_prefetch_desc(&kp.tA);
+        tma_prefetch_desc(&kp.tB);
+        for (uint32_t j = 0; j < total; ++j) {
+          if (j >= static_cast<uint32_t>(Cfg::kStages) &&
+              !mbar_wait_bounded(&empty[j % Cfg::kStages], ((j / Cfg::kStages) & 1u) ^ 1u)) {
             set_status(kp.status, ST_TIMEOUT);
             return;
           }
-          mbar_arrive_expect_tx(&full[stage], Cfg::kStageBytes);
-          uint8_t* sA = smem + stage * Cfg::kStageBytes;
-          uint8_t* sB = sA + P * kBlkA;
-#pragma unroll
-          for (int t = 0; t < P; ++t)
-            tma_load_2d(sA + t * kBlkA, &kp.tA, &full[stage], (kk * P + t) * 32, tm * kBM);
-#pragma unroll
-          for (int t = 0; t < P; ++t)
-            tma_load_2d(sB + t * kBlkB, &kp.tB, &full[stage], (kk * P + t) * 32, tn * kBN);
+          issue_loads<P>(kp, smem, full, j);
         }
       }
+      return;
     }
-    return;
+  }
+  const bool producer = F8 && threadIdx.x == 0;  // inline producer of the E4M3 engine
+  if (producer) {
+    tma_prefetch_desc(&kp.tA);
+    tma_prefetch_desc(&kp.tB);
+    for (uint32_t j = 0; j < total && j + 1 < static_cast<uint32_t>(Cfg::kStages); ++j) issue_loads<P>(kp, smem, full, j);
   }
 
-  // -------------------------------------------------------------- consumers
   const int wm = warp >> 1, wn = warp & 1;
   const uint32_t a_off = swz32(wm * 16 + (lane & 15), lane >> 4);
   const uint32_t b_off = swz32(wn * 16 + (lane & 7) + ((lane >> 4) << 3), (lane >> 3) & 1);
@@ -123,7 +144,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_I_kernel(const __grid_consta
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     int tm, tn;
     tile_coords(tile, kp.tiles_m, kp.tiles_n, tm, tn);
-    int32_t acc[P][2][4];
+    Acc acc[P][2][4];
     __int128 S[2][4];
 #pragma unroll
     for (int s = 0; s < P; ++s)
@@ -138,6 +159,18 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_I_kernel(const __grid_consta
 
     int since_fold = 0;
     for (int kk = 0; kk < kp.nk32; ++kk, ++it) {
+      // keep the ring kStages - 1 iterations ahead: reuse a slot once every warp released it
+      if (producer) {
+        const uint32_t j = it + Cfg::kStages - 1;
+        if (j < total) {
+          if (j >= static_cast<uint32_t>(Cfg::kStages) &&
+              !mbar_wait_bounded(&empty[j % Cfg::kStages], ((j / Cfg::kStages) & 1u) ^ 1u)) {
+            set_status(kp.status, ST_TIMEOUT);
+            return;
+          }
+          issue_loads<P>(kp, smem, full, j);
+        }
+      }
       const uint32_t stage = it % Cfg::kStages;
       const uint32_t par = (it / Cfg::kStages) & 1u;
       if (!mbar_wait_bounded(&full[stage], par)) {
@@ -149,11 +182,11 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_I_kernel(const __grid_consta
       uint32_t af[P][4];
 #pragma unroll
       for (int i = 0; i < P; ++i) ldsm_x4(sA + i * kBlkA + a_off, af[i][0], af[i][1], af[i][2], af[i][3]);
-      TriAll<P, kBlkB>::run(acc, af, sB, b_off);
+      TriAll<P, kBlkB, F8>::run(acc, af, sB, b_off);
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[stage]);
       if (OUT != OUT_PARTIALS && ++since_fold == kp.kc32) {
-        fold<P>(acc, S);
+        fold<P, F8>(acc, S);
         since_fold = 0;
       }
     }
@@ -169,12 +202,13 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_I_kernel(const __grid_consta
           if (row < kp.M && col < kp.N) {
 #pragma unroll
             for (int s = 0; s < P; ++s)
-              kp.partials[(static_cast<int64_t>(s) * kp.M + row) * kp.N + col] = acc[s][nt][q];
+              kp.partials[(static_cast<int64_t>(s) * kp.M + row) * kp.N + col] =
+                  static_cast<int32_t>(Engine<F8>::to_int(acc[s][nt][q]));
           }
         }
       continue;
     }
-    fold<P>(acc, S);
+    fold<P, F8>(acc, S);
 #pragma unroll
     for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
@@ -196,10 +230,10 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_I_kernel(const __grid_consta
   }
 }
 
-template <int P, int OUT>
+template <int P, int OUT, bool F8>
 cudaError_t launch_p(const GemmIArgs& a, cudaStream_t st) {
   using Cfg = CfgI<P>;
-  cudaError_t e = cudaFuncSetAttribute(gemm_I_kernel<P, OUT>,
+  cudaError_t e = cudaFuncSetAttribute(gemm_I_kernel<P, OUT, F8>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
   if (e != cudaSuccess) return e;
   KParamsI kp;
@@ -213,7 +247,7 @@ cudaError_t launch_p(const GemmIArgs& a, cudaStream_t st) {
   kp.tiles_n = (a.N + kBN - 1) / kBN;
   kp.EA = a.EA;
   kp.FB = a.FB;
-  kp.escale = -14 - 8 * (P - 1);
+  kp.escale = F8 ? -8 - 5 * (P - 1) : -14 - 8 * (P - 1);
   kp.alpha = a.alpha;
   kp.beta = a.beta;
   kp.C = a.C;
@@ -223,7 +257,7 @@ cudaError_t launch_p(const GemmIArgs& a, cudaStream_t st) {
   int ntiles = kp.tiles_m * kp.tiles_n;
   if (ntiles == 0) return cudaSuccess;
   int grid = ntiles < a.num_sms ? ntiles : a.num_sms;
-  gemm_I_kernel<P, OUT><<<grid, kThreads, Cfg::kSmem, st>>>(kp);
+  gemm_I_kernel<P, OUT, F8><<<grid, threads_of<F8>(), Cfg::kSmem, st>>>(kp);
   return cudaGetLastError();
 }
 
@@ -232,12 +266,17 @@ cudaError_t launch_p(const GemmIArgs& a, cudaStream_t st) {
 int gemm_I_tile_m() { return kBM; }
 int gemm_I_tile_n() { return kBN; }
 
-cudaError_t launch_gemm_I(int p, int out_mode, const GemmIArgs& a, cudaStream_t st) {
-#define EMU_P(PP)                                                        \
-  case PP:                                                               \
-    if (out_mode == OUT_F64) return launch_p<PP, OUT_F64>(a, st);        \
-    if (out_mode == OUT_F32) return launch_p<PP, OUT_F32>(a, st);        \
-    return launch_p<PP, OUT_PARTIALS>(a, st);
+cudaError_t launch_gemm_I(int p, int out_mode, const GemmIArgs& a, cudaStream_t st, bool f8) {
+#define EMU_P(PP)                                                                       \
+  case PP:                                                                              \
+    if (f8) {                                                                           \
+      if (out_mode == OUT_F64) return launch_p<PP, OUT_F64, true>(a, st);               \
+      if (out_mode == OUT_F32) return launch_p<PP, OUT_F32, true>(a, st);               \
+      return launch_p<PP, OUT_PARTIALS, true>(a, st);                                   \
+    }                                                                                   \
+    if (out_mode == OUT_F64) return launch_p<PP, OUT_F64, false>(a, st);                \
+    if (out_mode == OUT_F32) return launch_p<PP, OUT_F32, false>(a, st);                \
+    return launch_p<PP, OUT_PARTIALS, false>(a, st);
   switch (p) {
     EMU_P(1) EMU_P(2) EMU_P(3) EMU_P(4) EMU_P(5) EMU_P(6)
     EMU_P(7) EMU_P(8) EMU_P(9) EMU_P(10) EMU_P(11) EMU_P(12)

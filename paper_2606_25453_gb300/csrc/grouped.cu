@@ -313,15 +313,15 @@ __global__ void __launch_bounds__(CfgG<P, BM, BN>::kThreads, CfgG<P, BM, BN>::kO
       uint32_t af[P][4];
 #pragma unroll
       for (int i = 0; i < P; ++i) ldsm_x4(sA + i * Cfg::kBlkA + a_off, af[i][0], af[i][1], af[i][2], af[i][3]);
-      TriAll<P, Cfg::kBlkB>::run(acc, af, sB, b_off);
+      TriAll<P, Cfg::kBlkB, false>::run(acc, af, sB, b_off);
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[stage]);
       if (++since == kc32) {
-        fold<P>(acc, S);
+        fold<P, false>(acc, S);
         since = 0;
       }
     }
-    fold<P>(acc, S);
+    fold<P, false>(acc, S);
     const int row0 = tl.y * BM + wm * 16 + (lane >> 2);
     const int col0 = tl.z * BN + wn * 16 + (lane & 3) * 2;
 #pragma unroll

@@ -11,6 +11,9 @@
 // the slices (leading slice signed, tails unsigned), written interleaved:
 // row r, K-chunk c (32 wide), slice t at bytes [(c*p+t)*32, +32).
 //
+// Split I on E4M3 slices: the same layout with beta = 5 balanced base-32
+// digits stored as exact E4M3 bytes (the FP8 formulation of Sec. VII).
+//
 // Split II (Eq. 5): a' = trunc(a * 2^(b-E)), symmetric residues modulo the
 // moduli, one plane per modulus; complex input also writes the residues of
 // a'_re + a'_im for the 3M product (Eq. 16).
@@ -124,6 +127,32 @@ __device__ __forceinline__ void slice_digits(uint64_t bits, int E, uint32_t* out
   }
 }
 
+// E4M3 slices (beta = 5): balanced base-32 digits of x = sign * (mag << lsh),
+// |x| < 2^(5P-1) <= 2^59, from the lowest digit up (d in [-16, 15], the
+// leading digit in [-16, 16]), each encoded as its exact E4M3 byte.
+template <int P>
+__device__ __forceinline__ void slice_digits_f8(uint64_t bits, int E, uint32_t* out) {
+  ScaledInt s = scaled_trunc_bits(bits, 5 * P - 1 - E);
+  long long x = static_cast<long long>(s.lsh < 64 ? (s.mag << s.lsh) : 0ull);
+  if ((bits >> 63) != 0) x = -x;
+#pragma unroll
+  for (int t = P - 1; t >= 1; --t) {
+    int r = static_cast<int>(x & 31);
+    if (r >= 16) r -= 32;
+    out[t] = e4m3_of_int(r);
+    x = (x - r) >> 5;  // exact: x - r is a multiple of 32
+  }
+  out[0] = e4m3_of_int(static_cast<int>(x));
+}
+
+template <int P, bool F8>
+__device__ __forceinline__ void digits_any(uint64_t bits, int E, uint32_t* out) {
+  if (F8)
+    slice_digits_f8<P>(bits, E, out);
+  else
+    slice_digits<P>(bits, E, out);
+}
+
 __device__ __forceinline__ int exp_from_maxbits(const unsigned long long* maxbits, int64_t r,
                                                 int64_t rows) {
   if (r >= rows) return 0;
@@ -133,7 +162,7 @@ __device__ __forceinline__ int exp_from_maxbits(const unsigned long long* maxbit
 }
 
 // K-contiguous source: one warp per (row, 32-wide K-chunk); lane = h % 32.
-template <typename T, int P>
+template <typename T, int P, bool F8>
 __global__ void split_I_kcontig(const T* __restrict__ X, int64_t ld, int64_t rows, int64_t k,
                                 int64_t rows_pad, int64_t nchunks,
                                 const unsigned long long* __restrict__ maxbits,
@@ -146,7 +175,7 @@ __global__ void split_I_kcontig(const T* __restrict__ X, int64_t ld, int64_t row
   int E = exp_from_maxbits(maxbits, r, rows);
   uint32_t dg[P];
   if (r < rows && h < k) {
-    slice_digits<P>(load_bits(X + r * ld + h), E, dg);
+    digits_any<P, F8>(load_bits(X + r * ld + h), E, dg);
   } else {
 #pragma unroll
     for (int t = 0; t < P; ++t) dg[t] = 0;
@@ -160,7 +189,7 @@ __global__ void split_I_kcontig(const T* __restrict__ X, int64_t ld, int64_t row
 // K-strided source (element (r, h) at X[h*ld + r]): one thread per
 // (vector r, K-chunk c), lanes over consecutive r (coalesced reads); each
 // thread assembles 32 bytes per slice and writes them as two 16-byte stores.
-template <typename T, int P>
+template <typename T, int P, bool F8>
 __global__ void split_I_kstrided(const T* __restrict__ X, int64_t ld, int64_t rows, int64_t k,
                                  int64_t rows_pad, int64_t nchunks,
                                  const unsigned long long* __restrict__ maxbits,
@@ -184,7 +213,7 @@ __global__ void split_I_kstrided(const T* __restrict__ X, int64_t ld, int64_t ro
       int64_t h = c * 32 + wq * 4 + qq;
       uint32_t dg[P];
       if (r < rows && h < k) {
-        slice_digits<P>(load_bits(X + h * ld + r), E, dg);
+        digits_any<P, F8>(load_bits(X + h * ld + r), E, dg);
       } else {
 #pragma unroll
         for (int t = 0; t < P; ++t) dg[t] = 0;
@@ -314,7 +343,7 @@ template void launch_scan<double>(const double*, int64_t, bool, int64_t, int64_t
 template void launch_scan<float>(const float*, int64_t, bool, int64_t, int64_t, int,
                                  unsigned long long*, int*, cudaStream_t);
 
-template <typename T, int P>
+template <typename T, int P, bool F8>
 static void launch_split_I_p(const T* X, int64_t ld, bool kcontig, int64_t rows, int64_t k,
                              const unsigned long long* maxbits, int8_t* hat, int32_t* E,
                              cudaStream_t st) {
@@ -323,21 +352,24 @@ static void launch_split_I_p(const T* X, int64_t ld, bool kcontig, int64_t rows,
   if (kcontig) {
     int64_t warps = rows_pad * nchunks;
     int64_t blocks = (warps + 7) / 8;
-    split_I_kcontig<T, P><<<static_cast<unsigned>(blocks), 256, 0, st>>>(X, ld, rows, k, rows_pad,
-                                                                         nchunks, maxbits, hat, E);
+    split_I_kcontig<T, P, F8><<<static_cast<unsigned>(blocks), 256, 0, st>>>(X, ld, rows, k, rows_pad,
+                                                                             nchunks, maxbits, hat, E);
   } else {
     dim3 grid(static_cast<unsigned>((rows_pad + 127) / 128), static_cast<unsigned>(nchunks));
-    split_I_kstrided<T, P><<<grid, 128, 0, st>>>(X, ld, rows, k, rows_pad, nchunks, maxbits, hat, E);
+    split_I_kstrided<T, P, F8><<<grid, 128, 0, st>>>(X, ld, rows, k, rows_pad, nchunks, maxbits, hat, E);
   }
 }
 
 template <typename T>
 void launch_split_I(const T* X, int64_t ld, bool kcontig, int64_t rows, int64_t k, int p,
-                    const unsigned long long* maxbits, int8_t* hat, int32_t* E, cudaStream_t st) {
+                    const unsigned long long* maxbits, int8_t* hat, int32_t* E, cudaStream_t st, bool f8) {
   switch (p) {
-#define EMU_CASE(PP) \
-  case PP:           \
-    launch_split_I_p<T, PP>(X, ld, kcontig, rows, k, maxbits, hat, E, st); \
+#define EMU_CASE(PP)                                                                         \
+  case PP:                                                                                   \
+    if (f8)                                                                                  \
+      launch_split_I_p<T, PP, true>(X, ld, kcontig, rows, k, maxbits, hat, E, st);          \
+    else                                                                                     \
+      launch_split_I_p<T, PP, false>(X, ld, kcontig, rows, k, maxbits, hat, E, st);         \
     break;
     EMU_CASE(1) EMU_CASE(2) EMU_CASE(3) EMU_CASE(4) EMU_CASE(5) EMU_CASE(6)
     EMU_CASE(7) EMU_CASE(8) EMU_CASE(9) EMU_CASE(10) EMU_CASE(11) EMU_CASE(12)
@@ -347,9 +379,9 @@ void launch_split_I(const T* X, int64_t ld, bool kcontig, int64_t rows, int64_t 
   }
 }
 template void launch_split_I<double>(const double*, int64_t, bool, int64_t, int64_t, int,
-                                     const unsigned long long*, int8_t*, int32_t*, cudaStream_t);
+                                     const unsigned long long*, int8_t*, int32_t*, cudaStream_t, bool);
 template void launch_split_I<float>(const float*, int64_t, bool, int64_t, int64_t, int,
-                                    const unsigned long long*, int8_t*, int32_t*, cudaStream_t);
+                                    const unsigned long long*, int8_t*, int32_t*, cudaStream_t, bool);
 
 template <typename T>
 void launch_split_II(const T* X, int64_t ld, bool kcontig, int64_t rows, int64_t k, int nm, int b,

@@ -282,3 +282,79 @@ def test_full_size_sampled_rows(orc, h, scheme, p):
     got = C[rows].cpu().numpy()
     ref = orc.emu_I(A[rows], B, p) if scheme == "I" else orc.emu_II(A[rows], B, p)
     assert np.array_equal(got, ref)
+
+
+# ---------------------------------------------------------------- Scheme I on E4M3 slices
+def e4m3_to_int(b: np.ndarray) -> np.ndarray:
+    """Decode E4M3 bytes that hold integers (sign, exponent bias 7, 3-bit mantissa)."""
+    b = b.astype(np.uint8).astype(np.int64)
+    e = (b >> 3) & 15
+    m = b & 7
+    mag = np.where(e == 0, 0, ((8 + m) << np.maximum(e - 7, 0)) >> 3)
+    return np.where(b & 0x80, -mag, mag)
+
+
+@pytest.mark.parametrize("p", [1, 4, 11, 12])
+@pytest.mark.parametrize("operand", [0, 1])
+def test_split_F8_bit_exact(orc, h, p, operand):
+    rows, k = 70, 77
+    X = synth.test_matrix(rows, k, 4.0, 300 + p) if operand == 0 else synth.test_matrix(k, rows, 4.0, 300 + p)
+    hat, E = emu.split_I(dev(X), p, operand=operand, handle=h, f8=True)
+    Xr = X if operand == 0 else X.T
+    hn = hat.cpu().numpy()
+    nck = -(-k // 32)
+    blk = hn[:rows, :nck * 32 * p].reshape(rows, nck, p, 32)
+    got = e4m3_to_int(np.transpose(blk, (2, 0, 1, 3)).reshape(p, rows, nck * 32))
+    assert np.array_equal(got[:, :, :k], orc.split_F8_rows(Xr, p))
+    assert not got[:, :, k:].any() and not hn[rows:].any()
+    assert np.array_equal(E.cpu().numpy(), orc.row_exponents(Xr))
+
+
+@pytest.mark.parametrize("p", [2, 5, 11])
+def test_partials_F8_bit_exact(orc, h, p):
+    m, n, k = 130, 97, 1000
+    A, B = synth.gemm_pair(m, n, k, 2.0, 20 + p)
+    Cs = emu.partials_I(dev(A), dev(B), p, handle=h, f8=True)
+    ref = orc.partials_F8(A, B, p)
+    assert ref.shape[0] == 1
+    assert np.array_equal(Cs.cpu().numpy().astype(np.int64), ref[0])
+
+
+CASES_F8 = [
+    (256, 256, 256, 11, 0.5, 0),
+    (200, 130, 300, 4, 1.0, 1),
+    (65, 33, 31, 1, 0.5, 2),
+    (129, 70, 500, 12, 4.0, 4),
+    (64, 40, 6000, 11, 2.0, 6),     # k > K_c(11) = 5888: two FP32-exact chunks
+]
+
+
+@pytest.mark.parametrize("m,n,k,p,phi,seed", CASES_F8)
+def test_dgemm_F8_bit_exact(orc, h, m, n, k, p, phi, seed):
+    A, B = synth.gemm_pair(m, n, k, phi, seed)
+    C = emu.dgemm(dev(A), dev(B), scheme="I_F8", p=p, handle=h)
+    torch.cuda.synchronize()
+    assert h.status() == 0
+    assert np.array_equal(C.cpu().numpy(), orc.emu_F8(A, B, p))
+
+
+def test_dgemm_F8_layouts_alpha_beta_f32(orc, h):
+    m, n, k, p = 150, 90, 120, 9
+    A, B = synth.gemm_pair(m, n, k, 1.0, 41)
+    C0 = synth.test_matrix(m, n, 1.0, 42)
+    Cd = colmajor(C0)
+    emu.dgemm(colmajor(A), colmajor(B), Cd, alpha=1.5, beta=-0.25, scheme="I_F8", p=p, handle=h)
+    assert np.array_equal(Cd.cpu().numpy(), orc.emu_F8(A, B, p, alpha=1.5, beta=-0.25, C=C0))
+    Af, Bf = A.astype(np.float32), B.astype(np.float32)
+    Cf = emu.sgemm(dev(Af), dev(Bf), scheme="I_F8", p=6, handle=h).cpu().numpy()
+    assert np.array_equal(Cf, orc.emu_F8(Af.astype(np.float64), Bf.astype(np.float64), 6, out_f32=True))
+
+
+def test_F8_full_size_sampled_rows(orc, h):
+    n, p = 8192, 11
+    A, B = synth.gemm_pair(n, n, n, 0.5, 321)
+    C = emu.dgemm(dev(A), dev(B), scheme="I_F8", p=p, handle=h)
+    torch.cuda.synchronize()
+    assert h.status() == 0
+    rows = [1, 5000]
+    assert np.array_equal(C[rows].cpu().numpy(), orc.emu_F8(A[rows], B, p))
