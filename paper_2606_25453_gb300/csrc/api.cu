@@ -390,6 +390,17 @@ namespace emu {
 
 static inline size_t al256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
+// EMU_F8_ENGINE=mma selects the warp-level FP8 kernel for E4M3 slices (for
+// comparison); the default is the tcgen05 kernel.
+static bool f8_engine_mma() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = std::getenv("EMU_F8_ENGINE");
+    v = (e && std::strcmp(e, "mma") == 0) ? 1 : 0;
+  }
+  return v == 1;
+}
+
 Plan plan_I(int64_t m, int64_t n, int64_t k, int p) {
   Plan pl{};
   pl.rows_a = split_rows(m);
@@ -482,8 +493,11 @@ emu_status_t run_scheme_I(emu_handle_s* h, const View& v, int64_t k, int p, doub
   launch_split_I<T>(A, v.ldA, v.a_kcontig, v.M, k, p, maxA, hatA, EA, st, f8);
   launch_split_I<T>(B, v.ldB, v.b_kcontig, v.N, k, p, maxB, hatB, FB, st, f8);
   trace_end(h, PH_SPLIT, st, 2);
+  // E4M3 slices with a product output run on the tcgen05 kernel (128-row A
+  // boxes); the INT8 engine and the partials ablation use the mma.sync kernel.
+  const bool tc = f8 && out_mode != OUT_PARTIALS && !f8_engine_mma();
   CUtensorMap ta, tb;
-  if (!make_tmap_i8(&ta, hatA, static_cast<uint64_t>(pl.cols), static_cast<uint64_t>(pl.rows_a), 64) ||
+  if (!make_tmap_i8(&ta, hatA, static_cast<uint64_t>(pl.cols), static_cast<uint64_t>(pl.rows_a), tc ? 128 : 64) ||
       !make_tmap_i8(&tb, hatB, static_cast<uint64_t>(pl.cols), static_cast<uint64_t>(pl.rows_b), 32))
     return EMU_ERR_CUDA;
   GemmIArgs a{};
@@ -503,7 +517,7 @@ emu_status_t run_scheme_I(emu_handle_s* h, const View& v, int64_t k, int p, doub
   a.status = h->status;
   a.num_sms = h->num_sms;
   trace_begin(h, PH_GEMM, st);
-  cudaError_t e = launch_gemm_I(p, out_mode, a, st, f8);
+  cudaError_t e = tc ? launch_gemm_f8tc(p, out_mode, a, st) : launch_gemm_I(p, out_mode, a, st, f8);
   trace_end(h, PH_GEMM, st, 1);
   return cuda_err(e);
 }

@@ -75,6 +75,8 @@ struct GemmIArgs {
   int num_sms;
 };
 cudaError_t launch_gemm_I(int p, int out_mode, const GemmIArgs& a, cudaStream_t st, bool f8 = false);
+// Scheme I on E4M3 slices with tcgen05 / TMEM (128 x 32 output tiles).
+cudaError_t launch_gemm_f8tc(int p, int out_mode, const GemmIArgs& a, cudaStream_t st);
 
 // Scheme II kernel modes.
 enum GemmIIOut : int { II_F64 = 0, II_F32 = 1, II_RESIDUES = 2, II_Z3M = 3 };
