@@ -128,21 +128,26 @@ __device__ __forceinline__ void slice_digits(uint64_t bits, int E, uint32_t* out
 }
 
 // E4M3 slices (beta = 5): balanced base-32 digits of x = sign * (mag << lsh),
-// |x| < 2^(5P-1) <= 2^59, from the lowest digit up (d in [-16, 15], the
-// leading digit in [-16, 16]), each encoded as its exact E4M3 byte.
+// |x| < 2^(5P-1) <= 2^59 (leading digit in [-16, 16], the others in
+// [-16, 15]), each encoded as its exact E4M3 byte.  Adding 16 * 32^t for
+// every lower position t turns the balanced digits into plain base-32 digits
+// of the biased value y, so all digits come from independent shifts:
+// d_t = ((y >> 5(P-1-t)) & 31) - 16 for t >= 1, d_0 = y >> 5(P-1).
 template <int P>
 __device__ __forceinline__ void slice_digits_f8(uint64_t bits, int E, uint32_t* out) {
   ScaledInt s = scaled_trunc_bits(bits, 5 * P - 1 - E);
   long long x = static_cast<long long>(s.lsh < 64 ? (s.mag << s.lsh) : 0ull);
   if ((bits >> 63) != 0) x = -x;
+  constexpr long long kBias = [] {
+    long long b = 0;
+    for (int t = 1; t < P; ++t) b = b * 32 + 16;
+    return b;
+  }();
+  const long long y = x + kBias;
 #pragma unroll
-  for (int t = P - 1; t >= 1; --t) {
-    int r = static_cast<int>(x & 31);
-    if (r >= 16) r -= 32;
-    out[t] = e4m3_of_int(r);
-    x = (x - r) >> 5;  // exact: x - r is a multiple of 32
-  }
-  out[0] = e4m3_of_int(static_cast<int>(x));
+  for (int t = 1; t < P; ++t)
+    out[t] = e4m3_of_int(static_cast<int>((y >> (5 * (P - 1 - t))) & 31) - 16);
+  out[0] = e4m3_of_int(static_cast<int>(y >> (5 * (P - 1))));
 }
 
 template <int P, bool F8>
@@ -161,28 +166,43 @@ __device__ __forceinline__ int exp_from_maxbits(const unsigned long long* maxbit
   return frexp_exp_bits(mb);
 }
 
-// K-contiguous source: one warp per (row, 32-wide K-chunk); lane = h % 32.
+// K-contiguous source: one warp per (row, group of four 32-wide K-chunks);
+// lane l handles h = 4l .. 4l+3 of the group and writes one 4-byte word per
+// slice (lanes 8c .. 8c+7 fill the 32-byte block of chunk c).
 template <typename T, int P, bool F8>
 __global__ void split_I_kcontig(const T* __restrict__ X, int64_t ld, int64_t rows, int64_t k,
                                 int64_t rows_pad, int64_t nchunks,
                                 const unsigned long long* __restrict__ maxbits,
                                 int8_t* __restrict__ hat, int32_t* __restrict__ E_out) {
-  int lane = threadIdx.x & 31;
-  int64_t w = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (w >= rows_pad * nchunks) return;
-  int64_t r = w / nchunks, c = w % nchunks;
-  int64_t h = c * 32 + lane;
-  int E = exp_from_maxbits(maxbits, r, rows);
-  uint32_t dg[P];
-  if (r < rows && h < k) {
-    digits_any<P, F8>(load_bits(X + r * ld + h), E, dg);
-  } else {
+  const int lane = threadIdx.x & 31;
+  const int64_t ngroups = (nchunks + 3) / 4;
+  const int64_t w = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (w >= rows_pad * ngroups) return;
+  const int64_t r = w / ngroups, g = w % ngroups;
+  const int64_t c = g * 4 + (lane >> 3);  // chunk of this lane
+  if (c >= nchunks) return;
+  const int64_t h0 = c * 32 + (lane & 7) * 4;
+  const int E = exp_from_maxbits(maxbits, r, rows);
+  uint32_t word[P];
 #pragma unroll
-    for (int t = 0; t < P; ++t) dg[t] = 0;
+  for (int t = 0; t < P; ++t) word[t] = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int64_t h = h0 + q;
+    uint32_t dg[P];
+    if (r < rows && h < k) {
+      digits_any<P, F8>(load_bits(X + r * ld + h), E, dg);
+    } else {
+#pragma unroll
+      for (int t = 0; t < P; ++t) dg[t] = 0;
+    }
+#pragma unroll
+    for (int t = 0; t < P; ++t) word[t] |= (dg[t] & 0xFFu) << (8 * q);
   }
   uint8_t* row = reinterpret_cast<uint8_t*>(hat) + r * (nchunks * 32 * P);
 #pragma unroll
-  for (int t = 0; t < P; ++t) row[(c * P + t) * 32 + lane] = static_cast<uint8_t>(dg[t]);
+  for (int t = 0; t < P; ++t)
+    *reinterpret_cast<uint32_t*>(row + (c * P + t) * 32 + (lane & 7) * 4) = word[t];
   if (c == 0 && lane == 0 && r < rows && E_out) E_out[r] = E;
 }
 
@@ -350,7 +370,7 @@ static void launch_split_I_p(const T* X, int64_t ld, bool kcontig, int64_t rows,
   int64_t rows_pad = split_rows(rows), nchunks = split_cols_I(k, 1) / 32;
   if (rows_pad == 0 || nchunks == 0) return;
   if (kcontig) {
-    int64_t warps = rows_pad * nchunks;
+    int64_t warps = rows_pad * ((nchunks + 3) / 4);
     int64_t blocks = (warps + 7) / 8;
     split_I_kcontig<T, P, F8><<<static_cast<unsigned>(blocks), 256, 0, st>>>(X, ld, rows, k, rows_pad,
                                                                              nchunks, maxbits, hat, E);
