@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--scheme", default="I", choices=["I", "I_F8", "II"],
                     help="I: INT8 slices; I_F8: E4M3 slices on the FP8 tensor path; II: CRT (p = moduli)")
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--cpu-rows", type=int, default=16, help="rows of C in the CPU oracle sample")
+    ap.add_argument("--cpu-rows", type=int, default=96, help="rows of C in the CPU oracle sample")
     ap.add_argument("--no-extras", action="store_true", help="skip cuBLAS / accuracy / CPU legs")
     ap.add_argument("--suite", default=None, help="write the secondary measurements (all paths) to this JSONL file")
     return ap.parse_args()
@@ -166,6 +166,39 @@ def max_over_ranks(x: float, dist, device) -> float:
 def aggregate_tflops(world: int, flops_per_rank_step: float, steps: int, ms_max: float) -> float:
     """Whole-job throughput: all ranks' work divided by the slowest rank's time."""
     return world * flops_per_rank_step * steps / (ms_max * 1e-3) / 1e12
+
+
+def fp8_engine_leg(emu, h, Ad, Bd, Cd, n, stream, ri, ci, A, B, hi, lo, den, cublas_tflops):
+    """Scheme I on E4M3 slices (p = 11 and 12) on the same inputs: TFLOP/s,
+    GEMM-kernel 8-bit TOP/s and sampled error, with the same CUDA-event timing."""
+    import torch
+    out = {}
+    for p in (11, 12):
+        def call():
+            emu.check(emu.emu_dgemm(h.h, emu.EMU_ROW_MAJOR, n, n, n, 1.0, Ad.data_ptr(), n, Bd.data_ptr(), n, 0.0,
+                                    Cd.data_ptr(), n, emu.EMU_SCHEME_I_F8, p, stream.cuda_stream), "emu_dgemm")
+        for _ in range(3):
+            call()
+        torch.cuda.synchronize()
+        h.trace(True)
+        h.trace_read()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(5):
+            call()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+        tr = h.trace_read()
+        h.trace(False)
+        got = Cd[ri][:, ci].cpu().numpy()
+        err = float(np.max(np.abs((got - hi) - lo) / den))
+        gms = tr["ms_gemm"] / max(tr["gemm_launches"], 1)
+        out["p%d" % p] = {"tflops": 2.0 * n ** 3 / (ms * 1e-3) / 1e12, "ms_per_step": ms,
+                          "gemm_8bit_tops": p * (p + 1) * n ** 3 / (gms * 1e-3) / 1e12,
+                          "err_max_rel_absAB": err, "speedup_vs_cublas_dgemm": 2.0 * n ** 3 / (ms * 1e-3) / 1e12 / cublas_tflops,
+                          "bits_per_slice": 5}
+    return out
 
 
 def measured_peaks():
@@ -332,6 +365,11 @@ def run_ours(args, rank, world, local_rank):
         extras = {"cublas_dgemm_tflops": cublas_tflops, "speedup_vs_cublas_dgemm": value / world / cublas_tflops,
                   "err_max_rel_absAB": err_ours, "err_cublas_dgemm": err_cub,
                   "err_bound_4k_u": 4 * n * 2.0 ** -53, "err_sample": "8 x 64 entries vs double-double"}
+        if args.scheme == "I":
+            # the same product on the FP8 tensor path (Scheme I with E4M3 slices,
+            # tcgen05 kernel) at FP64-level accuracy, timed the same way
+            extras["fp8_tcgen05_engine"] = fp8_engine_leg(emu, h, Ad, Bd, Cd, n, stream, ri, ci, A, B, hi, lo, den,
+                                                          cublas_tflops)
         del ref
         # CPU oracle baseline on a bounded sample of rows
         rows = list(range(args.cpu_rows))
