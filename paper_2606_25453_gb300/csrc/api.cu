@@ -193,15 +193,18 @@ EncodeFn get_encode() {
 }
 }  // namespace
 
-bool make_tmap_i8(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint32_t box_rows) {
+bool make_tmap_i8(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint32_t box_rows,
+                  uint32_t box_bytes) {
   EncodeFn enc = get_encode();
   if (!enc) return false;
+  if (box_bytes != 32 && box_bytes != 128) return false;
   cuuint64_t dims[2] = {cols, rows};
   cuuint64_t strides[1] = {cols};
-  cuuint32_t box[2] = {32, box_rows};
+  cuuint32_t box[2] = {box_bytes, box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides, box,
-                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
+                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   box_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_32B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -493,11 +496,14 @@ emu_status_t run_scheme_I(emu_handle_s* h, const View& v, int64_t k, int p, doub
   launch_split_I<T>(A, v.ldA, v.a_kcontig, v.M, k, p, maxA, hatA, EA, st, f8);
   launch_split_I<T>(B, v.ldB, v.b_kcontig, v.N, k, p, maxB, hatB, FB, st, f8);
   trace_end(h, PH_SPLIT, st, 2);
-  // E4M3 slices with a product output run on the tcgen05 kernel (128-row A
-  // boxes); the INT8 engine and the partials ablation use the mma.sync kernel.
+  // E4M3 slices with a product output run on the tcgen05 kernel (A boxes of
+  // 128 B x 128 / cluster rows, multicast across the cluster); the INT8
+  // engine and the partials ablation use the mma.sync kernel (32 B x 64 rows).
   const bool tc = f8 && out_mode != OUT_PARTIALS && !f8_engine_mma();
+  const int cluster = tc ? gemm_f8tc_cluster() : 1;
   CUtensorMap ta, tb;
-  if (!make_tmap_i8(&ta, hatA, static_cast<uint64_t>(pl.cols), static_cast<uint64_t>(pl.rows_a), tc ? 128 : 64) ||
+  if (!make_tmap_i8(&ta, hatA, static_cast<uint64_t>(pl.cols), static_cast<uint64_t>(pl.rows_a),
+                    tc ? static_cast<uint32_t>(128 / cluster) : 64, tc ? 128 : 32) ||
       !make_tmap_i8(&tb, hatB, static_cast<uint64_t>(pl.cols), static_cast<uint64_t>(pl.rows_b), 32))
     return EMU_ERR_CUDA;
   GemmIArgs a{};
@@ -516,6 +522,7 @@ emu_status_t run_scheme_I(emu_handle_s* h, const View& v, int64_t k, int p, doub
   a.partials = partials;
   a.status = h->status;
   a.num_sms = h->num_sms;
+  a.cluster = cluster;
   trace_begin(h, PH_GEMM, st);
   cudaError_t e = tc ? launch_gemm_f8tc(p, out_mode, a, st) : launch_gemm_I(p, out_mode, a, st, f8);
   trace_end(h, PH_GEMM, st, 1);

@@ -73,10 +73,12 @@ struct GemmIArgs {
   int32_t* partials;
   int* status;
   int num_sms;
+  int cluster;  // tcgen05 kernel: CTAs per cluster sharing the A tiles (1, 2, 4)
 };
 cudaError_t launch_gemm_I(int p, int out_mode, const GemmIArgs& a, cudaStream_t st, bool f8 = false);
 // Scheme I on E4M3 slices with tcgen05 / TMEM (128 x 32 output tiles).
 cudaError_t launch_gemm_f8tc(int p, int out_mode, const GemmIArgs& a, cudaStream_t st);
+int gemm_f8tc_cluster();
 
 // Scheme II kernel modes.
 enum GemmIIOut : int { II_F64 = 0, II_F32 = 1, II_RESIDUES = 2, II_Z3M = 3 };
@@ -101,9 +103,10 @@ struct GemmIIArgs {
 cudaError_t launch_gemm_II(int out_mode, const GemmIIArgs& a, const ModTables& mt,
                            const CrtTables& ct, cudaStream_t st);
 
-// Tensor map for a row-major int8 matrix [rows][cols] read in boxes of
-// 32 bytes x box_rows with 32-byte swizzling.
+// Tensor map for a row-major byte matrix [rows][cols] read in boxes of
+// box_bytes x box_rows: 32-byte boxes with 32-byte swizzling, or 128-byte
+// boxes with 128-byte swizzling.
 bool make_tmap_i8(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows,
-                  uint32_t box_rows);
+                  uint32_t box_rows, uint32_t box_bytes = 32);
 
 }  // namespace emu

@@ -11,41 +11,64 @@
 // in the columns of accumulator i + j).  A K-chunk therefore costs about P
 // tensor-core instructions (N split at 256) instead of P(P+1)/2.
 //
-// Roles (192 threads): warps 0-3 drain TMEM (thread t = tile row t) into
-// exact 128-bit sums and write C; warp 4 lane 0 issues the TMA loads; warp 5
-// owns the TMEM allocation and lane 0 issues the MMAs.  Slices are balanced
+// Roles (320 threads): warps 0-7 drain TMEM into exact 128-bit sums and write
+// C (warp w: tile rows 32 (w % 4) .. +31, one per lane, columns 16 (w / 4)
+// .. +15); warp 8 lane 0 issues the TMA loads; warp 9 owns the TMEM
+// allocation and lane 0 issues the MMAs.
+//
+// The A slices of a K-chunk travel as 128-byte rows (four slices per TMA box,
+// 128-byte swizzle; the MMA of slice 4g+u starts 32 u bytes into the row), so
+// one L2 request carries four slices instead of one.  A 128 x 32 tile reads
+// its A slices once per 32 output columns, so without help the A operand
+// crosses L2 -> SM N/32 times.  CTAs are therefore launched
+// in clusters of CL (1, 2 or 4) that work on the same row block and CL
+// neighbouring column tiles: each CTA fetches 128/CL rows of every A slice and
+// multicasts them to the whole cluster, dividing that traffic by CL.  A stage
+// is refilled only when the MMAs of every CTA in the cluster are done with it
+// (the MMA commits arrive on the stage barrier of all CTAs of the cluster).  Slices are balanced
 // base-32 digits stored as E4M3 bytes, so every product is exact and the FP32
 // accumulators stay exact integers while |sum| <= 2^24: they are drained
 // every K_c (the E4M3 chunk bound) and at the end of each tile.  All waits are
 // bounded; a timeout sets the status word, raises an abort flag for the other
 // roles, and the TMEM is still released.
+#include <cstdlib>
+
 #include "emu_internal.h"
 
 namespace emu {
 namespace {
 
 constexpr int kBM = 128, kBN = 32;
-constexpr int kThreadsTC = 192;
-constexpr int kEpiThreads = 128;
+constexpr int kThreadsTC = 320;
+constexpr int kEpiThreads = 256;
+constexpr int kProducerWarp = 8, kMmaWarp = 9;
 constexpr uint32_t kTmemCols = 512;
 
 template <int P>
 struct CfgTC {
-  static constexpr int kBlkA = kBM * 32;  // one slice of A: 128 rows x 32 B
-  static constexpr int kBlkB = kBN * 32;  // one slice of B:  32 rows x 32 B
-  static constexpr int kStageBytes = P * (kBlkA + kBlkB);
+  // A: slices in groups of four, each group one 128-byte-wide TMA box per row
+  // (the four 32-byte slice blocks of a K-chunk are adjacent in the
+  // interleaved layout), 128-byte swizzle: 128 rows x 128 B per group.
+  // B: one 32-row x 32-byte box per slice, slices stacked along N.
+  static constexpr int kGroups = (P + 3) / 4;
+  static constexpr int kBlkAg = kBM * 128;  // one group of A slices
+  static constexpr int kBlkB = kBN * 32;    // one slice of B
+  static constexpr int kStageBytes = kGroups * kBlkAg + P * kBlkB;
   static constexpr int kRaw = 196608 / kStageBytes;
   static constexpr int kStages = kRaw < 2 ? 2 : (kRaw > 6 ? 6 : kRaw);
   // at least 116 KB so that a single CTA (holding all 512 TMEM columns) runs per SM
   static constexpr int kSmemUsed = kStages * kStageBytes + 1024 + 256;
   static constexpr int kSmem = kSmemUsed < 118784 ? 118784 : kSmemUsed;
   static_assert(P * kBN <= static_cast<int>(kTmemCols), "accumulators must fit in TMEM");
+  static_assert(kStageBytes % 1024 == 0, "stages must keep the 1024-byte swizzle alignment");
 };
 
 struct KParamsTC {
-  CUtensorMap tA;
-  CUtensorMap tB;
+  CUtensorMap tA;  // box: 128 B x (128 / cl) rows, 128-byte swizzle
+  CUtensorMap tB;  // box: 32 B x 32 rows
   int M, N, nk32, kc32, tiles_m, tiles_n;
+  int cl;          // CTAs per cluster (1, 2 or 4), neighbours along N
+  int tiles_ng;    // column-tile groups of cl tiles
   const int32_t* EA;
   const int32_t* FB;
   int escale;
@@ -66,6 +89,19 @@ __device__ __forceinline__ uint64_t smem_desc_k32(uint32_t saddr) {
   d |= static_cast<uint64_t>((256u >> 4) & 0x3FFFu) << 32;     // stride byte offset: 8 rows x 32 B
   d |= static_cast<uint64_t>(1u) << 46;                        // descriptor version
   d |= static_cast<uint64_t>(6u) << 61;                        // 32-byte swizzle
+  return d;
+}
+
+// The same for a K-major block [rows][128 B] with the 128-byte swizzle:
+// 8-row atoms 1024 B apart, layout type 2.  The 32-byte K-step u inside the
+// 128-byte row is selected by starting 32 u bytes into the (1024-aligned) atom.
+__device__ __forceinline__ uint64_t smem_desc_k128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr >> 4) & 0x3FFFu);         // start address
+  d |= static_cast<uint64_t>(1u) << 16;                        // leading byte offset (unused)
+  d |= static_cast<uint64_t>((1024u >> 4) & 0x3FFFu) << 32;    // stride byte offset: 8 rows x 128 B
+  d |= static_cast<uint64_t>(1u) << 46;                        // descriptor version
+  d |= static_cast<uint64_t>(2u) << 61;                        // 128-byte swizzle
   return d;
 }
 
@@ -92,23 +128,88 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
                : "memory");
 }
 
+// The same, arriving on the barrier at this offset in every CTA of `mask`.
+__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
+
+// 2D tiled TMA load written to the same shared-memory offset of every CTA in
+// `mask`, completion counted on the barrier at `bar`'s offset in each of them.
+__device__ __forceinline__ void tma_load_2d_mc(void* smem_dst, const void* desc, uint64_t* bar, int x, int y,
+                                               uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_u32(smem_dst)),
+      "l"(reinterpret_cast<uint64_t>(desc)), "r"(smem_u32(bar)), "r"(x), "r"(y), "h"(mask)
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_id_x() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_count_x() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return r;
+}
+// Every thread of every CTA in the cluster (release / acquire).
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release;\nbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// 32 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
+// 8 consecutive FP32 columns of this thread's TMEM lane, as integers (the
+// accumulators hold exact integers of magnitude <= 2^24).
+__device__ __forceinline__ void tmem_ld8_int(uint32_t taddr, int32_t* v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 8; ++i) v[i] = __float2int_rn(__uint_as_float(r[i]));
+}
+
+// Fold digits S0 .. S1-1 of the P accumulators of 8 columns (base 2^5
+// Horner scheme) in 64-bit integers -- at most six digits, so the partial
+// stays below 2^50 -- and add the partial into S at its weight
+// 2^(5 (P - S1)).
+template <int P, int S0, int S1>
+__device__ __forceinline__ void fold_range(uint32_t taddr, __int128* S) {
+  long long acc[8];
+#pragma unroll
+  for (int s = S0; s < S1; ++s) {
+    int32_t v[8];
+    tmem_ld8_int(taddr + static_cast<uint32_t>(s * kBN), v);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = (s == S0) ? static_cast<long long>(v[c]) : acc[c] * 32 + v[c];
+  }
+#pragma unroll
+  for (int c = 0; c < 8; ++c) S[c] += static_cast<__int128>(acc[c]) << (5 * (P - S1));
+}
+
+// Add the P accumulators of 16 columns, sum_s C_s 2^(5 (P - 1 - s)), to S.
+template <int P>
+__device__ __forceinline__ void drain16(uint32_t taddr, __int128* S) {
+  constexpr int H = (P + 1) / 2;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    fold_range<P, 0, H>(taddr + 8u * h, S + 8 * h);
+    if constexpr (H < P) fold_range<P, H, P>(taddr + 8u * h, S + 8 * h);
+  }
 }
 
 __device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, int& tm, int& tn) {
@@ -146,59 +247,95 @@ __global__ void __launch_bounds__(kThreadsTC, 1) gemm_f8tc_kernel(const __grid_c
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cl = kp.cl;
+  const uint16_t cl_mask = static_cast<uint16_t>((1u << cl) - 1u);
+  const int crank = cl > 1 ? static_cast<int>(cluster_ctarank()) : 0;
+  const int cid = cl > 1 ? static_cast<int>(cluster_id_x()) : static_cast<int>(blockIdx.x);
+  const int ncl = cl > 1 ? static_cast<int>(cluster_count_x()) : static_cast<int>(gridDim.x);
   if (threadIdx.x == 0) {
     for (int s = 0; s < Cfg::kStages; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], static_cast<uint32_t>(cl));  // one MMA commit from each CTA of the cluster
     }
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, kEpiThreads);
     *abort_flag = 0;
     fence_mbar_init();
   }
-  if (warp == 5) {  // the whole warp allocates the tensor memory
+  if (warp == kMmaWarp) {  // the whole warp allocates the tensor memory
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     tc_fence_before();
   }
-  __syncthreads();
+  // barriers initialised in every CTA before any CTA multicasts into them
+  if (cl > 1)
+    cluster_sync_all();
+  else
+    __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  const int ntiles = kp.tiles_m * kp.tiles_n;
-  const int my_tiles = static_cast<int>(blockIdx.x) < ntiles ? (ntiles - 1 - static_cast<int>(blockIdx.x)) / gridDim.x + 1 : 0;
+  // the cluster walks tiles of 128 rows x (cl x 32) columns; CTA `crank` owns
+  // the crank-th 32-column tile of each
+  const int ntiles = kp.tiles_m * kp.tiles_ng;
+  const int my_tiles = cid < ntiles ? (ntiles - 1 - cid) / ncl + 1 : 0;
   const int drains_per_tile = (kp.nk32 + kp.kc32 - 1) / kp.kc32;
 
-  if (warp == 4) {
+  if (warp == kProducerWarp) {
     // ---------------------------------------------------------------- producer
     if (lane == 0) {
       tma_prefetch_desc(&kp.tA);
       tma_prefetch_desc(&kp.tB);
+      const int piece_rows = kBM / cl;
       const uint32_t total = static_cast<uint32_t>(my_tiles) * static_cast<uint32_t>(kp.nk32);
+      bool ok = true;
       for (uint32_t j = 0; j < total; ++j) {
         const uint32_t stage = j % Cfg::kStages;
+        // the stage is free once every CTA of the cluster has consumed it
         if (j >= static_cast<uint32_t>(Cfg::kStages) &&
-            !wait_or_abort(&empty[stage], ((j / Cfg::kStages) & 1u) ^ 1u, abort_flag, kp.status))
+            !wait_or_abort(&empty[stage], ((j / Cfg::kStages) & 1u) ^ 1u, abort_flag, kp.status)) {
+          ok = false;
           break;
-        const int tile = blockIdx.x + static_cast<int>(j / kp.nk32) * gridDim.x;
+        }
+        const int tile = cid + static_cast<int>(j / kp.nk32) * ncl;
         const int kk = static_cast<int>(j % kp.nk32);
-        int tm, tn;
-        tile_coords(tile, kp.tiles_m, kp.tiles_n, tm, tn);
+        int tm, tg;
+        tile_coords(tile, kp.tiles_m, kp.tiles_ng, tm, tg);
+        const int tn = tg * cl + crank;
         mbar_arrive_expect_tx(&full[stage], Cfg::kStageBytes);
         uint8_t* sA = smem + stage * Cfg::kStageBytes;
-        uint8_t* sB = sA + P * Cfg::kBlkA;
+        uint8_t* sB = sA + Cfg::kGroups * Cfg::kBlkAg;
+        // A: slices 4g .. 4g+3 of the chunk in one 128-byte box (a group that
+        // runs past slice P-1 reads the next chunk's slices, or the zero fill
+        // past the last chunk; the MMAs never use them)
+        if (cl > 1) {
 #pragma unroll
-        for (int t = 0; t < P; ++t)
-          tma_load_2d(sA + t * Cfg::kBlkA, &kp.tA, &full[stage], (kk * P + t) * 32, tm * kBM);
+          for (int g = 0; g < Cfg::kGroups; ++g)
+            tma_load_2d_mc(sA + g * Cfg::kBlkAg + crank * piece_rows * 128, &kp.tA, &full[stage],
+                           (kk * P + 4 * g) * 32, tm * kBM + crank * piece_rows, cl_mask);
+        } else {
+#pragma unroll
+          for (int g = 0; g < Cfg::kGroups; ++g)
+            tma_load_2d(sA + g * Cfg::kBlkAg, &kp.tA, &full[stage], (kk * P + 4 * g) * 32, tm * kBM);
+        }
 #pragma unroll
         for (int t = 0; t < P; ++t)
           tma_load_2d(sB + t * Cfg::kBlkB, &kp.tB, &full[stage], (kk * P + t) * 32, tn * kBN);
       }
+      // Drain: wait until the last commits of every CTA of the cluster have
+      // arrived on this CTA's stage barriers, so none lands after it exits.
+      if (ok && cl > 1) {
+        for (uint32_t j = total; j < total + Cfg::kStages; ++j) {
+          if (j < static_cast<uint32_t>(Cfg::kStages)) continue;
+          const uint32_t stage = j % Cfg::kStages;
+          if (!wait_or_abort(&empty[stage], ((j / Cfg::kStages) & 1u) ^ 1u, abort_flag, kp.status)) break;
+        }
+      }
     }
     __syncwarp();
-  } else if (warp == 5) {
+  } else if (warp == kMmaWarp) {
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
       uint32_t it = 0, drain = 0;
@@ -220,10 +357,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1) gemm_f8tc_kernel(const __grid_c
           }
           tc_fence_after();
           const uint32_t sA = base + stage * Cfg::kStageBytes;
-          const uint32_t sB = sA + P * Cfg::kBlkA;
+          const uint32_t sB = sA + Cfg::kGroups * Cfg::kBlkAg;
 #pragma unroll
           for (int i = 0; i < P; ++i) {
-            const uint64_t adesc = smem_desc_k32(sA + i * Cfg::kBlkA);
+            const uint64_t adesc = smem_desc_k128(sA + (i >> 2) * Cfg::kBlkAg + (i & 3) * 32);
             // columns [32 i, 32 P) += A'_i x [B'_0 .. B'_{P-1-i}], N split at 256
 #pragma unroll
             for (int q = 0; q * 256 < (P - i) * kBN; ++q) {
@@ -233,7 +370,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1) gemm_f8tc_kernel(const __grid_c
               umma_e4m3(tmem + static_cast<uint32_t>(i * kBN + q * 256), adesc, bdesc, idesc_e4m3(kBM, n), acc);
             }
           }
-          umma_commit(&empty[stage]);  // the stage is free once these MMAs finish
+          // the stage is free (in every CTA of the cluster) once these MMAs finish
+          if (cl > 1)
+            umma_commit_mc(&empty[stage], cl_mask);
+          else
+            umma_commit(&empty[stage]);
           if ((kk + 1) % kp.kc32 == 0 || kk + 1 == kp.nk32) {
             umma_commit(acc_full);  // accumulators ready for the epilogue
             ++drain;
@@ -244,32 +385,28 @@ __global__ void __launch_bounds__(kThreadsTC, 1) gemm_f8tc_kernel(const __grid_c
     __syncwarp();
   } else {
     // ---------------------------------------------------------------- epilogue (warps 0-3)
-    const int row_in_tile = threadIdx.x;  // TMEM lane
-    const uint32_t lane_base = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+    // warp w reads TMEM lanes 32 (w % 4) .. +31 (tile rows) and columns
+    // 16 (w / 4) .. +15 of every accumulator
+    const int row_in_tile = (warp & 3) * 32 + lane;
+    const int c0 = (warp >> 2) * 16;
+    const uint32_t lane_base = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16) + static_cast<uint32_t>(c0);
     uint32_t drain = 0;
     bool stop = false;
     for (int t = 0; t < my_tiles && !stop; ++t) {
-      const int tile = blockIdx.x + t * gridDim.x;
-      int tm, tn;
-      tile_coords(tile, kp.tiles_m, kp.tiles_n, tm, tn);
-      __int128 S[kBN];
+      const int tile = cid + t * ncl;
+      int tm, tg;
+      tile_coords(tile, kp.tiles_m, kp.tiles_ng, tm, tg);
+      const int tn = tg * cl + crank;
+      __int128 S[16];
 #pragma unroll
-      for (int c = 0; c < kBN; ++c) S[c] = 0;
+      for (int c = 0; c < 16; ++c) S[c] = 0;
       for (int d = 0; d < drains_per_tile; ++d, ++drain) {
         if (!wait_or_abort(acc_full, drain & 1u, abort_flag, kp.status)) {
           stop = true;
           break;
         }
         tc_fence_after();
-#pragma unroll 1
-        for (int s = 0; s < P; ++s) {
-          float v[kBN];
-          tmem_ld32(lane_base + static_cast<uint32_t>(s * kBN), v);
-          const int sh = 5 * (P - 1 - s);
-#pragma unroll
-          for (int c = 0; c < kBN; ++c)
-            S[c] += static_cast<__int128>(__float2ll_rn(v[c])) * (static_cast<__int128>(1) << sh);
-        }
+        drain16<P>(lane_base, S);
         tc_fence_before();
         mbar_arrive(acc_empty);
       }
@@ -278,8 +415,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) gemm_f8tc_kernel(const __grid_c
       if (row < kp.M) {
         const int erow = kp.EA[row] + kp.escale;
 #pragma unroll
-        for (int c = 0; c < kBN; ++c) {
-          const int col = tn * kBN + c;
+        for (int c = 0; c < 16; ++c) {
+          const int col = tn * kBN + c0 + c;
           if (col >= kp.N) continue;
           double dv = i128_to_double_rn(S[c]);
           double r = scale2(dv, erow + kp.FB[col]);
@@ -296,11 +433,42 @@ __global__ void __launch_bounds__(kThreadsTC, 1) gemm_f8tc_kernel(const __grid_c
     }
   }
   tc_fence_before();
-  __syncthreads();
-  if (warp == 5) {
+  // no CTA leaves while a peer may still write into its shared memory
+  if (cl > 1)
+    cluster_sync_all();
+  else
+    __syncthreads();
+  if (warp == kMmaWarp) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }
+}
+
+// Largest number of co-resident clusters of `cl` CTAs of this kernel (0 if
+// it cannot run with that cluster size).
+template <int P, int OUT>
+int max_clusters(int cl) {
+  using Cfg = CfgTC<P>;
+  if (cudaFuncSetAttribute(gemm_f8tc_kernel<P, OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem) !=
+      cudaSuccess)
+    return 0;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = static_cast<unsigned>(cl);
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(static_cast<unsigned>(cl) * 64u);
+  cfg.blockDim = dim3(kThreadsTC);
+  cfg.dynamicSmemBytes = Cfg::kSmem;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, gemm_f8tc_kernel<P, OUT>, &cfg) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  return n;
 }
 
 template <int P, int OUT>
@@ -309,6 +477,8 @@ cudaError_t launch_tc(const GemmIArgs& a, cudaStream_t st) {
   cudaError_t e =
       cudaFuncSetAttribute(gemm_f8tc_kernel<P, OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
   if (e != cudaSuccess) return e;
+  const int cl = a.cluster;
+  if (cl != 1 && cl != 2 && cl != 4) return cudaErrorInvalidValue;
   KParamsTC kp;
   kp.tA = *a.descA;
   kp.tB = *a.descB;
@@ -318,6 +488,8 @@ cudaError_t launch_tc(const GemmIArgs& a, cudaStream_t st) {
   kp.kc32 = a.kc32;
   kp.tiles_m = (a.M + kBM - 1) / kBM;
   kp.tiles_n = (a.N + kBN - 1) / kBN;
+  kp.cl = cl;
+  kp.tiles_ng = (kp.tiles_n + cl - 1) / cl;
   kp.EA = a.EA;
   kp.FB = a.FB;
   kp.escale = -8 - 5 * (P - 1);
@@ -326,17 +498,51 @@ cudaError_t launch_tc(const GemmIArgs& a, cudaStream_t st) {
   kp.C = a.C;
   kp.ldc = a.ldc;
   kp.status = a.status;
-  const int ntiles = kp.tiles_m * kp.tiles_n;
+  const int ntiles = kp.tiles_m * kp.tiles_ng;
   if (ntiles == 0 || kp.nk32 == 0) return cudaSuccess;
-  const int grid = ntiles < a.num_sms ? ntiles : a.num_sms;
-  gemm_f8tc_kernel<P, OUT><<<grid, kThreadsTC, Cfg::kSmem, st>>>(kp);
-  return cudaGetLastError();
+  if (cl == 1) {
+    const int grid = ntiles < a.num_sms ? ntiles : a.num_sms;
+    gemm_f8tc_kernel<P, OUT><<<grid, kThreadsTC, Cfg::kSmem, st>>>(kp);
+    return cudaGetLastError();
+  }
+  static int cached[3] = {-1, -1, -1};  // per cluster size 1, 2, 4 (index cl / 2)
+  int& mc = cached[cl / 2];
+  if (mc < 0) mc = max_clusters<P, OUT>(cl);
+  if (mc <= 0) return cudaErrorInvalidConfiguration;
+  const int nclusters = ntiles < mc ? ntiles : mc;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = static_cast<unsigned>(cl);
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(static_cast<unsigned>(nclusters * cl));
+  cfg.blockDim = dim3(kThreadsTC);
+  cfg.dynamicSmemBytes = Cfg::kSmem;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, gemm_f8tc_kernel<P, OUT>, kp);
 }
 
 }  // namespace
 
 int gemm_f8tc_tile_m() { return kBM; }
 int gemm_f8tc_tile_n() { return kBN; }
+
+// CTAs per cluster for the E4M3 tcgen05 kernel: EMU_TC_CLUSTER (1, 2 or 4)
+// if set, else 2 (pairs of CTAs halve the L2 reads of A and still fill all
+// 152 SMs; clusters of 4 leave some SMs idle).  The A tensor map's box is
+// 128 / cluster rows.
+int gemm_f8tc_cluster() {
+  static int v = 0;
+  if (v == 0) {
+    const char* e = std::getenv("EMU_TC_CLUSTER");
+    const int x = e ? std::atoi(e) : 2;
+    v = (x == 1 || x == 2 || x == 4) ? x : 2;
+  }
+  return v;
+}
 
 cudaError_t launch_gemm_f8tc(int p, int out_mode, const GemmIArgs& a, cudaStream_t st) {
 #define EMU_TC(PP)                                                \

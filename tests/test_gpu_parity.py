@@ -326,6 +326,8 @@ CASES_F8 = [
     (65, 33, 31, 1, 0.5, 2),
     (129, 70, 500, 12, 4.0, 4),
     (64, 40, 6000, 11, 2.0, 6),     # k > K_c(11) = 5888: two FP32-exact chunks
+    (1000, 1000, 96, 12, 1.0, 7),   # several tiles per cluster of CTAs; 32 column tiles
+    (300, 170, 64, 10, 0.5, 8),     # 6 column tiles: the last cluster group half empty
 ]
 
 
