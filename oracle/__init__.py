@@ -76,6 +76,7 @@ def _load():
                 "orc_split_F8": (None, [i64, i64, vp, vp, i32, vp]),
                 "orc_chunk_len_F8": (i64, [i32]),
                 "orc_emu_F8": (i32, [i64, i64, i64, i32, dbl, vp, vp, dbl, vp, vp, i32]),
+                "orc_emu_Z4M_I": (i32, [i64, i64, i64, i32, i32, dbl, dbl, vp, vp, dbl, dbl, vp, vp, i32]),
                 "orc_dd_gemm": (None, [i64, i64, i64, vp, vp, vp, vp]),
                 "orc_dd_zgemm": (None, [i64, i64, i64, vp, vp, vp, vp]),
             }
@@ -332,6 +333,28 @@ def emu_Z3M(A, B, nm: int, alpha: complex = 1.0, beta: complex = 0.0, C=None) ->
     if rc:
         raise ValueError("non-finite input")
     return Cz
+
+
+def emu_Z4M_I(A, B, p: int, f8: bool = False, alpha: complex = 1.0, beta: complex = 0.0, C=None,
+              out_f32: bool = False) -> np.ndarray:
+    """Scheme I complex (4M, reading R8) C = alpha*A@B + beta*C with INT8
+    (f8=False) or E4M3 (f8=True) slices.  out_f32: complex64 result (CGEMM)."""
+    A = np.ascontiguousarray(A, dtype=np.complex128)
+    Bt = np.ascontiguousarray(np.asarray(B, dtype=np.complex128).T)
+    m, k = A.shape
+    n = Bt.shape[0]
+    alpha, beta = complex(alpha), complex(beta)
+    if out_f32:
+        Cf = np.zeros((m, n), dtype=np.complex64) if C is None else np.array(C, dtype=np.complex64, order="C")
+        Cz = np.zeros((1, 1), dtype=np.complex128)
+    else:
+        Cz = np.zeros((m, n), dtype=np.complex128) if C is None else np.array(C, dtype=np.complex128, order="C")
+        Cf = np.zeros((1, 1), dtype=np.complex64)
+    rc = _load().orc_emu_Z4M_I(m, n, k, p, int(f8), alpha.real, alpha.imag, _p(A), _p(Bt), beta.real, beta.imag,
+                               _p(Cz), _p(Cf), int(out_f32))
+    if rc:
+        raise ValueError("non-finite input")
+    return Cf if out_f32 else Cz
 
 
 # ---------------------------------------------------------------- reference

@@ -59,6 +59,18 @@
  *       every slice product is exact and FP32 sums of them are exact while
  *       |sum| <= 2^24.  Result: RN(S) * 2^(E_i + F_j - 8 - 5(p-1)) with
  *       S = sum_s 32^(p-1-s) C_s exact.
+ *   R8  Scheme I complex (the 4M formulation the paper uses for its Scheme I
+ *       CGEMM/ZGEMM, Sec. VI): one exponent per complex row of A and per
+ *       complex column of B (over real and imaginary parts); the four real
+ *       products are the triangle sums T_s(X, Y) = sum_{t<=s} <X_t, Y_{s-t}>
+ *       of Eq. (2) on the slices of Re A, Im A, Re B, Im B and of -Im B (the
+ *       slices of the negated integers, as for any other operand), combined
+ *       exactly before the single rounding of R2:
+ *         S_re = sum_s w_s (T_s(Re A, Re B) + T_s(Im A, -Im B)),
+ *         S_im = sum_s w_s (T_s(Re A, Im B) + T_s(Im A, Re B)),
+ *       w_s = 2^(beta (p-1-s)).  This is Scheme I applied to the real
+ *       matrices [Re A, Im A] and [[Re B, Im B], [-Im B, Re B]].  The complex
+ *       BLAS update is that of R6 for complex numbers.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -830,5 +842,109 @@ out:
   free(F);
   free(DA);
   free(DB);
+  return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Scheme I complex, 4M (reading R8)                                   */
+/* ------------------------------------------------------------------ */
+
+/* T_s for one output: sum_{t<=s} <X_t, Y_{s-t}> over k, exact. */
+static int64_t tri_sum(const int16_t *DX, int64_t rx, int64_t nx, const int16_t *DY, int64_t ry, int64_t ny,
+                       int64_t k, int s) {
+  int64_t acc = 0;
+  for (int t = 0; t <= s; ++t) {
+    const int16_t *a = DX + ((int64_t)t * nx + rx) * k;
+    const int16_t *b = DY + ((int64_t)(s - t) * ny + ry) * k;
+    for (int64_t h = 0; h < k; ++h) acc += (int64_t)a[h] * (int64_t)b[h];
+  }
+  return acc;
+}
+
+/* A: m x k complex, Bt: n x k complex (B^T, not conjugated), both
+ * interleaved (re, im).  f8 selects the slices: 0 = INT8 bytes (R1), 1 =
+ * E4M3 digits (R7).  C: m x n complex (interleaved) in/out; with out_f32 the
+ * result goes to Cf (m x n complex float, interleaved), each component
+ * rounded once more to binary32 (CGEMM).  Returns 0, or -1 on non-finite
+ * input. */
+int orc_emu_Z4M_I(int64_t m, int64_t n, int64_t k, int p, int f8, double alpha_re, double alpha_im,
+                  const double *A, const double *Bt, double beta_re, double beta_im, double *C, float *Cf,
+                  int out_f32) {
+  const int beta_bits = f8 ? 5 : 8;
+  const int escale = f8 ? -8 - 5 * (p - 1) : -14 - 8 * (p - 1);
+  size_t mk = (size_t)(m * k > 0 ? m * k : 1), nk = (size_t)(n * k > 0 ? n * k : 1);
+  int32_t *E = malloc(sizeof(int32_t) * (m > 0 ? m : 1));
+  int32_t *F = malloc(sizeof(int32_t) * (n > 0 ? n : 1));
+  double *Ar = malloc(sizeof(double) * mk), *Ai = malloc(sizeof(double) * mk);
+  double *Br = malloc(sizeof(double) * nk), *Bi = malloc(sizeof(double) * nk), *Bn = malloc(sizeof(double) * nk);
+  int16_t *DAr = malloc(sizeof(int16_t) * p * mk), *DAi = malloc(sizeof(int16_t) * p * mk);
+  int16_t *DBr = malloc(sizeof(int16_t) * p * nk), *DBi = malloc(sizeof(int16_t) * p * nk);
+  int16_t *DBn = malloc(sizeof(int16_t) * p * nk);
+  int rc = 0;
+  if (orc_row_exponents_z(m, k, A, E) || orc_row_exponents_z(n, k, Bt, F)) {
+    rc = -1;
+    goto out;
+  }
+  for (int64_t q = 0; q < m * k; ++q) {
+    Ar[q] = A[2 * q];
+    Ai[q] = A[2 * q + 1];
+  }
+  for (int64_t q = 0; q < n * k; ++q) {
+    Br[q] = Bt[2 * q];
+    Bi[q] = Bt[2 * q + 1];
+    Bn[q] = -Bt[2 * q + 1];
+  }
+  if (f8) {
+    orc_split_F8(m, k, Ar, E, p, DAr);
+    orc_split_F8(m, k, Ai, E, p, DAi);
+    orc_split_F8(n, k, Br, F, p, DBr);
+    orc_split_F8(n, k, Bi, F, p, DBi);
+    orc_split_F8(n, k, Bn, F, p, DBn);
+  } else {
+    orc_split_I(m, k, Ar, E, p, DAr);
+    orc_split_I(m, k, Ai, E, p, DAi);
+    orc_split_I(n, k, Br, F, p, DBr);
+    orc_split_I(n, k, Bi, F, p, DBi);
+    orc_split_I(n, k, Bn, F, p, DBn);
+  }
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int64_t i = 0; i < m; ++i)
+    for (int64_t j = 0; j < n; ++j) {
+      i128 Sre = 0, Sim = 0;
+      for (int s = 0; s < p; ++s) {
+        const int64_t tre = tri_sum(DAr, i, m, DBr, j, n, k, s) + tri_sum(DAi, i, m, DBn, j, n, k, s);
+        const int64_t tim = tri_sum(DAr, i, m, DBi, j, n, k, s) + tri_sum(DAi, i, m, DBr, j, n, k, s);
+        Sre += (i128)tre << (beta_bits * (p - 1 - s));
+        Sim += (i128)tim << (beta_bits * (p - 1 - s));
+      }
+      const double rr = ldexp(i128_to_double(Sre), E[i] + F[j] + escale);
+      const double ri = ldexp(i128_to_double(Sim), E[i] + F[j] + escale);
+      double cr = 0.0, ci = 0.0;
+      if (beta_re != 0.0 || beta_im != 0.0) {
+        cr = out_f32 ? (double)Cf[2 * (i * n + j)] : C[2 * (i * n + j)];
+        ci = out_f32 ? (double)Cf[2 * (i * n + j) + 1] : C[2 * (i * n + j) + 1];
+      }
+      zupdate(alpha_re, alpha_im, rr, ri, beta_re, beta_im, &cr, &ci);
+      if (out_f32) {
+        Cf[2 * (i * n + j)] = (float)cr;
+        Cf[2 * (i * n + j) + 1] = (float)ci;
+      } else {
+        C[2 * (i * n + j)] = cr;
+        C[2 * (i * n + j) + 1] = ci;
+      }
+    }
+out:
+  free(E);
+  free(F);
+  free(Ar);
+  free(Ai);
+  free(Br);
+  free(Bi);
+  free(Bn);
+  free(DAr);
+  free(DAi);
+  free(DBr);
+  free(DBi);
+  free(DBn);
   return rc;
 }
