@@ -117,8 +117,9 @@ emu_status_t emu_selftest_wait(emu_handle_t h, int64_t limit_cycles, emu_stream_
 /* Human-readable name of a status code (static string). */
 const char *emu_status_string(emu_status_t s);
 
-/* Bytes of device workspace one call needs (is_complex selects the 3M
- * Scheme II layout: three residue sets per operand). */
+/* Bytes of device workspace one call needs (is_complex selects the complex
+ * layouts: three residue sets per operand for the Scheme II 3M method, the
+ * real embedding plus the slices of the 2K-deep product for Scheme I 4M). */
 emu_status_t emu_workspace_size(emu_scheme_t scheme, int64_t m, int64_t n, int64_t k, int p_or_nm,
                                 int is_complex, size_t *bytes_host);
 
@@ -160,15 +161,35 @@ emu_status_t emu_sgemm(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n
                        float beta, float *C, int64_t ldc, emu_scheme_t scheme, int p_or_nm,
                        emu_stream_t stream);
 
-/* complex128 C = alpha*A*B + beta*C by Scheme II with the 3M method
- * (Sec. IV-B, Eq. 16): per modulus T1 = Re*Re, T2 = Im*Im, T3 = Sum*Sum,
- * Re(C') = T1 - T2, Im(C') = T3 - T1 - T2 (mod m_l), one CRT per part.
- * One power-of-two scale per row of A / column of B covers both parts.
- * scheme must be EMU_SCHEME_II (EMU_SCHEME_I returns EMU_ERR_UNSUPPORTED). */
+/* complex128 C = alpha*A*B + beta*C.  A, B, C are interleaved (re, im)
+ * arrays; lda, ldb, ldc count complex elements; alpha_host and beta_host
+ * are host arrays {re, im}.  One power-of-two scale per row of A / column of
+ * B covers both parts.
+ *  - EMU_SCHEME_II, p_or_nm = N moduli: the 3M method (Sec. IV-B, Eq. 16):
+ *    per modulus T1 = Re*Re, T2 = Im*Im, T3 = Sum*Sum, Re(C') = T1 - T2,
+ *    Im(C') = T3 - T1 - T2 (mod m_l), one CRT per part.
+ *  - EMU_SCHEME_I / EMU_SCHEME_I_F8, p_or_nm = p slices: the 4M formulation
+ *    (the paper's Scheme I CGEMM/ZGEMM, Sec. VI): the four real triangle
+ *    sums of Eq. 2, the Im*Im term from the slices of -Im B, combined exactly
+ *    before one rounding per part -- Scheme I on the real matrices [Re A, Im A]
+ *    and [[Re B, Im B], [-Im B, Re B]].  Workspace: emu_workspace_size with
+ *    is_complex = 1 (the embedding of A and B, 48 (M + 2N) K bytes, plus the
+ *    slices of the 2K-deep real product).
+ * beta == 0: C is not read.  Errors as emu_dgemm. */
 emu_status_t emu_zgemm(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k,
                        const double *alpha_host, const double *A, int64_t lda, const double *B,
                        int64_t ldb, const double *beta_host, double *C, int64_t ldc,
-                       emu_scheme_t scheme, int nm, emu_stream_t stream);
+                       emu_scheme_t scheme, int p_or_nm, emu_stream_t stream);
+
+/* complex64 C = alpha*A*B + beta*C by Scheme I (4M, as emu_zgemm with
+ * EMU_SCHEME_I or EMU_SCHEME_I_F8): inputs widened to binary64 exactly, the
+ * complex update done in binary64, each part rounded once more to binary32
+ * (the paper's Scheme I CGEMM, Sec. VI).  alpha_host, beta_host: {re, im}.
+ * EMU_SCHEME_II returns EMU_ERR_UNSUPPORTED. */
+emu_status_t emu_cgemm(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k,
+                       const float *alpha_host, const float *A, int64_t lda, const float *B,
+                       int64_t ldb, const float *beta_host, float *C, int64_t ldc,
+                       emu_scheme_t scheme, int p_or_nm, emu_stream_t stream);
 
 /* Allocation-free Scheme I DGEMM.  The paper has no counterpart: this entry
  * point exists for callers that may not allocate device memory while they

@@ -58,6 +58,8 @@ _SIGS = {
                          _i32, _vp]),
     "emu_zgemm": (_i32, [_vp, _i32, _i64, _i64, _i64, _vp, _vp, _i64, _vp, _i64, _vp, _vp, _i64, _i32, _i32,
                          _vp]),
+    "emu_cgemm": (_i32, [_vp, _i32, _i64, _i64, _i64, _vp, _vp, _i64, _vp, _i64, _vp, _vp, _i64, _i32, _i32,
+                         _vp]),
     "emu_split_rows": (_i64, [_i64]),
     "emu_split_cols_I": (_i64, [_i64, _i32]),
     "emu_split_cols_II": (_i64, [_i64]),
@@ -215,8 +217,10 @@ def sgemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, scheme="I", p: in
     return C
 
 
-def zgemm(A, B, C=None, alpha: complex = 1.0, beta: complex = 0.0, nm: int = 16, handle=None, stream=None):
-    """complex128 C = alpha*A@B + beta*C through emu_zgemm (Scheme II, 3M)."""
+def zgemm(A, B, C=None, alpha: complex = 1.0, beta: complex = 0.0, nm: int = 16, handle=None, stream=None,
+          scheme="II", p: int | None = None):
+    """complex128 C = alpha*A@B + beta*C through emu_zgemm: Scheme II 3M with
+    nm moduli (default), or scheme="I" / "I_F8" (4M) with p slices."""
     import torch
     m, k = A.shape
     n = B.shape[1]
@@ -227,8 +231,27 @@ def zgemm(A, B, C=None, alpha: complex = 1.0, beta: complex = 0.0, nm: int = 16,
     al = (ctypes.c_double * 2)(complex(alpha).real, complex(alpha).imag)
     be = (ctypes.c_double * 2)(complex(beta).real, complex(beta).imag)
     h = handle or default_handle(A.device.index or 0)
-    check(emu_zgemm(h.h, layout, m, n, k, al, _ptr(A), lda, _ptr(B), ldb, be, _ptr(C), ldc, EMU_SCHEME_II,
-                    nm, _stream_ptr(stream)), "emu_zgemm")
+    sc = _scheme(scheme)
+    check(emu_zgemm(h.h, layout, m, n, k, al, _ptr(A), lda, _ptr(B), ldb, be, _ptr(C), ldc, sc,
+                    nm if sc == EMU_SCHEME_II else p, _stream_ptr(stream)), "emu_zgemm")
+    return C
+
+
+def cgemm(A, B, C=None, alpha: complex = 1.0, beta: complex = 0.0, p: int = 4, scheme="I", handle=None,
+          stream=None):
+    """complex64 C = alpha*A@B + beta*C through emu_cgemm (Scheme I, 4M)."""
+    import torch
+    m, k = A.shape
+    n = B.shape[1]
+    if C is None:
+        C = torch.empty((m, n), dtype=torch.complex64, device=A.device)
+        beta = 0.0
+    layout, lda, ldb, ldc = _layout_of(A, B, C)
+    al = (ctypes.c_float * 2)(complex(alpha).real, complex(alpha).imag)
+    be = (ctypes.c_float * 2)(complex(beta).real, complex(beta).imag)
+    h = handle or default_handle(A.device.index or 0)
+    check(emu_cgemm(h.h, layout, m, n, k, al, _ptr(A), lda, _ptr(B), ldb, be, _ptr(C), ldc, _scheme(scheme), p,
+                    _stream_ptr(stream)), "emu_cgemm")
     return C
 
 

@@ -218,19 +218,22 @@ __global__ void scale_c_kernel(T* C, int64_t ldc, int64_t m, int64_t n, double b
   T* p = C + i * ldc + j;
   *p = beta == 0.0 ? T(0) : static_cast<T>(__dmul_rn(beta, static_cast<double>(*p)));
 }
-__global__ void scale_z_kernel(double* C, int64_t ldc, int64_t m, int64_t n, double br, double bi) {
+// k == 0: C = beta * C for complex beta (C not read when beta == 0); float
+// C (CGEMM) is widened, updated in binary64 and rounded once per part.
+template <typename T>
+__global__ void scale_z_kernel(T* C, int64_t ldc, int64_t m, int64_t n, double br, double bi) {
   int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (idx >= m * n) return;
   int64_t i = idx / n, j = idx % n;
-  double* p = C + 2 * (i * ldc + j);
+  T* p = C + 2 * (i * ldc + j);
   if (br == 0.0 && bi == 0.0) {
-    p[0] = 0.0;
-    p[1] = 0.0;
+    p[0] = T(0);
+    p[1] = T(0);
     return;
   }
-  double cr = p[0], ci = p[1];
-  p[0] = __fma_rn(br, cr, -__dmul_rn(bi, ci));
-  p[1] = __fma_rn(br, ci, __dmul_rn(bi, cr));
+  double cr = static_cast<double>(p[0]), ci = static_cast<double>(p[1]);
+  p[0] = static_cast<T>(__fma_rn(br, cr, -__dmul_rn(bi, ci)));
+  p[1] = static_cast<T>(__fma_rn(br, ci, __dmul_rn(bi, cr)));
 }
 
 // One warp waits on an mbarrier that nothing arrives on; the bounded wait
@@ -612,8 +615,8 @@ emu_status_t emu_workspace_size(emu_scheme_t scheme, int64_t m, int64_t n, int64
                                 int is_complex, size_t* bytes) {
   if (!bytes || m < 0 || n < 0 || k < 0) return EMU_ERR_INVALID_ARG;
   if (scheme == EMU_SCHEME_I || scheme == EMU_SCHEME_I_F8) {
-    if (p_or_nm < EMU_P_MIN || p_or_nm > EMU_P_MAX || is_complex) return EMU_ERR_UNSUPPORTED;
-    *bytes = plan_I(m, n, k, p_or_nm).bytes;
+    if (p_or_nm < EMU_P_MIN || p_or_nm > EMU_P_MAX) return EMU_ERR_UNSUPPORTED;
+    *bytes = is_complex ? workspace_complex_I(m, n, k, p_or_nm) : plan_I(m, n, k, p_or_nm).bytes;
     return EMU_OK;
   }
   if (scheme == EMU_SCHEME_II) {
@@ -689,7 +692,6 @@ emu_status_t emu_zgemm(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n
                        const double* alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
                        const double* beta, double* C, int64_t ldc, emu_scheme_t scheme, int nm,
                        emu_stream_t stream) {
-  if (scheme == EMU_SCHEME_I) return h ? EMU_ERR_UNSUPPORTED : EMU_ERR_INVALID_ARG;
   if (!alpha || !beta) return EMU_ERR_INVALID_ARG;
   emu_status_t s = gemm_common(h, layout, m, n, k, A, lda, B, ldb, C, ldc, scheme, nm);
   if (s != EMU_OK) return s;
@@ -699,11 +701,38 @@ emu_status_t emu_zgemm(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n
   if (v.M == 0 || v.N == 0) return EMU_OK;
   if (k == 0) {
     int64_t tot = v.M * v.N;
-    scale_z_kernel<<<static_cast<unsigned>((tot + 255) / 256), 256, 0, st>>>(C, ldc, v.M, v.N, beta[0], beta[1]);
+    scale_z_kernel<double>
+        <<<static_cast<unsigned>((tot + 255) / 256), 256, 0, st>>>(C, ldc, v.M, v.N, beta[0], beta[1]);
     return cuda_err(cudaGetLastError());
   }
+  if (scheme == EMU_SCHEME_I || scheme == EMU_SCHEME_I_F8)
+    return run_complex_I<double>(h, layout, m, n, k, A, lda, B, ldb, nm, scheme == EMU_SCHEME_I_F8, alpha, beta,
+                                 C, ldc, st);
   return run_scheme_II<double>(h, v, k, nm, 2, alpha[0], alpha[1], beta[0], beta[1], C, ldc, II_Z3M,
                                nullptr, st);
+}
+
+emu_status_t emu_cgemm(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k,
+                       const float* alpha, const float* A, int64_t lda, const float* B, int64_t ldb,
+                       const float* beta, float* C, int64_t ldc, emu_scheme_t scheme, int p_or_nm,
+                       emu_stream_t stream) {
+  if (!alpha || !beta) return EMU_ERR_INVALID_ARG;
+  if (scheme == EMU_SCHEME_II) return h ? EMU_ERR_UNSUPPORTED : EMU_ERR_INVALID_ARG;
+  emu_status_t s = gemm_common(h, layout, m, n, k, A, lda, B, ldb, C, ldc, scheme, p_or_nm);
+  if (s != EMU_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  View v;
+  normalize(layout, m, n, A, lda, B, ldb, &v);
+  if (v.M == 0 || v.N == 0) return EMU_OK;
+  const double al[2] = {alpha[0], alpha[1]}, be[2] = {beta[0], beta[1]};
+  if (k == 0) {
+    int64_t tot = v.M * v.N;
+    scale_z_kernel<float>
+        <<<static_cast<unsigned>((tot + 255) / 256), 256, 0, st>>>(C, ldc, v.M, v.N, be[0], be[1]);
+    return cuda_err(cudaGetLastError());
+  }
+  return run_complex_I<float>(h, layout, m, n, k, A, lda, B, ldb, p_or_nm, scheme == EMU_SCHEME_I_F8, al, be, C,
+                              ldc, st);
 }
 
 // ---------------------------------------------------------------- steps

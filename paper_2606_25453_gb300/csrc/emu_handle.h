@@ -57,4 +57,12 @@ emu_status_t run_scheme_I(emu_handle_s* h, const View& v, int64_t k, int p, doub
                           void* C, int64_t ldc, int out_mode, int32_t* partials, cudaStream_t st,
                           uint8_t* ws_override, bool f8 = false);
 
+// Scheme I complex (4M) through the real embedding; T = double (ZGEMM) or
+// float (CGEMM) for both the inputs and C.  alpha, beta: {re, im}.
+size_t workspace_complex_I(int64_t M, int64_t N, int64_t K, int p);
+template <typename T>
+emu_status_t run_complex_I(emu_handle_s* h, emu_layout_t layout, int64_t M, int64_t N, int64_t K, const T* A,
+                           int64_t lda, const T* B, int64_t ldb, int p, bool f8, const double* alpha,
+                           const double* beta, T* C, int64_t ldc, cudaStream_t st);
+
 }  // namespace emu
