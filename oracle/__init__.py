@@ -73,6 +73,7 @@ def _load():
                 "orc_emu_II": (i32, [i64, i64, i64, i32, dbl, vp, vp, dbl, vp, vp, i32]),
                 "orc_modprod_Z3M": (None, [i64, i64, i64, i32, vp, vp, vp, vp, vp, vp, vp, vp]),
                 "orc_emu_Z3M": (i32, [i64, i64, i64, i32, dbl, dbl, vp, vp, dbl, dbl, vp]),
+                "orc_emu_C3M": (i32, [i64, i64, i64, i32, dbl, dbl, vp, vp, dbl, dbl, vp]),
                 "orc_split_F8": (None, [i64, i64, vp, vp, i32, vp]),
                 "orc_chunk_len_F8": (i64, [i32]),
                 "orc_emu_F8": (i32, [i64, i64, i64, i32, dbl, vp, vp, dbl, vp, vp, i32]),
@@ -320,19 +321,27 @@ def modprod_Z3M(A3, B3t):
     return ore, oim
 
 
-def emu_Z3M(A, B, nm: int, alpha: complex = 1.0, beta: complex = 0.0, C=None) -> np.ndarray:
-    """Scheme II 3M complex C = alpha*A@B + beta*C (Eqs. 5-8, 16)."""
+def emu_Z3M(A, B, nm: int, alpha: complex = 1.0, beta: complex = 0.0, C=None, out_f32: bool = False) -> np.ndarray:
+    """Scheme II 3M complex C = alpha*A@B + beta*C (Eqs. 5-8, 16).  out_f32:
+    complex64 result (CGEMM; the inputs are used as given, widened exactly)."""
     A = np.ascontiguousarray(A, dtype=np.complex128)
     Bt = np.ascontiguousarray(np.asarray(B, dtype=np.complex128).T)
     m, k = A.shape
     n = Bt.shape[0]
-    Cz = np.zeros((m, n), dtype=np.complex128) if C is None else np.array(C, dtype=np.complex128, order="C")
     alpha, beta = complex(alpha), complex(beta)
-    rc = _load().orc_emu_Z3M(m, n, k, nm, alpha.real, alpha.imag, _p(A), _p(Bt), beta.real, beta.imag,
-                             _p(Cz))
+    if out_f32:
+        Cf = np.zeros((m, n), dtype=np.complex64) if C is None else np.array(C, dtype=np.complex64, order="C")
+        rc = _load().orc_emu_C3M(m, n, k, nm, alpha.real, alpha.imag, _p(A), _p(Bt), beta.real, beta.imag,
+                                 _p(Cf))
+        out = Cf
+    else:
+        Cz = np.zeros((m, n), dtype=np.complex128) if C is None else np.array(C, dtype=np.complex128, order="C")
+        rc = _load().orc_emu_Z3M(m, n, k, nm, alpha.real, alpha.imag, _p(A), _p(Bt), beta.real, beta.imag,
+                                 _p(Cz))
+        out = Cz
     if rc:
         raise ValueError("non-finite input")
-    return Cz
+    return out
 
 
 def emu_Z4M_I(A, B, p: int, f8: bool = False, alpha: complex = 1.0, beta: complex = 0.0, C=None,

@@ -653,9 +653,13 @@ static void zupdate(double ar, double ai, double rr, double ri, double br, doubl
 }
 
 /* Full 3M complex emulated product.  A: m x k complex (interleaved re, im),
- * Bt: n x k complex (Bt = B^T, NOT conjugated), C: m x n complex in/out. */
-int orc_emu_Z3M(int64_t m, int64_t n, int64_t k, int nm, double alpha_re, double alpha_im,
-                const double *A, const double *Bt, double beta_re, double beta_im, double *C) {
+ * Bt: n x k complex (Bt = B^T, NOT conjugated), C: m x n complex in/out.
+ * With out_f32 the result goes to Cf (m x n complex float, read when beta
+ * != 0): the complex update is done in binary64 as for C, then each part is
+ * rounded once more to binary32 (CGEMM). */
+static int emu_Z3M_core(int64_t m, int64_t n, int64_t k, int nm, double alpha_re, double alpha_im,
+                        const double *A, const double *Bt, double beta_re, double beta_im, double *C, float *Cf,
+                        int out_f32) {
   int32_t *E = malloc(sizeof(int32_t) * (m > 0 ? m : 1));
   int32_t *F = malloc(sizeof(int32_t) * (n > 0 ? n : 1));
   size_t sa = (size_t)(nm * m * k > 0 ? nm * m * k : 1), sb = (size_t)(nm * n * k > 0 ? nm * n * k : 1);
@@ -689,12 +693,17 @@ int orc_emu_Z3M(int64_t m, int64_t n, int64_t k, int nm, double alpha_re, double
         double ri = ldexp(vi, E[i] + F[j] - 2 * b);
         double cr = 0.0, ci = 0.0;
         if (beta_re != 0.0 || beta_im != 0.0) {
-          cr = C[2 * (i * n + j)];
-          ci = C[2 * (i * n + j) + 1];
+          cr = out_f32 ? (double)Cf[2 * (i * n + j)] : C[2 * (i * n + j)];
+          ci = out_f32 ? (double)Cf[2 * (i * n + j) + 1] : C[2 * (i * n + j) + 1];
         }
         zupdate(alpha_re, alpha_im, rr, ri, beta_re, beta_im, &cr, &ci);
-        C[2 * (i * n + j)] = cr;
-        C[2 * (i * n + j) + 1] = ci;
+        if (out_f32) {
+          Cf[2 * (i * n + j)] = (float)cr;
+          Cf[2 * (i * n + j) + 1] = (float)ci;
+        } else {
+          C[2 * (i * n + j)] = cr;
+          C[2 * (i * n + j) + 1] = ci;
+        }
       }
   }
 out:
@@ -706,6 +715,18 @@ out:
   free(ORe);
   free(OIm);
   return rc;
+}
+
+int orc_emu_Z3M(int64_t m, int64_t n, int64_t k, int nm, double alpha_re, double alpha_im,
+                const double *A, const double *Bt, double beta_re, double beta_im, double *C) {
+  return emu_Z3M_core(m, n, k, nm, alpha_re, alpha_im, A, Bt, beta_re, beta_im, C, NULL, 0);
+}
+
+/* CGEMM by the 3M method: A, Bt complex double (the complex64 inputs widened
+ * exactly), Cf complex float in/out. */
+int orc_emu_C3M(int64_t m, int64_t n, int64_t k, int nm, double alpha_re, double alpha_im,
+                const double *A, const double *Bt, double beta_re, double beta_im, float *Cf) {
+  return emu_Z3M_core(m, n, k, nm, alpha_re, alpha_im, A, Bt, beta_re, beta_im, NULL, Cf, 1);
 }
 
 /* ------------------------------------------------------------------ */

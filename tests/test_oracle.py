@@ -493,3 +493,19 @@ def test_golden_gemm_counts():
     g = golden()
     assert [p * (p + 1) // 2 for p in range(1, 9)] == [int(v) for v in g["scheme_I_int8_gemms"]]
     assert (8 + 1) / 2 == float(g["fusion_intensity_gain_p8"][0])
+
+
+def test_3m_cgemm_is_zgemm_rounded_once(orc):
+    """CGEMM by 3M: the complex64 inputs widened exactly, the update in
+    binary64, each part rounded once to binary32."""
+    m, n, k = 14, 9, 33
+    A, B = synth.gemm_pair_complex(m, n, k, 1.0, 51)
+    Af, Bf = A.astype(np.complex64), B.astype(np.complex64)
+    Aw, Bw = Af.astype(np.complex128), Bf.astype(np.complex128)
+    C0 = synth.test_matrix_complex(m, n, 1.0, 52).astype(np.complex64)
+    for al, be in ((1.0, 0.0), (0.5 - 2.0j, 1.5 + 0.25j)):
+        Cf = orc.emu_Z3M(Af, Bf, 10, alpha=al, beta=be, C=C0, out_f32=True)
+        Cz = orc.emu_Z3M(Aw, Bw, 10, alpha=al, beta=be, C=C0.astype(np.complex128))
+        assert Cf.dtype == np.complex64
+        assert np.array_equal(Cf.real, Cz.real.astype(np.float32))
+        assert np.array_equal(Cf.imag, Cz.imag.astype(np.float32))
