@@ -181,11 +181,11 @@ emu_status_t emu_zgemm(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n
                        int64_t ldb, const double *beta_host, double *C, int64_t ldc,
                        emu_scheme_t scheme, int p_or_nm, emu_stream_t stream);
 
-/* complex64 C = alpha*A*B + beta*C by Scheme I (4M, as emu_zgemm with
- * EMU_SCHEME_I or EMU_SCHEME_I_F8): inputs widened to binary64 exactly, the
- * complex update done in binary64, each part rounded once more to binary32
- * (the paper's Scheme I CGEMM, Sec. VI).  alpha_host, beta_host: {re, im}.
- * EMU_SCHEME_II returns EMU_ERR_UNSUPPORTED. */
+/* complex64 C = alpha*A*B + beta*C, as emu_zgemm: EMU_SCHEME_I /
+ * EMU_SCHEME_I_F8 (4M, p_or_nm = p) or EMU_SCHEME_II (3M, p_or_nm = N
+ * moduli).  Inputs widened to binary64 exactly, the complex update done in
+ * binary64, each part rounded once more to binary32 (the paper's CGEMM
+ * emulation, Sec. VI).  alpha_host, beta_host: {re, im}. */
 emu_status_t emu_cgemm(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k,
                        const float *alpha_host, const float *A, int64_t lda, const float *B,
                        int64_t ldb, const float *beta_host, float *C, int64_t ldc,

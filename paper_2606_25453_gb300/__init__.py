@@ -239,7 +239,8 @@ def zgemm(A, B, C=None, alpha: complex = 1.0, beta: complex = 0.0, nm: int = 16,
 
 def cgemm(A, B, C=None, alpha: complex = 1.0, beta: complex = 0.0, p: int = 4, scheme="I", handle=None,
           stream=None):
-    """complex64 C = alpha*A@B + beta*C through emu_cgemm (Scheme I, 4M)."""
+    """complex64 C = alpha*A@B + beta*C through emu_cgemm: Scheme I / I_F8
+    (4M, p slices) or Scheme II (3M, p = number of moduli)."""
     import torch
     m, k = A.shape
     n = B.shape[1]

@@ -717,7 +717,6 @@ emu_status_t emu_cgemm(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n
                        const float* beta, float* C, int64_t ldc, emu_scheme_t scheme, int p_or_nm,
                        emu_stream_t stream) {
   if (!alpha || !beta) return EMU_ERR_INVALID_ARG;
-  if (scheme == EMU_SCHEME_II) return h ? EMU_ERR_UNSUPPORTED : EMU_ERR_INVALID_ARG;
   emu_status_t s = gemm_common(h, layout, m, n, k, A, lda, B, ldb, C, ldc, scheme, p_or_nm);
   if (s != EMU_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -731,6 +730,8 @@ emu_status_t emu_cgemm(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n
         <<<static_cast<unsigned>((tot + 255) / 256), 256, 0, st>>>(C, ldc, v.M, v.N, be[0], be[1]);
     return cuda_err(cudaGetLastError());
   }
+  if (scheme == EMU_SCHEME_II)
+    return run_scheme_II<float>(h, v, k, p_or_nm, 2, al[0], al[1], be[0], be[1], C, ldc, II_C3M, nullptr, st);
   return run_complex_I<float>(h, layout, m, n, k, A, lda, B, ldb, p_or_nm, scheme == EMU_SCHEME_I_F8, al, be, C,
                               ldc, st);
 }

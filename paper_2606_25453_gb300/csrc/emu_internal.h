@@ -81,7 +81,7 @@ cudaError_t launch_gemm_f8tc(int p, int out_mode, const GemmIArgs& a, cudaStream
 int gemm_f8tc_cluster();
 
 // Scheme II kernel modes.
-enum GemmIIOut : int { II_F64 = 0, II_F32 = 1, II_RESIDUES = 2, II_Z3M = 3 };
+enum GemmIIOut : int { II_F64 = 0, II_F32 = 1, II_RESIDUES = 2, II_Z3M = 3, II_C3M = 4 };
 
 struct GemmIIArgs {
   const CUtensorMap* descA;

@@ -16,6 +16,8 @@
 // and T2 are kept as residues in registers, and Re = T1 - T2,
 // Im = T3 - T1 - T2 (mod m_l) feed two CRT sums.
 // II_RESIDUES writes the per-modulus residues (the paper's kernel output).
+#include <type_traits>
+
 #include "emu_internal.h"
 
 namespace emu {
@@ -172,7 +174,8 @@ template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_II_kernel(const __grid_constant__ KParamsII kp, const __grid_constant__ CrtTables ct,
                    const __grid_constant__ ModTables mt) {
-  constexpr int NSET = MODE == II_Z3M ? 3 : 1;
+  constexpr bool CPLX = MODE == II_Z3M || MODE == II_C3M;  // 3M complex, f64 or f32 output
+  constexpr int NSET = CPLX ? 3 : 1;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -236,15 +239,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int row0 = tm * kBM + wm * 16 + (lane >> 2);
     const int col0 = tn * kBN + wn * 16 + (lane & 3) * 2;
     uint32_t Sre[8][kSL];
-    uint32_t Sim[MODE == II_Z3M ? 8 : 1][kSL];
+    uint32_t Sim[CPLX ? 8 : 1][kSL];
 #pragma unroll
     for (int e = 0; e < 8; ++e)
 #pragma unroll
       for (int i = 0; i < kSL; ++i) {
         Sre[e][i] = 0;
-        if (MODE == II_Z3M) Sim[e][i] = 0;
+        if (CPLX) Sim[e][i] = 0;
       }
-    uint32_t t1[MODE == II_Z3M ? 8 : 1], t2[MODE == II_Z3M ? 8 : 1];
+    uint32_t t1[CPLX ? 8 : 1], t2[CPLX ? 8 : 1];
     for (int l = 0; l < nm; ++l) {
       const uint32_t m = mt.mods[l];
       for (int set = 0; set < NSET; ++set) {
@@ -282,7 +285,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             int row = row0 + (q >> 1) * 8, col = col0 + nt * 8 + (q & 1);
             if (row < kp.M && col < kp.N)
               kp.residues[(static_cast<int64_t>(l) * kp.M + row) * kp.N + col] = static_cast<uint8_t>(r);
-          } else if (MODE == II_Z3M) {
+          } else if (CPLX) {
             if (set == 0) {
               t1[e] = r;
             } else if (set == 1) {
@@ -307,20 +310,22 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (row >= kp.M || col >= kp.N) continue;
       const int sc = kp.EA[row] + kp.FB[col] + kp.escale;
       double rr = scale2(crt_finish(Sre[e], ct), sc);
-      if (MODE == II_Z3M) {
+      if (CPLX) {
+        // complex update in binary64; complex64 output rounds each part once more
+        using TO = typename std::conditional<MODE == II_C3M, float, double>::type;
         double ri = scale2(crt_finish(Sim[e], ct), sc);
-        double* cp = static_cast<double*>(kp.C) + 2 * (static_cast<int64_t>(row) * kp.ldc + col);
+        TO* cp = static_cast<TO*>(kp.C) + 2 * (static_cast<int64_t>(row) * kp.ldc + col);
         double tr = __fma_rn(kp.alpha_re, rr, -__dmul_rn(kp.alpha_im, ri));
         double ti = __fma_rn(kp.alpha_re, ri, __dmul_rn(kp.alpha_im, rr));
         if (kp.beta_re != 0.0 || kp.beta_im != 0.0) {
-          double cr = cp[0], ci = cp[1];
+          double cr = static_cast<double>(cp[0]), ci = static_cast<double>(cp[1]);
           double ur = __fma_rn(kp.beta_re, cr, -__dmul_rn(kp.beta_im, ci));
           double ui = __fma_rn(kp.beta_re, ci, __dmul_rn(kp.beta_im, cr));
           tr = __dadd_rn(tr, ur);
           ti = __dadd_rn(ti, ui);
         }
-        cp[0] = tr;
-        cp[1] = ti;
+        cp[0] = static_cast<TO>(tr);
+        cp[1] = static_cast<TO>(ti);
       } else if (MODE == II_F64) {
         double* cp = static_cast<double*>(kp.C) + static_cast<int64_t>(row) * kp.ldc + col;
         *cp = blas_update(kp.alpha_re, rr, kp.beta_re, kp.beta_re != 0.0 ? *cp : 0.0);
@@ -383,6 +388,8 @@ cudaError_t launch_gemm_II(int out_mode, const GemmIIArgs& a, const ModTables& m
       return launch_mode<II_RESIDUES>(a, mt, ct, st);
     case II_Z3M:
       return launch_mode<II_Z3M>(a, mt, ct, st);
+    case II_C3M:
+      return launch_mode<II_C3M>(a, mt, ct, st);
     default:
       return cudaErrorInvalidValue;
   }

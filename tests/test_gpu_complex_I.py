@@ -115,3 +115,18 @@ def test_zgemm_4m_accuracy_vs_double_double(orc, h):
     e8 = orc.err_metric(emu.zgemm(dev(A), dev(B), scheme="I", p=8, handle=h).cpu().numpy(), ref, A, B)
     e12 = orc.err_metric(emu.zgemm(dev(A), dev(B), scheme="I_F8", p=12, handle=h).cpu().numpy(), ref, A, B)
     assert e8 <= 4 * 2 * k * 2.0 ** -53 and e12 <= 4 * 2 * k * 2.0 ** -53
+
+
+def test_cgemm_3m_scheme_II_bit_exact(orc, h):
+    m, n, k, nm = 120, 80, 150, 10
+    A, B = synth.gemm_pair_complex(m, n, k, 1.0, 60)
+    Af, Bf = A.astype(np.complex64), B.astype(np.complex64)
+    C = emu.cgemm(dev(Af), dev(Bf), p=nm, scheme="II", handle=h)
+    torch.cuda.synchronize()
+    assert h.status() == 0
+    assert np.array_equal(C.cpu().numpy(), orc.emu_Z3M(Af, Bf, nm, out_f32=True))
+    C0 = synth.test_matrix_complex(m, n, 1.0, 61).astype(np.complex64)
+    al, be = -0.5 + 1.0j, 0.25 - 0.75j
+    Cd = colmajor(C0)
+    emu.cgemm(colmajor(Af), colmajor(Bf), Cd, alpha=al, beta=be, p=nm, scheme="II", handle=h)
+    assert np.array_equal(Cd.cpu().numpy(), orc.emu_Z3M(Af, Bf, nm, alpha=al, beta=be, C=C0, out_f32=True))
