@@ -500,7 +500,39 @@ def run_suite(path, args):
         ms = timed(lambda: emu.dgemm(Ad, Bd, Cd, scheme="I", p=p, handle=h), reps=1)
         emit({"path": "emu_dgemm_I", "n": n, "phi": 0.5, "p": p, "tflops": 2 * n ** 3 / ms / 1e9,
               "int8_tops": p * (p + 1) * n ** 3 / ms / 1e9, "ms": ms, "err": sampled_err(A, B, Cd.cpu().numpy())})
+    # Scheme I on E4M3 slices (tcgen05 kernel)
+    for p in (8, 10, 11, 12):
+        ms = timed(lambda: emu.dgemm(Ad, Bd, Cd, scheme="I_F8", p=p, handle=h), reps=1)
+        emit({"path": "emu_dgemm_I_F8", "n": n, "phi": 0.5, "p": p, "tflops": 2 * n ** 3 / ms / 1e9,
+              "f8_tops": p * (p + 1) * n ** 3 / ms / 1e9, "ms": ms, "err": sampled_err(A, B, Cd.cpu().numpy())})
     del Ad, Bd, Cd
+    for n in (4096, 8192):
+        for phi in (0.5, 4.0):
+            A, B, Ad, Bd = pair(n, phi)
+            Cd = torch.empty((n, n), dtype=torch.float64, device=dev)
+            for p in (8, 10, 11, 12):
+                ms = timed(lambda: emu.dgemm(Ad, Bd, Cd, scheme="I_F8", p=p, handle=h))
+                emit({"path": "emu_dgemm_I_F8", "n": n, "phi": phi, "p": p, "tflops": 2 * n ** 3 / ms / 1e9,
+                      "f8_tops": p * (p + 1) * n ** 3 / ms / 1e9, "ms": ms,
+                      "err": sampled_err(A, B, Cd.cpu().numpy())})
+    # naive (INT32 partials to HBM + separate shift-reduce) vs fused, k <= K_c
+    n = 4096
+    A, B, Ad, Bd = pair(n, 0.5)
+    for f8, p in ((False, 8), (True, 11)):
+        _, EA = emu.split_I(Ad, p, operand=0, handle=h, f8=f8)
+        _, FB = emu.split_I(Bd, p, operand=1, handle=h, f8=f8)
+        Cn = torch.empty((n, n), dtype=torch.float64, device=dev)
+        Cf = torch.empty((n, n), dtype=torch.float64, device=dev)
+
+        def naive():
+            Cs = emu.partials_I(Ad, Bd, p, handle=h, f8=f8)
+            emu.shift_reduce_I(Cs, EA, FB, p, f8=f8, C=Cn, handle=h)
+
+        ms_naive = timed(naive)
+        ms_fused = timed(lambda: emu.dgemm(Ad, Bd, Cf, scheme="I_F8" if f8 else "I", p=p, handle=h))
+        emit({"path": "ablation_naive_vs_fused", "n": n, "p": p, "slices": "e4m3" if f8 else "int8",
+              "ms_naive": ms_naive, "ms_fused": ms_fused, "speedup_fused": ms_naive / ms_fused,
+              "int32_partials_bytes": 4 * p * n * n, "bit_identical": bool(torch.equal(Cn, Cf))})
     # Scheme I SGEMM
     for p in (3, 4):
         A, B, Ad, Bd = pair(8192, 0.5, np.float32)
@@ -531,7 +563,23 @@ def run_suite(path, args):
         emit({"path": "emu_zgemm_3m", "n": n, "phi": 1.0, "nm": nm, "tflops_8mnk": 8 * n ** 3 / ms / 1e9,
               "tflops_2mnk": 2 * n ** 3 / ms / 1e9, "int8_tops": 6 * nm * n ** 3 / ms / 1e9, "ms": ms,
               "err": sampled_err(A, B, Cd.cpu().numpy(), True)})
-    del Ad, Bd, Cd
+    # ZGEMM 4M (Scheme I)
+    for sc, p in (("I", 8), ("I_F8", 11), ("I_F8", 12)):
+        ms = timed(lambda: emu.zgemm(Ad, Bd, Cd, scheme=sc, p=p, handle=h), reps=1)
+        emit({"path": "emu_zgemm_4m", "scheme": sc, "n": n, "phi": 1.0, "p": p, "tflops_8mnk": 8 * n ** 3 / ms / 1e9,
+              "tflops_2mnk": 2 * n ** 3 / ms / 1e9, "ms": ms, "err": sampled_err(A, B, Cd.cpu().numpy(), True)})
+    # CGEMM (complex64): cuBLAS, Scheme I 4M, Scheme II 3M
+    Af, Bf = Ad.to(torch.complex64), Bd.to(torch.complex64)
+    A32, B32 = A.astype(np.complex64).astype(np.complex128), B.astype(np.complex64).astype(np.complex128)
+    ms = timed(lambda: Af @ Bf, reps=2)
+    emit({"path": "cublas_cgemm", "n": n, "tflops_8mnk": 8 * n ** 3 / ms / 1e9, "ms": ms,
+          "err": sampled_err(A32, B32, (Af @ Bf).cpu().numpy().astype(np.complex128), True)})
+    Cf = torch.empty((n, n), dtype=torch.complex64, device=dev)
+    for sc, p in (("I", 4), ("I_F8", 6), ("II", 8), ("II", 10)):
+        ms = timed(lambda: emu.cgemm(Af, Bf, Cf, scheme=sc, p=p, handle=h), reps=2)
+        emit({"path": "emu_cgemm", "scheme": sc, "n": n, "p_or_nm": p, "tflops_8mnk": 8 * n ** 3 / ms / 1e9,
+              "ms": ms, "err": sampled_err(A32, B32, Cf.cpu().numpy().astype(np.complex128), True)})
+    del Ad, Bd, Cd, Af, Bf, Cf
     # grouped: 512 uneven products, graph vs per-product loop
     shapes = synth.grouped_shapes(512, 0)
     As, Bs, Cs = [], [], []

@@ -173,7 +173,7 @@ emu_status_t emu_sgemm(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n
  *    sums of Eq. 2, the Im*Im term from the slices of -Im B, combined exactly
  *    before one rounding per part -- Scheme I on the real matrices [Re A, Im A]
  *    and [[Re B, Im B], [-Im B, Re B]].  Workspace: emu_workspace_size with
- *    is_complex = 1 (the embedding of A and B, 48 (M + 2N) K bytes, plus the
+ *    is_complex = 1 (the embedding of A and B, 16 (M + 2N) K bytes, plus the
  *    slices of the 2K-deep real product).
  * beta == 0: C is not read.  Errors as emu_dgemm. */
 emu_status_t emu_zgemm(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k,
@@ -279,6 +279,21 @@ emu_status_t emu_partials_I(emu_handle_t h, emu_layout_t layout, int64_t m, int6
 emu_status_t emu_partials_F8(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k,
                              const double *A, int64_t lda, const double *B, int64_t ldb, int p,
                              int32_t *Cs_dev, emu_stream_t stream);
+
+/* Unfused ("naive") Scheme I epilogue, Eq. (3): reads the p partials written
+ * by emu_partials_I (f8 = 0) or emu_partials_F8 (f8 = 1) and writes
+ *   C_ij = alpha * RN(sum_s Cs[s][i][j] * 2^(b (p-1-s))) * 2^(E_i + F_j + e) + beta * C_ij
+ * with b = 8, e = -14 - 8(p-1) (INT8) or b = 5, e = -8 - 5(p-1) (E4M3); S is
+ * formed exactly and rounded once (nearest, ties to even), as in the fused
+ * kernels.  EA_dev: m row exponents of A, FB_dev: n column exponents of B, as
+ * returned by emu_split_I / emu_split_F8 (operand 0 and 1).  C_dev:
+ * row-major m x n, ldc >= n; not read when beta == 0.  Together with
+ * emu_partials_I this is the INT32 round trip the fused kernel avoids
+ * (Eq. 9); results are bit-identical to emu_dgemm when k <= K_c.
+ * EMU_ERR_INVALID_ARG for bad sizes or null pointers. */
+emu_status_t emu_shift_reduce_I(emu_handle_t h, int64_t m, int64_t n, int p, int f8, const int32_t *Cs_dev,
+                                const int32_t *EA_dev, const int32_t *FB_dev, double alpha, double beta,
+                                double *C_dev, int64_t ldc, emu_stream_t stream);
 
 /* Paper-design Scheme II output (Sec. IV-A): per-modulus INT8 residues
  * C'_l = (A'_l B'_l) mod m_l in [0, m_l), as nm row-major m x n uint8

@@ -60,6 +60,7 @@ _SIGS = {
                          _vp]),
     "emu_cgemm": (_i32, [_vp, _i32, _i64, _i64, _i64, _vp, _vp, _i64, _vp, _i64, _vp, _vp, _i64, _i32, _i32,
                          _vp]),
+    "emu_shift_reduce_I": (_i32, [_vp, _i64, _i64, _i32, _i32, _vp, _vp, _vp, _dbl, _dbl, _vp, _i64, _vp]),
     "emu_split_rows": (_i64, [_i64]),
     "emu_split_cols_I": (_i64, [_i64, _i32]),
     "emu_split_cols_II": (_i64, [_i64]),
@@ -253,6 +254,21 @@ def cgemm(A, B, C=None, alpha: complex = 1.0, beta: complex = 0.0, p: int = 4, s
     h = handle or default_handle(A.device.index or 0)
     check(emu_cgemm(h.h, layout, m, n, k, al, _ptr(A), lda, _ptr(B), ldb, be, _ptr(C), ldc, _scheme(scheme), p,
                     _stream_ptr(stream)), "emu_cgemm")
+    return C
+
+
+def shift_reduce_I(Cs, EA, FB, p: int, f8: bool = False, C=None, alpha: float = 1.0, beta: float = 0.0,
+                   handle=None, stream=None):
+    """Unfused Scheme I epilogue (Eq. 3) on p x m x n int32 partials Cs with
+    row exponents EA (int32, m) and column exponents FB (int32, n)."""
+    import torch
+    _, m, n = Cs.shape
+    if C is None:
+        C = torch.empty((m, n), dtype=torch.float64, device=Cs.device)
+        beta = 0.0
+    h = handle or default_handle(Cs.device.index or 0)
+    check(emu_shift_reduce_I(h.h, m, n, p, int(f8), _ptr(Cs), _ptr(EA), _ptr(FB), alpha, beta, _ptr(C),
+                             max(C.stride(0), n, 1), _stream_ptr(stream)), "emu_shift_reduce_I")
     return C
 
 

@@ -60,6 +60,19 @@ def test_argument_validation_without_gpu(lib):
     assert lib.emu_status_string(6) == b"EMU_ERR_TIMEOUT"
     # column-major leading dimensions must cover the rows
     assert lib.emu_dgemm_noalloc(1, 8, 8, 8, 1.0, 1, 4, 1, 8, 0.0, 1, 8, 4, None, None) == 1
+    # complex Scheme I workspace covers the 2K-deep embedding; CGEMM needs a handle
+    assert lib.emu_workspace_size(1, 100, 100, 100, 8, 1, ctypes.byref(sz)) == 0 and sz.value > 16 * 300 * 100
+    lib.emu_cgemm.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                              ctypes.c_void_p]
+    one = (ctypes.c_float * 2)(1.0, 0.0)
+    assert lib.emu_cgemm(None, 0, 4, 4, 4, one, None, 4, None, 4, one, None, 4, 1, 4, None) == 1
+    # the separate epilogue rejects a null handle and short leading dimensions
+    lib.emu_shift_reduce_I.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+    assert lib.emu_shift_reduce_I(None, 4, 4, 8, 0, 1, 1, 1, 1.0, 0.0, 1, 4, None) == 1
 
 
 def test_create_without_gpu_reports_cuda_error(lib):
