@@ -499,10 +499,10 @@ emu_status_t run_scheme_I(emu_handle_s* h, const View& v, int64_t k, int p, doub
   launch_split_I<T>(A, v.ldA, v.a_kcontig, v.M, k, p, maxA, hatA, EA, st, f8);
   launch_split_I<T>(B, v.ldB, v.b_kcontig, v.N, k, p, maxB, hatB, FB, st, f8);
   trace_end(h, PH_SPLIT, st, 2);
-  // E4M3 slices with a product output run on the tcgen05 kernel (A boxes of
-  // 128 B x 128 / cluster rows, multicast across the cluster); the INT8
-  // engine and the partials ablation use the mma.sync kernel (32 B x 64 rows).
-  const bool tc = f8 && out_mode != OUT_PARTIALS && !f8_engine_mma();
+  // E4M3 slices run on the tcgen05 kernel (A boxes of 128 B x 128 / cluster
+  // rows, multicast across the cluster); the INT8 engine uses the mma.sync
+  // kernel (32 B x 64 rows).
+  const bool tc = f8 && !f8_engine_mma();
   const int cluster = tc ? gemm_f8tc_cluster() : 1;
   CUtensorMap ta, tb;
   if (!make_tmap_i8(&ta, hatA, static_cast<uint64_t>(pl.cols), static_cast<uint64_t>(pl.rows_a),

@@ -75,6 +75,7 @@ struct KParamsTC {
   double alpha, beta;
   void* C;
   int64_t ldc;
+  int32_t* partials;  // non-null: write the p accumulators (exact int32) instead of C (k <= K_c)
   int* status;
 };
 
@@ -406,11 +407,34 @@ __global__ void __launch_bounds__(kThreadsTC, 1) gemm_f8tc_kernel(const __grid_c
           break;
         }
         tc_fence_after();
-        drain16<P>(lane_base, S);
+        if (kp.partials) {
+          // unfused output: accumulator s of this thread's 16 columns to
+          // partials[s][row][col] (one drain per tile, since k <= K_c)
+          const int prow = tm * kBM + row_in_tile;
+#pragma unroll 1
+          for (int s = 0; s < P; ++s) {
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+              int32_t v[8];
+              tmem_ld8_int(lane_base + static_cast<uint32_t>(s * kBN + 8 * hh), v);
+              if (prow < kp.M) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                  const int col = tn * kBN + c0 + 8 * hh + c;
+                  if (col < kp.N)
+                    kp.partials[(static_cast<int64_t>(s) * kp.M + prow) * kp.N + col] = v[c];
+                }
+              }
+            }
+          }
+        } else {
+          drain16<P>(lane_base, S);
+        }
         tc_fence_before();
         mbar_arrive(acc_empty);
       }
       if (stop) break;
+      if (kp.partials) continue;
       const int row = tm * kBM + row_in_tile;
       if (row < kp.M) {
         const int erow = kp.EA[row] + kp.escale;
@@ -472,7 +496,7 @@ int max_clusters(int cl) {
 }
 
 template <int P, int OUT>
-cudaError_t launch_tc(const GemmIArgs& a, cudaStream_t st) {
+cudaError_t launch_tc(const GemmIArgs& a, cudaStream_t st, bool partials) {
   using Cfg = CfgTC<P>;
   cudaError_t e =
       cudaFuncSetAttribute(gemm_f8tc_kernel<P, OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
@@ -497,6 +521,7 @@ cudaError_t launch_tc(const GemmIArgs& a, cudaStream_t st) {
   kp.beta = a.beta;
   kp.C = a.C;
   kp.ldc = a.ldc;
+  kp.partials = partials ? a.partials : nullptr;
   kp.status = a.status;
   const int ntiles = kp.tiles_m * kp.tiles_ng;
   if (ntiles == 0 || kp.nk32 == 0) return cudaSuccess;
@@ -547,7 +572,8 @@ int gemm_f8tc_cluster() {
 cudaError_t launch_gemm_f8tc(int p, int out_mode, const GemmIArgs& a, cudaStream_t st) {
 #define EMU_TC(PP)                                                \
   case PP:                                                        \
-    return out_mode == OUT_F32 ? launch_tc<PP, OUT_F32>(a, st) : launch_tc<PP, OUT_F64>(a, st);
+    return out_mode == OUT_F32 ? launch_tc<PP, OUT_F32>(a, st, false)     \
+                               : launch_tc<PP, OUT_F64>(a, st, out_mode == OUT_PARTIALS);
   switch (p) {
     EMU_TC(1) EMU_TC(2) EMU_TC(3) EMU_TC(4) EMU_TC(5) EMU_TC(6)
     EMU_TC(7) EMU_TC(8) EMU_TC(9) EMU_TC(10) EMU_TC(11) EMU_TC(12)
