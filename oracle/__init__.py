@@ -71,6 +71,10 @@ def _load():
                 "orc_modprod_II": (None, [i64, i64, i64, i32, vp, vp, vp]),
                 "orc_crt": (i32, [i32, i64, vp, vp]),
                 "orc_emu_II": (i32, [i64, i64, i64, i32, dbl, vp, vp, dbl, vp, vp, i32]),
+                "orc_emu_II_ex": (i32, [i64, i64, i64, i32, i32, dbl, vp, vp, dbl, vp, vp, i32]),
+                "orc_norm_exponents": (i64, [i64, i64, i32, vp, vp]),
+                "orc_norm_halves_II": (None, [i32, vp, vp]),
+                "orc_emu_Z3M_norm": (i32, [i64, i64, i64, i32, dbl, dbl, vp, vp, dbl, dbl, vp, vp, i32]),
                 "orc_modprod_Z3M": (None, [i64, i64, i64, i32, vp, vp, vp, vp, vp, vp, vp, vp]),
                 "orc_emu_Z3M": (i32, [i64, i64, i64, i32, dbl, dbl, vp, vp, dbl, dbl, vp]),
                 "orc_emu_C3M": (i32, [i64, i64, i64, i32, dbl, dbl, vp, vp, dbl, dbl, vp]),
@@ -291,8 +295,31 @@ def crt(res: np.ndarray) -> np.ndarray:
     return out
 
 
-def emu_II(A, B, nm: int, alpha: float = 1.0, beta: float = 0.0, C=None, out_f32: bool = False):
-    """Scheme II emulated C = alpha*A@B + beta*C (Eqs. 5-8)."""
+def norm_exponents(X, complex_: bool = False) -> np.ndarray:
+    """Reading R9: e per row with ||x_row||_2 < 2^e, computed exactly."""
+    if complex_:
+        Xc = np.ascontiguousarray(X, dtype=np.complex128)
+        rows, cols = Xc.shape
+        buf = Xc.view(np.float64)
+    else:
+        buf = _f64(X)
+        rows, cols = buf.shape
+    E = np.zeros(max(rows, 1), dtype=np.int32)
+    if _load().orc_norm_exponents(rows, cols, 2 if complex_ else 1, _p(buf), _p(E)):
+        raise ValueError("non-finite input")
+    return E[:rows]
+
+
+def norm_halves_II(nm: int) -> tuple[int, int]:
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _load().orc_norm_halves_II(nm, ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+def emu_II(A, B, nm: int, alpha: float = 1.0, beta: float = 0.0, C=None, out_f32: bool = False,
+           norm: bool = False):
+    """Scheme II emulated C = alpha*A@B + beta*C (Eqs. 5-8); norm=True: the
+    norm-based scaling of reading R9 instead of R3."""
     A, Bt = _f64(A), _f64(np.asarray(B).T)
     m, k = A.shape
     n = Bt.shape[0]
@@ -302,8 +329,8 @@ def emu_II(A, B, nm: int, alpha: float = 1.0, beta: float = 0.0, C=None, out_f32
     else:
         Cd = np.zeros((m, n)) if C is None else np.array(C, dtype=np.float64, order="C")
         Cf = np.zeros(1, dtype=np.float32)
-    rc = _load().orc_emu_II(m, n, k, nm, float(alpha), _p(A), _p(Bt), float(beta), _p(Cd), _p(Cf),
-                            int(out_f32))
+    rc = _load().orc_emu_II_ex(m, n, k, nm, int(norm), float(alpha), _p(A), _p(Bt), float(beta), _p(Cd),
+                               _p(Cf), int(out_f32))
     if rc:
         raise ValueError("non-finite input")
     return Cf if out_f32 else Cd
@@ -321,7 +348,8 @@ def modprod_Z3M(A3, B3t):
     return ore, oim
 
 
-def emu_Z3M(A, B, nm: int, alpha: complex = 1.0, beta: complex = 0.0, C=None, out_f32: bool = False) -> np.ndarray:
+def emu_Z3M(A, B, nm: int, alpha: complex = 1.0, beta: complex = 0.0, C=None, out_f32: bool = False,
+            norm: bool = False) -> np.ndarray:
     """Scheme II 3M complex C = alpha*A@B + beta*C (Eqs. 5-8, 16).  out_f32:
     complex64 result (CGEMM; the inputs are used as given, widened exactly)."""
     A = np.ascontiguousarray(A, dtype=np.complex128)
@@ -329,7 +357,18 @@ def emu_Z3M(A, B, nm: int, alpha: complex = 1.0, beta: complex = 0.0, C=None, ou
     m, k = A.shape
     n = Bt.shape[0]
     alpha, beta = complex(alpha), complex(beta)
-    if out_f32:
+    if norm:
+        if out_f32:
+            out = np.zeros((m, n), dtype=np.complex64) if C is None else np.array(C, dtype=np.complex64, order="C")
+            Cz = np.zeros((1, 1), dtype=np.complex128)
+            Cf = out
+        else:
+            out = np.zeros((m, n), dtype=np.complex128) if C is None else np.array(C, dtype=np.complex128, order="C")
+            Cz = out
+            Cf = np.zeros((1, 1), dtype=np.complex64)
+        rc = _load().orc_emu_Z3M_norm(m, n, k, nm, alpha.real, alpha.imag, _p(A), _p(Bt), beta.real, beta.imag,
+                                      _p(Cz), _p(Cf), int(out_f32))
+    elif out_f32:
         Cf = np.zeros((m, n), dtype=np.complex64) if C is None else np.array(C, dtype=np.complex64, order="C")
         rc = _load().orc_emu_C3M(m, n, k, nm, alpha.real, alpha.imag, _p(A), _p(Bt), beta.real, beta.imag,
                                  _p(Cf))

@@ -71,6 +71,20 @@
  *       w_s = 2^(beta (p-1-s)).  This is Scheme I applied to the real
  *       matrices [Re A, Im A] and [[Re B, Im B], [-Im B, Re B]].  The complex
  *       BLAS update is that of R6 for complex numbers.
+ *   R9  Scheme II with norm-based scaling (a data-dependent bound for the
+ *       exactness condition after Eq. (8), in place of R3's worst case):
+ *       Cauchy-Schwarz gives sum_h |a'_ih||b'_hj| <= ||a'_i||_2 ||b'_j||_2,
+ *       so with e_i = an integer with ||a_i||_2 < 2^e_i (f_j likewise for the
+ *       columns of B) and a' = trunc(a * 2^(hA - e_i)), b' = trunc(b *
+ *       2^(hB - f_j)), hA = floor((floor(log2 P) - 1)/2), hB = floor(log2 P)
+ *       - 1 - hA, the condition 2 sum |a'||b'| < 2^floor(log2 P) <= P holds
+ *       for every input.  e_i is computed exactly so that any implementation
+ *       finds the same value: with E the frexp exponent of the row maximum
+ *       and y = a 2^-E (|y| < 1), S = sum_h ceil(y_h^2 2^64) (integers, an
+ *       upper bound of 2^64 ||y||^2), e_i = E + ceil((bitlen(S) - 64)/2);
+ *       all-zero rows get e_i = 0.  Complex rows use |y|^2 = re^2 + im^2; the
+ *       same hA, hB apply (|Re C'|, |Im C'| <= ||a_i|| ||b_j|| over complex
+ *       norms).  Result RN(C') * 2^(e_i + f_j - hA - hB).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -128,6 +142,65 @@ int64_t orc_row_exponents(int64_t rows, int64_t cols, const double *X, int32_t *
  * (interleaved re, im pairs). */
 int64_t orc_row_exponents_z(int64_t rows, int64_t cols, const double *X, int32_t *E) {
   return orc_row_exponents(rows, 2 * cols, X, E);
+}
+
+/* Reading R9: exact norm exponents.  ceil(y^2 2^64) for y = x 2^-E, |y| < 1,
+ * from the integer mantissa of x (y^2 = M^2 2^(2(ex - 53 - E)) with
+ * x = M 2^(ex-53), 2^52 <= M < 2^53). */
+static u128 sq_ceil64(double x, int E) {
+  if (x == 0.0) return 0;
+  int ex;
+  double f = frexp(fabs(x), &ex);
+  uint64_t M = (uint64_t)ldexp(f, 53);
+  u128 M2 = (u128)M * (u128)M; /* < 2^106 */
+  int s = 2 * (ex - 53 - E) + 64;
+  if (s >= 0) return M2 << s; /* y^2 2^64 < 2^64 */
+  if (-s >= 128) return 1;   /* nonzero, below one unit */
+  u128 q = M2 >> (-s);
+  if ((q << (-s)) != M2) q += 1;
+  return q;
+}
+
+static int bitlen128(u128 v) {
+  int L = 0;
+  while (v) {
+    ++L;
+    v >>= 1;
+  }
+  return L;
+}
+
+/* e per row of a rows x cols matrix (cw = 1 real, 2 complex interleaved).
+ * Returns the number of rows with non-finite entries (then E is unusable). */
+int64_t orc_norm_exponents(int64_t rows, int64_t cols, int cw, const double *X, int32_t *E) {
+  int64_t bad = 0;
+  for (int64_t i = 0; i < rows; ++i) {
+    int Emax;
+    if (row_exponent(X + i * cols * cw, cols * cw, &Emax)) {
+      ++bad;
+      E[i] = 0;
+      continue;
+    }
+    u128 S = 0;
+    for (int64_t h = 0; h < cols * cw; ++h) S += sq_ceil64(X[i * cols * cw + h], Emax);
+    if (S == 0) {
+      E[i] = 0;
+      continue;
+    }
+    int d = bitlen128(S) - 64; /* e' = ceil(d / 2) */
+    int ep = d >= 0 ? (d + 1) / 2 : -((-d) / 2);
+    E[i] = Emax + ep;
+  }
+  return bad;
+}
+
+int orc_log2P_floor(int nm);
+
+/* Reading R9: the scale bits of A and B. */
+void orc_norm_halves_II(int nm, int *hA, int *hB) {
+  int L = orc_log2P_floor(nm) - 1;
+  *hA = L >= 0 ? L / 2 : -((-L + 1) / 2);
+  *hB = L - *hA;
 }
 
 /* trunc(a * 2^shift) as an exact integer.  a = M * 2^(e-53) with the
@@ -557,8 +630,9 @@ int orc_crt(int nm, int64_t cnt, const uint8_t *res, double *out) {
 
 /* Full Scheme II emulated real product (Eqs. 5-8, readings R3-R6).
  * A: m x k, Bt: n x k, C: m x n in/out (or Cf when out_f32). */
-int orc_emu_II(int64_t m, int64_t n, int64_t k, int nm, double alpha, const double *A,
-               const double *Bt, double beta, double *C, float *Cf, int out_f32) {
+/* norm = 0: reading R3 (row-maximum exponents, one b); norm = 1: R9. */
+int orc_emu_II_ex(int64_t m, int64_t n, int64_t k, int nm, int norm, double alpha, const double *A,
+                  const double *Bt, double beta, double *C, float *Cf, int out_f32) {
   int32_t *E = malloc(sizeof(int32_t) * (m > 0 ? m : 1));
   int32_t *F = malloc(sizeof(int32_t) * (n > 0 ? n : 1));
   int8_t *RA = malloc((size_t)(nm * m * k > 0 ? nm * m * k : 1));
@@ -567,14 +641,20 @@ int orc_emu_II(int64_t m, int64_t n, int64_t k, int nm, double alpha, const doub
   int rc = 0;
   crt_ctx cx;
   cx.T = NULL;
-  if (orc_row_exponents(m, k, A, E) || orc_row_exponents(n, k, Bt, F)) {
+  if (norm ? (orc_norm_exponents(m, k, 1, A, E) || orc_norm_exponents(n, k, 1, Bt, F))
+           : (orc_row_exponents(m, k, A, E) || orc_row_exponents(n, k, Bt, F))) {
     rc = -1;
     goto out;
   }
   {
-    int b = orc_scale_bits_II(nm, k, 0);
-    orc_residues_II(m, k, A, E, b, nm, 0, 0, RA);
-    orc_residues_II(n, k, Bt, F, b, nm, 0, 0, RB);
+    int bA, bB;
+    if (norm) {
+      orc_norm_halves_II(nm, &bA, &bB);
+    } else {
+      bA = bB = orc_scale_bits_II(nm, k, 0);
+    }
+    orc_residues_II(m, k, A, E, bA, nm, 0, 0, RA);
+    orc_residues_II(n, k, Bt, F, bB, nm, 0, 0, RB);
     orc_modprod_II(m, n, k, nm, RA, RB, O);
     if (crt_init(&cx, nm)) {
       rc = -2;
@@ -584,7 +664,7 @@ int orc_emu_II(int64_t m, int64_t n, int64_t k, int nm, double alpha, const doub
     for (int64_t i = 0; i < m; ++i)
       for (int64_t j = 0; j < n; ++j) {
         double v = crt_value(&cx, O + i * n + j, m * n);
-        double r = ldexp(v, E[i] + F[j] - 2 * b);
+        double r = ldexp(v, E[i] + F[j] - bA - bB);
         if (out_f32)
           Cf[i * n + j] = (float)blas_update(alpha, r, beta, beta == 0.0 ? 0.0 : (double)Cf[i * n + j]);
         else
@@ -599,6 +679,11 @@ out:
   free(RB);
   free(O);
   return rc;
+}
+
+int orc_emu_II(int64_t m, int64_t n, int64_t k, int nm, double alpha, const double *A, const double *Bt,
+               double beta, double *C, float *Cf, int out_f32) {
+  return orc_emu_II_ex(m, n, k, nm, 0, alpha, A, Bt, beta, C, Cf, out_f32);
 }
 
 /* ------------------------------------------------------------------ */
@@ -657,7 +742,7 @@ static void zupdate(double ar, double ai, double rr, double ri, double br, doubl
  * With out_f32 the result goes to Cf (m x n complex float, read when beta
  * != 0): the complex update is done in binary64 as for C, then each part is
  * rounded once more to binary32 (CGEMM). */
-static int emu_Z3M_core(int64_t m, int64_t n, int64_t k, int nm, double alpha_re, double alpha_im,
+static int emu_Z3M_core(int64_t m, int64_t n, int64_t k, int nm, int norm, double alpha_re, double alpha_im,
                         const double *A, const double *Bt, double beta_re, double beta_im, double *C, float *Cf,
                         int out_f32) {
   int32_t *E = malloc(sizeof(int32_t) * (m > 0 ? m : 1));
@@ -669,15 +754,21 @@ static int emu_Z3M_core(int64_t m, int64_t n, int64_t k, int nm, double alpha_re
   int rc = 0;
   crt_ctx cx;
   cx.T = NULL;
-  if (orc_row_exponents_z(m, k, A, E) || orc_row_exponents_z(n, k, Bt, F)) {
+  if (norm ? (orc_norm_exponents(m, k, 2, A, E) || orc_norm_exponents(n, k, 2, Bt, F))
+           : (orc_row_exponents_z(m, k, A, E) || orc_row_exponents_z(n, k, Bt, F))) {
     rc = -1;
     goto out;
   }
   {
-    int b = orc_scale_bits_II(nm, k, 1);
+    int bA, bB;
+    if (norm) {
+      orc_norm_halves_II(nm, &bA, &bB);
+    } else {
+      bA = bB = orc_scale_bits_II(nm, k, 1);
+    }
     for (int q = 0; q < 3; ++q) {
-      orc_residues_II(m, k, A, E, b, nm, 1, q, A3 + q * sa);
-      orc_residues_II(n, k, Bt, F, b, nm, 1, q, B3 + q * sb);
+      orc_residues_II(m, k, A, E, bA, nm, 1, q, A3 + q * sa);
+      orc_residues_II(n, k, Bt, F, bB, nm, 1, q, B3 + q * sb);
     }
     orc_modprod_Z3M(m, n, k, nm, A3, A3 + sa, A3 + 2 * sa, B3, B3 + sb, B3 + 2 * sb, ORe, OIm);
     if (crt_init(&cx, nm)) {
@@ -689,8 +780,8 @@ static int emu_Z3M_core(int64_t m, int64_t n, int64_t k, int nm, double alpha_re
       for (int64_t j = 0; j < n; ++j) {
         double vr = crt_value(&cx, ORe + i * n + j, m * n);
         double vi = crt_value(&cx, OIm + i * n + j, m * n);
-        double rr = ldexp(vr, E[i] + F[j] - 2 * b);
-        double ri = ldexp(vi, E[i] + F[j] - 2 * b);
+        double rr = ldexp(vr, E[i] + F[j] - bA - bB);
+        double ri = ldexp(vi, E[i] + F[j] - bA - bB);
         double cr = 0.0, ci = 0.0;
         if (beta_re != 0.0 || beta_im != 0.0) {
           cr = out_f32 ? (double)Cf[2 * (i * n + j)] : C[2 * (i * n + j)];
@@ -719,14 +810,21 @@ out:
 
 int orc_emu_Z3M(int64_t m, int64_t n, int64_t k, int nm, double alpha_re, double alpha_im,
                 const double *A, const double *Bt, double beta_re, double beta_im, double *C) {
-  return emu_Z3M_core(m, n, k, nm, alpha_re, alpha_im, A, Bt, beta_re, beta_im, C, NULL, 0);
+  return emu_Z3M_core(m, n, k, nm, 0, alpha_re, alpha_im, A, Bt, beta_re, beta_im, C, NULL, 0);
 }
 
 /* CGEMM by the 3M method: A, Bt complex double (the complex64 inputs widened
  * exactly), Cf complex float in/out. */
 int orc_emu_C3M(int64_t m, int64_t n, int64_t k, int nm, double alpha_re, double alpha_im,
                 const double *A, const double *Bt, double beta_re, double beta_im, float *Cf) {
-  return emu_Z3M_core(m, n, k, nm, alpha_re, alpha_im, A, Bt, beta_re, beta_im, NULL, Cf, 1);
+  return emu_Z3M_core(m, n, k, nm, 0, alpha_re, alpha_im, A, Bt, beta_re, beta_im, NULL, Cf, 1);
+}
+
+/* 3M with the norm-based scaling of R9; out_f32 selects Cf (CGEMM). */
+int orc_emu_Z3M_norm(int64_t m, int64_t n, int64_t k, int nm, double alpha_re, double alpha_im,
+                     const double *A, const double *Bt, double beta_re, double beta_im, double *C, float *Cf,
+                     int out_f32) {
+  return emu_Z3M_core(m, n, k, nm, 1, alpha_re, alpha_im, A, Bt, beta_re, beta_im, C, Cf, out_f32);
 }
 
 /* ------------------------------------------------------------------ */
