@@ -75,16 +75,17 @@
  *       exactness condition after Eq. (8), in place of R3's worst case):
  *       Cauchy-Schwarz gives sum_h |a'_ih||b'_hj| <= ||a'_i||_2 ||b'_j||_2,
  *       so with e_i = an integer with ||a_i||_2 < 2^e_i (f_j likewise for the
- *       columns of B) and a' = trunc(a * 2^(hA - e_i)), b' = trunc(b *
- *       2^(hB - f_j)), hA = floor((floor(log2 P) - 1)/2), hB = floor(log2 P)
- *       - 1 - hA, the condition 2 sum |a'||b'| < 2^floor(log2 P) <= P holds
- *       for every input.  e_i is computed exactly so that any implementation
+ *       columns of B) and a' = trunc(a * 2^(h - e_i)), b' = trunc(b *
+ *       2^(h - f_j)), h = floor((floor(log2 P) - 1)/2) for both operands (so
+ *       the product is symmetric in A and B and does not depend on which one
+ *       is stored transposed), the condition 2 sum |a'||b'| < 2^(2h+1)
+ *       <= 2^floor(log2 P) <= P holds for every input.  e_i is computed exactly so that any implementation
  *       finds the same value: with E the frexp exponent of the row maximum
  *       and y = a 2^-E (|y| < 1), S = sum_h ceil(y_h^2 2^64) (integers, an
  *       upper bound of 2^64 ||y||^2), e_i = E + ceil((bitlen(S) - 64)/2);
  *       all-zero rows get e_i = 0.  Complex rows use |y|^2 = re^2 + im^2; the
  *       same hA, hB apply (|Re C'|, |Im C'| <= ||a_i|| ||b_j|| over complex
- *       norms).  Result RN(C') * 2^(e_i + f_j - hA - hB).
+ *       norms).  Result RN(C') * 2^(e_i + f_j - 2h).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -196,11 +197,11 @@ int64_t orc_norm_exponents(int64_t rows, int64_t cols, int cw, const double *X, 
 
 int orc_log2P_floor(int nm);
 
-/* Reading R9: the scale bits of A and B. */
+/* Reading R9: the scale bits of A and B (equal). */
 void orc_norm_halves_II(int nm, int *hA, int *hB) {
   int L = orc_log2P_floor(nm) - 1;
   *hA = L >= 0 ? L / 2 : -((-L + 1) / 2);
-  *hB = L - *hA;
+  *hB = *hA;
 }
 
 /* trunc(a * 2^shift) as an exact integer.  a = M * 2^(e-53) with the

@@ -51,7 +51,8 @@ def test_norm_exponents_closed_forms(orc):
 def test_norm_halves(orc):
     for nm in range(2, 21):
         hA, hB = orc.norm_halves_II(nm)
-        assert hA + hB == orc.log2P_floor(nm) - 1 and abs(hA - hB) <= 1
+        # equal halves, the largest with 2 (2^hA 2^hB) <= 2^floor(log2 P)
+        assert hA == hB and 2 * hA + 1 <= orc.log2P_floor(nm) < 2 * hA + 3
 
 
 @pytest.mark.parametrize("nm,phi", [(8, 4.0), (14, 8.0), (20, 0.5)])
