@@ -67,7 +67,15 @@ typedef enum { EMU_ROW_MAJOR = 0, EMU_COL_MAJOR = 1 } emu_layout_t;
  * balanced base-32 digits, all products exact, FP32 accumulation kept exact
  * by draining every K_c), the FP8 formulation Sec. VII names as future work.
  * p_or_nm is the number of E4M3 slices (5 bits each: p = 11 gives 54 bits). */
-typedef enum { EMU_SCHEME_I = 1, EMU_SCHEME_II = 2, EMU_SCHEME_I_F8 = 3 } emu_scheme_t;
+/* EMU_SCHEME_II_NORM: Scheme II with a data-dependent bound for the
+ * exactness condition after Eq. 8 instead of the worst case: by
+ * Cauchy-Schwarz, sum_h |a'_ih||b'_hj| <= ||a'_i||_2 ||b'_j||_2, so each row
+ * of A (column of B) is scaled by the exponent of its 2-norm (computed
+ * exactly, independent of summation order) and both operands get the same
+ * floor((floor(log2 P) - 1)/2) bits; inputs whose rows are not flat keep up to
+ * log2(k)/2 more bits per operand at the same number of moduli.  p_or_nm is
+ * the number of moduli; real, 3M complex, FP64 and FP32. */
+typedef enum { EMU_SCHEME_I = 1, EMU_SCHEME_II = 2, EMU_SCHEME_I_F8 = 3, EMU_SCHEME_II_NORM = 4 } emu_scheme_t;
 
 typedef enum {
   EMU_OK = 0,

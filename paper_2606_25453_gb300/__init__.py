@@ -16,7 +16,7 @@ from . import build as _build_mod
 _LIB_PATH = _build_mod.LIB
 
 EMU_ROW_MAJOR, EMU_COL_MAJOR = 0, 1
-EMU_SCHEME_I, EMU_SCHEME_II, EMU_SCHEME_I_F8 = 1, 2, 3
+EMU_SCHEME_I, EMU_SCHEME_II, EMU_SCHEME_I_F8, EMU_SCHEME_II_NORM = 1, 2, 3, 4
 STATUS = {0: "EMU_OK", 1: "EMU_ERR_INVALID_ARG", 2: "EMU_ERR_UNSUPPORTED", 3: "EMU_ERR_NONFINITE",
           4: "EMU_ERR_CUDA", 5: "EMU_ERR_ALLOC", 6: "EMU_ERR_TIMEOUT", 7: "EMU_ERR_TOL_NOT_MET"}
 EMU_P_MAX, EMU_NM_MAX, EMU_K_MAX_II = 12, 20, 131071
@@ -166,7 +166,9 @@ def _scheme(s) -> int:
         return EMU_SCHEME_II
     if s in (3, "I_F8", "F8", "f8", EMU_SCHEME_I_F8):
         return EMU_SCHEME_I_F8
-    raise ValueError("scheme must be 'I', 'II' or 'I_F8'")
+    if s in (4, "II_NORM", "II_N", "ii_norm", EMU_SCHEME_II_NORM):
+        return EMU_SCHEME_II_NORM
+    raise ValueError("scheme must be 'I', 'II', 'I_F8' or 'II_NORM'")
 
 
 def _layout_of(A, B, C):
@@ -234,7 +236,7 @@ def zgemm(A, B, C=None, alpha: complex = 1.0, beta: complex = 0.0, nm: int = 16,
     h = handle or default_handle(A.device.index or 0)
     sc = _scheme(scheme)
     check(emu_zgemm(h.h, layout, m, n, k, al, _ptr(A), lda, _ptr(B), ldb, be, _ptr(C), ldc, sc,
-                    nm if sc == EMU_SCHEME_II else p, _stream_ptr(stream)), "emu_zgemm")
+                    nm if sc in (EMU_SCHEME_II, EMU_SCHEME_II_NORM) else p, _stream_ptr(stream)), "emu_zgemm")
     return C
 
 

@@ -132,6 +132,15 @@ int host_scale_bits_II(int nm, int64_t k, int is_complex) {
   return num >= 0 ? num / 2 : -((-num + 1) / 2);
 }
 
+// Norm-based scaling: one exponent h for both operands (the product stays
+// symmetric in A and B, whichever one is stored transposed), 2h + 1 <=
+// floor(log2 P).
+void host_norm_halves_II(int nm, int* hA, int* hB) {
+  const int L = limbs_bitlen(limbs_P(nm)) - 2;  // floor(log2 P) - 1
+  *hA = L >= 0 ? L / 2 : -((-L + 1) / 2);
+  *hB = *hA;
+}
+
 void host_mod_tables(int nm, ModTables* t) {
   std::memset(t, 0, sizeof(*t));
   int32_t mods[kMaxModuli];
@@ -435,6 +444,11 @@ Plan plan_II(int64_t m, int64_t n, int64_t k, int nm, int nsets) {
   pl.off_FB = off; off += al256(4 * static_cast<size_t>(n > 0 ? n : 1));
   pl.off_hatA = off; off += al256(static_cast<size_t>(nsets) * nm * pl.rows_a * pl.cols);
   pl.off_hatB = off; off += al256(static_cast<size_t>(nsets) * nm * pl.rows_b * pl.cols);
+  // norm-based scaling: 128-bit sums of squares and the exponents
+  pl.off_accA = off; off += al256(16 * static_cast<size_t>(m > 0 ? m : 1));
+  pl.off_accB = off; off += al256(16 * static_cast<size_t>(n > 0 ? n : 1));
+  pl.off_nEA = off; off += al256(4 * static_cast<size_t>(m > 0 ? m : 1));
+  pl.off_nEB = off; off += al256(4 * static_cast<size_t>(n > 0 ? n : 1));
   pl.bytes = off;
   return pl;
 }
@@ -539,7 +553,7 @@ template emu_status_t run_scheme_I<float>(emu_handle_s*, const View&, int64_t, i
 template <typename T>
 emu_status_t run_scheme_II(emu_handle_s* h, const View& v, int64_t k, int nm, int cw, double ar,
                            double ai, double br, double bi, void* C, int64_t ldc, int out_mode,
-                           uint8_t* residues, cudaStream_t st) {
+                           uint8_t* residues, cudaStream_t st, bool norm = false) {
   const int nsets = cw == 2 ? 3 : 1;
   Plan pl = plan_II(v.M, v.N, k, nm, nsets);
   uint8_t* ws = nullptr;
@@ -553,7 +567,12 @@ emu_status_t run_scheme_II(emu_handle_s* h, const View& v, int64_t k, int nm, in
   auto* resB = reinterpret_cast<int8_t*>(ws + pl.off_hatB);
   const T* A = static_cast<const T*>(v.A);
   const T* B = static_cast<const T*>(v.B);
-  const int b = host_scale_bits_II(nm, k, cw == 2);
+  // worst-case scaling (one b for both operands, exponents of the row
+  // maxima) or norm-based scaling (hA, hB, exponents of the 2-norms)
+  int bA = host_scale_bits_II(nm, k, cw == 2), bB = bA;
+  if (norm) host_norm_halves_II(nm, &bA, &bB);
+  auto* nEA = reinterpret_cast<int32_t*>(ws + pl.off_nEA);
+  auto* nEB = reinterpret_cast<int32_t*>(ws + pl.off_nEB);
   ModTables mt;
   host_mod_tables(nm, &mt);
   CrtTables ct;
@@ -561,10 +580,16 @@ emu_status_t run_scheme_II(emu_handle_s* h, const View& v, int64_t k, int nm, in
   trace_begin(h, PH_SCAN, st);
   launch_scan<T>(A, v.ldA, v.a_kcontig, v.M, k, cw, maxA, h->status, st);
   launch_scan<T>(B, v.ldB, v.b_kcontig, v.N, k, cw, maxB, h->status, st);
-  trace_end(h, PH_SCAN, st, 2);
+  if (norm) {
+    launch_norm<T>(A, v.ldA, v.a_kcontig, v.M, k, cw, maxA, reinterpret_cast<unsigned long long*>(ws + pl.off_accA),
+                   nEA, st);
+    launch_norm<T>(B, v.ldB, v.b_kcontig, v.N, k, cw, maxB, reinterpret_cast<unsigned long long*>(ws + pl.off_accB),
+                   nEB, st);
+  }
+  trace_end(h, PH_SCAN, st, norm ? 6 : 2);
   trace_begin(h, PH_SPLIT, st);
-  launch_split_II<T>(A, v.ldA, v.a_kcontig, v.M, k, nm, b, cw, mt, maxA, resA, EA, st);
-  launch_split_II<T>(B, v.ldB, v.b_kcontig, v.N, k, nm, b, cw, mt, maxB, resB, FB, st);
+  launch_split_II<T>(A, v.ldA, v.a_kcontig, v.M, k, nm, bA, cw, mt, maxA, resA, EA, st, norm ? nEA : nullptr);
+  launch_split_II<T>(B, v.ldB, v.b_kcontig, v.N, k, nm, bB, cw, mt, maxB, resB, FB, st, norm ? nEB : nullptr);
   trace_end(h, PH_SPLIT, st, 2);
   CUtensorMap ta, tb;
   if (!make_tmap_i8(&ta, resA, static_cast<uint64_t>(pl.cols),
@@ -581,7 +606,7 @@ emu_status_t run_scheme_II(emu_handle_s* h, const View& v, int64_t k, int nm, in
   a.rowsA_pad = static_cast<int>(pl.rows_a);
   a.rowsB_pad = static_cast<int>(pl.rows_b);
   a.nm = nm;
-  a.escale = -2 * b;
+  a.escale = -(bA + bB);
   a.EA = EA;
   a.FB = FB;
   a.alpha_re = ar;
@@ -619,7 +644,7 @@ emu_status_t emu_workspace_size(emu_scheme_t scheme, int64_t m, int64_t n, int64
     *bytes = is_complex ? workspace_complex_I(m, n, k, p_or_nm) : plan_I(m, n, k, p_or_nm).bytes;
     return EMU_OK;
   }
-  if (scheme == EMU_SCHEME_II) {
+  if (scheme == EMU_SCHEME_II || scheme == EMU_SCHEME_II_NORM) {
     if (p_or_nm < EMU_NM_MIN || p_or_nm > EMU_NM_MAX) return EMU_ERR_UNSUPPORTED;
     *bytes = plan_II(m, n, k, p_or_nm, is_complex ? 3 : 1).bytes;
     return EMU_OK;
@@ -641,7 +666,7 @@ static emu_status_t gemm_common(emu_handle_t h, emu_layout_t layout, int64_t m, 
   if (m > 0 && n > 0 && k > 0 && (!A || !B)) return EMU_ERR_INVALID_ARG;
   if (scheme == EMU_SCHEME_I || scheme == EMU_SCHEME_I_F8) {
     if (p_or_nm < EMU_P_MIN || p_or_nm > EMU_P_MAX) return EMU_ERR_UNSUPPORTED;
-  } else if (scheme == EMU_SCHEME_II) {
+  } else if (scheme == EMU_SCHEME_II || scheme == EMU_SCHEME_II_NORM) {
     if (p_or_nm < EMU_NM_MIN || p_or_nm > EMU_NM_MAX) return EMU_ERR_UNSUPPORTED;
     if (k > EMU_K_MAX_II) return EMU_ERR_UNSUPPORTED;
   } else {
@@ -671,7 +696,7 @@ static emu_status_t real_gemm(emu_handle_t h, emu_layout_t layout, int64_t m, in
     return run_scheme_I<T>(h, v, k, p_or_nm, alpha, beta, C, ldc, out == 0 ? OUT_F64 : OUT_F32, nullptr,
                            st, nullptr, scheme == EMU_SCHEME_I_F8);
   return run_scheme_II<T>(h, v, k, p_or_nm, 1, alpha, 0.0, beta, 0.0, C, ldc, out == 0 ? II_F64 : II_F32,
-                          nullptr, st);
+                          nullptr, st, scheme == EMU_SCHEME_II_NORM);
 }
 
 extern "C" {
@@ -709,7 +734,7 @@ emu_status_t emu_zgemm(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n
     return run_complex_I<double>(h, layout, m, n, k, A, lda, B, ldb, nm, scheme == EMU_SCHEME_I_F8, alpha, beta,
                                  C, ldc, st);
   return run_scheme_II<double>(h, v, k, nm, 2, alpha[0], alpha[1], beta[0], beta[1], C, ldc, II_Z3M,
-                               nullptr, st);
+                               nullptr, st, scheme == EMU_SCHEME_II_NORM);
 }
 
 emu_status_t emu_cgemm(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k,
@@ -730,8 +755,9 @@ emu_status_t emu_cgemm(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n
         <<<static_cast<unsigned>((tot + 255) / 256), 256, 0, st>>>(C, ldc, v.M, v.N, be[0], be[1]);
     return cuda_err(cudaGetLastError());
   }
-  if (scheme == EMU_SCHEME_II)
-    return run_scheme_II<float>(h, v, k, p_or_nm, 2, al[0], al[1], be[0], be[1], C, ldc, II_C3M, nullptr, st);
+  if (scheme == EMU_SCHEME_II || scheme == EMU_SCHEME_II_NORM)
+    return run_scheme_II<float>(h, v, k, p_or_nm, 2, al[0], al[1], be[0], be[1], C, ldc, II_C3M, nullptr, st,
+                                scheme == EMU_SCHEME_II_NORM);
   return run_complex_I<float>(h, layout, m, n, k, A, lda, B, ldb, p_or_nm, scheme == EMU_SCHEME_I_F8, al, be, C,
                               ldc, st);
 }

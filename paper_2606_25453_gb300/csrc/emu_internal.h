@@ -54,7 +54,13 @@ void launch_split_I(const T* X, int64_t ld, bool kcontig, int64_t rows, int64_t 
 template <typename T>
 void launch_split_II(const T* X, int64_t ld, bool kcontig, int64_t rows, int64_t k, int nm, int b,
                      int cw, const ModTables& tabs, const unsigned long long* maxbits, int8_t* res,
-                     int32_t* E, cudaStream_t st);
+                     int32_t* E, cudaStream_t st, const int32_t* Ein = nullptr);
+// Norm-based Scheme II scaling: E[r] with ||x_r||_2 < 2^E[r], computed
+// exactly (maxbits from launch_scan; acc: 2 rows words of scratch).
+template <typename T>
+void launch_norm(const T* X, int64_t ld, bool kcontig, int64_t rows, int64_t k, int cw,
+                 const unsigned long long* maxbits, unsigned long long* acc, int32_t* E, cudaStream_t st);
+void host_norm_halves_II(int nm, int* hA, int* hB);
 
 // Output modes of the Scheme I kernel.
 enum GemmOut : int { OUT_F64 = 0, OUT_F32 = 1, OUT_PARTIALS = 2 };

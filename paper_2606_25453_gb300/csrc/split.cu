@@ -103,6 +103,104 @@ __global__ void scan_kernel(const T* __restrict__ X, int64_t ld, int64_t rows, i
   }
 }
 
+// ------------------------------------------------------------------ norm scan
+// Norm-based Scheme II scaling: e_r with ||x_r||_2 < 2^e_r, computed exactly
+// so that the value does not depend on the summation order.  With E the
+// frexp exponent of the row maximum and y = x 2^-E (|y| < 1), every square
+// is rounded UP to an integer number of units 2^-64, the integers are summed
+// (order-free, 128 bits), and e = E + ceil((bitlen(S) - 64) / 2).
+__device__ __forceinline__ unsigned __int128 sq_ceil64(uint64_t bits, int Emax) {
+  const uint64_t ab = bits & 0x7FFFFFFFFFFFFFFFull;
+  if (ab == 0) return 0;
+  const int ef = static_cast<int>(ab >> 52);
+  uint64_t M = ab & ((uint64_t{1} << 52) - 1);
+  int q;  // |x| = M 2^q
+  if (ef == 0) {
+    q = -1074;
+  } else {
+    M |= uint64_t{1} << 52;
+    q = ef - 1075;
+  }
+  const unsigned __int128 M2 = static_cast<unsigned __int128>(M) * M;
+  const int sh = 2 * (q - Emax) + 64;
+  if (sh >= 0) return M2 << sh;  // y^2 2^64 < 2^64
+  if (-sh >= 128) return 1;
+  unsigned __int128 r = M2 >> (-sh);
+  if ((r << (-sh)) != M2) r += 1;
+  return r;
+}
+
+// Exact 128-bit atomic add on (lo, hi) words.
+__device__ __forceinline__ void atomic_add_u128(unsigned long long* acc, unsigned __int128 v) {
+  const unsigned long long lo = static_cast<unsigned long long>(v), hi = static_cast<unsigned long long>(v >> 64);
+  const unsigned long long old = atomicAdd(acc, lo);
+  const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+  if (hi + carry) atomicAdd(acc + 1, hi + carry);
+}
+
+__device__ __forceinline__ unsigned __int128 shfl_add_u128(unsigned __int128 v) {
+  for (int o = 16; o; o >>= 1) {
+    const unsigned long long lo = __shfl_xor_sync(0xffffffffu, static_cast<unsigned long long>(v), o);
+    const unsigned long long hi = __shfl_xor_sync(0xffffffffu, static_cast<unsigned long long>(v >> 64), o);
+    v += (static_cast<unsigned __int128>(hi) << 64) | lo;
+  }
+  return v;
+}
+
+// Same launch shapes as scan_kernel; acc: 2 words per row, zeroed first.
+template <typename T, bool KCONTIG>
+__global__ void norm_kernel(const T* __restrict__ X, int64_t ld, int64_t rows, int64_t k, int cw,
+                            const unsigned long long* __restrict__ maxbits, unsigned long long* __restrict__ acc) {
+  if (KCONTIG) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= rows) return;
+    const uint64_t mb = maxbits[r];
+    if (mb == 0 || mb >= 0x7FF0000000000000ull) return;  // zero row / non-finite (flagged by the scan)
+    const int Emax = frexp_exp_bits(mb);
+    const int64_t len = k * cw, seg = 2048;
+    const int64_t h0 = static_cast<int64_t>(blockIdx.y) * seg;
+    const int64_t h1 = h0 + seg < len ? h0 + seg : len;
+    const T* row = X + r * ld * cw;
+    unsigned __int128 sum = 0;
+    for (int64_t h = h0 + lane; h < h1; h += 32) sum += sq_ceil64(load_bits(row + h), Emax);
+    sum = shfl_add_u128(sum);
+    if (lane == 0 && sum) atomic_add_u128(acc + 2 * r, sum);
+  } else {
+    const int64_t r = static_cast<int64_t>(blockIdx.x) * 32 + threadIdx.x;
+    const int64_t seg = 256;
+    const int64_t h0 = static_cast<int64_t>(blockIdx.y) * seg;
+    const int64_t h1 = h0 + seg < k ? h0 + seg : k;
+    if (r >= rows) return;
+    const uint64_t mb = maxbits[r];
+    if (mb == 0 || mb >= 0x7FF0000000000000ull) return;
+    const int Emax = frexp_exp_bits(mb);
+    unsigned __int128 sum = 0;
+    for (int64_t h = h0 + threadIdx.y; h < h1; h += blockDim.y) {
+      const T* p = X + (h * ld + r) * cw;
+      sum += sq_ceil64(load_bits(p), Emax);
+      if (cw == 2) sum += sq_ceil64(load_bits(p + 1), Emax);
+    }
+    if (sum) atomic_add_u128(acc + 2 * r, sum);
+  }
+}
+
+__global__ void norm_finish_kernel(int64_t rows, const unsigned long long* __restrict__ maxbits,
+                                   const unsigned long long* __restrict__ acc, int32_t* __restrict__ E) {
+  const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  const unsigned long long lo = acc[2 * r], hi = acc[2 * r + 1];
+  const uint64_t mb = maxbits[r];
+  if ((lo | hi) == 0 || mb >= 0x7FF0000000000000ull) {
+    E[r] = 0;
+    return;
+  }
+  const int L = hi ? 128 - __clzll(static_cast<long long>(hi)) : 64 - __clzll(static_cast<long long>(lo));
+  const int d = L - 64;
+  const int ep = d >= 0 ? (d + 1) / 2 : -((-d) / 2);  // ceil(d / 2)
+  E[r] = frexp_exp_bits(mb) + ep;
+}
+
 // ------------------------------------------------------------------ split I
 // Bytes of the 8P-bit two's complement of x = sign * (mag << lsh).
 template <int P>
@@ -287,7 +385,8 @@ __global__ void split_II_kernel(const T* __restrict__ X, int64_t ld, int64_t row
                                 int64_t rows_pad, int64_t kpad, int nm, int b, int cw,
                                 const __grid_constant__ ModTables mt,
                                 const unsigned long long* __restrict__ maxbits,
-                                int8_t* __restrict__ res, int32_t* __restrict__ E_out) {
+                                const int32_t* __restrict__ Ein, int8_t* __restrict__ res,
+                                int32_t* __restrict__ E_out) {
   __shared__ uint8_t tab[kMaxModuli][kPow2TabLen];
   __shared__ uint32_t mods[kMaxModuli], two32[kMaxModuli];
   for (int i = threadIdx.x; i < nm * kPow2TabLen; i += blockDim.x)
@@ -307,7 +406,8 @@ __global__ void split_II_kernel(const T* __restrict__ X, int64_t ld, int64_t row
     r = idx % rows_pad;
   }
   if (r >= rows_pad || h >= kpad) return;
-  int E = exp_from_maxbits(maxbits, r, rows);
+  // row exponent: of the maximum (worst-case scaling) or of the 2-norm (Ein)
+  int E = Ein ? (r < rows ? Ein[r] : 0) : exp_from_maxbits(maxbits, r, rows);
   bool valid = r < rows && h < k;
   int64_t plane = rows_pad * kpad;
   int64_t off = r * kpad + h;
@@ -406,23 +506,46 @@ template void launch_split_I<float>(const float*, int64_t, bool, int64_t, int64_
 template <typename T>
 void launch_split_II(const T* X, int64_t ld, bool kcontig, int64_t rows, int64_t k, int nm, int b,
                      int cw, const ModTables& tabs, const unsigned long long* maxbits, int8_t* res,
-                     int32_t* E, cudaStream_t st) {
+                     int32_t* E, cudaStream_t st, const int32_t* Ein) {
   int64_t rows_pad = split_rows(rows), kpad = split_cols_II(k);
   int64_t total = rows_pad * kpad;
   if (total == 0) return;
   int64_t blocks = (total + 255) / 256;
   if (kcontig)
     split_II_kernel<T, true><<<static_cast<unsigned>(blocks), 256, 0, st>>>(
-        X, ld, rows, k, rows_pad, kpad, nm, b, cw, tabs, maxbits, res, E);
+        X, ld, rows, k, rows_pad, kpad, nm, b, cw, tabs, maxbits, Ein, res, E);
   else
     split_II_kernel<T, false><<<static_cast<unsigned>(blocks), 256, 0, st>>>(
-        X, ld, rows, k, rows_pad, kpad, nm, b, cw, tabs, maxbits, res, E);
+        X, ld, rows, k, rows_pad, kpad, nm, b, cw, tabs, maxbits, Ein, res, E);
 }
+
+template <typename T>
+void launch_norm(const T* X, int64_t ld, bool kcontig, int64_t rows, int64_t k, int cw,
+                 const unsigned long long* maxbits, unsigned long long* acc, int32_t* E, cudaStream_t st) {
+  if (rows == 0) return;
+  cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * 2 * rows, st);
+  if (k > 0) {
+    if (kcontig) {
+      int64_t len = k * cw;
+      dim3 grid(static_cast<unsigned>((rows + 7) / 8), static_cast<unsigned>((len + 2047) / 2048));
+      norm_kernel<T, true><<<grid, 256, 0, st>>>(X, ld, rows, k, cw, maxbits, acc);
+    } else {
+      dim3 grid(static_cast<unsigned>((rows + 31) / 32), static_cast<unsigned>((k + 255) / 256));
+      norm_kernel<T, false><<<grid, dim3(32, 8), 0, st>>>(X, ld, rows, k, cw, maxbits, acc);
+    }
+  }
+  norm_finish_kernel<<<static_cast<unsigned>((rows + 255) / 256), 256, 0, st>>>(rows, maxbits, acc, E);
+}
+template void launch_norm<double>(const double*, int64_t, bool, int64_t, int64_t, int, const unsigned long long*,
+                                  unsigned long long*, int32_t*, cudaStream_t);
+template void launch_norm<float>(const float*, int64_t, bool, int64_t, int64_t, int, const unsigned long long*,
+                                 unsigned long long*, int32_t*, cudaStream_t);
+
 template void launch_split_II<double>(const double*, int64_t, bool, int64_t, int64_t, int, int, int,
                                       const ModTables&, const unsigned long long*, int8_t*, int32_t*,
-                                      cudaStream_t);
+                                      cudaStream_t, const int32_t*);
 template void launch_split_II<float>(const float*, int64_t, bool, int64_t, int64_t, int, int, int,
                                      const ModTables&, const unsigned long long*, int8_t*, int32_t*,
-                                     cudaStream_t);
+                                     cudaStream_t, const int32_t*);
 
 }  // namespace emu

@@ -55,7 +55,8 @@ def test_argument_validation_without_gpu(lib):
     assert lib.emu_workspace_size(1, 10, 10, 10, 13, 0, ctypes.byref(sz)) == 2
     assert lib.emu_workspace_size(2, 10, 10, 10, 21, 0, ctypes.byref(sz)) == 2
     assert lib.emu_workspace_size(3, 10, 10, 10, 5, 0, ctypes.byref(sz)) == 0  # E4M3 slices
-    assert lib.emu_workspace_size(4, 10, 10, 10, 5, 0, ctypes.byref(sz)) == 1
+    assert lib.emu_workspace_size(4, 10, 10, 10, 5, 0, ctypes.byref(sz)) == 0  # Scheme II, norm scaling
+    assert lib.emu_workspace_size(5, 10, 10, 10, 5, 0, ctypes.byref(sz)) == 1
     assert lib.emu_dgemm(None, 0, 4, 4, 4, 1.0, None, 4, None, 4, 0.0, None, 4, 1, 3, None) == 1
     assert lib.emu_status_string(6) == b"EMU_ERR_TIMEOUT"
     # column-major leading dimensions must cover the rows
