@@ -545,7 +545,7 @@ def run_suite(path, args):
     for phi in (0.5, 4.0):
         A, B, Ad, Bd = pair(8192, phi)
         Cd = torch.empty((8192, 8192), dtype=torch.float64, device=dev)
-        for nm in (12, 14, 16, 18, 20):
+        for nm in (8, 10, 12, 14, 16, 18, 20):
             ms = timed(lambda: emu.dgemm(Ad, Bd, Cd, scheme="II", p=nm, handle=h))
             emit({"path": "emu_dgemm_II", "n": 8192, "phi": phi, "nm": nm, "tflops": 2 * 8192 ** 3 / ms / 1e9,
                   "int8_tops": 2 * nm * 8192 ** 3 / ms / 1e9, "ms": ms, "err": sampled_err(A, B, Cd.cpu().numpy())})
