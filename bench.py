@@ -131,24 +131,27 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ helpers
-def file_sha(path):
-    with open(path, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()
+def file_sha(paths):
+    h = hashlib.sha256()
+    for path in paths:
+        with open(path, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
-def load_traffic(p, n):
-    """DRAM bytes per launch of the fused GEMM from the committed ncu summary,
-    only if the kernel source is unchanged since the capture."""
-    path = os.path.join(ROOT, "profiles", "gemm_I_traffic.json")
+def load_traffic(name, key):
+    """DRAM bytes per launch of a fused GEMM kernel from the committed ncu
+    summary profiles/<name>_traffic.json, only if the kernel sources are
+    unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", name + "_traffic.json")
     if not os.path.exists(path):
         return None
     try:
         d = json.load(open(path))
-        src = os.path.join(ROOT, "paper_2606_25453_gb300", "csrc", "gemm_I.cu")
-        if d.get("gemm_I_cu_sha256") != file_sha(src):
+        srcs = [os.path.join(ROOT, "paper_2606_25453_gb300", "csrc", f) for f in d["sources"]]
+        if d.get("source_sha256") != file_sha(srcs):
             return None
-        ent = d.get("per_launch", {}).get("p%d_n%d" % (p, n))
-        return ent
+        return d.get("per_launch", {}).get(key)
     except Exception:
         return None
 
@@ -194,10 +197,16 @@ def fp8_engine_leg(emu, h, Ad, Bd, Cd, n, stream, ri, ci, A, B, hi, lo, den, cub
         got = Cd[ri][:, ci].cpu().numpy()
         err = float(np.max(np.abs((got - hi) - lo) / den))
         gms = tr["ms_gemm"] / max(tr["gemm_launches"], 1)
+        f8_tops = p * (p + 1) * n ** 3 / (gms * 1e-3) / 1e12
+        bf16 = measured_peaks().get("bf16_tflops") or 1900.0
         out["p%d" % p] = {"tflops": 2.0 * n ** 3 / (ms * 1e-3) / 1e12, "ms_per_step": ms,
-                          "gemm_8bit_tops": p * (p + 1) * n ** 3 / (gms * 1e-3) / 1e12,
+                          "gemm_8bit_tops": f8_tops, "gemm_ms": gms,
+                          "frac_of_fp8_peak": f8_tops / (2.0 * bf16),
+                          "fp8_peak_tflops": 2.0 * bf16,
+                          "algorithmic_bytes": p * 2 * n * n + 8 * n * n,
+                          "dram_traffic_bytes": load_traffic("gemm_f8tc", "p%d_n%d" % (p, n)),
                           "err_max_rel_absAB": err, "speedup_vs_cublas_dgemm": 2.0 * n ** 3 / (ms * 1e-3) / 1e12 / cublas_tflops,
-                          "bits_per_slice": 5}
+                          "bits_per_slice": 5, "kernel": "gemm_f8tc_kernel<%d, OUT_F64> (tcgen05)" % p}
     return out
 
 
@@ -387,20 +396,28 @@ def run_ours(args, rank, world, local_rank):
             peak = 2.0 * bf16 if bf16 else 2.0 * 1900.0
             peak_src = ("FP8 dense peak = measured bf16 %s x nominal FP8/bf16 ratio 2 (4.5 / 2.25 PFLOP/s)"
                         % ("(MEASURED_PEAKS.json)" if bf16 else "(fallback 1.9 PFLOP/s)"))
-        traffic = load_traffic(p, n) if args.scheme == "I" else None
+        traffic = (load_traffic("gemm_I", "p%d_n%d" % (p, n)) if args.scheme == "I" else
+                   load_traffic("gemm_f8tc", "p%d_n%d" % (p, n)) if args.scheme == "I_F8" else None)
+        kname = ("gemm_II_kernel" if args.scheme == "II" else
+                 "gemm_f8tc_kernel<%d, OUT_F64> (tcgen05)" % p if args.scheme == "I_F8" else
+                 "gemm_I_kernel<%d, OUT_F64> (mma.sync INT8)" % p)
+        ops_desc = ("INT8 ops 2 N_m M N K" if args.scheme == "II" else
+                    "exact E4M3 products p(p+1) M N K (multiply+add = 2)" if args.scheme == "I_F8" else
+                    "INT8 ops p(p+1) M N K (multiply+add = 2)")
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "int8->int32 (f64 in/out)", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "e4m3->fp32 (f64 in/out)" if args.scheme == "I_F8" else "int8->int32 (f64 in/out)",
+                "data": "synthetic",
                 "config": config(args, world),
                 "int8_tops": int8_ops * args.steps * world / (ms * 1e-3) / 1e12,
                 "int8_frac_of_peak": (int8_ops * args.steps / (ms * 1e-3) / 1e12 / int8_peak) if int8_peak else None,
                 "roofline": {"bound": "tensor",
-                             "kernel": ("gemm_II_kernel" if args.scheme == "II" else
-                                        "gemm_I_kernel<%d, F8=%d>" % (p, args.scheme == "I_F8")),
+                             "kernel": kname,
                              "achieved": achieved,
                              "peak": peak, "unit": UNIT, "frac": (achieved / peak) if peak else None,
                              "traffic": traffic,
-                             "ops": "INT8 ops p(p+1) M N K (multiply+add = 2)",
+                             "ops": ops_desc,
                              "peak_source": peak_src},
                 "phase_ms_per_step": {k2: tr[k2] / args.steps for k2 in ("ms_scan", "ms_split", "ms_gemm")},
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * n * n,

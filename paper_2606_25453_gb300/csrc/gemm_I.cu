@@ -76,8 +76,12 @@ template <int P>
 __device__ __forceinline__ void issue_loads(const KParamsI& kp, uint8_t* smem, uint64_t* full, uint32_t j) {
   using Cfg = CfgI<P>;
   const uint32_t stage = j % Cfg::kStages;
-  const int tile = blockIdx.x + static_cast<int>(j / kp.nk32) * gridDim.x;
-  const int kk = static_cast<int>(j % kp.nk32);
+  const int t = static_cast<int>(j / kp.nk32);
+  const int tile = blockIdx.x + t * gridDim.x;
+  // every other wave of tiles walks K backwards: it starts on the chunks the
+  // previous wave read last, which are still in L2 (the sums are exact, so
+  // their order does not matter)
+  const int kk = (t & 1) ? kp.nk32 - 1 - static_cast<int>(j % kp.nk32) : static_cast<int>(j % kp.nk32);
   int tm, tn;
   tile_coords(tile, kp.tiles_m, kp.tiles_n, tm, tn);
   mbar_arrive_expect_tx(&full[stage], Cfg::kStageBytes);

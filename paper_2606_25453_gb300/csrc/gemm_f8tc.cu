@@ -300,8 +300,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1) gemm_f8tc_kernel(const __grid_c
           ok = false;
           break;
         }
-        const int tile = cid + static_cast<int>(j / kp.nk32) * ncl;
-        const int kk = static_cast<int>(j % kp.nk32);
+        const int tt = static_cast<int>(j / kp.nk32);
+        const int tile = cid + tt * ncl;
+        // every other wave of tiles walks K backwards, starting on the chunks
+        // the previous wave read last (still in L2); the sums are exact, so
+        // their order does not matter
+        const int kk = (tt & 1) ? kp.nk32 - 1 - static_cast<int>(j % kp.nk32) : static_cast<int>(j % kp.nk32);
         int tm, tg;
         tile_coords(tile, kp.tiles_m, kp.tiles_ng, tm, tg);
         const int tn = tg * cl + crank;
