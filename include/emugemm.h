@@ -368,6 +368,7 @@ emu_status_t emu_load_tuning(emu_handle_t h, const char *path);
 #define EMU_SEL_HID 64
 #define EMU_SEL_OUT 8
 #define EMU_SEL_P0 3
+#define EMU_SEL_NM0 6 /* Scheme II selector: classes N = 6, 8, .., 20 */
 #define EMU_SEL_NPARAM 8968
 
 /* Features of one product (device output float[66]): 32-bin histogram of
@@ -405,6 +406,10 @@ emu_status_t emu_sel_adam(emu_handle_t h, float *params_dev, const float *grad_d
 /* Install trained parameters (host array of 8968 floats) in the handle. */
 emu_status_t emu_sel_load(emu_handle_t h, const float *params_host);
 
+/* Install trained parameters of the Scheme II selector (same network,
+ * classes N = EMU_SEL_NM0 + 2c moduli, c = 0..7, for EMU_SCHEME_II_NORM). */
+emu_status_t emu_sel_load_II(emu_handle_t h, const float *params_host);
+
 /* Double-double reference of sampled output entries (the selector's judge):
  * for the `count` (i, j) pairs in idx_dev (int32 pairs), ref_dev receives
  * (hi, lo) of sum_h a_ih b_hj computed with error-free transformations in
@@ -429,6 +434,24 @@ emu_status_t emu_dgemm_auto(emu_handle_t h, emu_layout_t layout, int64_t m, int6
                             double alpha, const double *A, int64_t lda, const double *B,
                             int64_t ldb, double *C, int64_t ldc, double tol, int probe,
                             int *p_used_host, emu_stream_t stream);
+
+/* Auto precision with Scheme II (norm-based scaling, EMU_SCHEME_II_NORM):
+ * as emu_dgemm_auto with N moduli in place of p -- class c means N = 6 + 2c,
+ * the top class means EMU_NM_MAX; on a probe miss N is raised to
+ * max(N + 2, the bound-based N), then to EMU_NM_MAX.  *nm_used_host receives
+ * the N of the returned result; EMU_ERR_TOL_NOT_MET if EMU_NM_MAX misses. */
+emu_status_t emu_dgemm_auto_II(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k,
+                               double alpha, const double *A, int64_t lda, const double *B,
+                               int64_t ldb, double *C, int64_t ldc, double tol, int probe,
+                               int *nm_used_host, emu_stream_t stream);
+
+/* Bound-based number of moduli for EMU_SCHEME_II_NORM (host): the smallest
+ * N in 6, 8, .., 20 with 2^(-h(N) + spread + ceil(log2(k)/2) + 3) <= tol,
+ * h(N) the shared scale bits and spread as in emu_bound_p (20 if none
+ * does).  A heuristic from the per-term truncation error, not a guarantee. */
+emu_status_t emu_bound_nm(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k,
+                          const double *A, int64_t lda, const double *B, int64_t ldb, double tol,
+                          int *nm_host, emu_stream_t stream);
 
 /* Bound-based slice count for tolerance tol from the exponent statistics
  * (host): smallest p in [3, 10] whose worst-case truncation bound

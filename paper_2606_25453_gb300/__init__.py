@@ -90,6 +90,10 @@ _SIGS = {
     "emu_dgemm_auto": (_i32, [_vp, _i32, _i64, _i64, _i64, _dbl, _vp, _i64, _vp, _i64, _vp, _i64, _dbl, _i32,
                               ctypes.POINTER(_i32), _vp]),
     "emu_bound_p": (_i32, [_vp, _i32, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _dbl, ctypes.POINTER(_i32), _vp]),
+    "emu_sel_load_II": (_i32, [_vp, ctypes.POINTER(_flt)]),
+    "emu_dgemm_auto_II": (_i32, [_vp, _i32, _i64, _i64, _i64, _dbl, _vp, _i64, _vp, _i64, _vp, _i64, _dbl, _i32,
+                                 ctypes.POINTER(_i32), _vp]),
+    "emu_bound_nm": (_i32, [_vp, _i32, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _dbl, ctypes.POINTER(_i32), _vp]),
     "emu_trace_enable": (_i32, [_vp, _i32]),
     "emu_trace_read": (_i32, [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
 }
@@ -372,9 +376,11 @@ def tune_grouped(descs, p: int = 6, path: str | None = None, handle=None, stream
     return timed.value
 
 
-def dgemm_auto(A, B, tol: float, alpha: float = 1.0, probe: int = 64, handle=None, stream=None):
-    """C = alpha*A@B with the p chosen by the selector (or the bound if no
-    weights are loaded), checked on `probe` sampled entries; returns (C, p)."""
+def dgemm_auto(A, B, tol: float, alpha: float = 1.0, probe: int = 64, handle=None, stream=None, scheme="I"):
+    """C = alpha*A@B with the p (scheme="I") or the N moduli (scheme="II":
+    Scheme II with norm scaling) chosen by the selector -- the bound if no
+    weights are loaded -- checked on `probe` sampled entries; returns
+    (C, p or N, status code)."""
     import torch
     m, k = A.shape
     n = B.shape[1]
@@ -382,8 +388,9 @@ def dgemm_auto(A, B, tol: float, alpha: float = 1.0, probe: int = 64, handle=Non
     layout, lda, ldb, ldc = _layout_of(A, B, C)
     h = handle or default_handle(A.device.index or 0)
     p = _i32()
-    code = emu_dgemm_auto(h.h, layout, m, n, k, alpha, _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc, tol, probe,
-                          ctypes.byref(p), _stream_ptr(stream))
+    fn = emu_dgemm_auto_II if scheme in ("II", "II_NORM", 2, 4) else emu_dgemm_auto
+    code = fn(h.h, layout, m, n, k, alpha, _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc, tol, probe, ctypes.byref(p),
+              _stream_ptr(stream))
     if code not in (0, 7):
-        check(code, "emu_dgemm_auto")
+        check(code, fn.__name__)
     return C, p.value, code

@@ -25,8 +25,10 @@ constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kHid * kIn, kOffW2 = kOffB1 + kHid, 
 static_assert(kNParam == EMU_SEL_NPARAM, "parameter count");
 
 struct SelState {
-  float* params = nullptr;  // device, loaded weights
+  float* params = nullptr;  // device, loaded weights (Scheme I: classes p = 3..10)
   bool loaded = false;
+  float* params_II = nullptr;  // Scheme II, norm scaling: classes N = 6, 8, .., 20
+  bool loaded_II = false;
 };
 SelState* sel_of(emu_handle_s* h) {
   if (!h->selector) h->selector = new SelState();
@@ -230,6 +232,7 @@ void selector_release(emu_handle_s* h) {
   auto* s = static_cast<SelState*>(h->selector);
   if (!s) return;
   if (s->params) cudaFree(s->params);
+  if (s->params_II) cudaFree(s->params_II);
   delete s;
   h->selector = nullptr;
 }
@@ -271,6 +274,26 @@ bool valid_layout(emu_layout_t l) { return l == EMU_ROW_MAJOR || l == EMU_COL_MA
 
 // Bound-based p: smallest p in [3, 10] with 2^(-8p+3) * 2^spread * k <= tol,
 // spread = the upper edge of the largest exponent-deficit bin seen.
+// Scheme II with norm scaling: a' = trunc(a 2^(h - e_i)) errs by less than
+// 2^(e_i - h) and e_i exceeds the frexp exponent of an entry by at most the
+// deficit d against the row maximum plus ceil(log2(k) / 2), so every term
+// of the product errs by at most 2^(-h + d + ceil(log2(k)/2) + 3) of its
+// magnitude.  Smallest N in 6, 8, .., 20 meeting tol with d = spread (20 if
+// none does).  A heuristic fallback, like the Scheme I bound.
+int bound_nm_from_hist(const float* f, int64_t k, double tol) {
+  int spread = 0;
+  for (int i = 0; i < 64; ++i)
+    if (f[i] > 0.f) spread = std::max(spread, 3 * (i % 32) + 2);
+  int half_lk = 0;
+  while ((int64_t{1} << (2 * half_lk)) < k) ++half_lk;  // ceil(log2(k) / 2)
+  for (int nm = EMU_SEL_NM0; nm <= EMU_NM_MAX; nm += 2) {
+    int hA, hB;
+    host_norm_halves_II(nm, &hA, &hB);
+    if (std::ldexp(1.0, -hA + spread + half_lk + 3) <= tol) return nm;
+  }
+  return EMU_NM_MAX;
+}
+
 int bound_p_from_hist(const float* f, int64_t k, double tol) {
   int spread = 0;
   for (int i = 0; i < 64; ++i)
@@ -278,6 +301,32 @@ int bound_p_from_hist(const float* f, int64_t k, double tol) {
   for (int p = 3; p <= 10; ++p)
     if (std::ldexp(1.0, -8 * p + 3 + spread) * static_cast<double>(k) <= tol) return p;
   return 10;
+}
+
+// Bound-based choice (host), shared by emu_bound_p and emu_bound_nm.
+emu_status_t bound_impl(emu_handle_s* h, emu_layout_t layout, int64_t m, int64_t n, int64_t k, const double* A,
+                        int64_t lda, const double* B, int64_t ldb, double tol, int* out, emu_stream_t stream,
+                        bool scheme_II) {
+  if (!out || !h) return EMU_ERR_INVALID_ARG;
+  if ((layout != EMU_ROW_MAJOR && layout != EMU_COL_MAJOR) || m < 1 || n < 1 || k < 1 || !A || !B || !(tol > 0.0))
+    return EMU_ERR_INVALID_ARG;
+  cudaSetDevice(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  View v;
+  normalize(layout, m, n, A, lda, B, ldb, &v);
+  uint8_t* ws = nullptr;
+  const size_t need = feat_scratch(v) + 512;
+  emu_status_t s = handle_workspace(h, need, st, &ws);
+  if (s != EMU_OK) return s;
+  float* feat = reinterpret_cast<float*>(ws + feat_scratch(v));
+  s = features_impl(h, v, k, tol, 64, feat, ws, st);
+  if (s != EMU_OK) return s;
+  float f[kIn];
+  if (cudaMemcpyAsync(f, feat, sizeof(f), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return EMU_ERR_CUDA;
+  *out = scheme_II ? bound_nm_from_hist(f, k, tol) : bound_p_from_hist(f, k, tol);
+  return EMU_OK;
 }
 
 }  // namespace
@@ -348,6 +397,17 @@ emu_status_t emu_sel_load(emu_handle_t h, const float* params) {
   return EMU_OK;
 }
 
+emu_status_t emu_sel_load_II(emu_handle_t h, const float* params) {
+  if (!h || !params) return EMU_ERR_INVALID_ARG;
+  cudaSetDevice(h->device);
+  SelState* s = sel_of(h);
+  if (!s->params_II && cudaMalloc(&s->params_II, sizeof(float) * kNParam) != cudaSuccess) return EMU_ERR_ALLOC;
+  if (cudaMemcpy(s->params_II, params, sizeof(float) * kNParam, cudaMemcpyHostToDevice) != cudaSuccess)
+    return EMU_ERR_CUDA;
+  s->loaded_II = true;
+  return EMU_OK;
+}
+
 emu_status_t emu_probe_dd(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k, const double* A,
                           int64_t lda, const double* B, int64_t ldb, int count, const int32_t* idx, double* ref,
                           double* absab, emu_stream_t stream) {
@@ -366,33 +426,22 @@ emu_status_t emu_probe_dd(emu_handle_t h, emu_layout_t layout, int64_t m, int64_
 
 emu_status_t emu_bound_p(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k, const double* A,
                          int64_t lda, const double* B, int64_t ldb, double tol, int* p_out, emu_stream_t stream) {
-  if (!p_out) return EMU_ERR_INVALID_ARG;
-  float* feat = nullptr;
-  if (!h) return EMU_ERR_INVALID_ARG;
-  cudaSetDevice(h->device);
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // features into the tail of the workspace region
-  View v;
-  if (!valid_layout(layout) || m < 1 || n < 1 || k < 1 || !A || !B || !(tol > 0.0)) return EMU_ERR_INVALID_ARG;
-  normalize(layout, m, n, A, lda, B, ldb, &v);
-  uint8_t* ws = nullptr;
-  size_t need = feat_scratch(v) + 512;
-  emu_status_t s = handle_workspace(h, need, st, &ws);
-  if (s != EMU_OK) return s;
-  feat = reinterpret_cast<float*>(ws + feat_scratch(v));
-  s = features_impl(h, v, k, tol, 64, feat, ws, st);
-  if (s != EMU_OK) return s;
-  float f[kIn];
-  if (cudaMemcpyAsync(f, feat, sizeof(f), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess)
-    return EMU_ERR_CUDA;
-  *p_out = bound_p_from_hist(f, k, tol);
-  return EMU_OK;
+  return bound_impl(h, layout, m, n, k, A, lda, B, ldb, tol, p_out, stream, false);
 }
 
-emu_status_t emu_dgemm_auto(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k, double alpha,
-                            const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc,
-                            double tol, int probe, int* p_used, emu_stream_t stream) {
+emu_status_t emu_bound_nm(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k, const double* A,
+                          int64_t lda, const double* B, int64_t ldb, double tol, int* nm_out, emu_stream_t stream) {
+  return bound_impl(h, layout, m, n, k, A, lda, B, ldb, tol, nm_out, stream, true);
+}
+
+}  // extern "C"
+
+namespace {
+// Shared by the Scheme I (p) and Scheme II (N moduli, norm scaling) auto
+// entry points: selector class -> value, probe, escalation.
+emu_status_t auto_impl(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k, double alpha,
+                       const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc,
+                       double tol, int probe, int* p_used, emu_stream_t stream, bool scheme_II) {
   if (!h || !p_used || !A || !B || !C || m < 1 || n < 1 || k < 1 || !(tol > 0.0) || probe < 0 || !valid_layout(layout))
     return EMU_ERR_INVALID_ARG;
   if (!check_lds(layout, m, n, k, lda, ldb, ldc)) return EMU_ERR_INVALID_ARG;
@@ -412,14 +461,20 @@ emu_status_t emu_dgemm_auto(emu_handle_t h, emu_layout_t layout, int64_t m, int6
   s = features_impl(h, v, k, tol, 64, feat, ws, st);
   if (s != EMU_OK) return s;
   float f[kIn], pr[kOut];
-  if (ss->loaded) mlp_forward_kernel<<<1, kHid, 0, st>>>(ss->params, feat, 1, prob, nullptr);
+  const bool loaded = scheme_II ? ss->loaded_II : ss->loaded;
+  if (loaded) mlp_forward_kernel<<<1, kHid, 0, st>>>(scheme_II ? ss->params_II : ss->params, feat, 1, prob, nullptr);
   if (cudaMemcpyAsync(f, feat, sizeof(f), cudaMemcpyDeviceToHost, st) != cudaSuccess) return EMU_ERR_CUDA;
-  if (ss->loaded && cudaMemcpyAsync(pr, prob, sizeof(pr), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+  if (loaded && cudaMemcpyAsync(pr, prob, sizeof(pr), cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return EMU_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return EMU_ERR_CUDA;
-  const int pb = bound_p_from_hist(f, k, tol);
+  // value of class c and the largest value: p = 3 + c up to EMU_P_MAX, or
+  // N = 6 + 2c up to EMU_NM_MAX
+  const int top = scheme_II ? EMU_NM_MAX : EMU_P_MAX;
+  const int step = scheme_II ? 2 : 1;
+  const int base_v = scheme_II ? EMU_SEL_NM0 : EMU_SEL_P0;
+  const int pb = scheme_II ? bound_nm_from_hist(f, k, tol) : bound_p_from_hist(f, k, tol);
   int p = pb;
-  if (ss->loaded) {  // smallest class whose cumulative predicted probability reaches 0.8
+  if (loaded) {  // smallest class whose cumulative predicted probability reaches 0.8
     float c = 0.f;
     int cls = kOut - 1;
     for (int o = 0; o < kOut; ++o) {
@@ -429,8 +484,8 @@ emu_status_t emu_dgemm_auto(emu_handle_t h, emu_layout_t layout, int64_t m, int6
         break;
       }
     }
-    // the top class is open-ended ("10 or more"): go to the largest p at once
-    p = cls == kOut - 1 ? EMU_P_MAX : EMU_SEL_P0 + cls;
+    // the top class is open-ended ("10 or more" / "20"): go to the largest value at once
+    p = cls == kOut - 1 ? top : base_v + step * cls;
   }
   // probe entries: a deterministic spread over C (caller's coordinates)
   std::vector<int32_t> idx(2 * static_cast<size_t>(probe));
@@ -446,7 +501,8 @@ emu_status_t emu_dgemm_auto(emu_handle_t h, emu_layout_t layout, int64_t m, int6
     idx[2 * q + 1] = static_cast<int32_t>(x % static_cast<uint64_t>(n));
   }
   for (int attempt = 0; attempt < 3; ++attempt) {
-    s = emu_dgemm(h, layout, m, n, k, alpha, A, lda, B, ldb, 0.0, C, ldc, EMU_SCHEME_I, p, stream);
+    s = emu_dgemm(h, layout, m, n, k, alpha, A, lda, B, ldb, 0.0, C, ldc,
+                  scheme_II ? EMU_SCHEME_II_NORM : EMU_SCHEME_I, p, stream);
     if (s != EMU_OK) return s;
     *p_used = p;
     if (probe == 0) return EMU_OK;
@@ -485,12 +541,29 @@ emu_status_t emu_dgemm_auto(emu_handle_t h, emu_layout_t layout, int64_t m, int6
       worst = std::max(worst, e);
     }
     if (worst <= tol) return EMU_OK;
-    if (p >= EMU_P_MAX) return EMU_ERR_TOL_NOT_MET;
-    // a miss at the top class goes straight to the largest p
-    p = (attempt == 0 && p < EMU_SEL_P0 + kOut - 1) ? std::max(p + 1, pb) : EMU_P_MAX;
-    p = std::min(p, EMU_P_MAX);
+    if (p >= top) return EMU_ERR_TOL_NOT_MET;
+    // a miss at the top class goes straight to the largest value
+    p = (attempt == 0 && p < base_v + step * (kOut - 1)) ? std::max(p + step, pb) : top;
+    p = std::min(p, top);
   }
   return EMU_ERR_TOL_NOT_MET;
 }
+}  // namespace
+
+extern "C" {
+
+emu_status_t emu_dgemm_auto(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k, double alpha,
+                            const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc,
+                            double tol, int probe, int* p_used, emu_stream_t stream) {
+  return auto_impl(h, layout, m, n, k, alpha, A, lda, B, ldb, C, ldc, tol, probe, p_used, stream, false);
+}
+
+emu_status_t emu_dgemm_auto_II(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k, double alpha,
+                               const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc,
+                               double tol, int probe, int* nm_used, emu_stream_t stream) {
+  return auto_impl(h, layout, m, n, k, alpha, A, lda, B, ldb, C, ldc, tol, probe, nm_used, stream, true);
+}
+
+
 
 }  // extern "C"

@@ -24,14 +24,18 @@ import time
 
 import numpy as np
 
-from . import (GemmDesc, SEL_NPARAM, check, default_handle, emu_dgemm_grouped, emu_probe_dd, emu_sel_adam,
-               emu_sel_backward, emu_sel_features, emu_sel_forward, emu_sel_load, _stream_ptr)
+from . import (EMU_COL_MAJOR, EMU_ROW_MAJOR, EMU_SCHEME_II_NORM, GemmDesc, SEL_NPARAM, check, default_handle,
+               emu_dgemm, emu_dgemm_grouped, emu_moduli, emu_probe_dd, emu_sel_adam, emu_sel_backward,
+               emu_sel_features, emu_sel_forward, emu_sel_load, emu_sel_load_II, _stream_ptr)
 
 P0, NCLS = 3, 8
 P_TOP = 12  # escalation goes up to the library's largest p
 TOLS = (1e-8, 1e-12, 1e-15)
 SUB = 64
 WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "selector_weights.json")
+# Scheme II (norm-based scaling): classes N = 6, 8, .., 20 moduli
+NM_CLASSES = tuple(range(6, 21, 2))
+WEIGHTS_II = os.path.join(os.path.dirname(os.path.abspath(__file__)), "selector_weights_II.json")
 
 
 def _torch():
@@ -279,6 +283,128 @@ def evaluate(params, feats, errs, ks, train_errs):
     return res
 
 
+# ---------------------------------------------------------------- Scheme II
+def batch_errors_II(batch, h, stream=None, nms=NM_CLASSES):
+    """err[i, j] = max-relative error of the 64 x 64 block with Scheme II
+    (norm-based scaling) and N = nms[j] moduli.  Scheme II scales every row
+    of A and column of B on its own too, so the block equals that block of
+    the full product."""
+    torch = _torch()
+    dev = batch[0][2].device
+    n = len(batch)
+    ii, jj = np.meshgrid(np.arange(SUB), np.arange(SUB), indexing="ij")
+    idx = torch.from_numpy(np.stack([ii.ravel(), jj.ravel()], 1).astype(np.int32).ravel()).to(dev)
+    ref = torch.empty((n, SUB * SUB, 2), dtype=torch.float64, device=dev)
+    ab = torch.empty((n, SUB * SUB), dtype=torch.float64, device=dev)
+    C = torch.empty((n, len(nms), SUB, SUB), dtype=torch.float64, device=dev)
+    sp = _stream_ptr(stream)
+    for i, (_, k, A, B) in enumerate(batch):
+        check(emu_probe_dd(h.h, 0, SUB, SUB, k, A.data_ptr(), k, B.data_ptr(), SUB, SUB * SUB, idx.data_ptr(),
+                           ref[i].data_ptr(), ab[i].data_ptr(), sp), "emu_probe_dd")
+        for j, nm in enumerate(nms):
+            check(emu_dgemm(h.h, EMU_ROW_MAJOR, SUB, SUB, k, 1.0, A.data_ptr(), k, B.data_ptr(), SUB, 0.0,
+                            C[i, j].data_ptr(), SUB, EMU_SCHEME_II_NORM, nm, sp), "emu_dgemm")
+    hi, lo = ref[..., 0].unsqueeze(1), ref[..., 1].unsqueeze(1)
+    d = ((C.reshape(n, len(nms), SUB * SUB) - hi) - lo).abs()
+    abb = ab.unsqueeze(1)
+    rel = torch.where(abb > 0, d / torch.where(abb > 0, abb, torch.ones_like(abb)), torch.where(d > 0, math.inf, 0.0))
+    return rel.max(dim=2).values.cpu().numpy()
+
+
+def build_dataset_II(n_mats, seed, device="cuda", batch=256, log=None):
+    """features [n, 66] (tol entry 0), errors [n, 8] for N = 6, 8, .., 20, k [n], phi [n]."""
+    h = default_handle(0)
+    feats, errs, ks, phis = [], [], [], []
+    t0 = time.time()
+    for b0 in range(0, n_mats, batch):
+        seeds = [seed * 1000003 + i for i in range(b0, min(n_mats, b0 + batch))]
+        bt = gen_batch(seeds, device)
+        feats.append(batch_features(bt, h))
+        errs.append(batch_errors_II(bt, h))
+        ks += [k for _, k, _, _ in bt]
+        phis += [phi for phi, _, _, _ in bt]
+        if log:
+            log("dataset II %d/%d %.1fs" % (min(n_mats, b0 + batch), n_mats, time.time() - t0))
+    return np.concatenate(feats), np.concatenate(errs), np.array(ks), np.array(phis)
+
+
+def _scale_bits_II(nm):
+    """Shared scale bits h of the norm-based scaling: floor((floor(log2 P) - 1) / 2)."""
+    mods = (ctypes.c_int32 * nm)()
+    emu_moduli(nm, mods)
+    P = math.prod(int(x) for x in mods)
+    return (P.bit_length() - 2) // 2
+
+
+def bound_class_II(feats, ks, tols):
+    """Bound-based N (the emu_bound_nm rule) as a class index."""
+    hs = [_scale_bits_II(nm) for nm in NM_CLASSES]
+    out = []
+    for f, k, tol in zip(feats, ks, tols):
+        spread = max([3 * (i % 32) + 2 for i in range(64) if f[i] > 0] or [0])
+        half_lk = 0
+        while (1 << (2 * half_lk)) < k:
+            half_lk += 1
+        cls = NCLS - 1
+        for c, h in enumerate(hs):
+            if math.ldexp(1.0, -h + spread + half_lk + 3) <= tol:
+                cls = c
+                break
+        out.append(cls)
+    return np.array(out)
+
+
+def evaluate_II(params, feats, errs, ks, train_errs):
+    """As evaluate for Scheme II: classes N = 6, 8, .., 20, cost N (INT8 GEMMs);
+    the top class is N = 20 itself, a miss escalates to max(N + 2, bound N),
+    then to 20."""
+    res = {}
+    top = NCLS - 1
+    for tol in TOLS:
+        f = feats.copy()
+        f[:, 65] = np.float32(-math.log10(tol) / 16.0)
+        cls, _ = predict(params, f)
+        bcls = bound_class_II(f, ks, [tol] * len(f))
+        ok_train = train_errs <= tol
+        fixed = top
+        for c in range(top + 1):
+            if np.all(ok_train[:, c]):
+                fixed = c
+                break
+        used, costs, passed = [], [], []
+        for i in range(len(f)):
+            c = int(cls[i])
+            cst = NM_CLASSES[c]
+            tries = [max(c + 1, int(bcls[i])) if c < top else top, top]
+            for nxt in tries:
+                if errs[i, c] <= tol or c >= top:
+                    break
+                c = min(nxt, top)
+                cst += NM_CLASSES[c]
+            used.append(NM_CLASSES[c])
+            costs.append(cst)
+            passed.append(errs[i, c] <= tol)
+        bound_cost = float(np.mean([NM_CLASSES[c] for c in bcls]))
+        res["%g" % tol] = {
+            "learned": {"pass_rate": float(np.mean(passed)), "mean_nm": float(np.mean(used)),
+                        "mean_cost": float(np.mean(costs)),
+                        "first_try_rate": float(np.mean(errs[np.arange(len(f)), cls] <= tol))},
+            "fixed": {"nm": NM_CLASSES[fixed], "pass_rate": float(np.mean(errs[:, fixed] <= tol)),
+                      "mean_cost": float(NM_CLASSES[fixed])},
+            "bound": {"pass_rate": float(np.mean(errs[np.arange(len(f)), bcls] <= tol)),
+                      "mean_nm": float(np.mean([NM_CLASSES[c] for c in bcls])), "mean_cost": bound_cost},
+            "speedup_vs_fixed": float(NM_CLASSES[fixed] / np.mean(costs)),
+            "speedup_vs_bound": float(bound_cost / np.mean(costs)),
+        }
+    return res
+
+
+def install_II(params, handle=None):
+    h = handle or default_handle(0)
+    arr = np.ascontiguousarray(params, dtype=np.float32)
+    check(emu_sel_load_II(h.h, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_float))), "emu_sel_load_II")
+
+
 def save_weights(params, path=WEIGHTS, meta=None):
     with open(path, "w") as fh:
         json.dump({"n_param": int(SEL_NPARAM), "params": [float(x) for x in params], "meta": meta or {}}, fh)
@@ -304,18 +430,23 @@ def main(argv=None):
     ap.add_argument("--epochs", type=int, default=60)
     ap.add_argument("--out", default=WEIGHTS)
     ap.add_argument("--report", default=None)
+    ap.add_argument("--scheme", default="I", choices=["I", "II"],
+                    help="I: slices p = 3..10; II: moduli N = 6..20 of Scheme II with norm scaling")
     a = ap.parse_args(argv)
+    if a.scheme == "II" and a.out == WEIGHTS:
+        a.out = WEIGHTS_II
     log = lambda s: print(s, flush=True)  # noqa: E731
+    build = build_dataset_II if a.scheme == "II" else build_dataset
     t0 = time.time()
-    ftr, etr, ktr, _ = build_dataset(a.n_train, 1, log=log)
-    fev, eev, kev, _ = build_dataset(a.n_eval, 2, log=log)
+    ftr, etr, ktr, _ = build(a.n_train, 1, log=log)
+    fev, eev, kev, _ = build(a.n_eval, 2, log=log)
     t_data = time.time() - t0
     X, y, _ = expand(ftr, etr)
     t1 = time.time()
     params, hist = train(X, y, epochs=a.epochs, log=log)
     t_train = time.time() - t1
-    res = evaluate(params, fev, eev, kev, etr)
-    meta = {"n_train": a.n_train, "n_eval": a.n_eval, "epochs": a.epochs, "final_loss": hist[-1],
+    res = (evaluate_II if a.scheme == "II" else evaluate)(params, fev, eev, kev, etr)
+    meta = {"scheme": a.scheme, "n_train": a.n_train, "n_eval": a.n_eval, "epochs": a.epochs, "final_loss": hist[-1],
             "first_loss": hist[0], "data_seconds": t_data, "train_seconds": t_train}
     save_weights(params, a.out, meta)
     report = {"meta": meta, "eval": res}

@@ -129,3 +129,40 @@ def test_training_beats_fixed_p(h):
     A, B = synth.gemm_pair(256, 256, 512, 2.0, 77)
     C, p, code = emu.dgemm_auto(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), 1e-8, handle=h)
     assert code == 0 and 3 <= p <= emu.EMU_P_MAX
+
+
+def test_auto_II_bound_and_escalation(h):
+    m, n, k = 200, 150, 300
+    A, B = synth.gemm_pair(m, n, k, 1.0, 5)
+    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    nb = ctypes.c_int()
+    emu.check(emu.emu_bound_nm(h.h, 0, m, n, k, Ad.data_ptr(), k, Bd.data_ptr(), n, 1e-10, ctypes.byref(nb), None))
+    assert nb.value in sel.NM_CLASSES
+    h2 = emu.Handle(0)  # no Scheme II weights: the bound decides
+    try:
+        C, nm, code = emu.dgemm_auto(Ad, Bd, 1e-10, handle=h2, scheme="II")
+        assert code == 0 and nm >= nb.value and nm % 2 == 0
+        assert torch.equal(C, emu.dgemm(Ad, Bd, scheme="II_NORM", p=nm, handle=h2))
+        C2, nm2, code2 = emu.dgemm_auto(Ad, Bd, 1e-300, handle=h2, scheme="II")
+        assert code2 == 7 and nm2 == emu.EMU_NM_MAX
+    finally:
+        h2.close()
+
+
+def test_training_II_beats_fixed_nm(h):
+    """The Scheme II variant: train on 768 products, evaluate on 256; the
+    learned N (with probe escalation) passes as often as the fixed N and costs
+    less at tol = 1e-8."""
+    ftr, etr, ktr, _ = sel.build_dataset_II(768, 21)
+    fev, eev, kev, _ = sel.build_dataset_II(256, 22)
+    X, y, _ = sel.expand(ftr, etr)
+    params, hist = sel.train(X, y, epochs=40, batch=256, lr=3e-3)
+    assert hist[-1] < 0.8 * hist[0]
+    res = sel.evaluate_II(params, fev, eev, kev, etr)
+    for tol, r in res.items():
+        assert r["learned"]["pass_rate"] >= r["fixed"]["pass_rate"] - 0.03, (tol, r)
+    assert res["1e-08"]["speedup_vs_fixed"] > 1.1, res["1e-08"]
+    sel.install_II(params, h)
+    A, B = synth.gemm_pair(256, 256, 512, 2.0, 78)
+    C, nm, code = emu.dgemm_auto(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), 1e-8, handle=h, scheme="II")
+    assert code == 0 and nm in sel.NM_CLASSES
