@@ -456,5 +456,14 @@ def main(argv=None):
             json.dump(report, fh, indent=1)
 
 
+def install_default(handle=None):
+    """Install the committed weights of both selectors (Scheme I p and
+    Scheme II N) in a handle, so emu_dgemm_auto / emu_dgemm_auto_II use them."""
+    if os.path.exists(WEIGHTS):
+        install(load_weights(WEIGHTS)[0], handle)
+    if os.path.exists(WEIGHTS_II):
+        install_II(load_weights(WEIGHTS_II)[0], handle)
+
+
 if __name__ == "__main__":
     main()
