@@ -225,43 +225,76 @@ __device__ __forceinline__ void slice_digits(uint64_t bits, int E, uint32_t* out
   }
 }
 
-// E4M3 slices (beta = 5): balanced base-32 digits of x = sign * (mag << lsh),
-// |x| < 2^(5P-1) <= 2^59 (leading digit in [-16, 16], the others in
-// [-16, 15]), each encoded as its exact E4M3 byte.  Adding 16 * 32^t for
-// every lower position t turns the balanced digits into plain base-32 digits
-// of the biased value y, so all digits come from independent shifts:
-// d_t = ((y >> 5(P-1-t)) & 31) - 16 for t >= 1, d_0 = y >> 5(P-1).
-template <int P>
-__device__ __forceinline__ void slice_digits_f8(uint64_t bits, int E, uint32_t* out) {
-  ScaledInt s = scaled_trunc_bits(bits, 5 * P - 1 - E);
-  long long x = static_cast<long long>(s.lsh < 64 ? (s.mag << s.lsh) : 0ull);
-  if ((bits >> 63) != 0) x = -x;
-  constexpr long long kBias = [] {
-    long long b = 0;
-    for (int t = 1; t < P; ++t) b = b * 32 + 16;
-    return b;
-  }();
-  const long long y = x + kBias;
-#pragma unroll
-  for (int t = 1; t < P; ++t)
-    out[t] = e4m3_of_int(static_cast<int>((y >> (5 * (P - 1 - t))) & 31) - 16);
-  out[0] = e4m3_of_int(static_cast<int>(y >> (5 * (P - 1))));
-}
-
-template <int P, bool F8>
-__device__ __forceinline__ void digits_any(uint64_t bits, int E, uint32_t* out) {
-  if (F8)
-    slice_digits_f8<P>(bits, E, out);
-  else
-    slice_digits<P>(bits, E, out);
-}
-
 __device__ __forceinline__ int exp_from_maxbits(const unsigned long long* maxbits, int64_t r,
                                                 int64_t rows) {
   if (r >= rows) return 0;
   uint64_t mb = maxbits[r];
   if (mb >= 0x7FF0000000000000ull) return 0;  // non-finite: flagged by the scan
   return frexp_exp_bits(mb);
+}
+
+// E4M3 bytes of two digits given as exact small integers in float: the
+// conversion of a lands in the upper byte, that of b in the lower byte.
+__device__ __forceinline__ uint32_t e4m3x2(float a, float b) {
+  unsigned short r;
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(a), "f"(b));
+  return static_cast<uint32_t>(r);
+}
+
+// Four consecutive K elements of one vector (their binary64 bits) -> for
+// every slice t one 32-bit word holding the four slice bytes in K order
+// (byte q = element q).
+// E4M3 slices (beta = 5): balanced base-32 digits of x = sign * (mag << lsh),
+// |x| < 2^(5P-1) <= 2^59 (leading digit in [-16, 16], the others in
+// [-16, 15]), each encoded as its exact E4M3 byte.  Adding 16 * 32^t for
+// every lower position t turns the balanced digits into plain base-32 digits
+// of the biased value y, so all digits come from independent shifts:
+// d_t = ((y >> 5(P-1-t)) & 31) - 16 for t >= 1, d_0 = y >> 5(P-1).  Each
+// digit becomes an exact float through the 1.5 * 2^23 bit pattern (field f
+// -> f - 16 in one OR and one FADD), and the hardware conversion packs two
+// at a time.  INT8: the bytes of the two's complement (slice_digits).
+template <int P, bool F8>
+__device__ __forceinline__ void pack4(const uint64_t* bits, int E, uint32_t* word) {
+  if (F8) {
+    constexpr long long kBias = [] {
+      long long b = 0;
+      for (int t = 1; t < P; ++t) b = b * 32 + 16;
+      return b;
+    }();
+    long long y[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const ScaledInt sc = scaled_trunc_bits(bits[q], 5 * P - 1 - E);
+      long long x = static_cast<long long>(sc.lsh < 64 ? (sc.mag << sc.lsh) : 0ull);
+      if ((bits[q] >> 63) != 0) x = -x;
+      y[q] = x + kBias;
+    }
+#pragma unroll
+    for (int t = 0; t < P; ++t) {
+      float f[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (t == 0) {  // leading digit, in [-16, 16]
+          const int d = static_cast<int>(y[q] >> (5 * (P - 1)));
+          f[q] = __int_as_float(0x4B400000 + d) - 12582912.0f;
+        } else {  // field in [0, 31], digit = field - 16
+          const int fld = static_cast<int>((y[q] >> (5 * (P - 1 - t))) & 31);
+          f[q] = __int_as_float(0x4B400000 | fld) - 12582928.0f;
+        }
+      }
+      word[t] = e4m3x2(f[1], f[0]) | (e4m3x2(f[3], f[2]) << 16);
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < P; ++t) word[t] = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint32_t dg[P];
+      slice_digits<P>(bits[q], E, dg);
+#pragma unroll
+      for (int t = 0; t < P; ++t) word[t] |= (dg[t] & 0xFFu) << (8 * q);
+    }
+  }
 }
 
 // K-contiguous source: one warp per (row, group of four 32-wide K-chunks);
@@ -281,22 +314,11 @@ __global__ void split_I_kcontig(const T* __restrict__ X, int64_t ld, int64_t row
   if (c >= nchunks) return;
   const int64_t h0 = c * 32 + (lane & 7) * 4;
   const int E = exp_from_maxbits(maxbits, r, rows);
+  uint64_t bits[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) bits[q] = (r < rows && h0 + q < k) ? load_bits(X + r * ld + h0 + q) : 0ull;
   uint32_t word[P];
-#pragma unroll
-  for (int t = 0; t < P; ++t) word[t] = 0;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int64_t h = h0 + q;
-    uint32_t dg[P];
-    if (r < rows && h < k) {
-      digits_any<P, F8>(load_bits(X + r * ld + h), E, dg);
-    } else {
-#pragma unroll
-      for (int t = 0; t < P; ++t) dg[t] = 0;
-    }
-#pragma unroll
-    for (int t = 0; t < P; ++t) word[t] |= (dg[t] & 0xFFu) << (8 * q);
-  }
+  pack4<P, F8>(bits, E, word);
   uint8_t* row = reinterpret_cast<uint8_t*>(hat) + r * (nchunks * 32 * P);
 #pragma unroll
   for (int t = 0; t < P; ++t)
@@ -304,56 +326,48 @@ __global__ void split_I_kcontig(const T* __restrict__ X, int64_t ld, int64_t row
   if (c == 0 && lane == 0 && r < rows && E_out) E_out[r] = E;
 }
 
-// K-strided source (element (r, h) at X[h*ld + r]): one thread per
-// (vector r, K-chunk c), lanes over consecutive r (coalesced reads); each
-// thread assembles 32 bytes per slice and writes them as two 16-byte stores.
+// K-strided source (element (r, h) at X[h*ld + r]): a block of 256 threads
+// takes 32 vectors x 128 K-elements at a time, reads them coalesced along r
+// into shared memory, then works like the K-contiguous kernel (warp w:
+// vectors w, w+8, w+16, w+24; lane l: elements 4l .. 4l+3).  Element h of a
+// vector is kept at column (h mod 4) * 33 + h / 4 and vectors are 133 words
+// apart, so both the column-wise fill and the lane-wise reads are free of
+// bank conflicts.
 template <typename T, int P, bool F8>
-__global__ void split_I_kstrided(const T* __restrict__ X, int64_t ld, int64_t rows, int64_t k,
-                                 int64_t rows_pad, int64_t nchunks,
-                                 const unsigned long long* __restrict__ maxbits,
-                                 int8_t* __restrict__ hat, int32_t* __restrict__ E_out) {
-  int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  int64_t c = blockIdx.y;
-  if (r >= rows_pad) return;
-  int E = exp_from_maxbits(maxbits, r, rows);
-  uint32_t word[P][8];
-#pragma unroll
-  for (int t = 0; t < P; ++t)
-#pragma unroll
-    for (int q = 0; q < 8; ++q) word[t][q] = 0;
-#pragma unroll 1
-  for (int wq = 0; wq < 8; ++wq) {
-    uint32_t cur[P];
-#pragma unroll
-    for (int t = 0; t < P; ++t) cur[t] = 0;
-#pragma unroll
-    for (int qq = 0; qq < 4; ++qq) {
-      int64_t h = c * 32 + wq * 4 + qq;
-      uint32_t dg[P];
-      if (r < rows && h < k) {
-        digits_any<P, F8>(load_bits(X + h * ld + r), E, dg);
-      } else {
-#pragma unroll
-        for (int t = 0; t < P; ++t) dg[t] = 0;
-      }
-#pragma unroll
-      for (int t = 0; t < P; ++t) cur[t] |= dg[t] << (8 * qq);
+__global__ void __launch_bounds__(256) split_I_kstrided(const T* __restrict__ X, int64_t ld, int64_t rows, int64_t k,
+                                                        int64_t rows_pad, int64_t nchunks,
+                                                        const unsigned long long* __restrict__ maxbits,
+                                                        int8_t* __restrict__ hat, int32_t* __restrict__ E_out) {
+  __shared__ uint64_t tile[32][133];
+  const int64_t g = blockIdx.x;  // group of 4 chunks
+  const int64_t hbase = g * 128;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t c = g * 4 + (lane >> 3);
+  for (int64_t r0 = static_cast<int64_t>(blockIdx.y) * 32; r0 < rows_pad;
+       r0 += static_cast<int64_t>(gridDim.y) * 32) {
+    __syncthreads();  // the previous row block is done with the tile
+    for (int i = threadIdx.x; i < 32 * 128; i += 256) {
+      const int rl = i & 31, hl = i >> 5;
+      const int64_t r = r0 + rl, h = hbase + hl;
+      tile[rl][(hl & 3) * 33 + (hl >> 2)] = (r < rows && h < k) ? load_bits(X + h * ld + r) : 0ull;
     }
-    // place the finished 4-byte word at position wq (static register indices)
+    __syncthreads();
+    for (int rl = warp; rl < 32; rl += 8) {
+      const int64_t r = r0 + rl;
+      if (r >= rows_pad || c >= nchunks) continue;
+      const int E = exp_from_maxbits(maxbits, r, rows);
+      uint64_t bits[4];
 #pragma unroll
-    for (int t = 0; t < P; ++t) {
+      for (int q = 0; q < 4; ++q) bits[q] = tile[rl][q * 33 + lane];
+      uint32_t word[P];
+      pack4<P, F8>(bits, E, word);
+      uint8_t* row = reinterpret_cast<uint8_t*>(hat) + r * (nchunks * 32 * P);
 #pragma unroll
-      for (int z = 0; z < 8; ++z) word[t][z] = (wq == z) ? cur[t] : word[t][z];
+      for (int t = 0; t < P; ++t)
+        *reinterpret_cast<uint32_t*>(row + (c * P + t) * 32 + (lane & 7) * 4) = word[t];
+      if (c == 0 && lane == 0 && r < rows && E_out) E_out[r] = E;
     }
   }
-  uint8_t* row = reinterpret_cast<uint8_t*>(hat) + r * (nchunks * 32 * P);
-#pragma unroll
-  for (int t = 0; t < P; ++t) {
-    uint4* dst = reinterpret_cast<uint4*>(row + (c * P + t) * 32);
-    dst[0] = make_uint4(word[t][0], word[t][1], word[t][2], word[t][3]);
-    dst[1] = make_uint4(word[t][4], word[t][5], word[t][6], word[t][7]);
-  }
-  if (c == 0 && r < rows && E_out) E_out[r] = E;
 }
 
 // ------------------------------------------------------------------ split II
@@ -475,8 +489,9 @@ static void launch_split_I_p(const T* X, int64_t ld, bool kcontig, int64_t rows,
     split_I_kcontig<T, P, F8><<<static_cast<unsigned>(blocks), 256, 0, st>>>(X, ld, rows, k, rows_pad,
                                                                              nchunks, maxbits, hat, E);
   } else {
-    dim3 grid(static_cast<unsigned>((rows_pad + 127) / 128), static_cast<unsigned>(nchunks));
-    split_I_kstrided<T, P, F8><<<grid, 128, 0, st>>>(X, ld, rows, k, rows_pad, nchunks, maxbits, hat, E);
+    const int64_t rb = rows_pad / 32;
+    dim3 grid(static_cast<unsigned>((nchunks + 3) / 4), static_cast<unsigned>(rb < 65535 ? rb : 65535));
+    split_I_kstrided<T, P, F8><<<grid, 256, 0, st>>>(X, ld, rows, k, rows_pad, nchunks, maxbits, hat, E);
   }
 }
 
