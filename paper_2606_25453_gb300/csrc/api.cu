@@ -149,6 +149,7 @@ void host_mod_tables(int nm, ModTables* t) {
     uint32_t m = static_cast<uint32_t>(mods[l]);
     t->mods[l] = m;
     t->two32mod[l] = static_cast<uint32_t>((uint64_t{1} << 32) % m);
+    t->fastmod[l] = UINT64_MAX / m + 1;
     uint32_t v = 1 % m;
     for (int e = 0; e < kPow2TabLen; ++e) {
       t->pow2mod[l][e] = static_cast<uint8_t>(v);

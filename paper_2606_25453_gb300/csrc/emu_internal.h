@@ -23,6 +23,7 @@ inline int64_t split_cols_II(int64_t k) { return (k + 127) / 128 * 128; }
 struct ModTables {
   uint32_t mods[kMaxModuli];
   uint32_t two32mod[kMaxModuli];                 // 2^32 mod m_l
+  uint64_t fastmod[kMaxModuli];                  // ceil(2^64 / m_l): x mod m_l for 32-bit x by two products
   uint8_t pow2mod[kMaxModuli][kPow2TabLen];      // 2^e mod m_l
 };
 

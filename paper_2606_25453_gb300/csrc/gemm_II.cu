@@ -251,11 +251,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int l = 0; l < nm; ++l) {
       const uint32_t m = mt.mods[l];
       for (int set = 0; set < NSET; ++set) {
-        int32_t acc[2][4];
+        // two accumulator sets (even / odd K-chunks) give the tensor pipe
+        // four independent MMA chains per warp; summed before the reduction
+        // (exact: the total is the same INT32-bounded sum)
+        int32_t acc[2][4], acc2[2][4];
 #pragma unroll
         for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
-          for (int q = 0; q < 4; ++q) acc[nt][q] = 0;
+          for (int q = 0; q < 4; ++q) acc[nt][q] = acc2[nt][q] = 0;
         for (int ks = 0; ks < kp.nst; ++ks, ++it) {
           const uint32_t stage = it % kStages;
           const uint32_t par = (it / kStages) & 1u;
@@ -270,12 +273,21 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t af[4], bf[4];
             ldsm_x4(sA + c * kBlkA + a_off, af[0], af[1], af[2], af[3]);
             ldsm_x4(sB + c * kBlkB + b_off, bf[0], bf[1], bf[2], bf[3]);
-            mma_i8<true, true>(acc[0], af, bf);
-            mma_i8<true, true>(acc[1], af, bf + 2);
+            if (c & 1) {
+              mma_i8<true, true>(acc2[0], af, bf);
+              mma_i8<true, true>(acc2[1], af, bf + 2);
+            } else {
+              mma_i8<true, true>(acc[0], af, bf);
+              mma_i8<true, true>(acc[1], af, bf + 2);
+            }
           }
           __syncwarp();
           if (lane == 0) mbar_arrive(&empty[stage]);
         }
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[nt][q] += acc2[nt][q];
         // Eq. (7): residue in [0, m) per element, then CRT accumulation
 #pragma unroll
         for (int e = 0; e < 8; ++e) {

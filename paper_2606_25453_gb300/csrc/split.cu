@@ -371,90 +371,161 @@ __global__ void __launch_bounds__(256) split_I_kstrided(const T* __restrict__ X,
 }
 
 // ------------------------------------------------------------------ split II
+// x mod m for a 32-bit x from c = ceil(2^64 / m) (Lemire, Kaser, Kurz,
+// "Faster remainder by direct computation", 2019): the low 64 bits of c x,
+// times m, high 64 bits.  Exact for every 32-bit x and m < 2^32.
+__device__ __forceinline__ uint32_t fastmod32(uint32_t x, uint32_t m, uint64_t c) {
+  return static_cast<uint32_t>(__umul64hi(c * static_cast<uint64_t>(x), m));
+}
+
 // Residue of x = sign * (mag << lsh) modulo m, in [0, m); mag < 2^53 is
 // reduced in two 32-bit pieces, 2^lsh mod m comes from the table.
-__device__ __forceinline__ uint32_t mod_scaled(uint64_t mag, int lsh, bool neg, uint32_t m,
+__device__ __forceinline__ uint32_t mod_scaled(uint64_t mag, int lsh, bool neg, uint32_t m, uint64_t c,
                                                uint32_t two32m, const uint8_t* pow2tab_m) {
-  uint32_t hi = static_cast<uint32_t>(mag >> 32), lo = static_cast<uint32_t>(mag);
-  uint32_t r = ((hi % m) * two32m + lo % m) % m;
+  const uint32_t hi = static_cast<uint32_t>(mag >> 32), lo = static_cast<uint32_t>(mag);
+  uint32_t r = fastmod32(fastmod32(hi, m, c) * two32m + fastmod32(lo, m, c), m, c);
   if (lsh) {
-    uint32_t f = lsh < kPow2TabLen ? pow2tab_m[lsh] : 0u;  // lsh < b < 128 by construction
-    r = (r * f) % m;
+    const uint32_t f = lsh < kPow2TabLen ? pow2tab_m[lsh] : 0u;  // lsh < b < 128 by construction
+    r = fastmod32(r * f, m, c);
   }
   if (neg && r) r = m - r;
   return r;
 }
 
-__device__ __forceinline__ int8_t sym_res(uint32_t r, uint32_t m) {
+__device__ __forceinline__ uint32_t sym_byte(uint32_t r, uint32_t m) {
   int v = static_cast<int>(r);
   if (v > static_cast<int>((m - 1) / 2)) v -= static_cast<int>(m);
-  return static_cast<int8_t>(v);
+  return static_cast<uint32_t>(v) & 0xFFu;
 }
 
-// One thread per element of a (rows_pad x kpad) plane.  cw = 1 real, 2
-// complex (writes 3 residue sets: re, im, re+im).  Planes: set q, modulus l
-// at res + ((q*nm + l)*rows_pad + r)*kpad + h.
-template <typename T, bool KCONTIG>
-__global__ void split_II_kernel(const T* __restrict__ X, int64_t ld, int64_t rows, int64_t k,
-                                int64_t rows_pad, int64_t kpad, int nm, int b, int cw,
-                                const __grid_constant__ ModTables mt,
-                                const unsigned long long* __restrict__ maxbits,
-                                const int32_t* __restrict__ Ein, int8_t* __restrict__ res,
-                                int32_t* __restrict__ E_out) {
-  __shared__ uint8_t tab[kMaxModuli][kPow2TabLen];
-  __shared__ uint32_t mods[kMaxModuli], two32[kMaxModuli];
+struct ModSmem {
+  uint8_t tab[kMaxModuli][kPow2TabLen];
+  uint64_t c[kMaxModuli];
+  uint32_t mods[kMaxModuli], two32[kMaxModuli];
+};
+
+__device__ __forceinline__ void load_mod_smem(ModSmem& ms, const ModTables& mt, int nm) {
   for (int i = threadIdx.x; i < nm * kPow2TabLen; i += blockDim.x)
-    tab[i / kPow2TabLen][i % kPow2TabLen] = mt.pow2mod[i / kPow2TabLen][i % kPow2TabLen];
+    ms.tab[i / kPow2TabLen][i % kPow2TabLen] = mt.pow2mod[i / kPow2TabLen][i % kPow2TabLen];
   for (int i = threadIdx.x; i < nm; i += blockDim.x) {
-    mods[i] = mt.mods[i];
-    two32[i] = mt.two32mod[i];
+    ms.mods[i] = mt.mods[i];
+    ms.two32[i] = mt.two32mod[i];
+    ms.c[i] = mt.fastmod[i];
   }
+}
+
+// The residues of four consecutive K elements of one vector, packed four
+// bytes per word (byte q = element q), one word per plane: real (cw = 1)
+// one plane per modulus; complex three (re, im, re + im).  `re`/`im` hold
+// the binary64 bits of the elements.
+template <int CW>
+__device__ __forceinline__ void residues4(const ModSmem& ms, int nm, int shift, const uint64_t* re, const uint64_t* im,
+                                          int64_t plane, int8_t* base) {
+  ScaledInt sr[4], si[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    sr[q] = scaled_trunc_bits(re[q], shift);
+    if (CW == 2) si[q] = scaled_trunc_bits(im[q], shift);
+  }
+  for (int l = 0; l < nm; ++l) {
+    const uint32_t m = ms.mods[l];
+    const uint64_t c = ms.c[l];
+    uint32_t w0 = 0, w1 = 0, w2 = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t rr = mod_scaled(sr[q].mag, sr[q].lsh, (re[q] >> 63) != 0, m, c, ms.two32[l], ms.tab[l]);
+      w0 |= sym_byte(rr, m) << (8 * q);
+      if (CW == 2) {
+        const uint32_t ri = mod_scaled(si[q].mag, si[q].lsh, (im[q] >> 63) != 0, m, c, ms.two32[l], ms.tab[l]);
+        uint32_t rs = rr + ri;
+        if (rs >= m) rs -= m;
+        w1 |= sym_byte(ri, m) << (8 * q);
+        w2 |= sym_byte(rs, m) << (8 * q);
+      }
+    }
+    *reinterpret_cast<uint32_t*>(base + static_cast<int64_t>(l) * plane) = w0;
+    if (CW == 2) {
+      *reinterpret_cast<uint32_t*>(base + static_cast<int64_t>(nm + l) * plane) = w1;
+      *reinterpret_cast<uint32_t*>(base + static_cast<int64_t>(2 * nm + l) * plane) = w2;
+    }
+  }
+}
+
+// Scheme II split.  Planes: set q, modulus l at
+// res + ((q*nm + l)*rows_pad + r)*kpad + h (set = 0 for real; 0, 1, 2 = re,
+// im, re + im for complex).  Row exponent: of the maximum (worst-case
+// scaling) or of the 2-norm (Ein).  K-contiguous sources: one warp per
+// (vector, 128 K-elements), lane l takes elements 4l .. 4l+3 and writes one
+// word per plane; strided sources go through a shared-memory tile of 32
+// vectors (16 for complex) x 128 elements as in the Scheme I split.
+template <typename T, int CW>
+__global__ void split_II_kcontig(const T* __restrict__ X, int64_t ld, int64_t rows, int64_t k, int64_t rows_pad,
+                                 int64_t kpad, int nm, int b, const __grid_constant__ ModTables mt,
+                                 const unsigned long long* __restrict__ maxbits, const int32_t* __restrict__ Ein,
+                                 int8_t* __restrict__ res, int32_t* __restrict__ E_out) {
+  __shared__ ModSmem ms;
+  load_mod_smem(ms, mt, nm);
   __syncthreads();
-  int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  int64_t r, h;
-  if (KCONTIG) {
-    r = idx / kpad;
-    h = idx % kpad;
-  } else {  // consecutive threads over r for coalesced strided reads
-    h = idx / rows_pad;
-    r = idx % rows_pad;
+  const int lane = threadIdx.x & 31;
+  const int64_t ngroups = kpad / 128;
+  const int64_t w = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (w >= rows_pad * ngroups) return;
+  const int64_t r = w / ngroups, h0 = (w % ngroups) * 128 + lane * 4;
+  const int E = Ein ? (r < rows ? Ein[r] : 0) : exp_from_maxbits(maxbits, r, rows);
+  uint64_t re[4], im[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const bool valid = r < rows && h0 + q < k;
+    const T* p = X + (r * ld + h0 + q) * CW;
+    re[q] = valid ? load_bits(p) : 0ull;
+    im[q] = (CW == 2 && valid) ? load_bits(p + 1) : 0ull;
   }
-  if (r >= rows_pad || h >= kpad) return;
-  // row exponent: of the maximum (worst-case scaling) or of the 2-norm (Ein)
-  int E = Ein ? (r < rows ? Ein[r] : 0) : exp_from_maxbits(maxbits, r, rows);
-  bool valid = r < rows && h < k;
-  int64_t plane = rows_pad * kpad;
-  int64_t off = r * kpad + h;
-  if (cw == 1) {
-    uint64_t bits = 0;
-    if (valid) bits = load_bits(KCONTIG ? X + r * ld + h : X + h * ld + r);
-    ScaledInt s = scaled_trunc_bits(bits, b - E);
-    bool neg = (bits >> 63) != 0;
-    for (int l = 0; l < nm; ++l) {
-      uint32_t m = mods[l];
-      uint32_t rr = valid ? mod_scaled(s.mag, s.lsh, neg, m, two32[l], tab[l]) : 0u;
-      res[l * plane + off] = sym_res(rr, m);
+  residues4<CW>(ms, nm, b - E, re, im, rows_pad * kpad, res + r * kpad + h0);
+  if (h0 == 0 && r < rows && E_out) E_out[r] = E;
+}
+
+template <typename T, int CW>
+__global__ void __launch_bounds__(256) split_II_kstrided(const T* __restrict__ X, int64_t ld, int64_t rows, int64_t k,
+                                                         int64_t rows_pad, int64_t kpad, int nm, int b,
+                                                         const __grid_constant__ ModTables mt,
+                                                         const unsigned long long* __restrict__ maxbits,
+                                                         const int32_t* __restrict__ Ein, int8_t* __restrict__ res,
+                                                         int32_t* __restrict__ E_out) {
+  constexpr int TR = CW == 2 ? 16 : 32;  // vectors per tile (two tiles for complex)
+  __shared__ ModSmem ms;
+  __shared__ uint64_t tre[TR][133];
+  __shared__ uint64_t tim[CW == 2 ? TR : 1][CW == 2 ? 133 : 1];
+  load_mod_smem(ms, mt, nm);
+  const int64_t hbase = static_cast<int64_t>(blockIdx.x) * 128;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t r0 = static_cast<int64_t>(blockIdx.y) * TR; r0 < rows_pad;
+       r0 += static_cast<int64_t>(gridDim.y) * TR) {
+    __syncthreads();  // tables loaded / the previous row block is done with the tiles
+    for (int i = threadIdx.x; i < TR * 128; i += 256) {
+      const int rl = i % TR, hl = i / TR;
+      const int64_t r = r0 + rl, h = hbase + hl;
+      const bool valid = r < rows && h < k;
+      const T* p = X + (h * ld + r) * CW;
+      const int col = (hl & 3) * 33 + (hl >> 2);
+      tre[rl][col] = valid ? load_bits(p) : 0ull;
+      if (CW == 2) tim[rl][col] = valid ? load_bits(p + 1) : 0ull;
     }
-  } else {
-    uint64_t br = 0, bi = 0;
-    if (valid) {
-      const T* p = KCONTIG ? X + (r * ld + h) * 2 : X + (h * ld + r) * 2;
-      br = load_bits(p);
-      bi = load_bits(p + 1);
-    }
-    ScaledInt sr = scaled_trunc_bits(br, b - E), si = scaled_trunc_bits(bi, b - E);
-    bool nr = (br >> 63) != 0, ni = (bi >> 63) != 0;
-    for (int l = 0; l < nm; ++l) {
-      uint32_t m = mods[l];
-      uint32_t rr = valid ? mod_scaled(sr.mag, sr.lsh, nr, m, two32[l], tab[l]) : 0u;
-      uint32_t ri = valid ? mod_scaled(si.mag, si.lsh, ni, m, two32[l], tab[l]) : 0u;
-      uint32_t rs = (rr + ri) % m;
-      res[(0 * nm + l) * plane + off] = sym_res(rr, m);
-      res[(1 * nm + l) * plane + off] = sym_res(ri, m);
-      res[(2 * nm + l) * plane + off] = sym_res(rs, m);
+    __syncthreads();
+    for (int rl = warp; rl < TR; rl += 8) {
+      const int64_t r = r0 + rl;
+      if (r >= rows_pad) continue;
+      const int E = Ein ? (r < rows ? Ein[r] : 0) : exp_from_maxbits(maxbits, r, rows);
+      uint64_t re[4], im[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        re[q] = tre[rl][q * 33 + lane];
+        im[q] = CW == 2 ? tim[rl][q * 33 + lane] : 0ull;
+      }
+      const int64_t h0 = hbase + lane * 4;
+      residues4<CW>(ms, nm, b - E, re, im, rows_pad * kpad, res + r * kpad + h0);
+      if (h0 == 0 && r < rows && E_out) E_out[r] = E;
     }
   }
-  if (h == 0 && r < rows && E_out) E_out[r] = E;
 }
 
 // ------------------------------------------------------------------ launchers
@@ -522,16 +593,23 @@ template <typename T>
 void launch_split_II(const T* X, int64_t ld, bool kcontig, int64_t rows, int64_t k, int nm, int b,
                      int cw, const ModTables& tabs, const unsigned long long* maxbits, int8_t* res,
                      int32_t* E, cudaStream_t st, const int32_t* Ein) {
-  int64_t rows_pad = split_rows(rows), kpad = split_cols_II(k);
-  int64_t total = rows_pad * kpad;
-  if (total == 0) return;
-  int64_t blocks = (total + 255) / 256;
-  if (kcontig)
-    split_II_kernel<T, true><<<static_cast<unsigned>(blocks), 256, 0, st>>>(
-        X, ld, rows, k, rows_pad, kpad, nm, b, cw, tabs, maxbits, Ein, res, E);
-  else
-    split_II_kernel<T, false><<<static_cast<unsigned>(blocks), 256, 0, st>>>(
-        X, ld, rows, k, rows_pad, kpad, nm, b, cw, tabs, maxbits, Ein, res, E);
+  const int64_t rows_pad = split_rows(rows), kpad = split_cols_II(k);
+  if (rows_pad == 0 || kpad == 0) return;
+  if (kcontig) {
+    const int64_t warps = rows_pad * (kpad / 128);
+    const unsigned blocks = static_cast<unsigned>((warps + 7) / 8);
+    if (cw == 2)
+      split_II_kcontig<T, 2><<<blocks, 256, 0, st>>>(X, ld, rows, k, rows_pad, kpad, nm, b, tabs, maxbits, Ein, res, E);
+    else
+      split_II_kcontig<T, 1><<<blocks, 256, 0, st>>>(X, ld, rows, k, rows_pad, kpad, nm, b, tabs, maxbits, Ein, res, E);
+  } else {
+    const int64_t rb = rows_pad / (cw == 2 ? 16 : 32);
+    dim3 grid(static_cast<unsigned>(kpad / 128), static_cast<unsigned>(rb < 65535 ? rb : 65535));
+    if (cw == 2)
+      split_II_kstrided<T, 2><<<grid, 256, 0, st>>>(X, ld, rows, k, rows_pad, kpad, nm, b, tabs, maxbits, Ein, res, E);
+    else
+      split_II_kstrided<T, 1><<<grid, 256, 0, st>>>(X, ld, rows, k, rows_pad, kpad, nm, b, tabs, maxbits, Ein, res, E);
+  }
 }
 
 template <typename T>
