@@ -344,6 +344,15 @@ __global__ void __launch_bounds__(kThreadsTC, 1) gemm_f8tc_kernel(const __grid_c
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
       uint32_t it = 0, drain = 0;
+      const uint32_t total = static_cast<uint32_t>(my_tiles) * static_cast<uint32_t>(kp.nk32);
+      // A barrier probe stalls this thread until shared memory answers,
+      // which under full tensor-core load takes long enough to drain the MMA
+      // queue if the queue holds only the short MMAs at the end of a chunk.
+      // So the next chunk's barrier is probed early in the current chunk,
+      // right after the wide MMAs of the first rows are queued, and the wait
+      // at the next chunk is skipped when that probe already saw the data.
+      constexpr int kProbeRow = P >= 4 ? 2 : 0;
+      bool ready = false;
       bool stop = false;
       for (int t = 0; t < my_tiles && !stop; ++t) {
         for (int kk = 0; kk < kp.nk32; ++kk, ++it) {
@@ -356,10 +365,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1) gemm_f8tc_kernel(const __grid_c
             tc_fence_after();
           }
           const uint32_t stage = it % Cfg::kStages;
-          if (!wait_or_abort(&full[stage], (it / Cfg::kStages) & 1u, abort_flag, kp.status)) {
+          if (!ready && !wait_or_abort(&full[stage], (it / Cfg::kStages) & 1u, abort_flag, kp.status)) {
             stop = true;
             break;
           }
+          ready = false;
           tc_fence_after();
           const uint32_t sA = base + stage * Cfg::kStageBytes;
           const uint32_t sB = sA + Cfg::kGroups * Cfg::kBlkAg;
@@ -374,6 +384,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) gemm_f8tc_kernel(const __grid_c
               const uint32_t acc = (chunk_first && i == 0) ? 0u : 1u;
               umma_e4m3(tmem + static_cast<uint32_t>(i * kBN + q * 256), adesc, bdesc, idesc_e4m3(kBM, n), acc);
             }
+            if (i == kProbeRow && it + 1 < total)
+              ready = mbar_test_wait(&full[(it + 1) % Cfg::kStages], ((it + 1) / Cfg::kStages) & 1u);
           }
           // the stage is free (in every CTA of the cluster) once these MMAs finish
           if (cl > 1)
