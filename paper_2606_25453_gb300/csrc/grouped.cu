@@ -22,6 +22,7 @@
 #include "emu_handle.h"
 #include "emu_internal.h"
 #include "gemm_I_core.cuh"
+#include "split_core.cuh"
 
 namespace emu {
 
@@ -114,105 +115,77 @@ __global__ void grouped_scan_kernel(const GProb* __restrict__ probs, int count, 
 }
 
 // ---------------------------------------------------------------- split
-template <int P>
-__device__ __forceinline__ void digits_of(uint64_t bits, int E, uint32_t* out) {
-  ScaledInt s = scaled_trunc_bits(bits, 8 * P - 1 - E);
-  bool neg = (bits >> 63) != 0;
-  if (P <= 8) {
-    uint64_t v = s.lsh < 64 ? (s.mag << s.lsh) : 0ull;
-    if (neg) v = ~v + 1ull;
-#pragma unroll
-    for (int t = 0; t < P; ++t) out[t] = static_cast<uint32_t>((v >> (8 * (P - 1 - t))) & 0xFFu);
-  } else {
-    unsigned __int128 v = s.lsh < 128 ? (static_cast<unsigned __int128>(s.mag) << s.lsh)
-                                      : static_cast<unsigned __int128>(0);
-    if (neg) v = ~v + static_cast<unsigned __int128>(1);
-#pragma unroll
-    for (int t = 0; t < P; ++t) out[t] = static_cast<uint32_t>((v >> (8 * (P - 1 - t))) & 0xFFu);
-  }
-}
-
 __device__ __forceinline__ int exp_of(const unsigned long long* mb, int r, int rows) {
   if (r >= rows) return 0;
   uint64_t v = mb[r];
   return v >= 0x7FF0000000000000ull ? 0 : frexp_exp_bits(v);
 }
 
-// Blocks [0, startA[count]): A rows, one warp per (row, 32-wide chunk).
-// The rest: B columns, one thread per (column, chunk), 32 bytes per slice.
+// Blocks [0, startA[count]): A rows, one warp per (row, group of four
+// 32-wide K-chunks); lane l packs elements 4l .. 4l+3 of the group into one
+// word per slice.  The rest: B columns, a block per (32 columns, 128 K
+// elements), read coalesced along the row of B into shared memory and then
+// packed the same way (the layout of the dense strided split).
 template <int P>
-__global__ void grouped_split_kernel(const GProb* __restrict__ probs, int count, const int* __restrict__ startA,
-                                     const int* __restrict__ startB) {
+__global__ void __launch_bounds__(256) grouped_split_kernel(const GProb* __restrict__ probs, int count,
+                                                            const int* __restrict__ startA,
+                                                            const int* __restrict__ startB) {
+  __shared__ uint64_t tile[32][133];
   int blk = blockIdx.x;
   const int totA = startA[count];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (blk < totA) {
-    int pi = find_prob(startA, count, blk);
+    const int pi = find_prob(startA, count, blk);
     const GProb& pr = probs[pi];
-    int64_t w = static_cast<int64_t>(blk - startA[pi]) * 8 + (threadIdx.x >> 5);
-    if (w >= pr.rows_a * pr.nchunks) return;
-    int lane = threadIdx.x & 31;
-    int r = static_cast<int>(w / pr.nchunks);
-    int c = static_cast<int>(w % pr.nchunks);
-    int h = c * 32 + lane;
-    int E = exp_of(pr.maxA, r, pr.M);
-    uint32_t dg[P];
-    if (r < pr.M && h < pr.K) {
-      digits_of<P>(dbits(__ldg(pr.A + static_cast<int64_t>(r) * pr.lda + h)), E, dg);
-    } else {
+    const int64_t ngroups = (pr.nchunks + 3) / 4;
+    const int64_t w = static_cast<int64_t>(blk - startA[pi]) * 8 + warp;
+    if (w >= pr.rows_a * ngroups) return;
+    const int r = static_cast<int>(w / ngroups);
+    const int64_t c = (w % ngroups) * 4 + (lane >> 3);
+    if (c >= pr.nchunks) return;
+    const int64_t h0 = c * 32 + (lane & 7) * 4;
+    const int E = exp_of(pr.maxA, r, pr.M);
+    uint64_t bits[4];
 #pragma unroll
-      for (int t = 0; t < P; ++t) dg[t] = 0;
-    }
+    for (int q = 0; q < 4; ++q)
+      bits[q] = (r < pr.M && h0 + q < pr.K) ? dbits(__ldg(pr.A + static_cast<int64_t>(r) * pr.lda + h0 + q)) : 0ull;
+    uint32_t word[P];
+    pack4<P, false>(bits, E, word);
     uint8_t* row = reinterpret_cast<uint8_t*>(pr.hatA) + static_cast<int64_t>(r) * pr.nchunks * 32 * P;
 #pragma unroll
-    for (int t = 0; t < P; ++t) row[(c * P + t) * 32 + lane] = static_cast<uint8_t>(dg[t]);
+    for (int t = 0; t < P; ++t) *reinterpret_cast<uint32_t*>(row + (c * P + t) * 32 + (lane & 7) * 4) = word[t];
     if (c == 0 && lane == 0 && r < pr.M) pr.EA[r] = E;
     return;
   }
   blk -= totA;
-  int pi = find_prob(startB, count, blk);
+  const int pi = find_prob(startB, count, blk);
   const GProb& pr = probs[pi];
-  int local = blk - startB[pi];
-  int rblocks = static_cast<int>((pr.rows_b + 255) / 256);
-  int c = local / rblocks;
-  int r = (local % rblocks) * 256 + threadIdx.x;
-  if (r >= pr.rows_b) return;
-  int E = exp_of(pr.maxB, r, pr.N);
-  uint32_t word[P][8];
-#pragma unroll
-  for (int t = 0; t < P; ++t)
-#pragma unroll
-    for (int q = 0; q < 8; ++q) word[t][q] = 0;
-#pragma unroll 1
-  for (int wq = 0; wq < 8; ++wq) {
-    uint32_t cur[P];
-#pragma unroll
-    for (int t = 0; t < P; ++t) cur[t] = 0;
-#pragma unroll
-    for (int qq = 0; qq < 4; ++qq) {
-      int h = c * 32 + wq * 4 + qq;
-      uint32_t dg[P];
-      if (r < pr.N && h < pr.K) {
-        digits_of<P>(dbits(__ldg(pr.B + static_cast<int64_t>(h) * pr.ldb + r)), E, dg);
-      } else {
-#pragma unroll
-        for (int t = 0; t < P; ++t) dg[t] = 0;
-      }
-#pragma unroll
-      for (int t = 0; t < P; ++t) cur[t] |= dg[t] << (8 * qq);
-    }
-#pragma unroll
-    for (int t = 0; t < P; ++t)
-#pragma unroll
-      for (int z = 0; z < 8; ++z) word[t][z] = (wq == z) ? cur[t] : word[t][z];
+  const int64_t ngroups = (pr.nchunks + 3) / 4;
+  const int local = blk - startB[pi];
+  const int64_t g = local % ngroups;
+  const int64_t r0 = static_cast<int64_t>(local / ngroups) * 32;
+  for (int i = threadIdx.x; i < 32 * 128; i += 256) {
+    const int rl = i & 31, hl = i >> 5;
+    const int64_t r = r0 + rl, h = g * 128 + hl;
+    tile[rl][(hl & 3) * 33 + (hl >> 2)] =
+        (r < pr.N && h < pr.K) ? dbits(__ldg(pr.B + h * pr.ldb + r)) : 0ull;
   }
-  uint8_t* row = reinterpret_cast<uint8_t*>(pr.hatB) + static_cast<int64_t>(r) * pr.nchunks * 32 * P;
+  __syncthreads();
+  const int64_t c = g * 4 + (lane >> 3);
+  for (int rl = warp; rl < 32; rl += 8) {
+    const int64_t r = r0 + rl;
+    if (r >= pr.rows_b || c >= pr.nchunks) continue;
+    const int E = exp_of(pr.maxB, static_cast<int>(r), pr.N);
+    uint64_t bits[4];
 #pragma unroll
-  for (int t = 0; t < P; ++t) {
-    uint4* dst = reinterpret_cast<uint4*>(row + (c * P + t) * 32);
-    dst[0] = make_uint4(word[t][0], word[t][1], word[t][2], word[t][3]);
-    dst[1] = make_uint4(word[t][4], word[t][5], word[t][6], word[t][7]);
+    for (int q = 0; q < 4; ++q) bits[q] = tile[rl][q * 33 + lane];
+    uint32_t word[P];
+    pack4<P, false>(bits, E, word);
+    uint8_t* row = reinterpret_cast<uint8_t*>(pr.hatB) + r * pr.nchunks * 32 * P;
+#pragma unroll
+    for (int t = 0; t < P; ++t) *reinterpret_cast<uint32_t*>(row + (c * P + t) * 32 + (lane & 7) * 4) = word[t];
+    if (c == 0 && lane == 0 && r < pr.N) pr.FB[r] = E;
   }
-  if (c == 0 && r < pr.N) pr.FB[r] = E;
 }
 
 // ---------------------------------------------------------------- GEMM
@@ -520,8 +493,8 @@ emu_status_t build_plan(emu_handle_s* h, int count, const emu_gemm_desc_t* d, in
     int64_t rows_a = split_rows(M), rows_b = split_rows(N), nch = (K + 31) / 32;
     sA[i + 1] = sA[i] + static_cast<int>(((M + 7) / 8) * ((K + 2047) / 2048));
     sB[i + 1] = sB[i] + static_cast<int>(((N + 31) / 32) * ((K + 255) / 256));
-    pA[i + 1] = pA[i] + static_cast<int>((rows_a * nch + 7) / 8);
-    pB[i + 1] = pB[i] + static_cast<int>(((rows_b + 255) / 256) * nch);
+    pA[i + 1] = pA[i] + static_cast<int>((rows_a * ((nch + 3) / 4) + 7) / 8);
+    pB[i + 1] = pB[i] + static_cast<int>((rows_b / 32) * ((nch + 3) / 4));
   }
   size_t o_starts = off; off += al256(sizeof(int) * 4 * (count + 1));
   // per-problem workspace

@@ -18,6 +18,7 @@
 // moduli, one plane per modulus; complex input also writes the residues of
 // a'_re + a'_im for the 3M product (Eq. 16).
 #include "emu_internal.h"
+#include "split_core.cuh"
 
 namespace emu {
 
@@ -202,101 +203,6 @@ __global__ void norm_finish_kernel(int64_t rows, const unsigned long long* __res
 }
 
 // ------------------------------------------------------------------ split I
-// Bytes of the 8P-bit two's complement of x = sign * (mag << lsh).
-template <int P>
-struct Digits {
-  uint32_t d[P];
-};
-template <int P>
-__device__ __forceinline__ void slice_digits(uint64_t bits, int E, uint32_t* out) {
-  ScaledInt s = scaled_trunc_bits(bits, 8 * P - 1 - E);
-  bool neg = (bits >> 63) != 0;
-  if (P <= 8) {
-    uint64_t v = s.lsh < 64 ? (s.mag << s.lsh) : 0ull;  // < 2^(8P-1) <= 2^63
-    if (neg) v = ~v + 1ull;
-#pragma unroll
-    for (int t = 0; t < P; ++t) out[t] = static_cast<uint32_t>((v >> (8 * (P - 1 - t))) & 0xFFu);
-  } else {
-    unsigned __int128 v = s.lsh < 128 ? (static_cast<unsigned __int128>(s.mag) << s.lsh)
-                                      : static_cast<unsigned __int128>(0);
-    if (neg) v = ~v + static_cast<unsigned __int128>(1);
-#pragma unroll
-    for (int t = 0; t < P; ++t) out[t] = static_cast<uint32_t>((v >> (8 * (P - 1 - t))) & 0xFFu);
-  }
-}
-
-__device__ __forceinline__ int exp_from_maxbits(const unsigned long long* maxbits, int64_t r,
-                                                int64_t rows) {
-  if (r >= rows) return 0;
-  uint64_t mb = maxbits[r];
-  if (mb >= 0x7FF0000000000000ull) return 0;  // non-finite: flagged by the scan
-  return frexp_exp_bits(mb);
-}
-
-// E4M3 bytes of two digits given as exact small integers in float: the
-// conversion of a lands in the upper byte, that of b in the lower byte.
-__device__ __forceinline__ uint32_t e4m3x2(float a, float b) {
-  unsigned short r;
-  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(a), "f"(b));
-  return static_cast<uint32_t>(r);
-}
-
-// Four consecutive K elements of one vector (their binary64 bits) -> for
-// every slice t one 32-bit word holding the four slice bytes in K order
-// (byte q = element q).
-// E4M3 slices (beta = 5): balanced base-32 digits of x = sign * (mag << lsh),
-// |x| < 2^(5P-1) <= 2^59 (leading digit in [-16, 16], the others in
-// [-16, 15]), each encoded as its exact E4M3 byte.  Adding 16 * 32^t for
-// every lower position t turns the balanced digits into plain base-32 digits
-// of the biased value y, so all digits come from independent shifts:
-// d_t = ((y >> 5(P-1-t)) & 31) - 16 for t >= 1, d_0 = y >> 5(P-1).  Each
-// digit becomes an exact float through the 1.5 * 2^23 bit pattern (field f
-// -> f - 16 in one OR and one FADD), and the hardware conversion packs two
-// at a time.  INT8: the bytes of the two's complement (slice_digits).
-template <int P, bool F8>
-__device__ __forceinline__ void pack4(const uint64_t* bits, int E, uint32_t* word) {
-  if (F8) {
-    constexpr long long kBias = [] {
-      long long b = 0;
-      for (int t = 1; t < P; ++t) b = b * 32 + 16;
-      return b;
-    }();
-    long long y[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const ScaledInt sc = scaled_trunc_bits(bits[q], 5 * P - 1 - E);
-      long long x = static_cast<long long>(sc.lsh < 64 ? (sc.mag << sc.lsh) : 0ull);
-      if ((bits[q] >> 63) != 0) x = -x;
-      y[q] = x + kBias;
-    }
-#pragma unroll
-    for (int t = 0; t < P; ++t) {
-      float f[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        if (t == 0) {  // leading digit, in [-16, 16]
-          const int d = static_cast<int>(y[q] >> (5 * (P - 1)));
-          f[q] = __int_as_float(0x4B400000 + d) - 12582912.0f;
-        } else {  // field in [0, 31], digit = field - 16
-          const int fld = static_cast<int>((y[q] >> (5 * (P - 1 - t))) & 31);
-          f[q] = __int_as_float(0x4B400000 | fld) - 12582928.0f;
-        }
-      }
-      word[t] = e4m3x2(f[1], f[0]) | (e4m3x2(f[3], f[2]) << 16);
-    }
-  } else {
-#pragma unroll
-    for (int t = 0; t < P; ++t) word[t] = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      uint32_t dg[P];
-      slice_digits<P>(bits[q], E, dg);
-#pragma unroll
-      for (int t = 0; t < P; ++t) word[t] |= (dg[t] & 0xFFu) << (8 * q);
-    }
-  }
-}
-
 // K-contiguous source: one warp per (row, group of four 32-wide K-chunks);
 // lane l handles h = 4l .. 4l+3 of the group and writes one 4-byte word per
 // slice (lanes 8c .. 8c+7 fill the 32-byte block of chunk c).
