@@ -146,14 +146,15 @@ void host_mod_tables(int nm, ModTables* t) {
   int32_t mods[kMaxModuli];
   host_moduli(nm, mods);
   for (int l = 0; l < nm; ++l) {
-    uint32_t m = static_cast<uint32_t>(mods[l]);
-    t->mods[l] = m;
-    t->two32mod[l] = static_cast<uint32_t>((uint64_t{1} << 32) % m);
-    t->fastmod[l] = UINT64_MAX / m + 1;
-    uint32_t v = 1 % m;
-    for (int e = 0; e < kPow2TabLen; ++e) {
-      t->pow2mod[l][e] = static_cast<uint8_t>(v);
-      v = (v * 2) % m;
+    const int32_t m = mods[l], hi = (m - 1) / 2;
+    t->mods[l] = static_cast<uint32_t>(m);
+    t->off[l] = m - 1 - hi;
+    t->inv[l] = 1.0f / static_cast<float>(m);
+    t->offinv[l] = static_cast<float>(t->off[l]) / static_cast<float>(m);
+    int64_t v = 1 % m;  // 2^(16 j) mod m
+    for (int j = 0; j < kResDigits; ++j) {
+      t->pow16[l][j] = static_cast<int32_t>(v > hi ? v - m : v);
+      v = (v << 16) % m;
     }
   }
 }

@@ -10,7 +10,6 @@
 namespace emu {
 
 constexpr int kMaxModuli = 20;  // Scheme II moduli supported
-constexpr int kPow2TabLen = 128; // 2^e mod m for e < 128 (a' < 2^b, b < 128)
 constexpr int kCrtLimbs = 5;     // P < 2^160 for up to 20 moduli
 constexpr int kSplitRowAlign = 128;
 
@@ -20,11 +19,16 @@ inline int64_t split_cols_I(int64_t k, int p) { return (k + 31) / 32 * 32 * p; }
 inline int64_t split_cols_II(int64_t k) { return (k + 127) / 128 * 128; }
 
 // Scheme II tables, passed by value to kernels.
+// Residues of the scaled integers a' (|a'| < 2^80) are taken from their
+// 16-bit digits: a' = sum_j d_j 2^(16 j), a' mod m = sum_j d_j (2^(16 j) mod m)
+// mod m, the last reduction in single precision (the sum stays below 2^26).
+constexpr int kResDigits = 5;
 struct ModTables {
   uint32_t mods[kMaxModuli];
-  uint32_t two32mod[kMaxModuli];                 // 2^32 mod m_l
-  uint64_t fastmod[kMaxModuli];                  // ceil(2^64 / m_l): x mod m_l for 32-bit x by two products
-  uint8_t pow2mod[kMaxModuli][kPow2TabLen];      // 2^e mod m_l
+  int32_t off[kMaxModuli];                 // m - 1 - floor((m - 1)/2): symmetric residues lie in [-off, m - 1 - off]
+  float inv[kMaxModuli];                   // 1/m rounded to nearest
+  float offinv[kMaxModuli];                // off/m rounded to nearest
+  int32_t pow16[kMaxModuli][kResDigits];   // symmetric residue of 2^(16 j) mod m
 };
 
 // CRT tables of Eq. (8) for a given number of moduli.

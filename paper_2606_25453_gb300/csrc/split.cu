@@ -277,82 +277,83 @@ __global__ void __launch_bounds__(256) split_I_kstrided(const T* __restrict__ X,
 }
 
 // ------------------------------------------------------------------ split II
-// x mod m for a 32-bit x from c = ceil(2^64 / m) (Lemire, Kaser, Kurz,
-// "Faster remainder by direct computation", 2019): the low 64 bits of c x,
-// times m, high 64 bits.  Exact for every 32-bit x and m < 2^32.
-__device__ __forceinline__ uint32_t fastmod32(uint32_t x, uint32_t m, uint64_t c) {
-  return static_cast<uint32_t>(__umul64hi(c * static_cast<uint64_t>(x), m));
+// The 16-bit digits of |a'| = trunc(|a| 2^shift) (|a'| < 2^80, so five
+// digits), negated for a negative element: a' = sum_j d_j 2^(16 j).
+__device__ __forceinline__ void digits16(uint64_t bits, int shift, int* d) {
+  const ScaledInt s = scaled_trunc_bits(bits, shift);
+  // s.mag 2^s.lsh = |a'| < 2^80 (the row exponent bounds every element), so s.lsh < 80
+  const unsigned __int128 v = static_cast<unsigned __int128>(s.mag) << s.lsh;
+  const uint64_t lo = static_cast<uint64_t>(v);
+  const uint32_t hi = static_cast<uint32_t>(v >> 64);
+  const int sg = (bits >> 63) ? -1 : 1;
+  d[0] = sg * static_cast<int>(lo & 0xFFFFu);
+  d[1] = sg * static_cast<int>((lo >> 16) & 0xFFFFu);
+  d[2] = sg * static_cast<int>((lo >> 32) & 0xFFFFu);
+  d[3] = sg * static_cast<int>(lo >> 48);
+  d[4] = sg * static_cast<int>(hi & 0xFFFFu);
 }
 
-// Residue of x = sign * (mag << lsh) modulo m, in [0, m); mag < 2^53 is
-// reduced in two 32-bit pieces, 2^lsh mod m comes from the table.
-__device__ __forceinline__ uint32_t mod_scaled(uint64_t mag, int lsh, bool neg, uint32_t m, uint64_t c,
-                                               uint32_t two32m, const uint8_t* pow2tab_m) {
-  const uint32_t hi = static_cast<uint32_t>(mag >> 32), lo = static_cast<uint32_t>(mag);
-  uint32_t r = fastmod32(fastmod32(hi, m, c) * two32m + fastmod32(lo, m, c), m, c);
-  if (lsh) {
-    const uint32_t f = lsh < kPow2TabLen ? pow2tab_m[lsh] : 0u;  // lsh < b < 128 by construction
-    r = fastmod32(r * f, m, c);
-  }
-  if (neg && r) r = m - r;
+// Symmetric residue of a' modulo m_l from its digits.  t = sum_j d_j c_j
+// with c_j the symmetric residue of 2^(16 j) (|c_j| <= 128) satisfies
+// |t| <= 65535 (1 + 4 * 128) < 2^25.1.  q = floor(RN(RN(t) / m + off / m)) is
+// floor((t + off) / m) or one off (the three roundings move the quotient,
+// which is below 2^18, by less than 0.05), so r = t - q m lies in
+// [-off - m, 2m - off) and one correction each way puts it in
+// [-off, m - 1 - off].
+__device__ __forceinline__ int sym_residue(const int* d, const ModTables& mt, int l) {
+  int t = d[0];
+#pragma unroll
+  for (int j = 1; j < kResDigits; ++j) t += d[j] * mt.pow16[l][j];
+  const int m = static_cast<int>(mt.mods[l]), off = mt.off[l];
+  const int q = __float2int_rd(__fmaf_rn(__int2float_rn(t), mt.inv[l], mt.offinv[l]));
+  int r = t - q * m;
+  if (r < -off) r += m;
+  if (r >= m - off) r -= m;
   return r;
 }
 
-__device__ __forceinline__ uint32_t sym_byte(uint32_t r, uint32_t m) {
-  int v = static_cast<int>(r);
-  if (v > static_cast<int>((m - 1) / 2)) v -= static_cast<int>(m);
-  return static_cast<uint32_t>(v) & 0xFFu;
-}
-
-struct ModSmem {
-  uint8_t tab[kMaxModuli][kPow2TabLen];
-  uint64_t c[kMaxModuli];
-  uint32_t mods[kMaxModuli], two32[kMaxModuli];
-};
-
-__device__ __forceinline__ void load_mod_smem(ModSmem& ms, const ModTables& mt, int nm) {
-  for (int i = threadIdx.x; i < nm * kPow2TabLen; i += blockDim.x)
-    ms.tab[i / kPow2TabLen][i % kPow2TabLen] = mt.pow2mod[i / kPow2TabLen][i % kPow2TabLen];
-  for (int i = threadIdx.x; i < nm; i += blockDim.x) {
-    ms.mods[i] = mt.mods[i];
-    ms.two32[i] = mt.two32mod[i];
-    ms.c[i] = mt.fastmod[i];
-  }
+__device__ __forceinline__ uint32_t pack_bytes(int r0, int r1, int r2, int r3) {
+  const uint32_t lo = __byte_perm(static_cast<uint32_t>(r0), static_cast<uint32_t>(r1), 0x0040u);
+  const uint32_t hi = __byte_perm(static_cast<uint32_t>(r2), static_cast<uint32_t>(r3), 0x0040u);
+  return __byte_perm(lo, hi, 0x5410u);
 }
 
 // The residues of four consecutive K elements of one vector, packed four
 // bytes per word (byte q = element q), one word per plane: real (cw = 1)
 // one plane per modulus; complex three (re, im, re + im).  `re`/`im` hold
-// the binary64 bits of the elements.
+// the binary64 bits of the elements.  The modulus loop is unrolled so that
+// the table entries are kernel-parameter operands.
 template <int CW>
-__device__ __forceinline__ void residues4(const ModSmem& ms, int nm, int shift, const uint64_t* re, const uint64_t* im,
-                                          int64_t plane, int8_t* base) {
-  ScaledInt sr[4], si[4];
+__device__ __forceinline__ void residues4(const ModTables& mt, int nm, int shift, const uint64_t* re,
+                                          const uint64_t* im, int64_t plane, int8_t* base) {
+  int dr[4][kResDigits], di[4][kResDigits];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    sr[q] = scaled_trunc_bits(re[q], shift);
-    if (CW == 2) si[q] = scaled_trunc_bits(im[q], shift);
+    digits16(re[q], shift, dr[q]);
+    if (CW == 2) digits16(im[q], shift, di[q]);
   }
-  for (int l = 0; l < nm; ++l) {
-    const uint32_t m = ms.mods[l];
-    const uint64_t c = ms.c[l];
-    uint32_t w0 = 0, w1 = 0, w2 = 0;
+#pragma unroll
+  for (int l = 0; l < kMaxModuli; ++l) {
+    if (l >= nm) break;
+    int rr[4], ri[4], rs[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const uint32_t rr = mod_scaled(sr[q].mag, sr[q].lsh, (re[q] >> 63) != 0, m, c, ms.two32[l], ms.tab[l]);
-      w0 |= sym_byte(rr, m) << (8 * q);
+      rr[q] = sym_residue(dr[q], mt, l);
       if (CW == 2) {
-        const uint32_t ri = mod_scaled(si[q].mag, si[q].lsh, (im[q] >> 63) != 0, m, c, ms.two32[l], ms.tab[l]);
-        uint32_t rs = rr + ri;
-        if (rs >= m) rs -= m;
-        w1 |= sym_byte(ri, m) << (8 * q);
-        w2 |= sym_byte(rs, m) << (8 * q);
+        ri[q] = sym_residue(di[q], mt, l);
+        const int m = static_cast<int>(mt.mods[l]), off = mt.off[l];
+        int v = rr[q] + ri[q];
+        if (v < -off) v += m;
+        if (v >= m - off) v -= m;
+        rs[q] = v;
       }
     }
-    *reinterpret_cast<uint32_t*>(base + static_cast<int64_t>(l) * plane) = w0;
+    *reinterpret_cast<uint32_t*>(base + static_cast<int64_t>(l) * plane) = pack_bytes(rr[0], rr[1], rr[2], rr[3]);
     if (CW == 2) {
-      *reinterpret_cast<uint32_t*>(base + static_cast<int64_t>(nm + l) * plane) = w1;
-      *reinterpret_cast<uint32_t*>(base + static_cast<int64_t>(2 * nm + l) * plane) = w2;
+      *reinterpret_cast<uint32_t*>(base + static_cast<int64_t>(nm + l) * plane) =
+          pack_bytes(ri[0], ri[1], ri[2], ri[3]);
+      *reinterpret_cast<uint32_t*>(base + static_cast<int64_t>(2 * nm + l) * plane) =
+          pack_bytes(rs[0], rs[1], rs[2], rs[3]);
     }
   }
 }
@@ -369,9 +370,6 @@ __global__ void split_II_kcontig(const T* __restrict__ X, int64_t ld, int64_t ro
                                  int64_t kpad, int nm, int b, const __grid_constant__ ModTables mt,
                                  const unsigned long long* __restrict__ maxbits, const int32_t* __restrict__ Ein,
                                  int8_t* __restrict__ res, int32_t* __restrict__ E_out) {
-  __shared__ ModSmem ms;
-  load_mod_smem(ms, mt, nm);
-  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t ngroups = kpad / 128;
   const int64_t w = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -386,7 +384,7 @@ __global__ void split_II_kcontig(const T* __restrict__ X, int64_t ld, int64_t ro
     re[q] = valid ? load_bits(p) : 0ull;
     im[q] = (CW == 2 && valid) ? load_bits(p + 1) : 0ull;
   }
-  residues4<CW>(ms, nm, b - E, re, im, rows_pad * kpad, res + r * kpad + h0);
+  residues4<CW>(mt, nm, b - E, re, im, rows_pad * kpad, res + r * kpad + h0);
   if (h0 == 0 && r < rows && E_out) E_out[r] = E;
 }
 
@@ -398,15 +396,13 @@ __global__ void __launch_bounds__(256) split_II_kstrided(const T* __restrict__ X
                                                          const int32_t* __restrict__ Ein, int8_t* __restrict__ res,
                                                          int32_t* __restrict__ E_out) {
   constexpr int TR = CW == 2 ? 16 : 32;  // vectors per tile (two tiles for complex)
-  __shared__ ModSmem ms;
   __shared__ uint64_t tre[TR][133];
   __shared__ uint64_t tim[CW == 2 ? TR : 1][CW == 2 ? 133 : 1];
-  load_mod_smem(ms, mt, nm);
   const int64_t hbase = static_cast<int64_t>(blockIdx.x) * 128;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int64_t r0 = static_cast<int64_t>(blockIdx.y) * TR; r0 < rows_pad;
        r0 += static_cast<int64_t>(gridDim.y) * TR) {
-    __syncthreads();  // tables loaded / the previous row block is done with the tiles
+    __syncthreads();  // the previous row block is done with the tiles
     for (int i = threadIdx.x; i < TR * 128; i += 256) {
       const int rl = i % TR, hl = i / TR;
       const int64_t r = r0 + rl, h = hbase + hl;
@@ -428,7 +424,7 @@ __global__ void __launch_bounds__(256) split_II_kstrided(const T* __restrict__ X
         im[q] = CW == 2 ? tim[rl][q * 33 + lane] : 0ull;
       }
       const int64_t h0 = hbase + lane * 4;
-      residues4<CW>(ms, nm, b - E, re, im, rows_pad * kpad, res + r * kpad + h0);
+      residues4<CW>(mt, nm, b - E, re, im, rows_pad * kpad, res + r * kpad + h0);
       if (h0 == 0 && r < rows && E_out) E_out[r] = E;
     }
   }
