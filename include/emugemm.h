@@ -15,10 +15,15 @@
  *
  *   Scheme II (Sec. II-C-2, Eqs. 4-8; fused kernel of Sec. IV-A)
  *     A and B are scaled to integers, reduced modulo N pairwise-coprime
- *     moduli m_l <= 256 (256, 255, 253, 251, ...), multiplied with one INT8
- *     GEMM per modulus, reduced modulo m_l and reconstructed by the Chinese
- *     Remainder Theorem (Eq. 8), all inside one kernel.  Complex input uses
- *     the 3M method (Eq. 16).
+ *     moduli m_l <= 256 (256, 255, 253, 251, ...), multiplied with one
+ *     integer GEMM per modulus, reduced modulo m_l and reconstructed by the
+ *     Chinese Remainder Theorem (Eq. 8), all inside one kernel.  Complex
+ *     input uses the 3M method (Eq. 16).  On sm_103a the per-modulus GEMMs
+ *     run on the bf16 tensor cores (tcgen05): symmetric residues are exact
+ *     bf16 values and FP32 sums of up to 960 of their products are exact
+ *     integers, so each 960-deep K segment is reduced modulo m_l as it
+ *     leaves the accumulator.  EMU_II_ENGINE=mma selects the INT8 mma.sync
+ *     kernel instead (same results, k <= EMU_K_MAX_II).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -93,7 +98,7 @@ typedef enum {
 #define EMU_P_MAX 12
 #define EMU_NM_MIN 1         /* Scheme II moduli                        */
 #define EMU_NM_MAX 20
-#define EMU_K_MAX_II 131071  /* Scheme II: |products| <= 2^14, INT32 exact */
+#define EMU_K_MAX_II 131071  /* Scheme II on the INT8 engine (EMU_II_ENGINE=mma): |products| <= 2^14, INT32 exact */
 
 /* ------------------------------------------------------------------ */
 /* Handle, status, workspace                                           */
@@ -125,6 +130,11 @@ emu_status_t emu_selftest_wait(emu_handle_t h, int64_t limit_cycles, emu_stream_
 /* Human-readable name of a status code (static string). */
 const char *emu_status_string(emu_status_t s);
 
+/* The CUDA runtime's description of the error behind the calling thread's
+ * most recent EMU_ERR_CUDA from a launch or a tensor-map encoding ("no
+ * error" if there was none); a static string. */
+const char *emu_last_cuda_error(void);
+
 /* Bytes of device workspace one call needs (is_complex selects the complex
  * layouts: three residue sets per operand for the Scheme II 3M method, the
  * real embedding plus the slices of the 2K-deep product for Scheme I 4M). */
@@ -154,7 +164,9 @@ emu_status_t emu_trace_read(emu_handle_t h, double *ms_host, int64_t *gemm_launc
 
 /* FP64 C = alpha*A*B + beta*C.  scheme = EMU_SCHEME_I or EMU_SCHEME_I_F8
  * with p_or_nm = p in [EMU_P_MIN, EMU_P_MAX] slices, or EMU_SCHEME_II with
- * p_or_nm = N in [EMU_NM_MIN, EMU_NM_MAX] moduli (k <= EMU_K_MAX_II).
+ * p_or_nm = N in [EMU_NM_MIN, EMU_NM_MAX] moduli (k <= EMU_K_MAX_II when the
+ * environment selects the INT8 engine with EMU_II_ENGINE=mma; the default
+ * bf16 tcgen05 engine reduces every 960-deep segment modulo m and takes any k).
  * Sec. II-C. */
 emu_status_t emu_dgemm(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k,
                        double alpha, const double *A, int64_t lda, const double *B, int64_t ldb,

@@ -49,6 +49,7 @@ _SIGS = {
     "emu_destroy": (_i32, [_vp]),
     "emu_get_status": (_i32, [_vp, _vp]),
     "emu_status_string": (ctypes.c_char_p, [_i32]),
+    "emu_last_cuda_error": (ctypes.c_char_p, []),
     "emu_selftest_wait": (_i32, [_vp, _i64, _vp]),
     "emu_workspace_size": (_i32, [_i32, _i64, _i64, _i64, _i32, _i32, ctypes.POINTER(_sz)]),
     "emu_set_workspace": (_i32, [_vp, _vp, _sz]),
@@ -106,6 +107,8 @@ for _name, (_res, _args) in _SIGS.items():
 
 def check(code: int, where: str = "") -> None:
     if code != 0:
+        if code == 4:  # EMU_ERR_CUDA: name the runtime error
+            where = "%s (%s)" % (where, emu_last_cuda_error().decode())
         raise EmuError(code, where)
 
 

@@ -264,7 +264,17 @@ __global__ void selftest_wait_kernel(int* status, long long limit) {
 using namespace emu;
 
 // ================================================================ handle
-static emu_status_t cuda_err(cudaError_t e) { return e == cudaSuccess ? EMU_OK : EMU_ERR_CUDA; }
+// What was behind this thread's last EMU_ERR_CUDA (emu_last_cuda_error).
+static thread_local const char* g_last_cuda_error = "no error";
+static emu_status_t cuda_err(cudaError_t e) {
+  if (e == cudaSuccess) return EMU_OK;
+  g_last_cuda_error = cudaGetErrorString(e);
+  return EMU_ERR_CUDA;
+}
+static emu_status_t tmap_err() {
+  g_last_cuda_error = "tensor map encoding failed";
+  return EMU_ERR_CUDA;
+}
 
 namespace emu {
 // EMU_FAULT=alloc: host-side fault injection for the allocation failure path.
@@ -364,6 +374,8 @@ emu_status_t emu_selftest_wait(emu_handle_t h, int64_t limit_cycles, emu_stream_
   return cuda_err(cudaGetLastError());
 }
 
+const char* emu_last_cuda_error(void) { return g_last_cuda_error; }
+
 const char* emu_status_string(emu_status_t s) {
   switch (s) {
     case EMU_OK: return "EMU_OK";
@@ -418,6 +430,17 @@ static bool f8_engine_mma() {
   return v == 1;
 }
 
+// EMU_II_ENGINE=mma selects the INT8 mma.sync kernel for Scheme II (for
+// comparison; identical results); the default is the bf16 tcgen05 kernel.
+bool ii_engine_tc() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = std::getenv("EMU_II_ENGINE");
+    v = (e && std::strcmp(e, "mma") == 0) ? 0 : 1;
+  }
+  return v == 1;
+}
+
 Plan plan_I(int64_t m, int64_t n, int64_t k, int p) {
   Plan pl{};
   pl.rows_a = split_rows(m);
@@ -434,7 +457,8 @@ Plan plan_I(int64_t m, int64_t n, int64_t k, int p) {
   return pl;
 }
 
-Plan plan_II(int64_t m, int64_t n, int64_t k, int nm, int nsets) {
+// es: bytes per residue (1: INT8 planes, 2: bf16 planes of the tcgen05 kernel)
+Plan plan_II(int64_t m, int64_t n, int64_t k, int nm, int nsets, int es) {
   Plan pl{};
   pl.rows_a = split_rows(m);
   pl.rows_b = split_rows(n);
@@ -444,13 +468,15 @@ Plan plan_II(int64_t m, int64_t n, int64_t k, int nm, int nsets) {
   pl.off_maxB = off; off += al256(8 * static_cast<size_t>(n > 0 ? n : 1));
   pl.off_EA = off; off += al256(4 * static_cast<size_t>(m > 0 ? m : 1));
   pl.off_FB = off; off += al256(4 * static_cast<size_t>(n > 0 ? n : 1));
-  pl.off_hatA = off; off += al256(static_cast<size_t>(nsets) * nm * pl.rows_a * pl.cols);
-  pl.off_hatB = off; off += al256(static_cast<size_t>(nsets) * nm * pl.rows_b * pl.cols);
+  pl.off_hatA = off; off += al256(static_cast<size_t>(es) * nsets * nm * pl.rows_a * pl.cols);
+  pl.off_hatB = off; off += al256(static_cast<size_t>(es) * nsets * nm * pl.rows_b * pl.cols);
   // norm-based scaling: 128-bit sums of squares and the exponents
   pl.off_accA = off; off += al256(16 * static_cast<size_t>(m > 0 ? m : 1));
   pl.off_accB = off; off += al256(16 * static_cast<size_t>(n > 0 ? n : 1));
   pl.off_nEA = off; off += al256(4 * static_cast<size_t>(m > 0 ? m : 1));
   pl.off_nEB = off; off += al256(4 * static_cast<size_t>(n > 0 ? n : 1));
+  // tcgen05 kernel: per-CTA residue slots
+  pl.off_scratch = off; off += es == 2 ? al256(gemm_II_tc_scratch_bytes(nm, nsets == 3)) : 0;
   pl.bytes = off;
   return pl;
 }
@@ -524,7 +550,7 @@ emu_status_t run_scheme_I(emu_handle_s* h, const View& v, int64_t k, int p, doub
   if (!make_tmap_i8(&ta, hatA, static_cast<uint64_t>(pl.cols), static_cast<uint64_t>(pl.rows_a),
                     tc ? static_cast<uint32_t>(128 / cluster) : 64, tc ? 128 : 32) ||
       !make_tmap_i8(&tb, hatB, static_cast<uint64_t>(pl.cols), static_cast<uint64_t>(pl.rows_b), 32))
-    return EMU_ERR_CUDA;
+    return tmap_err();
   GemmIArgs a{};
   a.descA = &ta;
   a.descB = &tb;
@@ -557,7 +583,11 @@ emu_status_t run_scheme_II(emu_handle_s* h, const View& v, int64_t k, int nm, in
                            double ai, double br, double bi, void* C, int64_t ldc, int out_mode,
                            uint8_t* residues, cudaStream_t st, bool norm = false) {
   const int nsets = cw == 2 ? 3 : 1;
-  Plan pl = plan_II(v.M, v.N, k, nm, nsets);
+  // the tcgen05 kernel takes bf16 residue planes; the INT8 kernel sums a
+  // modulus's products over the whole K in INT32 (|sum| <= k 2^14)
+  const bool tc = out_mode != II_RESIDUES && ii_engine_tc();
+  if (!tc && k > EMU_K_MAX_II) return EMU_ERR_UNSUPPORTED;
+  Plan pl = plan_II(v.M, v.N, k, nm, nsets, tc ? 2 : 1);
   uint8_t* ws = nullptr;
   emu_status_t s = handle_workspace(h, pl.bytes, st, &ws);
   if (s != EMU_OK) return s;
@@ -590,15 +620,20 @@ emu_status_t run_scheme_II(emu_handle_s* h, const View& v, int64_t k, int nm, in
   }
   trace_end(h, PH_SCAN, st, norm ? 6 : 2);
   trace_begin(h, PH_SPLIT, st);
-  launch_split_II<T>(A, v.ldA, v.a_kcontig, v.M, k, nm, bA, cw, mt, maxA, resA, EA, st, norm ? nEA : nullptr);
-  launch_split_II<T>(B, v.ldB, v.b_kcontig, v.N, k, nm, bB, cw, mt, maxB, resB, FB, st, norm ? nEB : nullptr);
+  launch_split_II<T>(A, v.ldA, v.a_kcontig, v.M, k, nm, bA, cw, mt, maxA, resA, EA, st, norm ? nEA : nullptr, tc);
+  launch_split_II<T>(B, v.ldB, v.b_kcontig, v.N, k, nm, bB, cw, mt, maxB, resB, FB, st, norm ? nEB : nullptr, tc);
   trace_end(h, PH_SPLIT, st, 2);
   CUtensorMap ta, tb;
-  if (!make_tmap_i8(&ta, resA, static_cast<uint64_t>(pl.cols),
-                    static_cast<uint64_t>(pl.rows_a) * nm * nsets, 64) ||
-      !make_tmap_i8(&tb, resB, static_cast<uint64_t>(pl.cols),
-                    static_cast<uint64_t>(pl.rows_b) * nm * nsets, 32))
-    return EMU_ERR_CUDA;
+  // tcgen05: the bf16 planes as bytes, 128-byte (64-element) boxes of 128
+  // rows (A) and 256 / cluster rows (B, multicast to the cluster); INT8:
+  // 32-byte boxes of 64 / 32 rows
+  const uint64_t row_bytes = static_cast<uint64_t>(pl.cols) * (tc ? 2 : 1);
+  const int cluster = tc ? gemm_II_tc_cluster() : 1;
+  if (!make_tmap_i8(&ta, resA, row_bytes, static_cast<uint64_t>(pl.rows_a) * nm * nsets,
+                    tc ? static_cast<uint32_t>(gemm_II_tc_tile_m()) : 64, tc ? 128 : 32) ||
+      !make_tmap_i8(&tb, resB, row_bytes, static_cast<uint64_t>(pl.rows_b) * nm * nsets,
+                    tc ? static_cast<uint32_t>(gemm_II_tc_tile_n() / cluster) : 32, tc ? 128 : 32))
+    return tmap_err();
   GemmIIArgs a{};
   a.descA = &ta;
   a.descB = &tb;
@@ -620,8 +655,10 @@ emu_status_t run_scheme_II(emu_handle_s* h, const View& v, int64_t k, int nm, in
   a.residues = residues;
   a.status = h->status;
   a.num_sms = h->num_sms;
+  a.cluster = cluster;
+  a.scratch = ws + pl.off_scratch;
   trace_begin(h, PH_GEMM, st);
-  cudaError_t e = launch_gemm_II(out_mode, a, mt, ct, st);
+  cudaError_t e = tc ? launch_gemm_II_tc(out_mode, a, mt, ct, st) : launch_gemm_II(out_mode, a, mt, ct, st);
   trace_end(h, PH_GEMM, st, 1);
   return cuda_err(e);
 }
@@ -648,7 +685,7 @@ emu_status_t emu_workspace_size(emu_scheme_t scheme, int64_t m, int64_t n, int64
   }
   if (scheme == EMU_SCHEME_II || scheme == EMU_SCHEME_II_NORM) {
     if (p_or_nm < EMU_NM_MIN || p_or_nm > EMU_NM_MAX) return EMU_ERR_UNSUPPORTED;
-    *bytes = plan_II(m, n, k, p_or_nm, is_complex ? 3 : 1).bytes;
+    *bytes = plan_II(m, n, k, p_or_nm, is_complex ? 3 : 1, ii_engine_tc() ? 2 : 1).bytes;
     return EMU_OK;
   }
   return EMU_ERR_INVALID_ARG;
@@ -670,7 +707,7 @@ static emu_status_t gemm_common(emu_handle_t h, emu_layout_t layout, int64_t m, 
     if (p_or_nm < EMU_P_MIN || p_or_nm > EMU_P_MAX) return EMU_ERR_UNSUPPORTED;
   } else if (scheme == EMU_SCHEME_II || scheme == EMU_SCHEME_II_NORM) {
     if (p_or_nm < EMU_NM_MIN || p_or_nm > EMU_NM_MAX) return EMU_ERR_UNSUPPORTED;
-    if (k > EMU_K_MAX_II) return EMU_ERR_UNSUPPORTED;
+    if (k > EMU_K_MAX_II && !ii_engine_tc()) return EMU_ERR_UNSUPPORTED;
   } else {
     return EMU_ERR_INVALID_ARG;
   }

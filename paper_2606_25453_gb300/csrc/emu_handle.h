@@ -26,9 +26,11 @@ struct Plan {
   int64_t rows_a, rows_b, cols;
   size_t off_maxA, off_maxB, off_EA, off_FB, off_hatA, off_hatB, bytes;
   size_t off_accA = 0, off_accB = 0, off_nEA = 0, off_nEB = 0;  // Scheme II norm-based scaling
+  size_t off_scratch = 0;                                        // Scheme II tcgen05 residue slots
 };
 Plan plan_I(int64_t m, int64_t n, int64_t k, int p);
-Plan plan_II(int64_t m, int64_t n, int64_t k, int nm, int nsets);
+Plan plan_II(int64_t m, int64_t n, int64_t k, int nm, int nsets, int es);
+bool ii_engine_tc();
 
 // Row-major view of a product (see normalize in api.cu).
 struct View {

@@ -59,7 +59,7 @@ void launch_split_I(const T* X, int64_t ld, bool kcontig, int64_t rows, int64_t 
 template <typename T>
 void launch_split_II(const T* X, int64_t ld, bool kcontig, int64_t rows, int64_t k, int nm, int b,
                      int cw, const ModTables& tabs, const unsigned long long* maxbits, int8_t* res,
-                     int32_t* E, cudaStream_t st, const int32_t* Ein = nullptr);
+                     int32_t* E, cudaStream_t st, const int32_t* Ein = nullptr, bool bf16 = false);
 // Norm-based Scheme II scaling: E[r] with ||x_r||_2 < 2^E[r], computed
 // exactly (maxbits from launch_scan; acc: 2 rows words of scratch).
 template <typename T>
@@ -110,9 +110,22 @@ struct GemmIIArgs {
   uint8_t* residues;
   int* status;
   int num_sms;
+  int cluster;       // tcgen05 kernel: CTAs per cluster sharing the B chunks (1, 2, 4)
+  uint8_t* scratch;  // tcgen05 kernel: per-CTA residue slots
 };
 cudaError_t launch_gemm_II(int out_mode, const GemmIIArgs& a, const ModTables& mt,
                            const CrtTables& ct, cudaStream_t st);
+// Scheme II on bf16 residue planes with tcgen05 / TMEM (128 x 256 tiles);
+// modes II_F64, II_F32, II_Z3M, II_C3M.  GemmIIArgs::scratch: at least
+// gemm_II_tc_scratch_bytes(nm, complex) bytes of device memory for the
+// per-CTA residue slots (at most kGemmIITcMaxCtas CTAs).
+constexpr int kGemmIITcMaxCtas = 160;
+cudaError_t launch_gemm_II_tc(int out_mode, const GemmIIArgs& a, const ModTables& mt,
+                              const CrtTables& ct, cudaStream_t st);
+int gemm_II_tc_tile_m();
+int gemm_II_tc_tile_n();
+size_t gemm_II_tc_scratch_bytes(int nm, bool is_complex);
+int gemm_II_tc_cluster();
 
 // Tensor map for a row-major byte matrix [rows][cols] read in boxes of
 // box_bytes x box_rows: 32-byte boxes with 32-byte swizzling, or 128-byte

@@ -34,6 +34,7 @@
 #include <cstdlib>
 
 #include "emu_internal.h"
+#include "tc_core.cuh"
 
 namespace emu {
 namespace {
@@ -93,19 +94,6 @@ __device__ __forceinline__ uint64_t smem_desc_k32(uint32_t saddr) {
   return d;
 }
 
-// The same for a K-major block [rows][128 B] with the 128-byte swizzle:
-// 8-row atoms 1024 B apart, layout type 2.  The 32-byte K-step u inside the
-// 128-byte row is selected by starting 32 u bytes into the (1024-aligned) atom.
-__device__ __forceinline__ uint64_t smem_desc_k128(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= static_cast<uint64_t>((saddr >> 4) & 0x3FFFu);         // start address
-  d |= static_cast<uint64_t>(1u) << 16;                        // leading byte offset (unused)
-  d |= static_cast<uint64_t>((1024u >> 4) & 0x3FFFu) << 32;    // stride byte offset: 8 rows x 128 B
-  d |= static_cast<uint64_t>(1u) << 46;                        // descriptor version
-  d |= static_cast<uint64_t>(2u) << 61;                        // 128-byte swizzle
-  return d;
-}
-
 // Instruction descriptor: E4M3 x E4M3 -> F32, both K-major, M x N.
 __device__ __forceinline__ uint32_t idesc_e4m3(int M, int N) {
   return (1u << 4)                                  // D format F32
@@ -122,55 +110,6 @@ __device__ __forceinline__ void umma_e4m3(uint32_t tmem_d, uint64_t adesc, uint6
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
-
-// Arrive on `bar` once every MMA issued so far by this thread has completed.
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-// The same, arriving on the barrier at this offset in every CTA of `mask`.
-__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-          smem_u32(bar)),
-      "h"(mask)
-      : "memory");
-}
-
-// 2D tiled TMA load written to the same shared-memory offset of every CTA in
-// `mask`, completion counted on the barrier at `bar`'s offset in each of them.
-__device__ __forceinline__ void tma_load_2d_mc(void* smem_dst, const void* desc, uint64_t* bar, int x, int y,
-                                               uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
-      " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_u32(smem_dst)),
-      "l"(reinterpret_cast<uint64_t>(desc)), "r"(smem_u32(bar)), "r"(x), "r"(y), "h"(mask)
-      : "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_ctarank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t cluster_id_x() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t cluster_count_x() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
-  return r;
-}
-// Every thread of every CTA in the cluster (release / acquire).
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release;\nbarrier.cluster.wait.acquire;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 // 8 consecutive FP32 columns of this thread's TMEM lane, as integers (the
 // accumulators hold exact integers of magnitude <= 2^24).
@@ -222,15 +161,6 @@ __device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, 
   int in = tile - g * per_group;
   tm = first + in % gsz;
   tn = in / gsz;
-}
-
-// Wait unless another role already gave up; false means "stop".
-__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status) {
-  if (*abort_flag) return false;
-  if (mbar_wait_bounded(bar, parity)) return true;
-  set_status(status, ST_TIMEOUT);
-  *abort_flag = 1;
-  return false;
 }
 
 template <int P, int OUT>

@@ -318,12 +318,30 @@ __device__ __forceinline__ uint32_t pack_bytes(int r0, int r1, int r2, int r3) {
   return __byte_perm(lo, hi, 0x5410u);
 }
 
-// The residues of four consecutive K elements of one vector, packed four
-// bytes per word (byte q = element q), one word per plane: real (cw = 1)
-// one plane per modulus; complex three (re, im, re + im).  `re`/`im` hold
-// the binary64 bits of the elements.  The modulus loop is unrolled so that
-// the table entries are kernel-parameter operands.
-template <int CW>
+// Four residues as bf16 (exact: |r| <= 128 has at most 8 significant bits,
+// so the upper half of the binary32 value is the bf16 value).
+__device__ __forceinline__ uint2 pack_bf16(int r0, int r1, int r2, int r3) {
+  const uint32_t f0 = __float_as_uint(__int2float_rn(r0)), f1 = __float_as_uint(__int2float_rn(r1));
+  const uint32_t f2 = __float_as_uint(__int2float_rn(r2)), f3 = __float_as_uint(__int2float_rn(r3));
+  return make_uint2(__byte_perm(f0, f1, 0x7632u), __byte_perm(f2, f3, 0x7632u));
+}
+
+template <bool BF>
+__device__ __forceinline__ void store4(int8_t* p, int r0, int r1, int r2, int r3) {
+  if (BF)
+    *reinterpret_cast<uint2*>(p) = pack_bf16(r0, r1, r2, r3);
+  else
+    *reinterpret_cast<uint32_t*>(p) = pack_bytes(r0, r1, r2, r3);
+}
+
+// The residues of four consecutive K elements of one vector, one store per
+// plane (INT8: four bytes, byte q = element q; BF: four bf16 values): real
+// (cw = 1) one plane per modulus; complex three (re, im, re + im).
+// `re`/`im` hold the binary64 bits of the elements; `base` is the address
+// of the first element in plane 0, `plane` the plane stride in bytes.  The
+// modulus loop is unrolled so that the table entries are kernel-parameter
+// operands.
+template <int CW, bool BF>
 __device__ __forceinline__ void residues4(const ModTables& mt, int nm, int shift, const uint64_t* re,
                                           const uint64_t* im, int64_t plane, int8_t* base) {
   int dr[4][kResDigits], di[4][kResDigits];
@@ -348,24 +366,23 @@ __device__ __forceinline__ void residues4(const ModTables& mt, int nm, int shift
         rs[q] = v;
       }
     }
-    *reinterpret_cast<uint32_t*>(base + static_cast<int64_t>(l) * plane) = pack_bytes(rr[0], rr[1], rr[2], rr[3]);
+    store4<BF>(base + static_cast<int64_t>(l) * plane, rr[0], rr[1], rr[2], rr[3]);
     if (CW == 2) {
-      *reinterpret_cast<uint32_t*>(base + static_cast<int64_t>(nm + l) * plane) =
-          pack_bytes(ri[0], ri[1], ri[2], ri[3]);
-      *reinterpret_cast<uint32_t*>(base + static_cast<int64_t>(2 * nm + l) * plane) =
-          pack_bytes(rs[0], rs[1], rs[2], rs[3]);
+      store4<BF>(base + static_cast<int64_t>(nm + l) * plane, ri[0], ri[1], ri[2], ri[3]);
+      store4<BF>(base + static_cast<int64_t>(2 * nm + l) * plane, rs[0], rs[1], rs[2], rs[3]);
     }
   }
 }
 
-// Scheme II split.  Planes: set q, modulus l at
-// res + ((q*nm + l)*rows_pad + r)*kpad + h (set = 0 for real; 0, 1, 2 = re,
-// im, re + im for complex).  Row exponent: of the maximum (worst-case
+// Scheme II split.  Planes: set q, modulus l at element
+// ((q*nm + l)*rows_pad + r)*kpad + h of `res` (set = 0 for real; 0, 1, 2 =
+// re, im, re + im for complex); elements are INT8, or bf16 (BF) for the
+// tcgen05 kernel.  Row exponent: of the maximum (worst-case
 // scaling) or of the 2-norm (Ein).  K-contiguous sources: one warp per
 // (vector, 128 K-elements), lane l takes elements 4l .. 4l+3 and writes one
 // word per plane; strided sources go through a shared-memory tile of 32
 // vectors (16 for complex) x 128 elements as in the Scheme I split.
-template <typename T, int CW>
+template <typename T, int CW, bool BF>
 __global__ void split_II_kcontig(const T* __restrict__ X, int64_t ld, int64_t rows, int64_t k, int64_t rows_pad,
                                  int64_t kpad, int nm, int b, const __grid_constant__ ModTables mt,
                                  const unsigned long long* __restrict__ maxbits, const int32_t* __restrict__ Ein,
@@ -384,11 +401,11 @@ __global__ void split_II_kcontig(const T* __restrict__ X, int64_t ld, int64_t ro
     re[q] = valid ? load_bits(p) : 0ull;
     im[q] = (CW == 2 && valid) ? load_bits(p + 1) : 0ull;
   }
-  residues4<CW>(mt, nm, b - E, re, im, rows_pad * kpad, res + r * kpad + h0);
+  residues4<CW, BF>(mt, nm, b - E, re, im, rows_pad * kpad * (BF ? 2 : 1), res + (r * kpad + h0) * (BF ? 2 : 1));
   if (h0 == 0 && r < rows && E_out) E_out[r] = E;
 }
 
-template <typename T, int CW>
+template <typename T, int CW, bool BF>
 __global__ void __launch_bounds__(256) split_II_kstrided(const T* __restrict__ X, int64_t ld, int64_t rows, int64_t k,
                                                          int64_t rows_pad, int64_t kpad, int nm, int b,
                                                          const __grid_constant__ ModTables mt,
@@ -424,7 +441,7 @@ __global__ void __launch_bounds__(256) split_II_kstrided(const T* __restrict__ X
         im[q] = CW == 2 ? tim[rl][q * 33 + lane] : 0ull;
       }
       const int64_t h0 = hbase + lane * 4;
-      residues4<CW>(mt, nm, b - E, re, im, rows_pad * kpad, res + r * kpad + h0);
+      residues4<CW, BF>(mt, nm, b - E, re, im, rows_pad * kpad * (BF ? 2 : 1), res + (r * kpad + h0) * (BF ? 2 : 1));
       if (h0 == 0 && r < rows && E_out) E_out[r] = E;
     }
   }
@@ -494,24 +511,30 @@ template void launch_split_I<float>(const float*, int64_t, bool, int64_t, int64_
 template <typename T>
 void launch_split_II(const T* X, int64_t ld, bool kcontig, int64_t rows, int64_t k, int nm, int b,
                      int cw, const ModTables& tabs, const unsigned long long* maxbits, int8_t* res,
-                     int32_t* E, cudaStream_t st, const int32_t* Ein) {
+                     int32_t* E, cudaStream_t st, const int32_t* Ein, bool bf16) {
   const int64_t rows_pad = split_rows(rows), kpad = split_cols_II(k);
   if (rows_pad == 0 || kpad == 0) return;
+#define EMU_SPLIT_II(KERNEL, GRID, CW)                                                                        \
+  (bf16 ? KERNEL<T, CW, true><<<GRID, 256, 0, st>>>(X, ld, rows, k, rows_pad, kpad, nm, b, tabs, maxbits, Ein, \
+                                                    res, E)                                                   \
+        : KERNEL<T, CW, false><<<GRID, 256, 0, st>>>(X, ld, rows, k, rows_pad, kpad, nm, b, tabs, maxbits, Ein, \
+                                                     res, E))
   if (kcontig) {
     const int64_t warps = rows_pad * (kpad / 128);
     const unsigned blocks = static_cast<unsigned>((warps + 7) / 8);
     if (cw == 2)
-      split_II_kcontig<T, 2><<<blocks, 256, 0, st>>>(X, ld, rows, k, rows_pad, kpad, nm, b, tabs, maxbits, Ein, res, E);
+      EMU_SPLIT_II(split_II_kcontig, blocks, 2);
     else
-      split_II_kcontig<T, 1><<<blocks, 256, 0, st>>>(X, ld, rows, k, rows_pad, kpad, nm, b, tabs, maxbits, Ein, res, E);
+      EMU_SPLIT_II(split_II_kcontig, blocks, 1);
   } else {
     const int64_t rb = rows_pad / (cw == 2 ? 16 : 32);
     dim3 grid(static_cast<unsigned>(kpad / 128), static_cast<unsigned>(rb < 65535 ? rb : 65535));
     if (cw == 2)
-      split_II_kstrided<T, 2><<<grid, 256, 0, st>>>(X, ld, rows, k, rows_pad, kpad, nm, b, tabs, maxbits, Ein, res, E);
+      EMU_SPLIT_II(split_II_kstrided, grid, 2);
     else
-      split_II_kstrided<T, 1><<<grid, 256, 0, st>>>(X, ld, rows, k, rows_pad, kpad, nm, b, tabs, maxbits, Ein, res, E);
+      EMU_SPLIT_II(split_II_kstrided, grid, 1);
   }
+#undef EMU_SPLIT_II
 }
 
 template <typename T>
@@ -538,9 +561,9 @@ template void launch_norm<float>(const float*, int64_t, bool, int64_t, int64_t, 
 
 template void launch_split_II<double>(const double*, int64_t, bool, int64_t, int64_t, int, int, int,
                                       const ModTables&, const unsigned long long*, int8_t*, int32_t*,
-                                      cudaStream_t, const int32_t*);
+                                      cudaStream_t, const int32_t*, bool);
 template void launch_split_II<float>(const float*, int64_t, bool, int64_t, int64_t, int, int, int,
                                      const ModTables&, const unsigned long long*, int8_t*, int32_t*,
-                                     cudaStream_t, const int32_t*);
+                                     cudaStream_t, const int32_t*, bool);
 
 }  // namespace emu
