@@ -210,6 +210,43 @@ def fp8_engine_leg(emu, h, Ad, Bd, Cd, n, stream, ri, ci, A, B, hi, lo, den, cub
     return out
 
 
+def scheme_II_leg(emu, h, Ad, Bd, Cd, n, stream, ri, ci, hi, lo, den, cublas_tflops):
+    """Scheme II (16 and 20 moduli) on the same inputs with the default engine
+    (bf16 tcgen05): TFLOP/s, GEMM-kernel bf16 TFLOP/s against the measured bf16
+    peak, and sampled error, with the same CUDA-event timing."""
+    import torch
+    out = {}
+    bf16 = measured_peaks().get("bf16_tflops") or 1900.0
+    for nm in (16, 20):
+        def call():
+            emu.check(emu.emu_dgemm(h.h, emu.EMU_ROW_MAJOR, n, n, n, 1.0, Ad.data_ptr(), n, Bd.data_ptr(), n, 0.0,
+                                    Cd.data_ptr(), n, emu.EMU_SCHEME_II, nm, stream.cuda_stream), "emu_dgemm")
+        for _ in range(3):
+            call()
+        torch.cuda.synchronize()
+        h.trace(True)
+        h.trace_read()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(5):
+            call()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+        tr = h.trace_read()
+        h.trace(False)
+        got = Cd[ri][:, ci].cpu().numpy()
+        err = float(np.max(np.abs((got - hi) - lo) / den))
+        gms = tr["ms_gemm"] / max(tr["gemm_launches"], 1)
+        tc = 2.0 * nm * n ** 3 / (gms * 1e-3) / 1e12
+        out["nm%d" % nm] = {"tflops": 2.0 * n ** 3 / (ms * 1e-3) / 1e12, "ms_per_step": ms, "gemm_ms": gms,
+                            "gemm_bf16_tflops": tc, "frac_of_bf16_peak": tc / bf16, "bf16_peak_tflops": bf16,
+                            "err_max_rel_absAB": err,
+                            "speedup_vs_cublas_dgemm": 2.0 * n ** 3 / (ms * 1e-3) / 1e12 / cublas_tflops,
+                            "kernel": "gemm_II_tc_kernel (tcgen05 bf16, 128 x 256 tiles)"}
+    return out
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -379,6 +416,8 @@ def run_ours(args, rank, world, local_rank):
             # tcgen05 kernel) at FP64-level accuracy, timed the same way
             extras["fp8_tcgen05_engine"] = fp8_engine_leg(emu, h, Ad, Bd, Cd, n, stream, ri, ci, A, B, hi, lo, den,
                                                           cublas_tflops)
+            extras["scheme_II_tcgen05_engine"] = scheme_II_leg(emu, h, Ad, Bd, Cd, n, stream, ri, ci, hi, lo, den,
+                                                               cublas_tflops)
         del ref
         # CPU oracle baseline on a bounded sample of rows
         rows = list(range(args.cpu_rows))
@@ -391,6 +430,12 @@ def run_ours(args, rank, world, local_rank):
         gemm_ms = tr["ms_gemm"] / max(tr["gemm_launches"], 1)
         achieved = int8_ops / (gemm_ms * 1e-3) / 1e12
         peak, peak_src = int8_peak, "measured live: cuBLASLt INT8 GEMM 8192^3 on this GPU"
+        ii_tc = args.scheme == "II" and os.environ.get("EMU_II_ENGINE") != "mma"
+        if ii_tc:
+            bf16 = measured_peaks().get("bf16_tflops")
+            peak = bf16 if bf16 else 1900.0
+            peak_src = ("measured dense bf16 peak (MEASURED_PEAKS.json)" if bf16 else
+                        "fallback dense bf16 peak 1.9 PFLOP/s")
         if args.scheme == "I_F8":
             bf16 = measured_peaks().get("bf16_tflops")
             peak = 2.0 * bf16 if bf16 else 2.0 * 1900.0
@@ -398,20 +443,23 @@ def run_ours(args, rank, world, local_rank):
                         % ("(MEASURED_PEAKS.json)" if bf16 else "(fallback 1.9 PFLOP/s)"))
         traffic = (load_traffic("gemm_I", "p%d_n%d" % (p, n)) if args.scheme == "I" else
                    load_traffic("gemm_f8tc", "p%d_n%d" % (p, n)) if args.scheme == "I_F8" else None)
-        kname = ("gemm_II_kernel" if args.scheme == "II" else
+        kname = ("gemm_II_tc_kernel (tcgen05 bf16)" if ii_tc else "gemm_II_kernel (mma.sync INT8)" if args.scheme == "II" else
                  "gemm_f8tc_kernel<%d, OUT_F64> (tcgen05)" % p if args.scheme == "I_F8" else
                  "gemm_I_kernel<%d, OUT_F64> (mma.sync INT8)" % p)
-        ops_desc = ("INT8 ops 2 N_m M N K" if args.scheme == "II" else
+        ops_desc = ("bf16 tensor ops 2 N_m M N K (residue products)" if ii_tc else
+                    "INT8 ops 2 N_m M N K" if args.scheme == "II" else
                     "exact E4M3 products p(p+1) M N K (multiply+add = 2)" if args.scheme == "I_F8" else
                     "INT8 ops p(p+1) M N K (multiply+add = 2)")
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
-                "dtype": "e4m3->fp32 (f64 in/out)" if args.scheme == "I_F8" else "int8->int32 (f64 in/out)",
+                "dtype": ("e4m3->fp32 (f64 in/out)" if args.scheme == "I_F8" else
+                          "bf16->fp32 (f64 in/out)" if ii_tc else "int8->int32 (f64 in/out)"),
                 "data": "synthetic",
                 "config": config(args, world),
-                "int8_tops": int8_ops * args.steps * world / (ms * 1e-3) / 1e12,
-                "int8_frac_of_peak": (int8_ops * args.steps / (ms * 1e-3) / 1e12 / int8_peak) if int8_peak else None,
+                "int8_tops": (int8_ops * args.steps * world / (ms * 1e-3) / 1e12) if not ii_tc else None,
+                "int8_frac_of_peak": ((int8_ops * args.steps / (ms * 1e-3) / 1e12 / int8_peak)
+                                      if int8_peak and args.scheme != "I_F8" and not ii_tc else None),
                 "roofline": {"bound": "tensor",
                              "kernel": kname,
                              "achieved": achieved,

@@ -180,6 +180,9 @@ void host_crt_tables(int nm, CrtTables* t) {
     int64_t q = inv_mod(pm, mods[l]);
     limbs_mul_small(Pl, static_cast<uint32_t>(q));
     for (int i = 0; i < kCrtLimbs && i < static_cast<int>(Pl.size()); ++i) t->w[l][i] = Pl[i];
+    double wd = 0.0;
+    for (int i = kCrtLimbs - 1; i >= 0; --i) wd = wd * 4294967296.0 + t->w[l][i];
+    t->wP[l] = static_cast<float>(wd / pd);
   }
 }
 

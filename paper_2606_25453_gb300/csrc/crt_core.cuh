@@ -112,4 +112,97 @@ __device__ __forceinline__ double crt_finish(const uint32_t* S, const CrtTables&
   return limbs_to_double_rn(R);
 }
 
+// ---------------------------------------------------------------- lazy form
+// S = sum_l w_l r_l kept as one 64-bit sum per 32-bit limb of w (each below
+// nm * 255 * 2^32 < 2^45, so no carries until the end), next to the binary32
+// estimate t = sum_l r_l (w_l / P) of S / P.
+struct CrtLazy {
+  uint64_t s[kCrtLimbs];
+  float t;
+};
+
+__device__ __forceinline__ void crt_lazy_init(CrtLazy& a) {
+#pragma unroll
+  for (int i = 0; i < kCrtLimbs; ++i) a.s[i] = 0;
+  a.t = 0.0f;
+}
+
+// a += w_l r_l, r in [0, m_l).
+__device__ __forceinline__ void crt_lazy_acc(CrtLazy& a, const CrtTables& ct, int l, uint32_t r) {
+#pragma unroll
+  for (int i = 0; i < kCrtLimbs; ++i) a.s[i] += static_cast<uint64_t>(ct.w[l][i]) * r;
+  a.t = __fmaf_rn(static_cast<float>(r), ct.wP[l], a.t);
+}
+
+// Eq. (8) finish from the lazy form: x = S - kP with k = rint(t), which is
+// round(S / P) or one off (t errs by less than 0.02 for up to 20 moduli), then
+// one exact correction each way into the symmetric range (-P/2, P/2] (the
+// lift of S mod P: above floor(P/2) it becomes negative), rounded once to
+// binary64.  All limb arithmetic is exact; only the choice of k is estimated.
+__device__ __forceinline__ double crt_finish_lazy(const CrtLazy& a, const CrtTables& ct) {
+  // S in 32-bit limbs (kSL of them)
+  uint32_t S[kSL];
+  uint64_t c = 0;
+#pragma unroll
+  for (int i = 0; i < kCrtLimbs; ++i) {
+    c += a.s[i];
+    S[i] = static_cast<uint32_t>(c);
+    c >>= 32;
+  }
+  S[kCrtLimbs] = static_cast<uint32_t>(c);
+  const uint32_t k = static_cast<uint32_t>(__float2int_rn(a.t));
+  // R = S - k P (two's complement in kSL limbs)
+  uint32_t R[kSL];
+  {
+    uint64_t mul = 0;
+    int64_t br = 0;
+#pragma unroll
+    for (int i = 0; i < kSL; ++i) {
+      mul += static_cast<uint64_t>(i < kCrtLimbs ? ct.P[i] : 0u) * k;
+      const int64_t d = static_cast<int64_t>(S[i]) - static_cast<int64_t>(static_cast<uint32_t>(mul)) - br;
+      mul >>= 32;
+      br = d < 0;
+      R[i] = static_cast<uint32_t>(d + (br ? (1ll << 32) : 0));
+    }
+  }
+  bool neg = static_cast<int32_t>(R[kSL - 1]) < 0;
+  uint32_t mag[kSL];
+  {  // |R|
+    uint64_t cc = neg ? 1u : 0u;
+#pragma unroll
+    for (int i = 0; i < kSL; ++i) {
+      cc += static_cast<uint64_t>(neg ? ~R[i] : R[i]);
+      mag[i] = static_cast<uint32_t>(cc);
+      cc >>= 32;
+    }
+  }
+  // compare |R| with floor(P/2) = P/2 (P is even: 256 is always a modulus)
+  int cmp = mag[kSL - 1] != 0 ? 1 : 0;
+#pragma unroll
+  for (int i = kCrtLimbs - 1; i >= 0; --i)
+    if (cmp == 0 && mag[i] != ct.Phalf[i]) cmp = mag[i] > ct.Phalf[i] ? 1 : -1;
+  // R > P/2: R - P (negative, magnitude P - R); R <= -P/2: R + P (magnitude P - |R|)
+  if ((!neg && cmp > 0) || (neg && cmp >= 0)) {
+    int64_t br = 0;
+#pragma unroll
+    for (int i = 0; i < kSL; ++i) {
+      const int64_t d = static_cast<int64_t>(i < kCrtLimbs ? ct.P[i] : 0u) - mag[i] - br;
+      br = d < 0;
+      mag[i] = static_cast<uint32_t>(d + (br ? (1ll << 32) : 0));
+    }
+    neg = !neg;
+  }
+  const double v = limbs_to_double_rn(mag);  // |x| <= P/2 < 2^159: five limbs
+  return neg ? -v : v;
+}
+
+// x 2^e for a nonzero finite x whose result stays normal: exponent-field
+// arithmetic (exact, as is ldexp); other cases go to ldexp.
+__device__ __forceinline__ double scale2_fast(double x, int e) {
+  const uint64_t b = dbits(x);
+  const int ex = static_cast<int>((b >> 52) & 0x7FF);
+  if (ex == 0 || ex == 0x7FF || ex + e <= 0 || ex + e >= 0x7FF) return ldexp(x, e);
+  return bitsd(b + (static_cast<uint64_t>(static_cast<int64_t>(e)) << 52));
+}
+
 }  // namespace emu

@@ -37,6 +37,7 @@ struct CrtTables {
   uint32_t P[kCrtLimbs];
   uint32_t Phalf[kCrtLimbs];          // floor(P/2)
   double invP;                        // 1/P rounded (quotient estimate only)
+  float wP[kMaxModuli];               // w_l / P rounded to binary32 (quotient estimate only)
   int nm;
 };
 

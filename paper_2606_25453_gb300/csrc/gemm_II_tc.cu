@@ -376,66 +376,82 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll 1
         for (int c0 = 0; c0 < ncols; c0 += 4) {
           const uint8_t* const p = sbase + c0;
-          uint32_t w[CPLX ? 1 : kMaxModuli];  // real: the residue bytes of columns c0 .. c0+3, per modulus
+          // CRT sums of columns c0 .. c0+3 (real) or of two of them at a time (complex)
           if constexpr (!CPLX) {
+            CrtLazy acc[4];
 #pragma unroll
-            for (int l = 0; l < kMaxModuli; ++l)
-              if (l < nm) w[l] = *reinterpret_cast<const uint32_t*>(p + static_cast<int64_t>(l) * kTileBytes);
-          }
+            for (int c = 0; c < 4; ++c) crt_lazy_init(acc[c]);
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            if (c0 + c >= ncols) break;
-            uint32_t S[kSL], Si[CPLX ? kSL : 1];
+            for (int l = 0; l < kMaxModuli; ++l) {
+              if (l >= nm) break;
+              const uint32_t w = *reinterpret_cast<const uint32_t*>(p + static_cast<int64_t>(l) * kTileBytes);
 #pragma unroll
-            for (int i = 0; i < kSL; ++i) {
-              S[i] = 0;
-              if (CPLX) Si[i] = 0;
+              for (int c = 0; c < 4; ++c) crt_lazy_acc(acc[c], ct, l, (w >> (8 * c)) & 0xFFu);
             }
-            if constexpr (!CPLX) {
 #pragma unroll
-              for (int l = 0; l < kMaxModuli; ++l)
-                if (l < nm) crt_acc(S, ct.w[l], (w[l] >> (8 * c)) & 0xFFu);
-            } else {
+            for (int c = 0; c < 4; ++c) {
+              if (c0 + c >= ncols) break;
+              const int cidx = tn * kBN + c0 + c;
+              const double xr = scale2_fast(crt_finish_lazy(acc[c], ct), erow + kp.FB[cidx]);
+              if (MODE == II_F64) {
+                double* cp = static_cast<double*>(kp.C) + static_cast<int64_t>(row) * kp.ldc + cidx;
+                *cp = blas_update(kp.alpha_re, xr, kp.beta_re, kp.beta_re != 0.0 ? *cp : 0.0);
+              } else {
+                float* cp = static_cast<float*>(kp.C) + static_cast<int64_t>(row) * kp.ldc + cidx;
+                *cp = static_cast<float>(
+                    blas_update(kp.alpha_re, xr, kp.beta_re, kp.beta_re != 0.0 ? static_cast<double>(*cp) : 0.0));
+              }
+            }
+          } else {
+#pragma unroll
+            for (int c2 = 0; c2 < 4; c2 += 2) {
+              CrtLazy are[2], aim[2];
+#pragma unroll
+              for (int c = 0; c < 2; ++c) {
+                crt_lazy_init(are[c]);
+                crt_lazy_init(aim[c]);
+              }
 #pragma unroll 1
               for (int l = 0; l < nm; ++l) {
                 // Eq. (16): Re = T1 - T2, Im = T3 - T1 - T2 (mod m)
                 const int m = static_cast<int>(mt.mods[l]);
-                const uint8_t* q = p + static_cast<int64_t>(l) * kTileBytes + c;
-                const int t1 = q[0], t2 = q[static_cast<int64_t>(nm) * kTileBytes],
-                          t3 = q[static_cast<int64_t>(2 * nm) * kTileBytes];
-                int re = t1 - t2;
-                if (re < 0) re += m;
-                int im = t3 - t1 - t2;
-                if (im < 0) im += m;
-                if (im < 0) im += m;
-                crt_acc(S, ct.w[l], static_cast<uint32_t>(re));
-                crt_acc(Si, ct.w[l], static_cast<uint32_t>(im));
+                const uint8_t* q = p + static_cast<int64_t>(l) * kTileBytes;
+                const uint32_t w1 = *reinterpret_cast<const uint32_t*>(q);
+                const uint32_t w2 = *reinterpret_cast<const uint32_t*>(q + static_cast<int64_t>(nm) * kTileBytes);
+                const uint32_t w3 = *reinterpret_cast<const uint32_t*>(q + static_cast<int64_t>(2 * nm) * kTileBytes);
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                  const int sh = 8 * (c2 + c);
+                  const int t1 = (w1 >> sh) & 0xFF, t2 = (w2 >> sh) & 0xFF, t3 = (w3 >> sh) & 0xFF;
+                  int re = t1 - t2;
+                  if (re < 0) re += m;
+                  int im = t3 - t1 - t2;
+                  if (im < 0) im += m;
+                  if (im < 0) im += m;
+                  crt_lazy_acc(are[c], ct, l, static_cast<uint32_t>(re));
+                  crt_lazy_acc(aim[c], ct, l, static_cast<uint32_t>(im));
+                }
               }
-            }
-            const int cidx = tn * kBN + c0 + c;
-            const int sc = erow + kp.FB[cidx];
-            const double xr = scale2(crt_finish(S, ct), sc);
-            if constexpr (CPLX) {
-              // complex update in binary64; complex64 output rounds each part once more
-              using TO = typename std::conditional<MODE == II_C3M, float, double>::type;
-              const double xi = scale2(crt_finish(Si, ct), sc);
-              TO* cp = static_cast<TO*>(kp.C) + 2 * (static_cast<int64_t>(row) * kp.ldc + cidx);
-              double tr = __fma_rn(kp.alpha_re, xr, -__dmul_rn(kp.alpha_im, xi));
-              double ti = __fma_rn(kp.alpha_re, xi, __dmul_rn(kp.alpha_im, xr));
-              if (kp.beta_re != 0.0 || kp.beta_im != 0.0) {
-                const double cr = static_cast<double>(cp[0]), ci = static_cast<double>(cp[1]);
-                tr = __dadd_rn(tr, __fma_rn(kp.beta_re, cr, -__dmul_rn(kp.beta_im, ci)));
-                ti = __dadd_rn(ti, __fma_rn(kp.beta_re, ci, __dmul_rn(kp.beta_im, cr)));
+#pragma unroll
+              for (int c = 0; c < 2; ++c) {
+                if (c0 + c2 + c >= ncols) break;
+                const int cidx = tn * kBN + c0 + c2 + c;
+                const int sc = erow + kp.FB[cidx];
+                const double xr = scale2_fast(crt_finish_lazy(are[c], ct), sc);
+                const double xi = scale2_fast(crt_finish_lazy(aim[c], ct), sc);
+                // complex update in binary64; complex64 output rounds each part once more
+                using TO = typename std::conditional<MODE == II_C3M, float, double>::type;
+                TO* cp = static_cast<TO*>(kp.C) + 2 * (static_cast<int64_t>(row) * kp.ldc + cidx);
+                double tr = __fma_rn(kp.alpha_re, xr, -__dmul_rn(kp.alpha_im, xi));
+                double ti = __fma_rn(kp.alpha_re, xi, __dmul_rn(kp.alpha_im, xr));
+                if (kp.beta_re != 0.0 || kp.beta_im != 0.0) {
+                  const double cr = static_cast<double>(cp[0]), ci = static_cast<double>(cp[1]);
+                  tr = __dadd_rn(tr, __fma_rn(kp.beta_re, cr, -__dmul_rn(kp.beta_im, ci)));
+                  ti = __dadd_rn(ti, __fma_rn(kp.beta_re, ci, __dmul_rn(kp.beta_im, cr)));
+                }
+                cp[0] = static_cast<TO>(tr);
+                cp[1] = static_cast<TO>(ti);
               }
-              cp[0] = static_cast<TO>(tr);
-              cp[1] = static_cast<TO>(ti);
-            } else if (MODE == II_F64) {
-              double* cp = static_cast<double*>(kp.C) + static_cast<int64_t>(row) * kp.ldc + cidx;
-              *cp = blas_update(kp.alpha_re, xr, kp.beta_re, kp.beta_re != 0.0 ? *cp : 0.0);
-            } else {
-              float* cp = static_cast<float*>(kp.C) + static_cast<int64_t>(row) * kp.ldc + cidx;
-              *cp = static_cast<float>(
-                  blas_update(kp.alpha_re, xr, kp.beta_re, kp.beta_re != 0.0 ? static_cast<double>(*cp) : 0.0));
             }
           }
         }
