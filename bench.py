@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--cpu-rows", type=int, default=96, help="rows of C in the CPU oracle sample")
     ap.add_argument("--no-extras", action="store_true", help="skip cuBLAS / accuracy / CPU legs")
     ap.add_argument("--suite", default=None, help="write the secondary measurements (all paths) to this JSONL file")
+    ap.add_argument("--suite-part", default="all", choices=["all", "ii"],
+                    help="ii: only the Scheme II points (run in a child with EMU_II_ENGINE=mma by the full suite)")
     return ap.parse_args()
 
 
@@ -538,6 +540,27 @@ def run_suite(path, args):
             cache[key] = (A, B, torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev))
         return cache[key]
 
+    def scheme_II_points():
+        """Scheme II DGEMM at n = 8192 with the engine of this process (the
+        default bf16 tcgen05 one, or INT8 mma.sync under EMU_II_ENGINE=mma)."""
+        engine = "int8 mma.sync" if os.environ.get("EMU_II_ENGINE") == "mma" else "bf16 tcgen05"
+        for phi in (0.5, 4.0):
+            if args.suite_part == "ii" and phi != 0.5:
+                continue
+            A, B, Ad, Bd = pair(8192, phi)
+            Cd = torch.empty((8192, 8192), dtype=torch.float64, device=dev)
+            for nm in ((12, 16, 20) if args.suite_part == "ii" else (8, 10, 12, 14, 16, 18, 20)):
+                ms = timed(lambda: emu.dgemm(Ad, Bd, Cd, scheme="II", p=nm, handle=h))
+                emit({"path": "emu_dgemm_II", "n": 8192, "phi": phi, "nm": nm, "tflops": 2 * 8192 ** 3 / ms / 1e9,
+                      "engine": engine, "tensor_tops": 2 * nm * 8192 ** 3 / ms / 1e9, "ms": ms,
+                      "err": sampled_err(A, B, Cd.cpu().numpy())})
+
+    if args.suite_part == "ii":
+        scheme_II_points()
+        out.close()
+        h.close()
+        return
+
     # cuBLAS references on this GPU
     for n in (4096, 8192):
         A, B, Ad, Bd = pair(n, 0.5)
@@ -606,14 +629,18 @@ def run_suite(path, args):
         emit({"path": "emu_sgemm_I", "n": 8192, "phi": 0.5, "p": p, "tflops": 2 * 8192 ** 3 / ms / 1e9,
               "int8_tops": p * (p + 1) * 8192 ** 3 / ms / 1e9, "ms": ms,
               "err": sampled_err(A.astype(np.float64), B.astype(np.float64), Cd.cpu().numpy().astype(np.float64))})
-    # Scheme II DGEMM
-    for phi in (0.5, 4.0):
-        A, B, Ad, Bd = pair(8192, phi)
-        Cd = torch.empty((8192, 8192), dtype=torch.float64, device=dev)
-        for nm in (8, 10, 12, 14, 16, 18, 20):
-            ms = timed(lambda: emu.dgemm(Ad, Bd, Cd, scheme="II", p=nm, handle=h))
-            emit({"path": "emu_dgemm_II", "n": 8192, "phi": phi, "nm": nm, "tflops": 2 * 8192 ** 3 / ms / 1e9,
-                  "int8_tops": 2 * nm * 8192 ** 3 / ms / 1e9, "ms": ms, "err": sampled_err(A, B, Cd.cpu().numpy())})
+    scheme_II_points()
+    engine = "int8 mma.sync" if os.environ.get("EMU_II_ENGINE") == "mma" else "bf16 tcgen05"
+    import tempfile
+    with tempfile.NamedTemporaryFile(suffix=".jsonl", delete=False) as tf:
+        child_path = tf.name
+    subprocess.run([sys.executable, os.path.abspath(__file__), "--suite", child_path, "--suite-part", "ii"],
+                   env=dict(os.environ, EMU_II_ENGINE="mma"), check=True, stdout=subprocess.DEVNULL)
+    for line in open(child_path):
+        d = json.loads(line)
+        d["path"] = "emu_dgemm_II_int8"
+        emit(d)
+    os.unlink(child_path)
     # Scheme II with norm-based scaling: bits and speed at the same N_m
     for phi in (0.5, 4.0):
         A, B, Ad, Bd = pair(8192, phi)
@@ -621,7 +648,8 @@ def run_suite(path, args):
         for nm in (8, 10, 12, 14, 16):
             ms = timed(lambda: emu.dgemm(Ad, Bd, Cd, scheme="II_NORM", p=nm, handle=h))
             emit({"path": "emu_dgemm_II_norm", "n": 8192, "phi": phi, "nm": nm, "tflops": 2 * 8192 ** 3 / ms / 1e9,
-                  "int8_tops": 2 * nm * 8192 ** 3 / ms / 1e9, "ms": ms, "err": sampled_err(A, B, Cd.cpu().numpy())})
+                  "engine": engine, "tensor_tops": 2 * nm * 8192 ** 3 / ms / 1e9, "ms": ms,
+                  "err": sampled_err(A, B, Cd.cpu().numpy())})
     cache.clear()
     # ZGEMM 3M vs cuBLAS ZGEMM
     n = 8192
@@ -634,7 +662,7 @@ def run_suite(path, args):
     for nm in (12, 16, 20):
         ms = timed(lambda: emu.zgemm(Ad, Bd, Cd, nm=nm, handle=h), reps=1)
         emit({"path": "emu_zgemm_3m", "n": n, "phi": 1.0, "nm": nm, "tflops_8mnk": 8 * n ** 3 / ms / 1e9,
-              "tflops_2mnk": 2 * n ** 3 / ms / 1e9, "int8_tops": 6 * nm * n ** 3 / ms / 1e9, "ms": ms,
+              "tflops_2mnk": 2 * n ** 3 / ms / 1e9, "tensor_tops": 6 * nm * n ** 3 / ms / 1e9, "engine": engine, "ms": ms,
               "err": sampled_err(A, B, Cd.cpu().numpy(), True)})
     # ZGEMM 4M (Scheme I)
     for sc, p in (("I", 8), ("I_F8", 11), ("I_F8", 12)):
