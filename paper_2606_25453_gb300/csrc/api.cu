@@ -478,8 +478,9 @@ Plan plan_II(int64_t m, int64_t n, int64_t k, int nm, int nsets, int es) {
   pl.off_accB = off; off += al256(16 * static_cast<size_t>(n > 0 ? n : 1));
   pl.off_nEA = off; off += al256(4 * static_cast<size_t>(m > 0 ? m : 1));
   pl.off_nEB = off; off += al256(4 * static_cast<size_t>(n > 0 ? n : 1));
-  // tcgen05 kernel: per-CTA residue slots
-  pl.off_scratch = off; off += es == 2 ? al256(gemm_II_tc_scratch_bytes(nm, nsets == 3)) : 0;
+  // tcgen05 kernel: the residue planes (one byte per output and modulus; with
+  // clusters of up to 4 row tiles)
+  pl.off_scratch = off; off += es == 2 ? al256(gemm_II_tc_residue_bytes(m, n, nm, nsets == 3, 4)) : 0;
   pl.bytes = off;
   return pl;
 }

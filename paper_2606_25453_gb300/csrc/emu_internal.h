@@ -112,20 +112,19 @@ struct GemmIIArgs {
   int* status;
   int num_sms;
   int cluster;       // tcgen05 kernel: CTAs per cluster sharing the B chunks (1, 2, 4)
-  uint8_t* scratch;  // tcgen05 kernel: per-CTA residue slots
+  uint8_t* scratch;  // tcgen05 kernel: the residue planes
 };
 cudaError_t launch_gemm_II(int out_mode, const GemmIIArgs& a, const ModTables& mt,
                            const CrtTables& ct, cudaStream_t st);
-// Scheme II on bf16 residue planes with tcgen05 / TMEM (128 x 256 tiles);
-// modes II_F64, II_F32, II_Z3M, II_C3M.  GemmIIArgs::scratch: at least
-// gemm_II_tc_scratch_bytes(nm, complex) bytes of device memory for the
-// per-CTA residue slots (at most kGemmIITcMaxCtas CTAs).
-constexpr int kGemmIITcMaxCtas = 160;
+// Scheme II on bf16 residue planes with tcgen05 / TMEM (128 x 256 tiles,
+// modulus-major), then the CRT kernel; modes II_F64, II_F32, II_Z3M,
+// II_C3M.  GemmIIArgs::scratch: gemm_II_tc_residue_bytes(M, N, nm, complex,
+// cluster) bytes of device memory for the residue planes.
 cudaError_t launch_gemm_II_tc(int out_mode, const GemmIIArgs& a, const ModTables& mt,
                               const CrtTables& ct, cudaStream_t st);
 int gemm_II_tc_tile_m();
 int gemm_II_tc_tile_n();
-size_t gemm_II_tc_scratch_bytes(int nm, bool is_complex);
+size_t gemm_II_tc_residue_bytes(int64_t M, int64_t N, int nm, bool is_complex, int cluster);
 int gemm_II_tc_cluster();
 
 // Tensor map for a row-major byte matrix [rows][cols] read in boxes of

@@ -1,5 +1,5 @@
-// gemm_II_tc.cu -- fused Scheme II on the bf16 tensor cores (tcgen05.mma
-// kind::f16), accumulators in tensor memory, CRT in the same kernel.
+// gemm_II_tc.cu -- Scheme II on the bf16 tensor cores (tcgen05.mma
+// kind::f16) with accumulators in tensor memory, and the CRT.
 //
 // On sm_103a the 8-bit integer MMA exists only as the warp-level mma.sync.
 // The symmetric residues of Eq. (5) (|r| <= 128) are exact bf16 values, the
@@ -9,27 +9,29 @@
 // 5th-generation tensor cores in K segments of 960, and the result is
 // bit-identical to the INT8 kernel's.
 //
-// Tile: 128 rows x 256 columns, one 128 x 256 x 16 MMA per K-step (narrow
-// MMAs leave the tensor pipe idle while the MMA thread waits for data).  The
-// two FP32 accumulators take all 512 TMEM columns and alternate between K
-// segments, so the MMAs of one segment overlap the reduction of the last.
-// Roles (448 threads):
-//   warps 0-7   drain: each finished segment is added to a running residue
-//               modulo m_l (Eq. 7), four residues per register; after the
-//               last segment of a modulus the residues (bytes in [0, m)) go
-//               to this CTA's scratch slot in global memory (128 x 256
-//               bytes per modulus, rewritten every second tile, so it mostly
-//               stays in L2).  Warp w: TMEM lanes = tile rows 32 (w % 4) ..,
-//               columns 128 (w / 4) .. +127.
-//   warp 8      TMA producer (lane 0).
-//   warp 9      TMEM allocation, MMA issue (lane 0).
-//   warps 10-13 CRT of the previous tile from the scratch slot (Eq. 8, 3M
-//               combination of Eq. 16 for complex), S mod P, symmetric lift,
-//               one rounding to binary64, scaling and the BLAS update; they
-//               run while the tensor cores work on the next tile.
-// CTAs may run in clusters of cl (1, 2, 4) along M that share the B chunks
-// by TMA multicast.  All waits are bounded; a timeout sets the status word,
-// raises an abort flag for the other roles, and the TMEM is still released.
+// The work is modulus-major, as in the paper's Scheme II kernel (Sec. IV):
+// a persistent kernel walks (modulus, tile) items in that order, so that all
+// CTAs work on the same pair of residue planes at the same time and the
+// operand tiles are reused from L2 as in one plain GEMM (walking all moduli
+// of one tile before the next keeps 16 x more operand data live and reads
+// the planes from DRAM about 20 times).  Each item's product stays in TMEM;
+// the epilogue reduces it modulo m_l (Eq. 7) and writes only the residue
+// bytes (one per output and modulus).  A second kernel then forms the CRT
+// sum of Eq. (8) from the residues, reduces it modulo P, lifts it to the
+// symmetric range, rounds it once to binary64, scales it back and applies
+// the BLAS update (3M combination of Eq. (16) for complex input).
+//
+// GEMM tile: 128 rows x 256 columns, one 128 x 256 x 16 MMA per K-step
+// (narrow MMAs leave the tensor pipe idle while the MMA thread waits for
+// data).  The two FP32 accumulators take all 512 TMEM columns and alternate
+// between K segments, so the MMAs of one segment overlap the reduction of
+// the last.  Roles (320 threads): warps 0-7 drain (warp w: TMEM lanes = tile
+// rows 32 (w % 4) .., columns 128 (w / 4) .. +127; each finished segment is
+// added to a running residue, four per register), warp 8 lane 0 TMA, warp 9
+// TMEM allocation and (lane 0) MMAs.  CTAs may run in clusters of cl (1, 2,
+// 4) along M that share the B chunks by TMA multicast.  All waits are
+// bounded; a timeout sets the status word, raises an abort flag for the
+// other roles, and the TMEM is still released.
 #include <cstdlib>
 #include <type_traits>
 
@@ -41,9 +43,9 @@ namespace emu {
 namespace {
 
 constexpr int kBM = 128, kBN = 256;
-constexpr int kThreads = 448;
-constexpr int kDrainThreads = 256, kCrtThreads = 128;
-constexpr int kProducerWarp = 8, kMmaWarp = 9, kCrtWarp0 = 10;
+constexpr int kThreads = 320;
+constexpr int kDrainThreads = 256;
+constexpr int kProducerWarp = 8, kMmaWarp = 9;
 constexpr uint32_t kTmemCols = 512;
 constexpr int kSegStages = 15;  // 64-wide K chunks per exact FP32 segment (960 * 2^14 < 2^24)
 static_assert(kSegStages * 64 * 16384 < (1 << 24), "segment sums must stay exact in FP32");
@@ -52,30 +54,19 @@ constexpr int kBlkB = kBN * 128;
 constexpr int kStageBytes = kBlkA + kBlkB;
 constexpr int kStages = 4;
 constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
-constexpr int kTileBytes = kBM * kBN;  // one modulus's residues of a tile
 static_assert(kSmem <= 232448, "shared memory");
-
-template <int MODE>
-struct CfgIITC {
-  static constexpr bool CPLX = MODE == II_Z3M || MODE == II_C3M;
-  static constexpr int NSET = CPLX ? 3 : 1;
-};
 
 struct KParamsIITC {
   CUtensorMap tA;  // bf16 planes as bytes: 128-byte x 128-row boxes, 128-byte swizzle
   CUtensorMap tB;  // 128-byte x (256 / cl)-row boxes
-  int M, N, nst, tiles_m, tiles_n;  // nst: 64-wide K chunks per plane
+  int nst, tiles_m, tiles_n;  // nst: 64-wide K chunks per plane
   int cl;          // CTAs per cluster (1, 2 or 4): neighbours along M sharing the B chunks
   int tiles_mg;    // row-tile groups of cl tiles
+  int nplanes;     // NSET * nm residue planes (plane p = set * nm + l)
   int nm;
   int rowsA_pad, rowsB_pad;
-  const int32_t* EA;
-  const int32_t* FB;
-  int escale;
-  double alpha_re, alpha_im, beta_re, beta_im;
-  void* C;
-  int64_t ldc;
-  uint8_t* scratch;  // per CTA: two slots of NSET * nm * 128 * 256 bytes
+  uint8_t* R;      // residues: plane p, row r, column c at R[(p * tiles_m * 128 + r) * ldr + c]
+  int64_t ldr;     // tiles_n * 256
   int* status;
 };
 
@@ -128,6 +119,15 @@ __device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, 
   tn = in / gsz;
 }
 
+// Work item i of a cluster: plane p = i / (tiles per plane), then the tile.
+__device__ __forceinline__ void item_coords(const KParamsIITC& kp, int item, int crank, int& p, int& tm, int& tn) {
+  const int per_plane = kp.tiles_mg * kp.tiles_n;
+  p = item / per_plane;
+  int tg;
+  tile_coords(item - p * per_plane, kp.tiles_mg, kp.tiles_n, tg, tn);
+  tm = tg * kp.cl + crank;
+}
+
 // A warp-uniform bounded wait: every lane waits, and the warp goes on only
 // if all of them saw the phase complete.
 __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status) {
@@ -136,13 +136,8 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volati
 
 __device__ __forceinline__ int sbyte(uint32_t w, int i) { return static_cast<int>(static_cast<int8_t>(w >> (8 * i))); }
 
-template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
-    gemm_II_tc_kernel(const __grid_constant__ KParamsIITC kp, const __grid_constant__ CrtTables ct,
-                      const __grid_constant__ ModTables mt) {
-  using Cfg = CfgIITC<MODE>;
-  constexpr bool CPLX = Cfg::CPLX;
-  constexpr int NSET = Cfg::NSET;
+    gemm_II_tc_kernel(const __grid_constant__ KParamsIITC kp, const __grid_constant__ ModTables mt) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -151,9 +146,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* empty = full + kStages;
   uint64_t* acc_full = empty + kStages;  // two accumulators
   uint64_t* acc_empty = acc_full + 2;
-  uint64_t* res_full = acc_empty + 2;    // two scratch slots
-  uint64_t* res_empty = res_full + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(res_empty + 2);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -170,8 +163,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
       mbar_init(&acc_empty[b], kDrainThreads);
-      mbar_init(&res_full[b], kDrainThreads);
-      mbar_init(&res_empty[b], kCrtThreads);
     }
     *abort_flag = 0;
     fence_mbar_init();
@@ -191,14 +182,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  // the cluster walks tiles of (cl x 128) rows x 256 columns; CTA `crank`
-  // owns the crank-th 128-row tile of each
-  const int ntiles = kp.tiles_mg * kp.tiles_n;
-  const int my_tiles = cid < ntiles ? (ntiles - 1 - cid) / ncl + 1 : 0;
-  const int nm = kp.nm;
+  // the cluster walks items (plane, tile of (cl x 128) rows x 256 columns);
+  // CTA `crank` owns the crank-th 128-row tile of each
+  const int nitems = kp.nplanes * kp.tiles_mg * kp.tiles_n;
+  const int my_items = cid < nitems ? (nitems - 1 - cid) / ncl + 1 : 0;
   const int nseg = (kp.nst + kSegStages - 1) / kSegStages;
-  uint8_t* const my_scratch =
-      kp.scratch + static_cast<int64_t>(blockIdx.x) * 2 * NSET * nm * static_cast<int64_t>(kTileBytes);
 
   if (warp == kProducerWarp) {
     // ---------------------------------------------------------------- producer
@@ -208,31 +196,27 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int piece_rows = kBN / cl;
       uint32_t j = 0;
       bool stop = false;
-      for (int t = 0; t < my_tiles && !stop; ++t) {
-        int tg, tn;
-        tile_coords(cid + t * ncl, kp.tiles_mg, kp.tiles_n, tg, tn);
-        const int tm = tg * cl + crank;
-        for (int l = 0; l < nm && !stop; ++l)
-          for (int set = 0; set < NSET && !stop; ++set) {
-            const int ya = (set * nm + l) * kp.rowsA_pad + tm * kBM;
-            const int yb = (set * nm + l) * kp.rowsB_pad + tn * kBN;
-            for (int ks = 0; ks < kp.nst; ++ks, ++j) {
-              const uint32_t stage = j % kStages;
-              if (j >= static_cast<uint32_t>(kStages) &&
-                  !wait_or_abort(&empty[stage], ((j / kStages) & 1u) ^ 1u, abort_flag, kp.status)) {
-                stop = true;
-                break;
-              }
-              mbar_arrive_expect_tx(&full[stage], kStageBytes);
-              uint8_t* sA = smem + stage * kStageBytes;
-              tma_load_2d(sA, &kp.tA, &full[stage], ks * 128, ya);
-              if (cl > 1)  // this CTA's rows of the B chunk, to every CTA of the cluster
-                tma_load_2d_mc(sA + kBlkA + crank * piece_rows * 128, &kp.tB, &full[stage], ks * 128,
-                               yb + crank * piece_rows, cl_mask);
-              else
-                tma_load_2d(sA + kBlkA, &kp.tB, &full[stage], ks * 128, yb);
-            }
+      for (int t = 0; t < my_items && !stop; ++t) {
+        int p, tm, tn;
+        item_coords(kp, cid + t * ncl, crank, p, tm, tn);
+        const int ya = p * kp.rowsA_pad + tm * kBM;
+        const int yb = p * kp.rowsB_pad + tn * kBN;
+        for (int ks = 0; ks < kp.nst; ++ks, ++j) {
+          const uint32_t stage = j % kStages;
+          if (j >= static_cast<uint32_t>(kStages) &&
+              !wait_or_abort(&empty[stage], ((j / kStages) & 1u) ^ 1u, abort_flag, kp.status)) {
+            stop = true;
+            break;
           }
+          mbar_arrive_expect_tx(&full[stage], kStageBytes);
+          uint8_t* sA = smem + stage * kStageBytes;
+          tma_load_2d(sA, &kp.tA, &full[stage], ks * 128, ya);
+          if (cl > 1)  // this CTA's rows of the B chunk, to every CTA of the cluster
+            tma_load_2d_mc(sA + kBlkA + crank * piece_rows * 128, &kp.tB, &full[stage], ks * 128,
+                           yb + crank * piece_rows, cl_mask);
+          else
+            tma_load_2d(sA + kBlkA, &kp.tB, &full[stage], ks * 128, yb);
+        }
       }
       // Drain: wait until the last commits of every CTA of the cluster have
       // arrived on this CTA's stage barriers, so none lands after it exits.
@@ -251,212 +235,105 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t idesc = idesc_bf16(kBM, kBN);
       uint32_t it = 0, seg = 0;
       bool stop = false;
-      for (int t = 0; t < my_tiles && !stop; ++t)
-        for (int l = 0; l < nm && !stop; ++l)
-          for (int set = 0; set < NSET && !stop; ++set)
-            for (int ks = 0; ks < kp.nst; ++ks, ++it) {
-              const bool first = ks % kSegStages == 0;
-              const uint32_t b = seg & 1u;
-              if (first && seg >= 2) {  // the drain warps must have read this accumulator's last segment
-                if (!wait_or_abort(&acc_empty[b], ((seg >> 1) - 1) & 1u, abort_flag, kp.status)) {
-                  stop = true;
-                  break;
-                }
-                tc_fence_after();
-              }
-              const uint32_t stage = it % kStages;
-              if (!wait_or_abort(&full[stage], (it / kStages) & 1u, abort_flag, kp.status)) {
-                stop = true;
-                break;
-              }
-              tc_fence_after();
-              const uint32_t sA = base + stage * kStageBytes;
-#pragma unroll
-              for (int q = 0; q < 4; ++q)  // four K-steps of 16 inside the 128-byte rows
-                umma_bf16(tmem + b * kBN, smem_desc_k128(sA + 32 * q), smem_desc_k128(sA + kBlkA + 32 * q), idesc,
-                          (first && q == 0) ? 0u : 1u);
-              // the stage is free (in every CTA of the cluster) once these MMAs finish
-              if (cl > 1)
-                umma_commit_mc(&empty[stage], cl_mask);
-              else
-                umma_commit(&empty[stage]);
-              if ((ks + 1) % kSegStages == 0 || ks + 1 == kp.nst) {
-                umma_commit(&acc_full[b]);
-                ++seg;
-              }
+      for (int t = 0; t < my_items && !stop; ++t)
+        for (int ks = 0; ks < kp.nst; ++ks, ++it) {
+          const bool first = ks % kSegStages == 0;
+          const uint32_t b = seg & 1u;
+          if (first && seg >= 2) {  // the drain warps must have read this accumulator's last segment
+            if (!wait_or_abort(&acc_empty[b], ((seg >> 1) - 1) & 1u, abort_flag, kp.status)) {
+              stop = true;
+              break;
             }
+            tc_fence_after();
+          }
+          const uint32_t stage = it % kStages;
+          if (!wait_or_abort(&full[stage], (it / kStages) & 1u, abort_flag, kp.status)) {
+            stop = true;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sA = base + stage * kStageBytes;
+#pragma unroll
+          for (int q = 0; q < 4; ++q)  // four K-steps of 16 inside the 128-byte rows
+            umma_bf16(tmem + b * kBN, smem_desc_k128(sA + 32 * q), smem_desc_k128(sA + kBlkA + 32 * q), idesc,
+                      (first && q == 0) ? 0u : 1u);
+          // the stage is free (in every CTA of the cluster) once these MMAs finish
+          if (cl > 1)
+            umma_commit_mc(&empty[stage], cl_mask);
+          else
+            umma_commit(&empty[stage]);
+          if ((ks + 1) % kSegStages == 0 || ks + 1 == kp.nst) {
+            umma_commit(&acc_full[b]);
+            ++seg;
+          }
+        }
     }
     __syncwarp();
-  } else if (warp < kProducerWarp) {
+  } else {
     // ---------------------------------------------------------------- drain
     const int hh = warp >> 2;
     const int row_in_tile = (warp & 3) * 32 + lane;
     const uint32_t lane_addr = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16) + static_cast<uint32_t>(hh * 128);
     uint32_t seg = 0;
     bool stop = false;
-    for (int t = 0; t < my_tiles && !stop; ++t) {
-      const int slot = t & 1;
-      if (t >= 2 && !warp_wait(&res_empty[slot], ((t >> 1) - 1) & 1u, abort_flag, kp.status)) break;
-      uint8_t* const sbase = my_scratch + static_cast<int64_t>(slot) * NSET * nm * kTileBytes +
-                             row_in_tile * kBN + hh * 128;
-      for (int l = 0; l < nm && !stop; ++l) {
-        const int m = static_cast<int>(mt.mods[l]), off = mt.off[l];
-        const float inv = mt.inv[l], offinv = mt.offinv[l];
-        for (int set = 0; set < NSET && !stop; ++set) {
-          uint32_t run[32];  // symmetric residues of this thread's 128 columns, four per word
+    for (int t = 0; t < my_items && !stop; ++t) {
+      int p, tm, tn;
+      item_coords(kp, cid + t * ncl, crank, p, tm, tn);
+      const int l = p % kp.nm;
+      const int m = static_cast<int>(mt.mods[l]), off = mt.off[l];
+      const float inv = mt.inv[l], offinv = mt.offinv[l];
+      uint32_t run[32];  // symmetric residues of this thread's 128 columns, four per word
 #pragma unroll
-          for (int i = 0; i < 32; ++i) run[i] = 0;
-          for (int s = 0; s < nseg; ++s, ++seg) {
-            const uint32_t b = seg & 1u;
-            if (!warp_wait(&acc_full[b], (seg >> 1) & 1u, abort_flag, kp.status)) {
-              stop = true;
-              break;
-            }
-            tc_fence_after();
+      for (int i = 0; i < 32; ++i) run[i] = 0;
+      for (int s = 0; s < nseg; ++s, ++seg) {
+        const uint32_t b = seg & 1u;
+        if (!warp_wait(&acc_full[b], (seg >> 1) & 1u, abort_flag, kp.status)) {
+          stop = true;
+          break;
+        }
+        tc_fence_after();
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              uint32_t v[16];
-              tmem_ld16(lane_addr + b * kBN + 16 * q, v);
-              tmem_wait_ld();
-              if (q == 7) {
-                tc_fence_before();
-                mbar_arrive(&acc_empty[b]);  // the MMAs may refill this accumulator now
-              }
-#pragma unroll
-              for (int w = 0; w < 4; ++w) {
-                uint32_t o = 0;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                  const int x = sym_mod(sbyte(run[4 * q + w], i) + __float2int_rn(__uint_as_float(v[4 * w + i])), m,
-                                        off, inv, offinv);
-                  o |= (static_cast<uint32_t>(x) & 0xFFu) << (8 * i);
-                }
-                run[4 * q + w] = o;
-              }
-            }
+        for (int q = 0; q < 8; ++q) {
+          uint32_t v[16];
+          tmem_ld16(lane_addr + b * kBN + 16 * q, v);
+          tmem_wait_ld();
+          if (q == 7) {
+            tc_fence_before();
+            mbar_arrive(&acc_empty[b]);  // the MMAs may refill this accumulator now
           }
-          if (stop) break;
-          // Eq. (7): residues in [0, m) to the scratch slot, 128 bytes per thread
-          uint4* dst = reinterpret_cast<uint4*>(sbase + static_cast<int64_t>(set * nm + l) * kTileBytes);
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            uint32_t wv[4];
+          for (int w = 0; w < 4; ++w) {
+            uint32_t o = 0;
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              uint32_t o = 0;
-#pragma unroll
-              for (int k = 0; k < 4; ++k) {
-                int x = sbyte(run[4 * i + e], k);
-                if (x < 0) x += m;
-                o |= static_cast<uint32_t>(x) << (8 * k);
-              }
-              wv[e] = o;
+            for (int i = 0; i < 4; ++i) {
+              const int x = sym_mod(sbyte(run[4 * q + w], i) + __float2int_rn(__uint_as_float(v[4 * w + i])), m,
+                                    off, inv, offinv);
+              o |= (static_cast<uint32_t>(x) & 0xFFu) << (8 * i);
             }
-            dst[i] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+            run[4 * q + w] = o;
           }
         }
       }
       if (stop) break;
-      mbar_arrive(&res_full[slot]);  // release: the slot's bytes are visible to the CRT warps
-    }
-  } else {
-    // ---------------------------------------------------------------- CRT (warps 10-13)
-    const int row_in_tile = (warp - kCrtWarp0) * 32 + lane;
-    for (int t = 0; t < my_tiles; ++t) {
-      const int slot = t & 1;
-      if (!warp_wait(&res_full[slot], (t >> 1) & 1u, abort_flag, kp.status)) break;
-      int tg, tn;
-      tile_coords(cid + t * ncl, kp.tiles_mg, kp.tiles_n, tg, tn);
-      const int row = (tg * cl + crank) * kBM + row_in_tile;
-      const uint8_t* const sbase =
-          my_scratch + static_cast<int64_t>(slot) * NSET * nm * kTileBytes + row_in_tile * kBN;
-      const int ncols = kp.N - tn * kBN < kBN ? kp.N - tn * kBN : kBN;
-      if (row < kp.M) {
-        const int erow = kp.EA[row] + kp.escale;
-#pragma unroll 1
-        for (int c0 = 0; c0 < ncols; c0 += 4) {
-          const uint8_t* const p = sbase + c0;
-          // CRT sums of columns c0 .. c0+3 (real) or of two of them at a time (complex)
-          if constexpr (!CPLX) {
-            CrtLazy acc[4];
+      // Eq. (7): residues in [0, m), 128 bytes of this thread's row
+      uint4* dst = reinterpret_cast<uint4*>(
+          kp.R + (static_cast<int64_t>(p) * kp.tiles_m * kBM + tm * kBM + row_in_tile) * kp.ldr + tn * kBN + hh * 128);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) crt_lazy_init(acc[c]);
+      for (int i = 0; i < 8; ++i) {
+        uint32_t wv[4];
 #pragma unroll
-            for (int l = 0; l < kMaxModuli; ++l) {
-              if (l >= nm) break;
-              const uint32_t w = *reinterpret_cast<const uint32_t*>(p + static_cast<int64_t>(l) * kTileBytes);
+        for (int e = 0; e < 4; ++e) {
+          uint32_t o = 0;
 #pragma unroll
-              for (int c = 0; c < 4; ++c) crt_lazy_acc(acc[c], ct, l, (w >> (8 * c)) & 0xFFu);
-            }
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              if (c0 + c >= ncols) break;
-              const int cidx = tn * kBN + c0 + c;
-              const double xr = scale2_fast(crt_finish_lazy(acc[c], ct), erow + kp.FB[cidx]);
-              if (MODE == II_F64) {
-                double* cp = static_cast<double*>(kp.C) + static_cast<int64_t>(row) * kp.ldc + cidx;
-                *cp = blas_update(kp.alpha_re, xr, kp.beta_re, kp.beta_re != 0.0 ? *cp : 0.0);
-              } else {
-                float* cp = static_cast<float*>(kp.C) + static_cast<int64_t>(row) * kp.ldc + cidx;
-                *cp = static_cast<float>(
-                    blas_update(kp.alpha_re, xr, kp.beta_re, kp.beta_re != 0.0 ? static_cast<double>(*cp) : 0.0));
-              }
-            }
-          } else {
-#pragma unroll
-            for (int c2 = 0; c2 < 4; c2 += 2) {
-              CrtLazy are[2], aim[2];
-#pragma unroll
-              for (int c = 0; c < 2; ++c) {
-                crt_lazy_init(are[c]);
-                crt_lazy_init(aim[c]);
-              }
-#pragma unroll 1
-              for (int l = 0; l < nm; ++l) {
-                // Eq. (16): Re = T1 - T2, Im = T3 - T1 - T2 (mod m)
-                const int m = static_cast<int>(mt.mods[l]);
-                const uint8_t* q = p + static_cast<int64_t>(l) * kTileBytes;
-                const uint32_t w1 = *reinterpret_cast<const uint32_t*>(q);
-                const uint32_t w2 = *reinterpret_cast<const uint32_t*>(q + static_cast<int64_t>(nm) * kTileBytes);
-                const uint32_t w3 = *reinterpret_cast<const uint32_t*>(q + static_cast<int64_t>(2 * nm) * kTileBytes);
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                  const int sh = 8 * (c2 + c);
-                  const int t1 = (w1 >> sh) & 0xFF, t2 = (w2 >> sh) & 0xFF, t3 = (w3 >> sh) & 0xFF;
-                  int re = t1 - t2;
-                  if (re < 0) re += m;
-                  int im = t3 - t1 - t2;
-                  if (im < 0) im += m;
-                  if (im < 0) im += m;
-                  crt_lazy_acc(are[c], ct, l, static_cast<uint32_t>(re));
-                  crt_lazy_acc(aim[c], ct, l, static_cast<uint32_t>(im));
-                }
-              }
-#pragma unroll
-              for (int c = 0; c < 2; ++c) {
-                if (c0 + c2 + c >= ncols) break;
-                const int cidx = tn * kBN + c0 + c2 + c;
-                const int sc = erow + kp.FB[cidx];
-                const double xr = scale2_fast(crt_finish_lazy(are[c], ct), sc);
-                const double xi = scale2_fast(crt_finish_lazy(aim[c], ct), sc);
-                // complex update in binary64; complex64 output rounds each part once more
-                using TO = typename std::conditional<MODE == II_C3M, float, double>::type;
-                TO* cp = static_cast<TO*>(kp.C) + 2 * (static_cast<int64_t>(row) * kp.ldc + cidx);
-                double tr = __fma_rn(kp.alpha_re, xr, -__dmul_rn(kp.alpha_im, xi));
-                double ti = __fma_rn(kp.alpha_re, xi, __dmul_rn(kp.alpha_im, xr));
-                if (kp.beta_re != 0.0 || kp.beta_im != 0.0) {
-                  const double cr = static_cast<double>(cp[0]), ci = static_cast<double>(cp[1]);
-                  tr = __dadd_rn(tr, __fma_rn(kp.beta_re, cr, -__dmul_rn(kp.beta_im, ci)));
-                  ti = __dadd_rn(ti, __fma_rn(kp.beta_re, ci, __dmul_rn(kp.beta_im, cr)));
-                }
-                cp[0] = static_cast<TO>(tr);
-                cp[1] = static_cast<TO>(ti);
-              }
-            }
+          for (int k = 0; k < 4; ++k) {
+            int x = sbyte(run[4 * i + e], k);
+            if (x < 0) x += m;
+            o |= static_cast<uint32_t>(x) << (8 * k);
           }
+          wv[e] = o;
         }
+        dst[i] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
       }
-      mbar_arrive(&res_empty[slot]);  // the drain warps may refill this slot
     }
   }
   tc_fence_before();
@@ -471,9 +348,109 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-// Largest number of co-resident clusters of `cl` CTAs of this kernel (0 if
-// it cannot run with that cluster size).
+// ---------------------------------------------------------------- CRT
+struct KParamsCRT {
+  const uint8_t* R;
+  int64_t ldr, plane;  // residue row pitch and plane size (bytes)
+  int M, N, nm;
+  const int32_t* EA;
+  const int32_t* FB;
+  int escale;
+  double alpha_re, alpha_im, beta_re, beta_im;
+  void* C;
+  int64_t ldc;
+};
+
+// One thread per row and four consecutive columns: the CRT sums of Eq. (8)
+// from the residue planes (3M: Re = T1 - T2, Im = T3 - T1 - T2 mod m, Eq.
+// 16), S mod P with the symmetric lift, binary64, scaling and the update.
 template <int MODE>
+__global__ void __launch_bounds__(256) crt_II_kernel(const __grid_constant__ KParamsCRT kp,
+                                                     const __grid_constant__ CrtTables ct,
+                                                     const __grid_constant__ ModTables mt) {
+  constexpr bool CPLX = MODE == II_Z3M || MODE == II_C3M;
+  const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int ncq = (kp.N + 3) / 4;
+  if (idx >= static_cast<int64_t>(kp.M) * ncq) return;
+  const int row = static_cast<int>(idx / ncq), c0 = static_cast<int>(idx % ncq) * 4;
+  const uint8_t* const p = kp.R + static_cast<int64_t>(row) * kp.ldr + c0;
+  const int erow = kp.EA[row] + kp.escale;
+  if constexpr (!CPLX) {
+    CrtLazy acc[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) crt_lazy_init(acc[c]);
+#pragma unroll
+    for (int l = 0; l < kMaxModuli; ++l) {
+      if (l >= kp.nm) break;
+      const uint32_t w = *reinterpret_cast<const uint32_t*>(p + static_cast<int64_t>(l) * kp.plane);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) crt_lazy_acc(acc[c], ct, l, (w >> (8 * c)) & 0xFFu);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int cidx = c0 + c;
+      if (cidx >= kp.N) break;
+      const double xr = scale2_fast(crt_finish_lazy(acc[c], ct), erow + kp.FB[cidx]);
+      if (MODE == II_F64) {
+        double* cp = static_cast<double*>(kp.C) + static_cast<int64_t>(row) * kp.ldc + cidx;
+        *cp = blas_update(kp.alpha_re, xr, kp.beta_re, kp.beta_re != 0.0 ? *cp : 0.0);
+      } else {
+        float* cp = static_cast<float*>(kp.C) + static_cast<int64_t>(row) * kp.ldc + cidx;
+        *cp = static_cast<float>(
+            blas_update(kp.alpha_re, xr, kp.beta_re, kp.beta_re != 0.0 ? static_cast<double>(*cp) : 0.0));
+      }
+    }
+  } else {
+    CrtLazy are[4], aim[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      crt_lazy_init(are[c]);
+      crt_lazy_init(aim[c]);
+    }
+#pragma unroll 1
+    for (int l = 0; l < kp.nm; ++l) {
+      const int m = static_cast<int>(mt.mods[l]);
+      const uint8_t* q = p + static_cast<int64_t>(l) * kp.plane;
+      const uint32_t w1 = *reinterpret_cast<const uint32_t*>(q);
+      const uint32_t w2 = *reinterpret_cast<const uint32_t*>(q + static_cast<int64_t>(kp.nm) * kp.plane);
+      const uint32_t w3 = *reinterpret_cast<const uint32_t*>(q + static_cast<int64_t>(2 * kp.nm) * kp.plane);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int t1 = (w1 >> (8 * c)) & 0xFF, t2 = (w2 >> (8 * c)) & 0xFF, t3 = (w3 >> (8 * c)) & 0xFF;
+        int re = t1 - t2;
+        if (re < 0) re += m;
+        int im = t3 - t1 - t2;
+        if (im < 0) im += m;
+        if (im < 0) im += m;
+        crt_lazy_acc(are[c], ct, l, static_cast<uint32_t>(re));
+        crt_lazy_acc(aim[c], ct, l, static_cast<uint32_t>(im));
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int cidx = c0 + c;
+      if (cidx >= kp.N) break;
+      const int sc = erow + kp.FB[cidx];
+      const double xr = scale2_fast(crt_finish_lazy(are[c], ct), sc);
+      const double xi = scale2_fast(crt_finish_lazy(aim[c], ct), sc);
+      // complex update in binary64; complex64 output rounds each part once more
+      using TO = typename std::conditional<MODE == II_C3M, float, double>::type;
+      TO* cp = static_cast<TO*>(kp.C) + 2 * (static_cast<int64_t>(row) * kp.ldc + cidx);
+      double tr = __fma_rn(kp.alpha_re, xr, -__dmul_rn(kp.alpha_im, xi));
+      double ti = __fma_rn(kp.alpha_re, xi, __dmul_rn(kp.alpha_im, xr));
+      if (kp.beta_re != 0.0 || kp.beta_im != 0.0) {
+        const double cr = static_cast<double>(cp[0]), ci = static_cast<double>(cp[1]);
+        tr = __dadd_rn(tr, __fma_rn(kp.beta_re, cr, -__dmul_rn(kp.beta_im, ci)));
+        ti = __dadd_rn(ti, __fma_rn(kp.beta_re, ci, __dmul_rn(kp.beta_im, cr)));
+      }
+      cp[0] = static_cast<TO>(tr);
+      cp[1] = static_cast<TO>(ti);
+    }
+  }
+}
+
+// Largest number of co-resident clusters of `cl` CTAs of the GEMM kernel (0
+// if it cannot run with that cluster size).
 int max_clusters(int cl) {
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
@@ -487,57 +464,50 @@ int max_clusters(int cl) {
   cfg.attrs = at;
   cfg.numAttrs = 1;
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, gemm_II_tc_kernel<MODE>, &cfg) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveClusters(&n, gemm_II_tc_kernel, &cfg) != cudaSuccess) {
     (void)cudaGetLastError();
     return 0;
   }
   return n;
 }
 
-template <int MODE>
-cudaError_t launch_tc_mode(const GemmIIArgs& a, const ModTables& mt, const CrtTables& ct, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(gemm_II_tc_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+cudaError_t launch_residues(const GemmIIArgs& a, int nsets, const ModTables& mt, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(gemm_II_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
   if (e != cudaSuccess) return e;
   const int cl = a.cluster;
   if (cl != 1 && cl != 2 && cl != 4) return cudaErrorInvalidValue;
   KParamsIITC kp;
   kp.tA = *a.descA;
   kp.tB = *a.descB;
-  kp.M = a.M;
-  kp.N = a.N;
   kp.nst = a.nk32 / 2;  // planes are padded to 128 K-elements
   kp.tiles_m = (a.M + kBM - 1) / kBM;
   kp.tiles_n = (a.N + kBN - 1) / kBN;
   kp.cl = cl;
   kp.tiles_mg = (kp.tiles_m + cl - 1) / cl;
+  kp.nplanes = nsets * a.nm;
   kp.nm = a.nm;
   kp.rowsA_pad = a.rowsA_pad;
   kp.rowsB_pad = a.rowsB_pad;
-  kp.EA = a.EA;
-  kp.FB = a.FB;
-  kp.escale = a.escale;
-  kp.alpha_re = a.alpha_re;
-  kp.alpha_im = a.alpha_im;
-  kp.beta_re = a.beta_re;
-  kp.beta_im = a.beta_im;
-  kp.C = a.C;
-  kp.ldc = a.ldc;
-  kp.scratch = a.scratch;
+  kp.R = a.scratch;
+  kp.ldr = static_cast<int64_t>(kp.tiles_n) * kBN;
   kp.status = a.status;
-  const int ntiles = kp.tiles_mg * kp.tiles_n;
-  if (ntiles == 0 || kp.nst == 0) return cudaSuccess;
-  const int max_ctas = a.num_sms < kGemmIITcMaxCtas ? a.num_sms : kGemmIITcMaxCtas;  // scratch slots
+  // the residue planes hold cl-rounded row tiles, so every CTA's tile is in bounds
+  kp.tiles_m = kp.tiles_mg * cl;
+  const int nitems = kp.nplanes * kp.tiles_mg * kp.tiles_n;
+  if (nitems == 0 || kp.nst == 0) return cudaSuccess;
   if (cl == 1) {
-    const int grid = ntiles < max_ctas ? ntiles : max_ctas;
-    gemm_II_tc_kernel<MODE><<<grid, kThreads, kSmem, st>>>(kp, ct, mt);
+    const int grid = nitems < a.num_sms ? nitems : a.num_sms;
+    gemm_II_tc_kernel<<<grid, kThreads, kSmem, st>>>(kp, mt);
     return cudaGetLastError();
   }
-  static int cached[3] = {-1, -1, -1};  // per cluster size 1, 2, 4 (index cl / 2)
-  int& mc = cached[cl / 2];
-  if (mc < 0) mc = max_clusters<MODE>(cl);
+  static int mc = -1;
+  static int mc_cl = 0;
+  if (mc < 0 || mc_cl != cl) {
+    mc = max_clusters(cl);
+    mc_cl = cl;
+  }
   if (mc <= 0) return cudaErrorInvalidConfiguration;
-  int nclusters = ntiles < mc ? ntiles : mc;
-  if (nclusters * cl > max_ctas) nclusters = max_ctas / cl;
+  const int nclusters = nitems < mc ? nitems : mc;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -550,7 +520,41 @@ cudaError_t launch_tc_mode(const GemmIIArgs& a, const ModTables& mt, const CrtTa
   cfg.stream = st;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, gemm_II_tc_kernel<MODE>, kp, ct, mt);
+  return cudaLaunchKernelEx(&cfg, gemm_II_tc_kernel, kp, mt);
+}
+
+template <int MODE>
+cudaError_t launch_crt(const GemmIIArgs& a, const ModTables& mt, const CrtTables& ct, cudaStream_t st) {
+  KParamsCRT kp;
+  const int cl = a.cluster;
+  const int tiles_m = ((a.M + kBM - 1) / kBM + cl - 1) / cl * cl;
+  kp.R = a.scratch;
+  kp.ldr = static_cast<int64_t>((a.N + kBN - 1) / kBN) * kBN;
+  kp.plane = static_cast<int64_t>(tiles_m) * kBM * kp.ldr;
+  kp.M = a.M;
+  kp.N = a.N;
+  kp.nm = a.nm;
+  kp.EA = a.EA;
+  kp.FB = a.FB;
+  kp.escale = a.escale;
+  kp.alpha_re = a.alpha_re;
+  kp.alpha_im = a.alpha_im;
+  kp.beta_re = a.beta_re;
+  kp.beta_im = a.beta_im;
+  kp.C = a.C;
+  kp.ldc = a.ldc;
+  const int64_t threads = static_cast<int64_t>(a.M) * ((a.N + 3) / 4);
+  if (threads == 0) return cudaSuccess;
+  crt_II_kernel<MODE><<<static_cast<unsigned>((threads + 255) / 256), 256, 0, st>>>(kp, ct, mt);
+  return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t launch_mode(const GemmIIArgs& a, const ModTables& mt, const CrtTables& ct, cudaStream_t st) {
+  constexpr int NSET = (MODE == II_Z3M || MODE == II_C3M) ? 3 : 1;
+  cudaError_t e = launch_residues(a, NSET, mt, st);
+  if (e != cudaSuccess) return e;
+  return launch_crt<MODE>(a, mt, ct, st);
 }
 
 }  // namespace
@@ -558,14 +562,15 @@ cudaError_t launch_tc_mode(const GemmIIArgs& a, const ModTables& mt, const CrtTa
 int gemm_II_tc_tile_m() { return kBM; }
 int gemm_II_tc_tile_n() { return kBN; }
 
-size_t gemm_II_tc_scratch_bytes(int nm, bool is_complex) {
-  return static_cast<size_t>(kGemmIITcMaxCtas) * 2 * (is_complex ? 3 : 1) * nm * static_cast<size_t>(kTileBytes);
+size_t gemm_II_tc_residue_bytes(int64_t M, int64_t N, int nm, bool is_complex, int cluster) {
+  const int64_t tiles_m = ((M + kBM - 1) / kBM + cluster - 1) / cluster * cluster;
+  const int64_t tiles_n = (N + kBN - 1) / kBN;
+  return static_cast<size_t>(is_complex ? 3 : 1) * nm * static_cast<size_t>(tiles_m * kBM) *
+         static_cast<size_t>(tiles_n * kBN);
 }
 
 // CTAs per cluster for the Scheme II tcgen05 kernel: EMU_II_CLUSTER (1, 2
-// or 4) if set, else 2 (pairs of CTAs halve the L2 reads of B: 25.6 -> 22.3
-// ms for 16 moduli at n = 8192).  The B tensor map's box is 256 / cluster
-// rows.
+// or 4) if set, else 2.  The B tensor map's box is 256 / cluster rows.
 int gemm_II_tc_cluster() {
   static int v = 0;
   if (v == 0) {
@@ -580,13 +585,13 @@ cudaError_t launch_gemm_II_tc(int out_mode, const GemmIIArgs& a, const ModTables
                               cudaStream_t st) {
   switch (out_mode) {
     case II_F64:
-      return launch_tc_mode<II_F64>(a, mt, ct, st);
+      return launch_mode<II_F64>(a, mt, ct, st);
     case II_F32:
-      return launch_tc_mode<II_F32>(a, mt, ct, st);
+      return launch_mode<II_F32>(a, mt, ct, st);
     case II_Z3M:
-      return launch_tc_mode<II_Z3M>(a, mt, ct, st);
+      return launch_mode<II_Z3M>(a, mt, ct, st);
     case II_C3M:
-      return launch_tc_mode<II_C3M>(a, mt, ct, st);
+      return launch_mode<II_C3M>(a, mt, ct, st);
     default:
       return cudaErrorInvalidValue;
   }
