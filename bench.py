@@ -444,8 +444,9 @@ def run_ours(args, rank, world, local_rank):
             peak_src = ("FP8 dense peak = measured bf16 %s x nominal FP8/bf16 ratio 2 (4.5 / 2.25 PFLOP/s)"
                         % ("(MEASURED_PEAKS.json)" if bf16 else "(fallback 1.9 PFLOP/s)"))
         traffic = (load_traffic("gemm_I", "p%d_n%d" % (p, n)) if args.scheme == "I" else
-                   load_traffic("gemm_f8tc", "p%d_n%d" % (p, n)) if args.scheme == "I_F8" else None)
-        kname = ("gemm_II_tc_kernel (tcgen05 bf16)" if ii_tc else "gemm_II_kernel (mma.sync INT8)" if args.scheme == "II" else
+                   load_traffic("gemm_f8tc", "p%d_n%d" % (p, n)) if args.scheme == "I_F8" else
+                   load_traffic("gemm_II_tc", "nm%d_n%d" % (p, n)) if ii_tc else None)
+        kname = ("gemm_II_tc_kernel + crt_II_kernel (tcgen05 bf16 residue GEMM, then CRT)" if ii_tc else "gemm_II_kernel (mma.sync INT8)" if args.scheme == "II" else
                  "gemm_f8tc_kernel<%d, OUT_F64> (tcgen05)" % p if args.scheme == "I_F8" else
                  "gemm_I_kernel<%d, OUT_F64> (mma.sync INT8)" % p)
         ops_desc = ("bf16 tensor ops 2 N_m M N K (residue products)" if ii_tc else
