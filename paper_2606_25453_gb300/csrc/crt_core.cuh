@@ -19,16 +19,18 @@ __device__ __forceinline__ void crt_acc(uint32_t* S, const uint32_t* w, uint32_t
   S[kCrtLimbs] += static_cast<uint32_t>(c);
 }
 
-// Round a nonnegative 5-limb integer to binary64, nearest-even.
+// Round a nonnegative 5-limb integer to binary64, nearest-even.  Below
+// 2^128 the four low limbs are rounded directly; otherwise the window of
+// limbs 1..4 (>= 97 significant bits) plus a sticky bit for limb 0 has the
+// same rounding, scaled back by 2^32 exactly.  Straight-line code: no limb
+// is indexed at run time.
 __device__ __forceinline__ double limbs_to_double_rn(const uint32_t* x) {
-  int L = kCrtLimbs - 1;
-  while (L > 0 && x[L] == 0) --L;
-  if (L <= 3) {
-    unsigned __int128 u = 0;
-    for (int i = L; i >= 0; --i) u = (u << 32) | x[i];
+  if (x[4] == 0) {
+    const unsigned __int128 u = (static_cast<unsigned __int128>(x[3]) << 96) |
+                                (static_cast<unsigned __int128>(x[2]) << 64) |
+                                (static_cast<unsigned __int128>(x[1]) << 32) | x[0];
     return u128_to_double_rn(u);
   }
-  // L == 4: window of limbs 1..4 (>= 97 significant bits) plus a sticky bit
   unsigned __int128 u = (static_cast<unsigned __int128>(x[4]) << 96) |
                         (static_cast<unsigned __int128>(x[3]) << 64) |
                         (static_cast<unsigned __int128>(x[2]) << 32) | x[1];
@@ -131,7 +133,8 @@ __device__ __forceinline__ void crt_lazy_init(CrtLazy& a) {
 __device__ __forceinline__ void crt_lazy_acc(CrtLazy& a, const CrtTables& ct, int l, uint32_t r) {
 #pragma unroll
   for (int i = 0; i < kCrtLimbs; ++i) a.s[i] += static_cast<uint64_t>(ct.w[l][i]) * r;
-  a.t = __fmaf_rn(static_cast<float>(r), ct.wP[l], a.t);
+  // r as binary32 without a conversion instruction: 2^23 + r has r in its low mantissa bits
+  a.t = __fmaf_rn(__uint_as_float(0x4B000000u | r) - 8388608.0f, ct.wP[l], a.t);
 }
 
 // Eq. (8) finish from the lazy form: x = S - kP with k = rint(t), which is
@@ -193,7 +196,7 @@ __device__ __forceinline__ double crt_finish_lazy(const CrtLazy& a, const CrtTab
     neg = !neg;
   }
   const double v = limbs_to_double_rn(mag);  // |x| <= P/2 < 2^159: five limbs
-  return neg ? -v : v;
+  return neg ? bitsd(dbits(v) ^ 0x8000000000000000ull) : v;  // sign flip without an FP64 instruction
 }
 
 // x 2^e for a nonzero finite x whose result stays normal: exponent-field

@@ -196,7 +196,12 @@ __device__ __forceinline__ ScaledInt scaled_trunc_bits(uint64_t bits, int shift)
 // Round an unsigned 128-bit integer to binary64, nearest-even, from its bits.
 __device__ __forceinline__ double u128_to_double_rn(unsigned __int128 u) {
   uint64_t hi = static_cast<uint64_t>(u >> 64), lo = static_cast<uint64_t>(u);
-  if (hi == 0 && lo < (1ull << 53)) return static_cast<double>(lo);  // exact
+  if (hi == 0 && lo < (1ull << 53)) {  // exact: built from the bits (no FP64 instruction)
+    if (lo == 0) return 0.0;
+    const int Ls = 64 - __clzll(static_cast<long long>(lo));  // 1 .. 53 significant bits
+    const uint64_t m = lo << (53 - Ls);                       // in [2^52, 2^53)
+    return bitsd((static_cast<uint64_t>(Ls - 1 + 1023) << 52) | (m & 0x000FFFFFFFFFFFFFull));
+  }
   int L = hi ? 128 - __clzll(static_cast<long long>(hi)) : 64 - __clzll(static_cast<long long>(lo));
   int drop = L - 53;  // >= 1
   uint64_t top = static_cast<uint64_t>(u >> drop);

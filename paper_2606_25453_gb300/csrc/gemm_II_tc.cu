@@ -359,6 +359,7 @@ struct KParamsCRT {
   double alpha_re, alpha_im, beta_re, beta_im;
   void* C;
   int64_t ldc;
+  int plain;  // alpha = 1, beta = 0: C = the result (no FP64 update arithmetic)
 };
 
 // One thread per row and four consecutive columns: the CRT sums of Eq. (8)
@@ -391,7 +392,12 @@ __global__ void __launch_bounds__(256) crt_II_kernel(const __grid_constant__ KPa
       const int cidx = c0 + c;
       if (cidx >= kp.N) break;
       const double xr = scale2_fast(crt_finish_lazy(acc[c], ct), erow + kp.FB[cidx]);
-      if (MODE == II_F64) {
+      if (kp.plain) {  // FP64 is slow on this GPU: no multiply by alpha = 1
+        if (MODE == II_F64)
+          static_cast<double*>(kp.C)[static_cast<int64_t>(row) * kp.ldc + cidx] = xr;
+        else
+          static_cast<float*>(kp.C)[static_cast<int64_t>(row) * kp.ldc + cidx] = static_cast<float>(xr);
+      } else if (MODE == II_F64) {
         double* cp = static_cast<double*>(kp.C) + static_cast<int64_t>(row) * kp.ldc + cidx;
         *cp = blas_update(kp.alpha_re, xr, kp.beta_re, kp.beta_re != 0.0 ? *cp : 0.0);
       } else {
@@ -436,6 +442,11 @@ __global__ void __launch_bounds__(256) crt_II_kernel(const __grid_constant__ KPa
       // complex update in binary64; complex64 output rounds each part once more
       using TO = typename std::conditional<MODE == II_C3M, float, double>::type;
       TO* cp = static_cast<TO*>(kp.C) + 2 * (static_cast<int64_t>(row) * kp.ldc + cidx);
+      if (kp.plain) {
+        cp[0] = static_cast<TO>(xr);
+        cp[1] = static_cast<TO>(xi);
+        continue;
+      }
       double tr = __fma_rn(kp.alpha_re, xr, -__dmul_rn(kp.alpha_im, xi));
       double ti = __fma_rn(kp.alpha_re, xi, __dmul_rn(kp.alpha_im, xr));
       if (kp.beta_re != 0.0 || kp.beta_im != 0.0) {
@@ -543,6 +554,7 @@ cudaError_t launch_crt(const GemmIIArgs& a, const ModTables& mt, const CrtTables
   kp.beta_im = a.beta_im;
   kp.C = a.C;
   kp.ldc = a.ldc;
+  kp.plain = a.alpha_re == 1.0 && a.alpha_im == 0.0 && a.beta_re == 0.0 && a.beta_im == 0.0;
   const int64_t threads = static_cast<int64_t>(a.M) * ((a.N + 3) / 4);
   if (threads == 0) return cudaSuccess;
   crt_II_kernel<MODE><<<static_cast<unsigned>((threads + 255) / 256), 256, 0, st>>>(kp, ct, mt);
