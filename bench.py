@@ -570,7 +570,9 @@ def run_suite(path, args):
         emit({"path": "cublas_dgemm", "n": n, "tflops": 2 * n ** 3 / ms / 1e9, "ms": ms, "err": sampled_err(A, B, C)})
         Af, Bf = Ad.float(), Bd.float()
         ms = timed(lambda: Af @ Bf)
-        emit({"path": "cublas_sgemm", "n": n, "tflops": 2 * n ** 3 / ms / 1e9, "ms": ms})
+        emit({"path": "cublas_sgemm", "n": n, "tflops": 2 * n ** 3 / ms / 1e9, "ms": ms,
+              "err": sampled_err(A.astype(np.float32).astype(np.float64), B.astype(np.float32).astype(np.float64),
+                                 (Af @ Bf).cpu().numpy().astype(np.float64))})
     # Scheme I DGEMM: p sweep, phi sweep
     for n in (4096, 8192):
         for phi in (0.5, 2.0, 4.0):
@@ -629,6 +631,14 @@ def run_suite(path, args):
         ms = timed(lambda: emu.sgemm(Ad, Bd, Cd, scheme="I", p=p, handle=h))
         emit({"path": "emu_sgemm_I", "n": 8192, "phi": 0.5, "p": p, "tflops": 2 * 8192 ** 3 / ms / 1e9,
               "int8_tops": p * (p + 1) * 8192 ** 3 / ms / 1e9, "ms": ms,
+              "err": sampled_err(A.astype(np.float64), B.astype(np.float64), Cd.cpu().numpy().astype(np.float64))})
+    # Scheme II SGEMM on the bf16 engine: FP32-level accuracy from 6-8 moduli
+    A, B, Ad, Bd = pair(8192, 0.5, np.float32)
+    Cd = torch.empty((8192, 8192), dtype=torch.float32, device=dev)
+    for nm in (6, 7, 8):
+        ms = timed(lambda: emu.sgemm(Ad, Bd, Cd, scheme="II", p=nm, handle=h))
+        emit({"path": "emu_sgemm_II", "n": 8192, "phi": 0.5, "nm": nm, "tflops": 2 * 8192 ** 3 / ms / 1e9,
+              "tensor_tops": 2 * nm * 8192 ** 3 / ms / 1e9, "ms": ms,
               "err": sampled_err(A.astype(np.float64), B.astype(np.float64), Cd.cpu().numpy().astype(np.float64))})
     scheme_II_points()
     engine = "int8 mma.sync" if os.environ.get("EMU_II_ENGINE") == "mma" else "bf16 tcgen05"
