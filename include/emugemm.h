@@ -51,6 +51,13 @@
  *    handle must be ordered (same stream, or synchronised by the caller).
  *  - m, n or k equal to 0 is valid: with k == 0 the product is zero and
  *    C = beta * C (alpha ignored); with m == 0 or n == 0 nothing is done.
+ *  - Environment (read once per process; results do not depend on it):
+ *    EMU_II_ENGINE=mma runs Scheme II on the INT8 mma.sync kernel instead of
+ *    the bf16 tcgen05 one; EMU_F8_ENGINE=mma runs E4M3 slices on the warp
+ *    level instead of tcgen05; EMU_II_CLUSTER and EMU_TC_CLUSTER (1, 2, 4)
+ *    set the CTAs per cluster that share operand chunks by TMA multicast in
+ *    the two tcgen05 kernels (default 2); EMU_FAULT=alloc makes every
+ *    library-owned workspace allocation fail (fault injection).
  */
 #ifndef EMUGEMM_H
 #define EMUGEMM_H
