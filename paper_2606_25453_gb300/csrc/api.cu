@@ -156,6 +156,13 @@ void host_mod_tables(int nm, ModTables* t) {
       t->pow16[l][j] = static_cast<int32_t>(v > hi ? v - m : v);
       v = (v << 16) % m;
     }
+    t->mf[l] = static_cast<float>(m);
+    t->offf[l] = static_cast<float>(t->off[l]);
+    v = 1 % m;  // 2^(14 j) mod m
+    for (int j = 0; j < kResDigitsF; ++j) {
+      t->pow14f[l][j] = static_cast<float>(v > hi ? v - m : v);
+      v = (v << 14) % m;
+    }
   }
 }
 

@@ -23,12 +23,16 @@ inline int64_t split_cols_II(int64_t k) { return (k + 127) / 128 * 128; }
 // 16-bit digits: a' = sum_j d_j 2^(16 j), a' mod m = sum_j d_j (2^(16 j) mod m)
 // mod m, the last reduction in single precision (the sum stays below 2^26).
 constexpr int kResDigits = 5;
+constexpr int kResDigitsF = 6;
 struct ModTables {
   uint32_t mods[kMaxModuli];
   int32_t off[kMaxModuli];                 // m - 1 - floor((m - 1)/2): symmetric residues lie in [-off, m - 1 - off]
   float inv[kMaxModuli];                   // 1/m rounded to nearest
   float offinv[kMaxModuli];                // off/m rounded to nearest
   int32_t pow16[kMaxModuli][kResDigits];   // symmetric residue of 2^(16 j) mod m
+  // binary32 form for the bf16 planes: 14-bit digits (six cover 2^84)
+  float pow14f[kMaxModuli][kResDigitsF];   // symmetric residue of 2^(14 j) mod m
+  float mf[kMaxModuli], offf[kMaxModuli];  // m and off as binary32
 };
 
 // CRT tables of Eq. (8) for a given number of moduli.

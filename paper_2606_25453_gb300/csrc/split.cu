@@ -312,6 +312,41 @@ __device__ __forceinline__ int sym_residue(const int* d, const ModTables& mt, in
   return r;
 }
 
+// The same in binary32 for the bf16 planes: 14-bit digits of |a'| (six
+// cover 2^84), negated for a negative element.  Every partial sum of
+// t = sum_j d_j c_j is an integer with |t| <= 16383 (1 + 5 * 128) < 2^24, so
+// the FMA chain is exact; q = floor(RN(t / m + off / m)) is floor((t + off)
+// / m) or one off, r = t - q m is exact (|r| < 2^24), and one correction each
+// way gives the symmetric residue -- all on the FP32 pipe.
+__device__ __forceinline__ void digits14f(uint64_t bits, int shift, float* d) {
+  const ScaledInt s = scaled_trunc_bits(bits, shift);
+  // s.mag 2^s.lsh = |a'| < 2^80 (the row exponent bounds every element), so s.lsh < 80
+  const unsigned __int128 v = static_cast<unsigned __int128>(s.mag) << s.lsh;
+  const uint64_t lo = static_cast<uint64_t>(v);
+  const uint64_t hi = static_cast<uint64_t>(v >> 64);
+  const uint32_t sg = static_cast<uint32_t>(bits >> 63) << 31;
+  const uint32_t dg[kResDigitsF] = {static_cast<uint32_t>(lo & 0x3FFFu), static_cast<uint32_t>((lo >> 14) & 0x3FFFu),
+                                    static_cast<uint32_t>((lo >> 28) & 0x3FFFu),
+                                    static_cast<uint32_t>((lo >> 42) & 0x3FFFu),
+                                    static_cast<uint32_t>(((lo >> 56) | (hi << 8)) & 0x3FFFu),
+                                    static_cast<uint32_t>((hi >> 6) & 0x3FFFu)};
+#pragma unroll
+  for (int j = 0; j < kResDigitsF; ++j)  // 2^23 + d has d in its low mantissa bits; the sign by bit
+    d[j] = __uint_as_float(__float_as_uint(__uint_as_float(0x4B000000u | dg[j]) - 8388608.0f) | sg);
+}
+
+__device__ __forceinline__ float sym_residue_f(const float* d, const ModTables& mt, int l) {
+  float t = d[0];
+#pragma unroll
+  for (int j = 1; j < kResDigitsF; ++j) t = __fmaf_rn(d[j], mt.pow14f[l][j], t);
+  const float m = mt.mf[l], off = mt.offf[l];
+  const float q = floorf(__fmaf_rn(t, mt.inv[l], mt.offinv[l]));
+  float r = __fmaf_rn(-q, m, t);
+  if (r < -off) r += m;
+  if (r >= m - off) r -= m;
+  return r;
+}
+
 __device__ __forceinline__ uint32_t pack_bytes(int r0, int r1, int r2, int r3) {
   const uint32_t lo = __byte_perm(static_cast<uint32_t>(r0), static_cast<uint32_t>(r1), 0x0040u);
   const uint32_t hi = __byte_perm(static_cast<uint32_t>(r2), static_cast<uint32_t>(r3), 0x0040u);
@@ -341,35 +376,73 @@ __device__ __forceinline__ void store4(int8_t* p, int r0, int r1, int r2, int r3
 // of the first element in plane 0, `plane` the plane stride in bytes.  The
 // modulus loop is unrolled so that the table entries are kernel-parameter
 // operands.
+// Four binary32 residues as bf16 (+ 0 turns a -0 into +0).
+__device__ __forceinline__ void store4f(int8_t* p, float r0, float r1, float r2, float r3) {
+  const uint32_t f0 = __float_as_uint(r0 + 0.0f), f1 = __float_as_uint(r1 + 0.0f);
+  const uint32_t f2 = __float_as_uint(r2 + 0.0f), f3 = __float_as_uint(r3 + 0.0f);
+  *reinterpret_cast<uint2*>(p) = make_uint2(__byte_perm(f0, f1, 0x7632u), __byte_perm(f2, f3, 0x7632u));
+}
+
 template <int CW, bool BF>
 __device__ __forceinline__ void residues4(const ModTables& mt, int nm, int shift, const uint64_t* re,
                                           const uint64_t* im, int64_t plane, int8_t* base) {
-  int dr[4][kResDigits], di[4][kResDigits];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    digits16(re[q], shift, dr[q]);
-    if (CW == 2) digits16(im[q], shift, di[q]);
-  }
-#pragma unroll
-  for (int l = 0; l < kMaxModuli; ++l) {
-    if (l >= nm) break;
-    int rr[4], ri[4], rs[4];
+  if constexpr (BF) {  // bf16 planes: the binary32 form
+    float dr[4][kResDigitsF], di[CW == 2 ? 4 : 1][kResDigitsF];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      rr[q] = sym_residue(dr[q], mt, l);
+      digits14f(re[q], shift, dr[q]);
+      if (CW == 2) digits14f(im[q], shift, di[q]);
+    }
+#pragma unroll
+    for (int l = 0; l < kMaxModuli; ++l) {
+      if (l >= nm) break;
+      float rr[4], ri[4], rs[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        rr[q] = sym_residue_f(dr[q], mt, l);
+        if (CW == 2) {
+          ri[q] = sym_residue_f(di[q], mt, l);
+          const float m = mt.mf[l], off = mt.offf[l];
+          float v = rr[q] + ri[q];
+          if (v < -off) v += m;
+          if (v >= m - off) v -= m;
+          rs[q] = v;
+        }
+      }
+      store4f(base + static_cast<int64_t>(l) * plane, rr[0], rr[1], rr[2], rr[3]);
       if (CW == 2) {
-        ri[q] = sym_residue(di[q], mt, l);
-        const int m = static_cast<int>(mt.mods[l]), off = mt.off[l];
-        int v = rr[q] + ri[q];
-        if (v < -off) v += m;
-        if (v >= m - off) v -= m;
-        rs[q] = v;
+        store4f(base + static_cast<int64_t>(nm + l) * plane, ri[0], ri[1], ri[2], ri[3]);
+        store4f(base + static_cast<int64_t>(2 * nm + l) * plane, rs[0], rs[1], rs[2], rs[3]);
       }
     }
-    store4<BF>(base + static_cast<int64_t>(l) * plane, rr[0], rr[1], rr[2], rr[3]);
-    if (CW == 2) {
-      store4<BF>(base + static_cast<int64_t>(nm + l) * plane, ri[0], ri[1], ri[2], ri[3]);
-      store4<BF>(base + static_cast<int64_t>(2 * nm + l) * plane, rs[0], rs[1], rs[2], rs[3]);
+  } else {
+    int dr[4][kResDigits], di[4][kResDigits];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      digits16(re[q], shift, dr[q]);
+      if (CW == 2) digits16(im[q], shift, di[q]);
+    }
+#pragma unroll
+    for (int l = 0; l < kMaxModuli; ++l) {
+      if (l >= nm) break;
+      int rr[4], ri[4], rs[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        rr[q] = sym_residue(dr[q], mt, l);
+        if (CW == 2) {
+          ri[q] = sym_residue(di[q], mt, l);
+          const int m = static_cast<int>(mt.mods[l]), off = mt.off[l];
+          int v = rr[q] + ri[q];
+          if (v < -off) v += m;
+          if (v >= m - off) v -= m;
+          rs[q] = v;
+        }
+      }
+      store4<BF>(base + static_cast<int64_t>(l) * plane, rr[0], rr[1], rr[2], rr[3]);
+      if (CW == 2) {
+        store4<BF>(base + static_cast<int64_t>(nm + l) * plane, ri[0], ri[1], ri[2], ri[3]);
+        store4<BF>(base + static_cast<int64_t>(2 * nm + l) * plane, rs[0], rs[1], rs[2], rs[3]);
+      }
     }
   }
 }
