@@ -137,62 +137,89 @@ __device__ __forceinline__ void crt_lazy_acc(CrtLazy& a, const CrtTables& ct, in
   a.t = __fmaf_rn(__uint_as_float(0x4B000000u | r) - 8388608.0f, ct.wP[l], a.t);
 }
 
+// Six-limb (192-bit) helpers on 32-bit carry chains (PTX add/sub/mad with
+// carry; one instruction per limb).  Outputs are early-clobber: they are
+// written while later inputs are still to be read.
+// d = a - b (mod 2^192); returns 1 if a < b (unsigned).
+__device__ __forceinline__ uint32_t sub6(const uint32_t* a, const uint32_t* b, uint32_t* d) {
+  uint32_t br;
+  asm("sub.cc.u32 %0, %7, %13;\n\t"
+      "subc.cc.u32 %1, %8, %14;\n\t"
+      "subc.cc.u32 %2, %9, %15;\n\t"
+      "subc.cc.u32 %3, %10, %16;\n\t"
+      "subc.cc.u32 %4, %11, %17;\n\t"
+      "subc.cc.u32 %5, %12, %18;\n\t"
+      "subc.u32 %6, 0, 0;"
+      : "=&r"(d[0]), "=&r"(d[1]), "=&r"(d[2]), "=&r"(d[3]), "=&r"(d[4]), "=&r"(d[5]), "=&r"(br)
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(b[0]), "r"(b[1]), "r"(b[2]),
+        "r"(b[3]), "r"(b[4]), "r"(b[5]));
+  return br & 1u;
+}
+
+// d = k * P for a five-limb P and k < 2^32 (six limbs).
+__device__ __forceinline__ void mul6(const uint32_t* P, uint32_t k, uint32_t* d) {
+  uint32_t h0, h1, h2, h3;
+  asm("mul.lo.u32 %0, %10, %15;\n\t"
+      "mul.hi.u32 %6, %10, %15;\n\t"
+      "mul.hi.u32 %7, %11, %15;\n\t"
+      "mul.hi.u32 %8, %12, %15;\n\t"
+      "mul.hi.u32 %9, %13, %15;\n\t"
+      "mad.lo.cc.u32 %1, %11, %15, %6;\n\t"
+      "madc.lo.cc.u32 %2, %12, %15, %7;\n\t"
+      "madc.lo.cc.u32 %3, %13, %15, %8;\n\t"
+      "madc.lo.cc.u32 %4, %14, %15, %9;\n\t"
+      "madc.hi.u32 %5, %14, %15, 0;"
+      : "=&r"(d[0]), "=&r"(d[1]), "=&r"(d[2]), "=&r"(d[3]), "=&r"(d[4]), "=&r"(d[5]), "=&r"(h0), "=&r"(h1),
+        "=&r"(h2), "=&r"(h3)
+      : "r"(P[0]), "r"(P[1]), "r"(P[2]), "r"(P[3]), "r"(P[4]), "r"(k));
+}
+
 // Eq. (8) finish from the lazy form: x = S - kP with k = rint(t), which is
 // round(S / P) or one off (t errs by less than 0.02 for up to 20 moduli), then
 // one exact correction each way into the symmetric range (-P/2, P/2] (the
 // lift of S mod P: above floor(P/2) it becomes negative), rounded once to
 // binary64.  All limb arithmetic is exact; only the choice of k is estimated.
 __device__ __forceinline__ double crt_finish_lazy(const CrtLazy& a, const CrtTables& ct) {
-  // S in 32-bit limbs (kSL of them)
+  // S in six 32-bit limbs: the 64-bit lazy sums (each < 2^45) overlap by 32 bits
   uint32_t S[kSL];
-  uint64_t c = 0;
-#pragma unroll
-  for (int i = 0; i < kCrtLimbs; ++i) {
-    c += a.s[i];
-    S[i] = static_cast<uint32_t>(c);
-    c >>= 32;
-  }
-  S[kCrtLimbs] = static_cast<uint32_t>(c);
-  const uint32_t k = static_cast<uint32_t>(__float2int_rn(a.t));
-  // R = S - k P (two's complement in kSL limbs)
-  uint32_t R[kSL];
   {
-    uint64_t mul = 0;
-    int64_t br = 0;
+    uint32_t l[kCrtLimbs], h[kCrtLimbs];
 #pragma unroll
-    for (int i = 0; i < kSL; ++i) {
-      mul += static_cast<uint64_t>(i < kCrtLimbs ? ct.P[i] : 0u) * k;
-      const int64_t d = static_cast<int64_t>(S[i]) - static_cast<int64_t>(static_cast<uint32_t>(mul)) - br;
-      mul >>= 32;
-      br = d < 0;
-      R[i] = static_cast<uint32_t>(d + (br ? (1ll << 32) : 0));
+    for (int i = 0; i < kCrtLimbs; ++i) {
+      l[i] = static_cast<uint32_t>(a.s[i]);
+      h[i] = static_cast<uint32_t>(a.s[i] >> 32);
     }
+    S[0] = l[0];
+    asm("add.cc.u32 %0, %5, %10;\n\t"
+        "addc.cc.u32 %1, %6, %11;\n\t"
+        "addc.cc.u32 %2, %7, %12;\n\t"
+        "addc.cc.u32 %3, %8, %13;\n\t"
+        "addc.u32 %4, %9, 0;"
+        : "=&r"(S[1]), "=&r"(S[2]), "=&r"(S[3]), "=&r"(S[4]), "=&r"(S[5])
+        : "r"(l[1]), "r"(l[2]), "r"(l[3]), "r"(l[4]), "r"(h[4]), "r"(h[0]), "r"(h[1]), "r"(h[2]), "r"(h[3]));
   }
+  const uint32_t k = static_cast<uint32_t>(__float2int_rn(a.t));
+  uint32_t kP[kSL], R[kSL];
+  mul6(ct.P, k, kP);
+  sub6(S, kP, R);  // S - kP, two's complement
   bool neg = static_cast<int32_t>(R[kSL - 1]) < 0;
   uint32_t mag[kSL];
-  {  // |R|
-    uint64_t cc = neg ? 1u : 0u;
+  {
+    const uint32_t zero[kSL] = {0, 0, 0, 0, 0, 0};
+    uint32_t nr[kSL];
+    sub6(zero, R, nr);
 #pragma unroll
-    for (int i = 0; i < kSL; ++i) {
-      cc += static_cast<uint64_t>(neg ? ~R[i] : R[i]);
-      mag[i] = static_cast<uint32_t>(cc);
-      cc >>= 32;
-    }
+    for (int i = 0; i < kSL; ++i) mag[i] = neg ? nr[i] : R[i];
   }
-  // compare |R| with floor(P/2) = P/2 (P is even: 256 is always a modulus)
-  int cmp = mag[kSL - 1] != 0 ? 1 : 0;
-#pragma unroll
-  for (int i = kCrtLimbs - 1; i >= 0; --i)
-    if (cmp == 0 && mag[i] != ct.Phalf[i]) cmp = mag[i] > ct.Phalf[i] ? 1 : -1;
+  // |R| against floor(P/2) = P/2 (P is even: 256 is always a modulus)
+  const uint32_t half[kSL] = {ct.Phalf[0], ct.Phalf[1], ct.Phalf[2], ct.Phalf[3], ct.Phalf[4], 0};
+  uint32_t diff[kSL];
+  const bool below = sub6(mag, half, diff) != 0;  // |R| < P/2
+  const bool equal = !below && (diff[0] | diff[1] | diff[2] | diff[3] | diff[4] | diff[5]) == 0;
   // R > P/2: R - P (negative, magnitude P - R); R <= -P/2: R + P (magnitude P - |R|)
-  if ((!neg && cmp > 0) || (neg && cmp >= 0)) {
-    int64_t br = 0;
-#pragma unroll
-    for (int i = 0; i < kSL; ++i) {
-      const int64_t d = static_cast<int64_t>(i < kCrtLimbs ? ct.P[i] : 0u) - mag[i] - br;
-      br = d < 0;
-      mag[i] = static_cast<uint32_t>(d + (br ? (1ll << 32) : 0));
-    }
+  if ((!neg && !below && !equal) || (neg && !below)) {
+    const uint32_t P6[kSL] = {ct.P[0], ct.P[1], ct.P[2], ct.P[3], ct.P[4], 0};
+    sub6(P6, mag, mag);
     neg = !neg;
   }
   const double v = limbs_to_double_rn(mag);  // |x| <= P/2 < 2^159: five limbs
