@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--cpu-rows", type=int, default=96, help="rows of C in the CPU oracle sample")
     ap.add_argument("--no-extras", action="store_true", help="skip cuBLAS / accuracy / CPU legs")
     ap.add_argument("--suite", default=None, help="write the secondary measurements (all paths) to this JSONL file")
+    ap.add_argument("--suite-md", default=None, help="print the summary tables of a --suite JSONL file")
     ap.add_argument("--suite-part", default="all", choices=["all", "ii"],
                     help="ii: only the Scheme II points (run in a child with EMU_II_ENGINE=mma by the full suite)")
     return ap.parse_args()
@@ -487,6 +488,96 @@ def run_ours(args, rank, world, local_rank):
 
 
 # ------------------------------------------------------------------ suite
+def suite_markdown(path):
+    """The summary tables of a --suite JSONL file (the text of
+    profiles/bench_suite_gb300.md)."""
+    import math
+    rows = [json.loads(line) for line in open(path)]
+
+    def bits(e):
+        return "-" if e is None else ("inf" if e == 0 else f"{-math.log2(e):.1f}")
+
+    o = []
+    o.append("# Measurement suite on one GB300 (all paths)\n")
+    o.append("Command: `python bench.py --suite gpurun_out/suite.jsonl`, then `python bench.py --suite-md")
+    o.append("gpurun_out/suite.jsonl > profiles/bench_suite_gb300.md` (device-resident inputs, CUDA events,")
+    o.append("1 warm-up + 3 timed calls per point, 1 at n = 16384 and for ZGEMM; accuracy = -log2 of")
+    o.append("max |C - C_ref| / (|A||B|) on 8 x 64 sampled entries against the double-double reference).")
+    o.append("Slice-product rates count executed products x 2: Scheme I p(p+1)MNK (8-bit), Scheme II 2 N_m MNK and 3M")
+    o.append("6 N_m MNK (residue products; bf16 on the default tcgen05 engine, INT8 on the mma.sync engine).")
+    o.append("Measured INT8 peak of this GPU: 150-156 TOP/s (cuBLASLt INT8 GEMM; register-only mma.sync s8 loop")
+    o.append("150.9).  FP8 tensor peak: 3789 TFLOP/s (measured bf16 1894.5 x 2, the recipe's derivation);")
+    o.append("ncu reports 4.87 POP/s at 2.07 GHz.\n")
+    o.append("## Native cuBLAS on the same GPU\n")
+    o.append("| routine | n | TFLOP/s | bits |\n|---|---|---|---|")
+    for d in rows:
+        if d["path"].startswith("cublas"):
+            t = d.get("tflops", d.get("tflops_8mnk"))
+            unit = " (8MNK)" if "tflops_8mnk" in d else ""
+            o.append(f"| {d['path']} | {d['n']} | {t:.3f}{unit} | {bits(d.get('err'))} |")
+    o.append("\n## Scheme I emulated DGEMM / SGEMM, INT8 slices (mma.sync)\n")
+    o.append("| path | n | phi | p | TFLOP/s | INT8 TOP/s | bits |\n|---|---|---|---|---|---|---|")
+    for d in rows:
+        if d["path"] in ("emu_dgemm_I", "emu_sgemm_I"):
+            o.append(f"| {d['path']} | {d['n']} | {d['phi']:g} | {d['p']} | {d['tflops']:.3f} | {d['int8_tops']:.1f} | {bits(d['err'])} |")
+    o.append("\n## Scheme I emulated DGEMM, E4M3 slices (tcgen05, TMEM accumulators)\n")
+    o.append("| n | phi | p | TFLOP/s | FP8 TOP/s | x cuBLAS DGEMM | bits |\n|---|---|---|---|---|---|---|")
+    cub = {d["n"]: d["tflops"] for d in rows if d["path"] == "cublas_dgemm"}
+    for d in rows:
+        if d["path"] == "emu_dgemm_I_F8":
+            c = cub.get(d["n"], cub.get(8192))
+            o.append(f"| {d['n']} | {d['phi']:g} | {d['p']} | {d['tflops']:.2f} | {d['f8_tops']:.0f} | {d['tflops']/c:.1f} | {bits(d['err'])} |")
+    o.append("\n## Scheme II emulated DGEMM, bf16 tcgen05 engine (default; residue GEMM, then the CRT kernel)\n")
+    o.append("| n | phi | N_m | TFLOP/s | tensor TOP/s | bits |\n|---|---|---|---|---|---|")
+    for d in rows:
+        if d["path"] == "emu_dgemm_II":
+            o.append(f"| {d['n']} | {d['phi']:g} | {d['nm']} | {d['tflops']:.3f} | {d['tensor_tops']:.1f} | {bits(d['err'])} |")
+    o.append("\n## SGEMM through Scheme II (bf16 tcgen05), n = 8192, phi = 0.5\n")
+    csg = {d["n"]: d for d in rows if d["path"] == "cublas_sgemm"}
+    o.append("| N_m | TFLOP/s | bits | x cuBLAS SGEMM (" + (f"{csg[8192]['tflops']:.1f} TFLOP/s, {bits(csg[8192].get('err'))} bits" if 8192 in csg else "-") + ") |\n|---|---|---|---|")
+    for d in rows:
+        if d["path"] == "emu_sgemm_II":
+            o.append(f"| {d['nm']} | {d['tflops']:.2f} | {bits(d['err'])} | {d['tflops'] / csg[8192]['tflops']:.2f}x |" if 8192 in csg else f"| {d['nm']} | {d['tflops']:.2f} | {bits(d['err'])} | - |")
+    o.append("\n## Scheme II on the INT8 mma.sync engine (EMU_II_ENGINE=mma), same inputs\n")
+    o.append("| n | phi | N_m | TFLOP/s | INT8 TOP/s | bits | bf16 tcgen05 speedup |\n|---|---|---|---|---|---|---|")
+    tc = {(d["phi"], d["nm"]): d["ms"] for d in rows if d["path"] == "emu_dgemm_II"}
+    for d in rows:
+        if d["path"] == "emu_dgemm_II_int8":
+            sp = d["ms"] / tc[(d["phi"], d["nm"])] if (d["phi"], d["nm"]) in tc else float("nan")
+            o.append(f"| {d['n']} | {d['phi']:g} | {d['nm']} | {d['tflops']:.3f} | {d['tensor_tops']:.1f} | {bits(d['err'])} | {sp:.2f}x |")
+    o.append("\n## Scheme II with norm-based scaling (EMU_SCHEME_II_NORM)\n")
+    o.append("| n | phi | N_m | TFLOP/s | tensor TOP/s | bits | bits, worst-case scaling |\n|---|---|---|---|---|---|---|")
+    worst = {(d["phi"], d["nm"]): d["err"] for d in rows if d["path"] == "emu_dgemm_II"}
+    for d in rows:
+        if d["path"] == "emu_dgemm_II_norm":
+            w = worst.get((d["phi"], d["nm"]))
+            o.append(f"| {d['n']} | {d['phi']:g} | {d['nm']} | {d['tflops']:.3f} | {d['tensor_tops']:.1f} | {bits(d['err'])} | {bits(w) if w is not None else '-'} |")
+    o.append("\n## Complex: ZGEMM (3M Scheme II, 4M Scheme I) and CGEMM, n = 8192, phi = 1\n")
+    o.append("| path | scheme | p / N_m | TFLOP/s (8MNK) | bits |\n|---|---|---|---|---|")
+    for d in rows:
+        if d["path"] == "emu_zgemm_3m":
+            o.append(f"| emu_zgemm | II (3M) | {d['nm']} | {d['tflops_8mnk']:.2f} | {bits(d['err'])} |")
+        if d["path"] == "emu_zgemm_4m":
+            o.append(f"| emu_zgemm | {d['scheme']} (4M) | {d['p']} | {d['tflops_8mnk']:.2f} | {bits(d['err'])} |")
+        if d["path"] == "emu_cgemm":
+            o.append(f"| emu_cgemm | {d['scheme']} ({'3M' if d['scheme']=='II' else '4M'}) | {d['p_or_nm']} | {d['tflops_8mnk']:.2f} | {bits(d['err'])} |")
+    o.append("\n## Naive (INT32 partials to HBM + separate shift-reduce) vs fused, n = 4096, k <= K_c\n")
+    o.append("`emu_partials_I` / `emu_partials_F8` + `emu_shift_reduce_I` against `emu_dgemm` (results")
+    o.append("bit-identical).\n")
+    o.append("| slices | p | naive ms | fused ms | fused speedup | INT32 partials bytes |\n|---|---|---|---|---|---|")
+    for d in rows:
+        if d["path"] == "ablation_naive_vs_fused":
+            o.append(f"| {'E4M3 (tcgen05)' if d['slices'] == 'e4m3' else 'INT8 (mma.sync)'} | {d['p']} | {d['ms_naive']:.2f} | "
+                     f"{d['ms_fused']:.2f} | {d['speedup_fused']:.2f} | {d['int32_partials_bytes']} |")
+    o.append("\n## Grouped: 512 uneven products (p = 6), one CUDA graph vs per-product loop\n")
+    for d in rows:
+        if d["path"] == "emu_dgemm_grouped":
+            o.append(f"graph (tuned tile) {d['ms_graph_tuned']:.2f} ms, default tile {d['ms_graph_default_tile']:.2f} ms, "
+                     f"loop {d['ms_loop']:.2f} ms: {d['speedup_graph_vs_loop']:.2f}x; {d['tflops_graph']:.2f} emulated "
+                     f"TFLOP/s, {d['int8_tops_graph']:.1f} INT8 TOP/s.")
+    return "\n".join(o)
+
+
 def run_suite(path, args):
     """Secondary measurements: every path of the library on one GPU, one JSON
     object per point (device-resident inputs, CUDA-event timing, 1 warm-up +
@@ -716,6 +807,9 @@ def run_suite(path, args):
 
 def main():
     args = parse()
+    if args.suite_md:
+        print(suite_markdown(args.suite_md))
+        return
     if args.suite:
         run_suite(args.suite, args)
         return
