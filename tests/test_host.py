@@ -110,3 +110,26 @@ def test_multirank_aggregation_gloo():
     assert out[0][0] == out[1][0] == 150.0
     expect = 2 * 2.0 * 8192 ** 3 * 5 / 0.150 / 1e12
     assert abs(out[0][1] - expect) < 1e-9 * expect
+
+
+def test_suite_markdown_tables(tmp_path):
+    # the summary of a --suite file: engine tables, speedups against the
+    # INT8 engine and against cuBLAS SGEMM, bits = -log2 of the sampled error
+    import json
+
+    import bench
+    rows = [
+        {"path": "cublas_sgemm", "n": 8192, "tflops": 70.0, "ms": 15.7, "err": 2.0 ** -22},
+        {"path": "emu_dgemm_II", "n": 8192, "phi": 0.5, "nm": 16, "tflops": 62.0, "engine": "bf16 tcgen05",
+         "tensor_tops": 992.0, "ms": 17.7, "err": 2.0 ** -56},
+        {"path": "emu_dgemm_II_int8", "n": 8192, "phi": 0.5, "nm": 16, "tflops": 8.7, "engine": "int8 mma.sync",
+         "tensor_tops": 139.0, "ms": 126.4, "err": 2.0 ** -56},
+        {"path": "emu_sgemm_II", "n": 8192, "phi": 0.5, "nm": 8, "tflops": 116.0, "tensor_tops": 928.0, "ms": 9.5,
+         "err": 2.0 ** -24},
+    ]
+    path = tmp_path / "s.jsonl"
+    path.write_text("".join(json.dumps(r) + "\n" for r in rows))
+    md = bench.suite_markdown(str(path))
+    assert "| 8192 | 0.5 | 16 | 62.000 | 992.0 | 56.0 |" in md
+    assert "| 8192 | 0.5 | 16 | 8.700 | 139.0 | 56.0 | 7.14x |" in md
+    assert "| 8 | 116.00 | 24.0 | 1.66x |" in md
