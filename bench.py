@@ -499,8 +499,8 @@ def suite_markdown(path):
 
     o = []
     o.append("# Measurement suite on one GB300 (all paths)\n")
-    o.append("Command: `python bench.py --suite gpurun_out/suite.jsonl`, then `python bench.py --suite-md")
-    o.append("gpurun_out/suite.jsonl > profiles/bench_suite_gb300.md` (device-resident inputs, CUDA events,")
+    o.append("Command: `python bench.py --suite suite.jsonl`, then `python bench.py --suite-md suite.jsonl")
+    o.append("> profiles/bench_suite_gb300.md` (device-resident inputs, CUDA events,")
     o.append("1 warm-up + 3 timed calls per point, 1 at n = 16384 and for ZGEMM; accuracy = -log2 of")
     o.append("max |C - C_ref| / (|A||B|) on 8 x 64 sampled entries against the double-double reference).")
     o.append("Slice-product rates count executed products x 2: Scheme I p(p+1)MNK (8-bit), Scheme II 2 N_m MNK and 3M")
