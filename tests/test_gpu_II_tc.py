@@ -159,3 +159,15 @@ def test_cluster_sizes(orc, tmp_path, cl):
     assert np.array_equal(r["C"], orc.emu_II(A, B, 14))
     Az, Bz = synth.gemm_pair_complex(140, 70, 1000, 1.0, 42)
     assert np.array_equal(r["Z"], orc.emu_Z3M(Az, Bz, 9))
+
+
+def test_zgemm_3m_sampled_rows_n4096(orc, h):
+    # many waves of 128 x 256 tiles over all 3 x 16 planes; the oracle computes
+    # row i of C from row i of A and all of B (the scales are per row / column)
+    n, nm = 4096, 16
+    A, B = synth.gemm_pair_complex(n, n, n, 1.0, 51)
+    C = emu.zgemm(dev(A), dev(B), nm=nm, handle=h)
+    torch.cuda.synchronize()
+    assert h.status() == 0
+    rows = [1, 3000]
+    assert np.array_equal(C[rows].cpu().numpy(), orc.emu_Z3M(A[rows], B, nm))
