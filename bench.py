@@ -569,6 +569,36 @@ def suite_markdown(path):
         if d["path"] == "ablation_naive_vs_fused":
             o.append(f"| {'E4M3 (tcgen05)' if d['slices'] == 'e4m3' else 'INT8 (mma.sync)'} | {d['p']} | {d['ms_naive']:.2f} | "
                      f"{d['ms_fused']:.2f} | {d['speedup_fused']:.2f} | {d['int32_partials_bytes']} |")
+    # Fig. 7 analogue: precision, throughput and workspace of every real DGEMM
+    # path at n = 8192, phi = 0.5 (workspace from the library's size query,
+    # default engines)
+    try:
+        import ctypes
+
+        import paper_2606_25453_gb300 as emu
+
+        def ws_gb(scheme, p):
+            sz = ctypes.c_size_t()
+            emu.check(emu.emu_workspace_size(scheme, 8192, 8192, 8192, p, 0, ctypes.byref(sz)), "workspace")
+            return sz.value / 2 ** 30
+        pts = []
+        for d in rows:
+            if d.get("n") != 8192 or d.get("phi") != 0.5:
+                continue
+            if d["path"] == "emu_dgemm_I":
+                pts.append(("Scheme I, INT8 (mma.sync)", "p = %d" % d["p"], d, ws_gb(emu.EMU_SCHEME_I, d["p"])))
+            elif d["path"] == "emu_dgemm_I_F8":
+                pts.append(("Scheme I, E4M3 (tcgen05)", "p = %d" % d["p"], d, ws_gb(emu.EMU_SCHEME_I_F8, d["p"])))
+            elif d["path"] == "emu_dgemm_II":
+                pts.append(("Scheme II (bf16 tcgen05)", "N = %d" % d["nm"], d, ws_gb(emu.EMU_SCHEME_II, d["nm"])))
+        if pts:
+            o.append("\n## Precision, throughput and workspace (n = 8192, phi = 0.5; the paper's Fig. 7 trade-off)\n")
+            o.append("| path | slices / moduli | bits | TFLOP/s | workspace GiB |\n|---|---|---|---|---|")
+            for name, par, d, gb in sorted(pts, key=lambda x: (-math.inf if x[2]["err"] == 0 else
+                                                                  -math.log2(x[2]["err"]))):
+                o.append(f"| {name} | {par} | {bits(d['err'])} | {d['tflops']:.2f} | {gb:.2f} |")
+    except ImportError:
+        pass
     o.append("\n## Grouped: 512 uneven products (p = 6), one CUDA graph vs per-product loop\n")
     for d in rows:
         if d["path"] == "emu_dgemm_grouped":
