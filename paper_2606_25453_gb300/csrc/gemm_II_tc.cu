@@ -54,6 +54,7 @@ constexpr int kBlkB = kBN * 128;
 constexpr int kStageBytes = kBlkA + kBlkB;
 constexpr int kStages = 4;
 constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
+constexpr int kPrefetch = 4;  // chunks ahead of the TMA loads that are prefetched into L2
 static_assert(kSmem <= 232448, "shared memory");
 
 struct KParamsIITC {
@@ -85,6 +86,14 @@ __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint6
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
+}
+
+// Hint: bring a 2D box of the tensor into L2 (no shared memory involved).
+__device__ __forceinline__ void tma_prefetch_l2(const void* desc, int x, int y) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                   reinterpret_cast<uint64_t>(desc)),
+               "r"(x), "r"(y)
+               : "memory");
 }
 
 // 16 consecutive 32-bit TMEM columns of this thread's lane.
@@ -201,7 +210,24 @@ __global__ void __launch_bounds__(kThreads, 1)
         item_coords(kp, cid + t * ncl, crank, p, tm, tn);
         const int ya = p * kp.rowsA_pad + tm * kBM;
         const int yb = p * kp.rowsB_pad + tn * kBN;
+        int pya = 0, pyb = 0;  // the next item's rows, for prefetches that run past this item's K
+        if (t + 1 < my_items) {
+          int p2, tm2, tn2;
+          item_coords(kp, cid + (t + 1) * ncl, crank, p2, tm2, tn2);
+          pya = p2 * kp.rowsA_pad + tm2 * kBM;
+          pyb = p2 * kp.rowsB_pad + tn2 * kBN + crank * piece_rows;
+        }
         for (int ks = 0; ks < kp.nst; ++ks, ++j) {
+          {  // warm L2 with the chunk kPrefetch steps ahead (this CTA's share of B)
+            const int kf = ks + kPrefetch;
+            if (kf < kp.nst) {
+              tma_prefetch_l2(&kp.tA, kf * 128, ya);
+              tma_prefetch_l2(&kp.tB, kf * 128, yb + crank * piece_rows);
+            } else if (t + 1 < my_items && kf - kp.nst < kp.nst) {
+              tma_prefetch_l2(&kp.tA, (kf - kp.nst) * 128, pya);
+              tma_prefetch_l2(&kp.tB, (kf - kp.nst) * 128, pyb);
+            }
+          }
           const uint32_t stage = j % kStages;
           if (j >= static_cast<uint32_t>(kStages) &&
               !wait_or_abort(&empty[stage], ((j / kStages) & 1u) ^ 1u, abort_flag, kp.status)) {
