@@ -104,6 +104,134 @@ __global__ void scan_kernel(const T* __restrict__ X, int64_t ld, int64_t rows, i
   }
 }
 
+// The same scan with 16-byte loads, for operands whose vectors start on
+// 16-byte boundaries (base and leading dimension aligned).  A uint4 holds
+// S = 16 / sizeof(T) scalars, CV = S / cw vectors of the strided layout.
+// Float magnitudes are compared on their own bit patterns and the largest
+// is widened once (widening is exact and monotone, so the result is the
+// same as that of the scalar scan).
+template <typename T>
+__device__ __forceinline__ uint64_t widen_absbits(uint64_t b);
+template <>
+__device__ __forceinline__ uint64_t widen_absbits<double>(uint64_t b) {
+  return b;
+}
+template <>
+__device__ __forceinline__ uint64_t widen_absbits<float>(uint64_t b) {
+  return dbits(static_cast<double>(__uint_as_float(static_cast<uint32_t>(b))));
+}
+// |scalar j| of a uint4 as unsigned bits of T's width (sign cleared)
+template <typename T>
+__device__ __forceinline__ uint64_t lane_absbits(const uint4& v, int j) {
+  if constexpr (sizeof(T) == 8) {
+    const uint32_t lo = j == 0 ? v.x : v.z, hi = j == 0 ? v.y : v.w;
+    return ((static_cast<uint64_t>(hi) << 32) | lo) & 0x7FFFFFFFFFFFFFFFull;
+  } else {
+    const uint32_t w = j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
+    return w & 0x7FFFFFFFu;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ uint64_t scalar_absbits(T x) {
+  if constexpr (sizeof(T) == 8)
+    return dbits(x) & 0x7FFFFFFFFFFFFFFFull;
+  else
+    return __float_as_uint(x) & 0x7FFFFFFFu;
+}
+
+template <typename T, bool KCONTIG>
+__global__ void scan_vec_kernel(const T* __restrict__ X, int64_t ld, int64_t rows, int64_t k, int cw,
+                                unsigned long long* __restrict__ maxbits, int* status) {
+  constexpr int S = 16 / static_cast<int>(sizeof(T));
+  if (KCONTIG) {
+    // one warp per (row, segment of 2048 scalars); lane l loads uint4 l, l + 32, ...
+    const int lane = threadIdx.x & 31;
+    const int64_t r = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= rows) return;
+    const int64_t len = k * cw, h0 = static_cast<int64_t>(blockIdx.y) * 2048;
+    const int64_t h1 = h0 + 2048 < len ? h0 + 2048 : len;
+    const T* row = X + r * ld * cw;
+    const int64_t nv = (h1 - h0) / S;
+    const uint4* pv = reinterpret_cast<const uint4*>(row + h0);
+    uint64_t mx = 0;
+#pragma unroll 4
+    for (int64_t i = lane; i < nv; i += 32) {
+      const uint4 v = __ldg(pv + i);
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        const uint64_t a = lane_absbits<T>(v, j);
+        mx = a > mx ? a : mx;
+      }
+    }
+    for (int64_t h = h0 + nv * S + lane; h < h1; h += 32) {  // ragged end of the row
+      const uint64_t a = scalar_absbits<T>(__ldg(row + h));
+      mx = a > mx ? a : mx;
+    }
+    for (int o = 16; o; o >>= 1) {
+      const uint64_t w = __shfl_xor_sync(0xffffffffu, mx, o);
+      mx = w > mx ? w : mx;
+    }
+    if (lane == 0 && h0 < h1) {
+      mx = widen_absbits<T>(mx);
+      atomicMax(maxbits + r, static_cast<unsigned long long>(mx));
+      if (mx >= 0x7FF0000000000000ull) set_status(status, ST_NONFINITE);
+    }
+  } else {
+    // block 32 x 8: lane x loads the CV vectors x*CV .. x*CV + CV - 1 of a
+    // block of 32*CV vectors (512 contiguous bytes per warp and K row);
+    // the 8 row-groups split a K segment of 256
+    const int cv = S / cw;
+    const int64_t rb = static_cast<int64_t>(blockIdx.x) * 32 * cv;
+    const int64_t r = rb + static_cast<int64_t>(threadIdx.x) * cv;
+    const int64_t h0 = static_cast<int64_t>(blockIdx.y) * 256;
+    const int64_t h1 = h0 + 256 < k ? h0 + 256 : k;
+    uint64_t mx[4] = {0, 0, 0, 0};
+    if (r + cv <= rows) {
+#pragma unroll 4
+      for (int64_t h = h0 + threadIdx.y; h < h1; h += 8) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(X + (h * ld + r) * cw));
+#pragma unroll
+        for (int j = 0; j < S; ++j) {  // scalar j belongs to vector j / cw (cw is 1 or 2)
+          const uint64_t a = lane_absbits<T>(v, j);
+          if (cw == 2)
+            mx[j >> 1] = a > mx[j >> 1] ? a : mx[j >> 1];
+          else
+            mx[j] = a > mx[j] ? a : mx[j];
+        }
+      }
+    } else if (r < rows) {  // the last vectors of the operand: scalar loads
+      for (int64_t h = h0 + threadIdx.y; h < h1; h += 8) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          if (c < cv && r + c < rows) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+              if (q < cw) {
+                const uint64_t a = scalar_absbits<T>(__ldg(X + (h * ld + r + c) * cw + q));
+                mx[c] = a > mx[c] ? a : mx[c];
+              }
+            }
+          }
+        }
+      }
+    }
+    __shared__ uint64_t red[8][32 * 4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      if (c < cv) red[threadIdx.y][threadIdx.x * cv + c] = mx[c];
+    __syncthreads();
+    const int t = threadIdx.y * 32 + threadIdx.x;
+    if (t < 32 * cv && rb + t < rows && h0 < h1) {
+      uint64_t m = red[0][t];
+      for (int q = 1; q < 8; ++q) m = red[q][t] > m ? red[q][t] : m;
+      m = widen_absbits<T>(m);
+      atomicMax(maxbits + rb + t, static_cast<unsigned long long>(m));
+      if (m >= 0x7FF0000000000000ull) set_status(status, ST_NONFINITE);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ norm scan
 // Norm-based Scheme II scaling: e_r with ||x_r||_2 < 2^e_r, computed exactly
 // so that the value does not depend on the summation order.  With E the
@@ -312,33 +440,44 @@ __device__ __forceinline__ int sym_residue(const int* d, const ModTables& mt, in
   return r;
 }
 
-// The same in binary32 for the bf16 planes: 14-bit digits of |a'| (six
-// cover 2^84), negated for a negative element.  Every partial sum of
+// The same in binary32 for the bf16 planes: the ND lowest 14-bit digits of
+// |a'|, negated for a negative element (|a'| < 2^b, so ND = ceil(b / 14),
+// rounded up to 2, 4 or 6, covers it; six cover 2^84).  Every partial sum of
 // t = sum_j d_j c_j is an integer with |t| <= 16383 (1 + 5 * 128) < 2^24, so
 // the FMA chain is exact; q = floor(RN(t / m + off / m)) is floor((t + off)
 // / m) or one off, r = t - q m is exact (|r| < 2^24), and one correction each
 // way gives the symmetric residue -- all on the FP32 pipe.
+template <int ND>
 __device__ __forceinline__ void digits14f(uint64_t bits, int shift, float* d) {
   const ScaledInt s = scaled_trunc_bits(bits, shift);
-  // s.mag 2^s.lsh = |a'| < 2^80 (the row exponent bounds every element), so s.lsh < 80
-  const unsigned __int128 v = static_cast<unsigned __int128>(s.mag) << s.lsh;
-  const uint64_t lo = static_cast<uint64_t>(v);
-  const uint64_t hi = static_cast<uint64_t>(v >> 64);
   const uint32_t sg = static_cast<uint32_t>(bits >> 63) << 31;
-  const uint32_t dg[kResDigitsF] = {static_cast<uint32_t>(lo & 0x3FFFu), static_cast<uint32_t>((lo >> 14) & 0x3FFFu),
-                                    static_cast<uint32_t>((lo >> 28) & 0x3FFFu),
-                                    static_cast<uint32_t>((lo >> 42) & 0x3FFFu),
-                                    static_cast<uint32_t>(((lo >> 56) | (hi << 8)) & 0x3FFFu),
-                                    static_cast<uint32_t>((hi >> 6) & 0x3FFFu)};
+  uint32_t dg[ND];
+  if constexpr (ND <= 4) {  // |a'| < 2^(14 ND) <= 2^56: one 64-bit word holds it
+    const uint64_t v = s.lsh < 64 ? s.mag << s.lsh : 0ull;
 #pragma unroll
-  for (int j = 0; j < kResDigitsF; ++j)  // 2^23 + d has d in its low mantissa bits; the sign by bit
+    for (int j = 0; j < ND; ++j) dg[j] = static_cast<uint32_t>(v >> (14 * j)) & 0x3FFFu;
+  } else {
+    // s.mag 2^s.lsh = |a'| < 2^80 (the row exponent bounds every element), so s.lsh < 80
+    const unsigned __int128 v = static_cast<unsigned __int128>(s.mag) << s.lsh;
+    const uint64_t lo = static_cast<uint64_t>(v);
+    const uint64_t hi = static_cast<uint64_t>(v >> 64);
+    dg[0] = static_cast<uint32_t>(lo & 0x3FFFu);
+    dg[1] = static_cast<uint32_t>((lo >> 14) & 0x3FFFu);
+    dg[2] = static_cast<uint32_t>((lo >> 28) & 0x3FFFu);
+    dg[3] = static_cast<uint32_t>((lo >> 42) & 0x3FFFu);
+    dg[4] = static_cast<uint32_t>(((lo >> 56) | (hi << 8)) & 0x3FFFu);
+    dg[5] = static_cast<uint32_t>((hi >> 6) & 0x3FFFu);
+  }
+#pragma unroll
+  for (int j = 0; j < ND; ++j)  // 2^23 + d has d in its low mantissa bits; the sign by bit
     d[j] = __uint_as_float(__float_as_uint(__uint_as_float(0x4B000000u | dg[j]) - 8388608.0f) | sg);
 }
 
+template <int ND>
 __device__ __forceinline__ float sym_residue_f(const float* d, const ModTables& mt, int l) {
   float t = d[0];
 #pragma unroll
-  for (int j = 1; j < kResDigitsF; ++j) t = __fmaf_rn(d[j], mt.pow14f[l][j], t);
+  for (int j = 1; j < ND; ++j) t = __fmaf_rn(d[j], mt.pow14f[l][j], t);
   const float m = mt.mf[l], off = mt.offf[l];
   const float q = floorf(__fmaf_rn(t, mt.inv[l], mt.offinv[l]));
   float r = __fmaf_rn(-q, m, t);
@@ -383,15 +522,15 @@ __device__ __forceinline__ void store4f(int8_t* p, float r0, float r1, float r2,
   *reinterpret_cast<uint2*>(p) = make_uint2(__byte_perm(f0, f1, 0x7632u), __byte_perm(f2, f3, 0x7632u));
 }
 
-template <int CW, bool BF>
+template <int CW, bool BF, int ND>
 __device__ __forceinline__ void residues4(const ModTables& mt, int nm, int shift, const uint64_t* re,
                                           const uint64_t* im, int64_t plane, int8_t* base) {
   if constexpr (BF) {  // bf16 planes: the binary32 form
-    float dr[4][kResDigitsF], di[CW == 2 ? 4 : 1][kResDigitsF];
+    float dr[4][ND], di[CW == 2 ? 4 : 1][ND];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      digits14f(re[q], shift, dr[q]);
-      if (CW == 2) digits14f(im[q], shift, di[q]);
+      digits14f<ND>(re[q], shift, dr[q]);
+      if (CW == 2) digits14f<ND>(im[q], shift, di[q]);
     }
 #pragma unroll
     for (int l = 0; l < kMaxModuli; ++l) {
@@ -399,9 +538,9 @@ __device__ __forceinline__ void residues4(const ModTables& mt, int nm, int shift
       float rr[4], ri[4], rs[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        rr[q] = sym_residue_f(dr[q], mt, l);
+        rr[q] = sym_residue_f<ND>(dr[q], mt, l);
         if (CW == 2) {
-          ri[q] = sym_residue_f(di[q], mt, l);
+          ri[q] = sym_residue_f<ND>(di[q], mt, l);
           const float m = mt.mf[l], off = mt.offf[l];
           float v = rr[q] + ri[q];
           if (v < -off) v += m;
@@ -455,7 +594,7 @@ __device__ __forceinline__ void residues4(const ModTables& mt, int nm, int shift
 // (vector, 128 K-elements), lane l takes elements 4l .. 4l+3 and writes one
 // word per plane; strided sources go through a shared-memory tile of 32
 // vectors (16 for complex) x 128 elements as in the Scheme I split.
-template <typename T, int CW, bool BF>
+template <typename T, int CW, bool BF, int ND>
 __global__ void split_II_kcontig(const T* __restrict__ X, int64_t ld, int64_t rows, int64_t k, int64_t rows_pad,
                                  int64_t kpad, int nm, int b, const __grid_constant__ ModTables mt,
                                  const unsigned long long* __restrict__ maxbits, const int32_t* __restrict__ Ein,
@@ -474,11 +613,11 @@ __global__ void split_II_kcontig(const T* __restrict__ X, int64_t ld, int64_t ro
     re[q] = valid ? load_bits(p) : 0ull;
     im[q] = (CW == 2 && valid) ? load_bits(p + 1) : 0ull;
   }
-  residues4<CW, BF>(mt, nm, b - E, re, im, rows_pad * kpad * (BF ? 2 : 1), res + (r * kpad + h0) * (BF ? 2 : 1));
+  residues4<CW, BF, ND>(mt, nm, b - E, re, im, rows_pad * kpad * (BF ? 2 : 1), res + (r * kpad + h0) * (BF ? 2 : 1));
   if (h0 == 0 && r < rows && E_out) E_out[r] = E;
 }
 
-template <typename T, int CW, bool BF>
+template <typename T, int CW, bool BF, int ND>
 __global__ void __launch_bounds__(256) split_II_kstrided(const T* __restrict__ X, int64_t ld, int64_t rows, int64_t k,
                                                          int64_t rows_pad, int64_t kpad, int nm, int b,
                                                          const __grid_constant__ ModTables mt,
@@ -514,7 +653,7 @@ __global__ void __launch_bounds__(256) split_II_kstrided(const T* __restrict__ X
         im[q] = CW == 2 ? tim[rl][q * 33 + lane] : 0ull;
       }
       const int64_t h0 = hbase + lane * 4;
-      residues4<CW, BF>(mt, nm, b - E, re, im, rows_pad * kpad * (BF ? 2 : 1), res + (r * kpad + h0) * (BF ? 2 : 1));
+      residues4<CW, BF, ND>(mt, nm, b - E, re, im, rows_pad * kpad * (BF ? 2 : 1), res + (r * kpad + h0) * (BF ? 2 : 1));
       if (h0 == 0 && r < rows && E_out) E_out[r] = E;
     }
   }
@@ -526,10 +665,20 @@ void launch_scan(const T* X, int64_t ld, bool kcontig, int64_t rows, int64_t k, 
                  unsigned long long* maxbits, int* status, cudaStream_t st) {
   cudaMemsetAsync(maxbits, 0, sizeof(unsigned long long) * (rows > 0 ? rows : 1), st);
   if (rows == 0 || k == 0) return;
+  // 16-byte loads when every vector starts on a 16-byte boundary
+  const bool vec = (reinterpret_cast<uintptr_t>(X) & 15u) == 0 &&
+                   (static_cast<uint64_t>(ld) * cw * sizeof(T)) % 16 == 0;
   if (kcontig) {
     int64_t len = k * cw;
     dim3 grid(static_cast<unsigned>((rows + 7) / 8), static_cast<unsigned>((len + 2047) / 2048));
-    scan_kernel<T, true><<<grid, 256, 0, st>>>(X, ld, rows, k, cw, maxbits, status);
+    if (vec)
+      scan_vec_kernel<T, true><<<grid, 256, 0, st>>>(X, ld, rows, k, cw, maxbits, status);
+    else
+      scan_kernel<T, true><<<grid, 256, 0, st>>>(X, ld, rows, k, cw, maxbits, status);
+  } else if (vec) {
+    const int64_t per_block = 32 * static_cast<int64_t>(16 / sizeof(T)) / cw;
+    dim3 grid(static_cast<unsigned>((rows + per_block - 1) / per_block), static_cast<unsigned>((k + 255) / 256));
+    scan_vec_kernel<T, false><<<grid, dim3(32, 8), 0, st>>>(X, ld, rows, k, cw, maxbits, status);
   } else {
     dim3 grid(static_cast<unsigned>((rows + 31) / 32), static_cast<unsigned>((k + 255) / 256));
     scan_kernel<T, false><<<grid, dim3(32, 8), 0, st>>>(X, ld, rows, k, cw, maxbits, status);
@@ -587,11 +736,14 @@ void launch_split_II(const T* X, int64_t ld, bool kcontig, int64_t rows, int64_t
                      int32_t* E, cudaStream_t st, const int32_t* Ein, bool bf16) {
   const int64_t rows_pad = split_rows(rows), kpad = split_cols_II(k);
   if (rows_pad == 0 || kpad == 0) return;
-#define EMU_SPLIT_II(KERNEL, GRID, CW)                                                                        \
-  (bf16 ? KERNEL<T, CW, true><<<GRID, 256, 0, st>>>(X, ld, rows, k, rows_pad, kpad, nm, b, tabs, maxbits, Ein, \
-                                                    res, E)                                                   \
-        : KERNEL<T, CW, false><<<GRID, 256, 0, st>>>(X, ld, rows, k, rows_pad, kpad, nm, b, tabs, maxbits, Ein, \
-                                                     res, E))
+  // 14-bit digits that hold |a'| < 2^b (bf16 planes; the INT8 form has its own)
+  const int nd = b <= 28 ? 2 : b <= 56 ? 4 : 6;
+#define EMU_SPLIT_II_ARGS X, ld, rows, k, rows_pad, kpad, nm, b, tabs, maxbits, Ein, res, E
+#define EMU_SPLIT_II(KERNEL, GRID, CW)                                             \
+  (!bf16      ? KERNEL<T, CW, false, 6><<<GRID, 256, 0, st>>>(EMU_SPLIT_II_ARGS) \
+   : nd == 2 ? KERNEL<T, CW, true, 2><<<GRID, 256, 0, st>>>(EMU_SPLIT_II_ARGS)  \
+   : nd == 4 ? KERNEL<T, CW, true, 4><<<GRID, 256, 0, st>>>(EMU_SPLIT_II_ARGS)  \
+             : KERNEL<T, CW, true, 6><<<GRID, 256, 0, st>>>(EMU_SPLIT_II_ARGS))
   if (kcontig) {
     const int64_t warps = rows_pad * (kpad / 128);
     const unsigned blocks = static_cast<unsigned>((warps + 7) / 8);
@@ -608,6 +760,7 @@ void launch_split_II(const T* X, int64_t ld, bool kcontig, int64_t rows, int64_t
       EMU_SPLIT_II(split_II_kstrided, grid, 1);
   }
 #undef EMU_SPLIT_II
+#undef EMU_SPLIT_II_ARGS
 }
 
 template <typename T>
