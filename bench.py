@@ -55,9 +55,13 @@ def parse():
     ap.add_argument("--cpu-rows", type=int, default=96, help="rows of C in the CPU oracle sample")
     ap.add_argument("--no-extras", action="store_true", help="skip cuBLAS / accuracy / CPU legs")
     ap.add_argument("--suite", default=None, help="write the secondary measurements (all paths) to this JSONL file")
-    ap.add_argument("--suite-md", default=None, help="print the summary tables of a --suite JSONL file")
-    ap.add_argument("--suite-part", default="all", choices=["all", "ii"],
-                    help="ii: only the Scheme II points (run in a child with EMU_II_ENGINE=mma by the full suite)")
+    ap.add_argument("--suite-md", default=None, nargs="+",
+                    help="print the summary tables of --suite JSONL files (rows of later files replace the "
+                         "matching rows of earlier ones)")
+    ap.add_argument("--suite-part", default="all", choices=["all", "ii", "scheme2"],
+                    help="ii: only the Scheme II DGEMM points (run in a child with EMU_II_ENGINE=mma by the full "
+                         "suite); scheme2: every row of the bf16 tcgen05 Scheme II paths (DGEMM, SGEMM, norm "
+                         "scaling, ZGEMM 3M, CGEMM 3M)")
     return ap.parse_args()
 
 
@@ -488,18 +492,32 @@ def run_ours(args, rank, world, local_rank):
 
 
 # ------------------------------------------------------------------ suite
-def suite_markdown(path):
-    """The summary tables of a --suite JSONL file (the text of
-    profiles/bench_suite_gb300.md)."""
+def suite_key(d):
+    """What a suite row measures (path and parameters), without its results."""
+    return tuple((f, d.get(f)) for f in ("path", "scheme", "n", "phi", "p", "nm", "p_or_nm", "count"))
+
+
+def suite_markdown(paths):
+    """The summary tables of --suite JSONL files (the text of
+    profiles/bench_suite_gb300.md); a row of a later file replaces the row
+    of an earlier file that measures the same path and parameters."""
     import math
-    rows = [json.loads(line) for line in open(path)]
+    if isinstance(paths, str):
+        paths = [paths]
+    merged = {}
+    for path in paths:
+        for line in open(path):
+            d = json.loads(line)
+            merged[suite_key(d)] = d
+    rows = list(merged.values())
 
     def bits(e):
         return "-" if e is None else ("inf" if e == 0 else f"{-math.log2(e):.1f}")
 
     o = []
     o.append("# Measurement suite on one GB300 (all paths)\n")
-    o.append("Command: `python bench.py --suite suite.jsonl`, then `python bench.py --suite-md suite.jsonl")
+    o.append("Command: `python bench.py --suite suite.jsonl`, then `python bench.py --suite-md suite.jsonl"
+             + "".join(" " + os.path.basename(x) for x in paths[1:]))
     o.append("> profiles/bench_suite_gb300.md` (device-resident inputs, CUDA events,")
     o.append("1 warm-up + 3 timed calls per point, 1 at n = 16384 and for ZGEMM; accuracy = -log2 of")
     o.append("max |C - C_ref| / (|A||B|) on 8 x 64 sampled entries against the double-double reference).")
@@ -508,6 +526,11 @@ def suite_markdown(path):
     o.append("Measured INT8 peak of this GPU: 150-156 TOP/s (cuBLASLt INT8 GEMM; register-only mma.sync s8 loop")
     o.append("150.9).  FP8 tensor peak: 3789 TFLOP/s (measured bf16 1894.5 x 2, the recipe's derivation);")
     o.append("ncu reports 4.87 POP/s at 2.07 GHz.\n")
+    for extra in paths[1:]:
+        o.append(f"Rows re-measured later with `python bench.py --suite {os.path.basename(extra)} --suite-part scheme2`")
+        o.append("(every row of the bf16 tcgen05 Scheme II paths) replace the matching rows of the full run.  The")
+        o.append("products are bit-identical; the sampler draws its 8 x 64 entries in call order, so those rows'")
+        o.append("bits come from other entries, which moves the phi = 4 figures by up to several bits.\n")
     o.append("## Native cuBLAS on the same GPU\n")
     o.append("| routine | n | TFLOP/s | bits |\n|---|---|---|---|")
     for d in rows:
@@ -682,9 +705,10 @@ def run_suite(path, args):
         out.close()
         h.close()
         return
+    every = args.suite_part == "all"  # scheme2: only the rows of the bf16 tcgen05 Scheme II paths
 
     # cuBLAS references on this GPU
-    for n in (4096, 8192):
+    for n in (4096, 8192) if every else ():
         A, B, Ad, Bd = pair(n, 0.5)
         ms = timed(lambda: Ad @ Bd, reps=2)
         C = (Ad @ Bd).cpu().numpy()
@@ -695,7 +719,7 @@ def run_suite(path, args):
               "err": sampled_err(A.astype(np.float32).astype(np.float64), B.astype(np.float32).astype(np.float64),
                                  (Af @ Bf).cpu().numpy().astype(np.float64))})
     # Scheme I DGEMM: p sweep, phi sweep
-    for n in (4096, 8192):
+    for n in (4096, 8192) if every else ():
         for phi in (0.5, 2.0, 4.0):
             A, B, Ad, Bd = pair(n, phi)
             Cd = torch.empty((n, n), dtype=torch.float64, device=dev)
@@ -705,20 +729,22 @@ def run_suite(path, args):
                       "int8_tops": p * (p + 1) * n ** 3 / ms / 1e9, "ms": ms,
                       "err": sampled_err(A, B, Cd.cpu().numpy())})
     n = 16384
-    A, B = synth.gemm_pair(n, n, n, 0.5, 7)
-    Ad, Bd = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
-    Cd = torch.empty((n, n), dtype=torch.float64, device=dev)
-    for p in (7, 8):
+    if every:
+        A, B = synth.gemm_pair(n, n, n, 0.5, 7)
+        Ad, Bd = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+        Cd = torch.empty((n, n), dtype=torch.float64, device=dev)
+    for p in (7, 8) if every else ():
         ms = timed(lambda: emu.dgemm(Ad, Bd, Cd, scheme="I", p=p, handle=h), reps=1)
         emit({"path": "emu_dgemm_I", "n": n, "phi": 0.5, "p": p, "tflops": 2 * n ** 3 / ms / 1e9,
               "int8_tops": p * (p + 1) * n ** 3 / ms / 1e9, "ms": ms, "err": sampled_err(A, B, Cd.cpu().numpy())})
     # Scheme I on E4M3 slices (tcgen05 kernel)
-    for p in (8, 10, 11, 12):
+    for p in (8, 10, 11, 12) if every else ():
         ms = timed(lambda: emu.dgemm(Ad, Bd, Cd, scheme="I_F8", p=p, handle=h), reps=1)
         emit({"path": "emu_dgemm_I_F8", "n": n, "phi": 0.5, "p": p, "tflops": 2 * n ** 3 / ms / 1e9,
               "f8_tops": p * (p + 1) * n ** 3 / ms / 1e9, "ms": ms, "err": sampled_err(A, B, Cd.cpu().numpy())})
-    del Ad, Bd, Cd
-    for n in (4096, 8192):
+    if every:
+        del Ad, Bd, Cd
+    for n in (4096, 8192) if every else ():
         for phi in (0.5, 4.0):
             A, B, Ad, Bd = pair(n, phi)
             Cd = torch.empty((n, n), dtype=torch.float64, device=dev)
@@ -729,8 +755,9 @@ def run_suite(path, args):
                       "err": sampled_err(A, B, Cd.cpu().numpy())})
     # naive (INT32 partials to HBM + separate shift-reduce) vs fused, k <= K_c
     n = 4096
-    A, B, Ad, Bd = pair(n, 0.5)
-    for f8, p in ((False, 8), (True, 11)):
+    if every:
+        A, B, Ad, Bd = pair(n, 0.5)
+    for f8, p in ((False, 8), (True, 11)) if every else ():
         _, EA = emu.split_I(Ad, p, operand=0, handle=h, f8=f8)
         _, FB = emu.split_I(Bd, p, operand=1, handle=h, f8=f8)
         Cn = torch.empty((n, n), dtype=torch.float64, device=dev)
@@ -746,7 +773,7 @@ def run_suite(path, args):
               "ms_naive": ms_naive, "ms_fused": ms_fused, "speedup_fused": ms_naive / ms_fused,
               "int32_partials_bytes": 4 * p * n * n, "bit_identical": bool(torch.equal(Cn, Cf))})
     # Scheme I SGEMM
-    for p in (3, 4):
+    for p in (3, 4) if every else ():
         A, B, Ad, Bd = pair(8192, 0.5, np.float32)
         Cd = torch.empty((8192, 8192), dtype=torch.float32, device=dev)
         ms = timed(lambda: emu.sgemm(Ad, Bd, Cd, scheme="I", p=p, handle=h))
@@ -764,15 +791,16 @@ def run_suite(path, args):
     scheme_II_points()
     engine = "int8 mma.sync" if os.environ.get("EMU_II_ENGINE") == "mma" else "bf16 tcgen05"
     import tempfile
-    with tempfile.NamedTemporaryFile(suffix=".jsonl", delete=False) as tf:
-        child_path = tf.name
-    subprocess.run([sys.executable, os.path.abspath(__file__), "--suite", child_path, "--suite-part", "ii"],
-                   env=dict(os.environ, EMU_II_ENGINE="mma"), check=True, stdout=subprocess.DEVNULL)
-    for line in open(child_path):
-        d = json.loads(line)
-        d["path"] = "emu_dgemm_II_int8"
-        emit(d)
-    os.unlink(child_path)
+    if every:
+        with tempfile.NamedTemporaryFile(suffix=".jsonl", delete=False) as tf:
+            child_path = tf.name
+        subprocess.run([sys.executable, os.path.abspath(__file__), "--suite", child_path, "--suite-part", "ii"],
+                       env=dict(os.environ, EMU_II_ENGINE="mma"), check=True, stdout=subprocess.DEVNULL)
+        for line in open(child_path):
+            d = json.loads(line)
+            d["path"] = "emu_dgemm_II_int8"
+            emit(d)
+        os.unlink(child_path)
     # Scheme II with norm-based scaling: bits and speed at the same N_m
     for phi in (0.5, 4.0):
         A, B, Ad, Bd = pair(8192, phi)
@@ -787,9 +815,10 @@ def run_suite(path, args):
     n = 8192
     A, B = synth.gemm_pair_complex(n, n, n, 1.0, 7)
     Ad, Bd = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
-    ms = timed(lambda: Ad @ Bd, reps=1)
-    emit({"path": "cublas_zgemm", "n": n, "tflops_8mnk": 8 * n ** 3 / ms / 1e9, "ms": ms,
-          "err": sampled_err(A, B, (Ad @ Bd).cpu().numpy(), True)})
+    if every:
+        ms = timed(lambda: Ad @ Bd, reps=1)
+        emit({"path": "cublas_zgemm", "n": n, "tflops_8mnk": 8 * n ** 3 / ms / 1e9, "ms": ms,
+              "err": sampled_err(A, B, (Ad @ Bd).cpu().numpy(), True)})
     Cd = torch.empty((n, n), dtype=torch.complex128, device=dev)
     for nm in (12, 16, 20):
         ms = timed(lambda: emu.zgemm(Ad, Bd, Cd, nm=nm, handle=h), reps=1)
@@ -797,22 +826,27 @@ def run_suite(path, args):
               "tflops_2mnk": 2 * n ** 3 / ms / 1e9, "tensor_tops": 6 * nm * n ** 3 / ms / 1e9, "engine": engine, "ms": ms,
               "err": sampled_err(A, B, Cd.cpu().numpy(), True)})
     # ZGEMM 4M (Scheme I)
-    for sc, p in (("I", 8), ("I_F8", 11), ("I_F8", 12)):
+    for sc, p in (("I", 8), ("I_F8", 11), ("I_F8", 12)) if every else ():
         ms = timed(lambda: emu.zgemm(Ad, Bd, Cd, scheme=sc, p=p, handle=h), reps=1)
         emit({"path": "emu_zgemm_4m", "scheme": sc, "n": n, "phi": 1.0, "p": p, "tflops_8mnk": 8 * n ** 3 / ms / 1e9,
               "tflops_2mnk": 2 * n ** 3 / ms / 1e9, "ms": ms, "err": sampled_err(A, B, Cd.cpu().numpy(), True)})
     # CGEMM (complex64): cuBLAS, Scheme I 4M, Scheme II 3M
     Af, Bf = Ad.to(torch.complex64), Bd.to(torch.complex64)
     A32, B32 = A.astype(np.complex64).astype(np.complex128), B.astype(np.complex64).astype(np.complex128)
-    ms = timed(lambda: Af @ Bf, reps=2)
-    emit({"path": "cublas_cgemm", "n": n, "tflops_8mnk": 8 * n ** 3 / ms / 1e9, "ms": ms,
-          "err": sampled_err(A32, B32, (Af @ Bf).cpu().numpy().astype(np.complex128), True)})
+    if every:
+        ms = timed(lambda: Af @ Bf, reps=2)
+        emit({"path": "cublas_cgemm", "n": n, "tflops_8mnk": 8 * n ** 3 / ms / 1e9, "ms": ms,
+              "err": sampled_err(A32, B32, (Af @ Bf).cpu().numpy().astype(np.complex128), True)})
     Cf = torch.empty((n, n), dtype=torch.complex64, device=dev)
-    for sc, p in (("I", 4), ("I_F8", 6), ("II", 8), ("II", 10)):
+    for sc, p in (("I", 4), ("I_F8", 6), ("II", 8), ("II", 10)) if every else (("II", 8), ("II", 10)):
         ms = timed(lambda: emu.cgemm(Af, Bf, Cf, scheme=sc, p=p, handle=h), reps=2)
         emit({"path": "emu_cgemm", "scheme": sc, "n": n, "p_or_nm": p, "tflops_8mnk": 8 * n ** 3 / ms / 1e9,
               "ms": ms, "err": sampled_err(A32, B32, Cf.cpu().numpy().astype(np.complex128), True)})
     del Ad, Bd, Cd, Af, Bf, Cf
+    if not every:
+        out.close()
+        h.close()
+        return
     # grouped: 512 uneven products, graph vs per-product loop
     shapes = synth.grouped_shapes(512, 0)
     As, Bs, Cs = [], [], []

@@ -133,3 +133,10 @@ def test_suite_markdown_tables(tmp_path):
     assert "| 8192 | 0.5 | 16 | 62.000 | 992.0 | 56.0 |" in md
     assert "| 8192 | 0.5 | 16 | 8.700 | 139.0 | 56.0 | 7.14x |" in md
     assert "| 8 | 116.00 | 24.0 | 1.66x |" in md
+    # a later file (a --suite-part scheme2 run) replaces the matching rows only
+    later = tmp_path / "s2.jsonl"
+    later.write_text(json.dumps(dict(rows[1], tflops=64.0, ms=17.2, tensor_tops=1023.0)) + "\n")
+    md2 = bench.suite_markdown([str(path), str(later)])
+    assert "| 8192 | 0.5 | 16 | 64.000 | 1023.0 | 56.0 |" in md2 and "| 8192 | 0.5 | 16 | 62.000 |" not in md2
+    assert "| 8192 | 0.5 | 16 | 8.700 | 139.0 | 56.0 | 7.35x |" in md2  # against the replaced row
+    assert "| 8 | 116.00 | 24.0 | 1.66x |" in md2 and "--suite-part scheme2" in md2
