@@ -27,8 +27,10 @@
 // between K segments, so the MMAs of one segment overlap the reduction of
 // the last.  Roles (320 threads): warps 0-7 drain (warp w: TMEM lanes = tile
 // rows 32 (w % 4) .., columns 128 (w / 4) .. +127; each finished segment is
-// added to a running residue, four per register), warp 8 lane 0 TMA, warp 9
-// TMEM allocation and (lane 0) MMAs.  CTAs may run in clusters of cl (1, 2,
+// added to a running residue, four per register), warp 8 lane 0 TMA (each
+// load preceded by an L2 prefetch of the chunk four K steps ahead, which
+// hides part of the DRAM latency the four stages do not cover), warp 9 TMEM
+// allocation and (lane 0) MMAs.  CTAs may run in clusters of cl (1, 2,
 // 4) along M that share the B chunks by TMA multicast.  All waits are
 // bounded; a timeout sets the status word, raises an abort flag for the
 // other roles, and the TMEM is still released.
