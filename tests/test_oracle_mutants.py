@@ -1,0 +1,200 @@
+"""The oracle's pins have teeth: each mutant below is the oracle's C source
+with one plausible mistake -- a dropped term, a wrong sign, index, bound or
+scale, a wrong rounding rule, a transposed operand -- and every one of them
+must fail at least one pin of test_oracle*.py.  The oracle is not changed:
+each mistake is a text substitution on a copy in a temporary directory,
+compiled with the oracle's own flags, and the pins run against it in a child
+process (a mutant that crashes counts as caught)."""
+import os
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "emu_oracle.c")
+
+# (name, text in the oracle, replacement, occurrence): occurrence None = the
+# text must occur once; an index picks one of several identical sites
+MUTANTS = [
+    # Eq. 1 scale vectors: floor(log2 max) instead of the frexp exponent
+    ("row exponent one low", "if (mx != 0.0) frexp(mx, &e);", "if (mx != 0.0) { frexp(mx, &e); e -= 1; }", None),
+    # Scheme I split (R1)
+    ("slice scale without the sign bit", "scaled_trunc(X[i * k + h], 8 * p - 1 - E[i])",
+     "scaled_trunc(X[i * k + h], 8 * p - E[i])", None),
+    ("wrong slice signed", "if (t == 0 && byte >= 128) byte -= 256;", "if (t == 1 && byte >= 128) byte -= 256;", None),
+    ("truncation rounds", "mag = (u128)(M >> (-sh));", "mag = (u128)((M + ((uint64_t)1 << (-sh - 1))) >> (-sh));", None),
+    # Eq. 11 layout
+    ("slice-major interleave", "Ahat[i * nck * p * tk + (c * p + t) * tk + r]",
+     "Ahat[i * nck * p * tk + (t * nck + c) * tk + r]", None),
+    # chunk length of R2
+    ("K_c bound one tail term too many", "(int64_t)(p - 2) * 255 * 255", "(int64_t)(p - 1) * 255 * 255", None),
+    # Eq. 2 triangle / Eq. 3 shift-reduce
+    ("partials drop the diagonal term", "int64_t acc = 0;\n          for (int t = 0; t <= s; ++t) {",
+     "int64_t acc = 0;\n          for (int t = 0; t < s; ++t) {", None),
+    # the INT8 product (orc_emu_I) comes before the E4M3 one, whose loop is the same text
+    ("Scheme I pairs slice t with t", "const int16_t *b = DB + ((int64_t)(s - t) * n + j) * k;\n          for (int64_t h = 0; h < k; ++h) Cs",
+     "const int16_t *b = DB + ((int64_t)t * n + j) * k;\n          for (int64_t h = 0; h < k; ++h) Cs", 0),
+    ("shift-reduce weight off by one slice", "S += (i128)Cs << (8 * (p - 1 - s));", "S += (i128)Cs << (8 * (p - s));", None),
+    ("Scheme I scale exponent", "E[i] + F[j] - 14 - 8 * (p - 1)", "E[i] + F[j] - 16 - 8 * (p - 1)", None),
+    ("rounding ties away from zero", "if (rest > half || (rest == half && (top & 1))) top += 1;",
+     "if (rest >= half) top += 1;", None),
+    ("BLAS update rounds twice", "return fma(alpha, r, beta * c);", "return alpha * r + beta * c;", None),
+    # Scheme II (R3, R4, Eqs. 5-8)
+    ("moduli start at 255", "for (int x = 256; x >= 2 && cnt < nm; --x)", "for (int x = 255; x >= 2 && cnt < nm; --x)", None),
+    ("scale bits one too many", "int num = orc_log2P_floor(nm) - (is_complex ? 2 : 1) - c;",
+     "int num = orc_log2P_floor(nm) - (is_complex ? 2 : 1) - c + 1;", None),
+    # (r > m / 2 would be an equivalent mutant: it differs only at r = 128
+    # for m = 256, which the int8 store wraps to -128 anyway)
+    ("residue range off by one", "if (r > (m - 1) / 2) r -= m;", "if (r >= (m - 1) / 2) r -= m;", None),
+    ("negative remainder not lifted", "  int r = (int)(x % m);\n  if (r < 0) r += m;", "  int r = (int)(x % m);", None),
+    ("output residue left negative", "        int64_t r = acc % mods[l];\n        if (r < 0) r += mods[l];",
+     "        int64_t r = acc % mods[l];", None),
+    ("CRT weight without the inverse", "big_mul_u32(&w, &Pl, (uint32_t)q);", "big_mul_u32(&w, &Pl, 1u);", None),
+    ("CRT lift maps P/2 to -P/2", "if (big_cmp(&S, &cx->halfP_floor) > 0) {", "if (big_cmp(&S, &cx->halfP_floor) >= 0) {", None),
+    ("Scheme II scale back", "double r = ldexp(v, E[i] + F[j] - bA - bB);", "double r = ldexp(v, E[i] + F[j] - bA - bB + 1);", None),
+    # 3M (Eq. 16)
+    ("3M real part adds T2", "int64_t re = ((t[0] - t[1]) % ml + ml) % ml;", "int64_t re = ((t[0] + t[1]) % ml + ml) % ml;", None),
+    ("3M imaginary part adds T2", "int64_t im = ((t[2] - t[0] - t[1]) % ml + 2 * ml) % ml;",
+     "int64_t im = ((t[2] - t[0] + t[1]) % ml + 2 * ml) % ml;", None),
+    ("3M sum residue is a difference", "v = part == 0 ? re : part == 1 ? im : re + im;",
+     "v = part == 0 ? re : part == 1 ? im : re - im;", None),
+    ("complex alpha sign", "double tr = fma(ar, rr, -(ai * ri));", "double tr = fma(ar, rr, ai * ri);", None),
+    # E4M3 slices (R7)
+    ("E4M3 digit range [-15, 16]", "if (r >= 16) r -= 32;", "if (r > 16) r -= 32;", None),
+    ("E4M3 scale exponent", "E[i] + F[j] - 8 - 5 * (p - 1)", "E[i] + F[j] - 10 - 5 * (p - 1)", None),
+    # 4M Scheme I complex (R8)
+    ("4M real part without -Im B", "tri_sum(DAi, i, m, DBn, j, n, k, s)", "tri_sum(DAi, i, m, DBi, j, n, k, s)", None),
+    # norm scaling (R9)
+    ("norm exponent rounds down", "int ep = d >= 0 ? (d + 1) / 2 : -((-d) / 2);",
+     "int ep = d >= 0 ? d / 2 : -((-d) / 2);", None),
+    ("norm halves one too many", "*hA = L >= 0 ? L / 2 : -((-L + 1) / 2);", "*hA = L >= 0 ? L / 2 + 1 : -((-L + 1) / 2);", None),
+    # double-double reference
+    ("dd ZGEMM real part adds Im*Im", "dot2(a, 1, b, 1, 2 * k, 1.0,", "dot2(a, 1, b, 1, 2 * k, 0.0,", None),
+]
+
+# The child: load the oracle module against the mutant library and run every
+# pin until one fails (exit 1) or all pass (exit 0).
+RUNNER = r"""
+import importlib.util, inspect, itertools, os, sys, tempfile, pathlib
+root, lib, src = sys.argv[1:4]
+sys.path[:0] = [root, os.path.join(root, "tests")]
+import pytest
+spec = importlib.util.spec_from_file_location("oracle_mutant", os.path.join(root, "oracle", "__init__.py"))
+orc = importlib.util.module_from_spec(spec)
+spec.loader.exec_module(orc)
+orc._LIB_PATH, orc._SRC, orc._OUT_DIR = lib, src, os.path.dirname(lib)
+
+def cases(fn):
+    grids = []
+    for m in getattr(fn, "pytestmark", []):
+        if m.name == "skip" or (m.name == "skipif" and m.args and m.args[0]):
+            return
+        if m.name != "parametrize":
+            continue
+        names = m.args[0]
+        names = [s.strip() for s in names.split(",")] if isinstance(names, str) else list(names)
+        vals = []
+        for v in m.args[1]:
+            if hasattr(v, "values") and hasattr(v, "marks"):
+                v = v.values if len(names) > 1 else v.values[0]
+            vals.append(dict(zip(names, v)) if len(names) > 1 else {names[0]: v})
+        grids.append(vals)
+    for combo in itertools.product(*grids):
+        kw = {}
+        for d in combo:
+            kw.update(d)
+        yield kw
+
+for modname in ("test_oracle", "test_oracle_f8", "test_oracle_norm", "test_oracle_z4m"):
+    mod = importlib.import_module(modname)
+    for name, fn in sorted(vars(mod).items()):
+        if not (name.startswith("test_") and callable(fn)):
+            continue
+        params = inspect.signature(fn).parameters
+        for kw in cases(fn):
+            args = {}
+            for p in params:
+                if p == "orc":
+                    args[p] = orc
+                elif p == "tmp_path":
+                    args[p] = pathlib.Path(tempfile.mkdtemp())
+                elif p in kw:
+                    args[p] = kw[p]
+                else:
+                    args = None
+                    break
+            if args is None:
+                continue
+            try:
+                fn(**args)
+            except pytest.skip.Exception:
+                continue
+            except Exception as e:
+                print("caught by", modname + "::" + name, kw, type(e).__name__)
+                sys.exit(1)
+print("survived every pin")
+sys.exit(0)
+"""
+
+
+def mutate(text, old, new, which):
+    """Replace occurrence `which` (None: the only one) of `old` by `new`."""
+    pos = -1
+    for _ in range((which or 0) + 1):
+        pos = text.find(old, pos + 1)
+        assert pos >= 0, f"mutation site not found: {old!r}"
+    return text[:pos] + new + text[pos + len(old):]
+
+
+def run_mutant(tmp, idx, name, old, new, which):
+    src = os.path.join(tmp, f"m{idx}.c")
+    lib = os.path.join(tmp, f"libm{idx}.so")
+    with open(SRC) as fh:
+        text = fh.read()
+    mutated = mutate(text, old, new, which)
+    assert mutated != text
+    with open(src, "w") as fh:
+        fh.write(mutated)
+    subprocess.run(["gcc"] + oracle.CFLAGS + ["-o", lib, src, "-lm"], check=True)
+    env = dict(os.environ, OMP_NUM_THREADS="2")
+    try:
+        r = subprocess.run([sys.executable, "-c", RUNNER, ROOT, lib, src], capture_output=True, text=True,
+                           timeout=600, env=env)
+    except subprocess.TimeoutExpired:
+        return name, None, "timed out"
+    return name, r.returncode, (r.stdout + r.stderr).strip().splitlines()[-1:] or [""]
+
+
+def test_every_mutant_fails_a_pin(tmp_path):
+    with ThreadPoolExecutor(max_workers=4) as ex:
+        res = list(ex.map(lambda a: run_mutant(str(tmp_path), *a),
+                          [(i,) + m for i, m in enumerate(MUTANTS)]))
+    survivors = [(name, out) for name, rc, out in res if rc == 0 or rc is None]
+    assert not survivors, f"mutants no pin catches: {survivors}"
+
+
+def test_unmutated_copy_passes_every_pin(tmp_path):
+    # the runner itself: the oracle's own source, compiled the same way, survives
+    src = os.path.join(str(tmp_path), "orig.c")
+    lib = os.path.join(str(tmp_path), "liborig.so")
+    with open(SRC) as fh, open(src, "w") as out:
+        out.write(fh.read())
+    subprocess.run(["gcc"] + oracle.CFLAGS + ["-o", lib, src, "-lm"], check=True)
+    r = subprocess.run([sys.executable, "-c", RUNNER, ROOT, lib, src], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "survived every pin" in r.stdout
+
+
+@pytest.mark.parametrize("i", range(len(MUTANTS)))
+def test_mutation_site_is_unique_or_indexed(i):
+    name, old, new, which = MUTANTS[i]
+    with open(SRC) as fh:
+        text = fh.read()
+    if which is None:
+        assert text.count(old) == 1, f"{name}: the site occurs {text.count(old)} times"
+    else:
+        assert text.count(old) > which, name
