@@ -189,6 +189,75 @@ def test_unmutated_copy_passes_every_pin(tmp_path):
     assert "survived every pin" in r.stdout
 
 
+# The selector oracle (oracle/selector.py, numpy): the same check against its
+# pins in test_selector_oracle.py.  (Moving eps inside the square root of the
+# Adam step is left out: it changes a step by about 5e-9 of itself.)
+SELECTOR_SRC = os.path.join(ROOT, "oracle", "selector.py")
+SELECTOR_MUTANTS = [
+    ("cross-entropy gradient not averaged", "    dz3 /= b\n", "", None),
+    ("softmax gradient sign", "dz3[np.arange(b), y] -= 1.0", "dz3[np.arange(b), y] += 1.0", None),
+    ("W2 gradient transposed", 'g["W2"] = dz2.T @ h1', 'g["W2"] = (dz2.T @ h1).T', None),
+    ("first ReLU not back-propagated", "dz1 = dh1 * (z1 > 0)", "dz1 = dh1", None),
+    ("b1 gradient averaged", 'g["b1"] = dz1.sum(axis=0)', 'g["b1"] = dz1.mean(axis=0)', None),
+    ("second layer without bias", 'z2 = h1 @ p["W2"].T + p["b2"]', 'z2 = h1 @ p["W2"].T', None),
+    ("Adam second moment of |g|", "v = b2 * v + (1 - b2) * grad * grad", "v = b2 * v + (1 - b2) * np.abs(grad)", None),
+    ("Adam without the second bias correction", "c2 = 1 - b2 ** step", "c2 = 1.0", None),
+    ("feature bins of 4 exponents", "h[min(max(d, 0) // 3, 31)] += 1", "h[min(max(d, 0) // 4, 31)] += 1", None),
+    ("zeros counted in bin 0", "h[31] += 1", "h[0] += 1", None),
+    ("row exponent of the first element", "E = _frexp_exp(float(np.max(np.abs(row)))) if row.size else 0",
+     "E = _frexp_exp(float(row[0])) if row.size else 0", None),
+    ("features of the rows of B", "Bt = np.ascontiguousarray(np.asarray(B, dtype=np.float64).T)",
+     "Bt = np.ascontiguousarray(np.asarray(B, dtype=np.float64))", None),
+    ("K feature scale", "f[64] = np.float32(math.log2(k) / 16.0)", "f[64] = np.float32(math.log2(k) / 8.0)", None),
+    ("tolerance feature sign", "f[65] = np.float32(-math.log10(tol) / 16.0)",
+     "f[65] = np.float32(math.log10(tol) / 16.0)", None),
+]
+
+SELECTOR_RUNNER = r"""
+import importlib.util, os, sys
+root, src = sys.argv[1:3]
+sys.path[:0] = [root, os.path.join(root, "tests")]
+import oracle
+spec = importlib.util.spec_from_file_location("oracle.selector", src)
+mod = importlib.util.module_from_spec(spec)
+spec.loader.exec_module(mod)
+sys.modules["oracle.selector"] = mod
+oracle.selector = mod
+import test_selector_oracle as T
+for name in sorted(dir(T)):
+    if name.startswith("test_"):
+        try:
+            getattr(T, name)()
+        except Exception as e:
+            print("caught by", name, type(e).__name__)
+            sys.exit(1)
+print("survived every pin")
+sys.exit(0)
+"""
+
+
+def run_selector_mutant(tmp, idx, name, old, new, which):
+    with open(SELECTOR_SRC) as fh:
+        text = fh.read()
+    src = os.path.join(tmp, f"selector_m{idx}.py")
+    with open(src, "w") as fh:
+        fh.write(mutate(text, old, new, which) if old is not None else text)
+    r = subprocess.run([sys.executable, "-c", SELECTOR_RUNNER, ROOT, src], capture_output=True, text=True,
+                       timeout=600)
+    return name, r.returncode, (r.stdout + r.stderr).strip().splitlines()[-1:] or [""]
+
+
+def test_every_selector_mutant_fails_a_pin(tmp_path):
+    with ThreadPoolExecutor(max_workers=4) as ex:
+        res = list(ex.map(lambda a: run_selector_mutant(str(tmp_path), *a),
+                          [(i,) + m for i, m in enumerate(SELECTOR_MUTANTS)]))
+    survivors = [(name, out) for name, rc, out in res if rc == 0]
+    assert not survivors, f"mutants no pin catches: {survivors}"
+    # and the unmutated copy passes
+    name, rc, out = run_selector_mutant(str(tmp_path), "orig", "unmutated", None, None, None)
+    assert rc == 0 and "survived" in out[0], out
+
+
 @pytest.mark.parametrize("i", range(len(MUTANTS)))
 def test_mutation_site_is_unique_or_indexed(i):
     name, old, new, which = MUTANTS[i]

@@ -14,7 +14,13 @@ def test_gradient_matches_finite_differences():
     X = rng.random((7, S.IN))
     y = rng.integers(0, S.OUT, 7)
     g = S.mlp_backward(theta, X, y)
-    idx = rng.choice(S.NPARAM, 60, replace=False)
+    # twelve entries of every parameter block (W1, b1, W2, b2, W3, b3), so a
+    # mistake confined to one small block cannot hide between samples
+    idx, off = [], 0
+    for _, shape in S.SIZES:
+        n = int(np.prod(shape))
+        idx += list(off + rng.choice(n, min(n, 12), replace=False))
+        off += n
     for i in idx:
         e = np.zeros(S.NPARAM)
         e[i] = 1e-6
@@ -51,3 +57,14 @@ def test_features_known_exponents():
     assert np.array_equal(f[:32], (expect / 8).astype(np.float32))
     assert f[32] == 1.0 and np.all(f[33:64] == 0)
     assert f[64] == np.float32(math.log2(4) / 16) and f[65] == np.float32(12 / 16)
+
+
+def test_features_use_the_columns_of_B():
+    # B (3 x 2): column 0 = 1, 0.5, 0.25 (E = 1: deficits 0, 1, 2 -> bin 0);
+    # column 1 = 8, 2^-10, 0 (E = 4: 8 -> bin 0, 2^-10 has e = -9, deficit 13
+    # -> bin 4, the zero -> bin 31).  Its rows would give other bins.
+    B = np.array([[1.0, 8.0], [0.5, 2.0 ** -10], [0.25, 0.0]])
+    f = S.features(np.ones((1, 3)), B, 1e-6)
+    expect = np.zeros(32)
+    expect[0], expect[4], expect[31] = 4, 1, 1
+    assert np.array_equal(f[32:64], (expect / 6).astype(np.float32))
