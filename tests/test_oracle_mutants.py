@@ -74,6 +74,25 @@ MUTANTS = [
     ("norm halves one too many", "*hA = L >= 0 ? L / 2 : -((-L + 1) / 2);", "*hA = L >= 0 ? L / 2 + 1 : -((-L + 1) / 2);", None),
     # double-double reference
     ("dd ZGEMM real part adds Im*Im", "dot2(a, 1, b, 1, 2 * k, 1.0,", "dot2(a, 1, b, 1, 2 * k, 0.0,", None),
+    ("dd dot drops the TwoSum error", "    c += err + e;\n  }\n  double t = s + c;", "    c += e;\n  }\n  double t = s + c;", None),
+    # more of the integer and rounding machinery
+    ("CRT rounding ignores the sticky bits", "if (guard && (sticky || (top & 1))) top += 1;",
+     "if (guard && (top & 1)) top += 1;", None),
+    ("CRT sum not reduced mod P", "    if (big_cmp(&S, &cx->P) >= 0) big_sub(&S, &S, &cx->P);\n  }\n  if (big_cmp(&S, &cx->halfP_floor) > 0)",
+     "  }\n  if (big_cmp(&S, &cx->halfP_floor) > 0)", None),
+    ("norm squares rounded down", "  if ((q << (-s)) != M2) q += 1;\n  return q;", "  return q;", None),
+    ("E4M3 leading digit dropped", "      D[i * k + h] = (int16_t)x;", "      D[i * k + h] = 0;", None),
+    ("interleave pads with ones", "int v = h < k ? D[((int64_t)t * rows + i) * k + h] : 0;",
+     "int v = h < k ? D[((int64_t)t * rows + i) * k + h] : 1;", None),
+    ("K_c not a multiple of 256", "  int64_t lim = 2147483647LL / bnd;\n  return (lim / 256) * 256;",
+     "  int64_t lim = 2147483647LL / bnd;\n  return lim;", None),
+    ("4M E4M3 scale exponent", "const int escale = f8 ? -8 - 5 * (p - 1) : -14 - 8 * (p - 1);",
+     "const int escale = f8 ? -8 - 5 * p : -14 - 8 * (p - 1);", None),
+    ("scaled integer loses its sign", "return a < 0 ? -(i128)mag : (i128)mag;", "return (i128)mag;", None),
+    ("residue product skips the last K term",
+     "        for (int64_t h = 0; h < k; ++h) acc += (int64_t)a[h] * (int64_t)b[h];\n        int64_t r = acc % mods[l];",
+     "        for (int64_t h = 0; h + 1 < k; ++h) acc += (int64_t)a[h] * (int64_t)b[h];\n        int64_t r = acc % mods[l];",
+     None),
 ]
 
 # The child: load the oracle module against the mutant library and run every
@@ -166,7 +185,7 @@ def run_mutant(tmp, idx, name, old, new, which):
                            timeout=600, env=env)
     except subprocess.TimeoutExpired:
         return name, None, "timed out"
-    return name, r.returncode, (r.stdout + r.stderr).strip().splitlines()[-1:] or [""]
+    return name, r.returncode, (r.stdout.strip() or r.stderr.strip()).splitlines()[-1:] or [""]
 
 
 def test_every_mutant_fails_a_pin(tmp_path):
@@ -244,7 +263,7 @@ def run_selector_mutant(tmp, idx, name, old, new, which):
         fh.write(mutate(text, old, new, which) if old is not None else text)
     r = subprocess.run([sys.executable, "-c", SELECTOR_RUNNER, ROOT, src], capture_output=True, text=True,
                        timeout=600)
-    return name, r.returncode, (r.stdout + r.stderr).strip().splitlines()[-1:] or [""]
+    return name, r.returncode, (r.stdout.strip() or r.stderr.strip()).splitlines()[-1:] or [""]
 
 
 def test_every_selector_mutant_fails_a_pin(tmp_path):

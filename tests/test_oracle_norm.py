@@ -48,6 +48,23 @@ def test_norm_exponents_closed_forms(orc):
         assert int(orc.norm_exponents(row)[0]) == q + j + 1
 
 
+def test_norm_exponent_rounds_each_square_up(orc):
+    # R9 sums ceil(y^2 2^64).  Row (x0, x1): x0 = 1 - 2^-26 gives E = 0 and
+    # x0^2 2^64 = 2^64 - 2^39 + 2^12 exactly; x1 = M 2^-65 has x1^2 2^64 =
+    # M^2 2^-66 in (T - 1, T], T = 2^39 - 2^12, with a fractional part.  The
+    # rounded-up sum is exactly 2^64 (bit length 65, e = 1) although the
+    # norm is below 1; squares rounded down would sum to 2^64 - 1 (e = 0).
+    T = 2 ** 39 - 2 ** 12
+    M = math.isqrt((T - 1) * 2 ** 66) + 1
+    while M % 2 == 0:
+        M += 1
+    assert 2 ** 52 <= M < 2 ** 53 and (T - 1) * 2 ** 66 < M * M <= T * 2 ** 66
+    x0, x1 = 1.0 - 2.0 ** -26, M * 2.0 ** -65
+    assert Fraction(x0) ** 2 * 2 ** 64 == 2 ** 64 - 2 ** 39 + 2 ** 12
+    assert Fraction(x0) ** 2 + Fraction(x1) ** 2 < 1
+    assert list(orc.norm_exponents(np.array([[x0, x1], [x1, x0]]))) == [1, 1]
+
+
 def test_norm_halves(orc):
     for nm in range(2, 21):
         hA, hB = orc.norm_halves_II(nm)
