@@ -89,6 +89,13 @@ MUTANTS = [
     ("4M E4M3 scale exponent", "const int escale = f8 ? -8 - 5 * (p - 1) : -14 - 8 * (p - 1);",
      "const int escale = f8 ? -8 - 5 * p : -14 - 8 * (p - 1);", None),
     ("scaled integer loses its sign", "return a < 0 ? -(i128)mag : (i128)mag;", "return (i128)mag;", None),
+    ("complex row exponent over half the row", "  return orc_row_exponents(rows, 2 * cols, X, E);",
+     "  return orc_row_exponents(rows, cols, X, E);", None),
+    ("multi-word subtraction borrow", "    br = d < 0;", "    br = d <= 0;", None),
+    ("complex beta term subtracted", "    tr = tr + ur;", "    tr = tr - ur;", None),
+    ("complex norm over the real parts only",
+     "    for (int64_t h = 0; h < cols * cw; ++h) S += sq_ceil64(X[i * cols * cw + h], Emax);",
+     "    for (int64_t h = 0; h < cols * cw; h += cw) S += sq_ceil64(X[i * cols * cw + h], Emax);", None),
     ("residue product skips the last K term",
      "        for (int64_t h = 0; h < k; ++h) acc += (int64_t)a[h] * (int64_t)b[h];\n        int64_t r = acc % mods[l];",
      "        for (int64_t h = 0; h + 1 < k; ++h) acc += (int64_t)a[h] * (int64_t)b[h];\n        int64_t r = acc % mods[l];",

@@ -111,6 +111,22 @@ def test_more_bits_than_worst_case_scaling(orc):
     assert orc.err_metric(orc.emu_II(A, B, 20, norm=True), ref, A, B) <= 4 * k * 2.0 ** -53
 
 
+def test_complex_norm_exponents_bound_the_norm(orc):
+    # complex rows use |x|^2 = re^2 + im^2; rows 0-2 have imaginary parts
+    # much larger than the real ones, row 3 the reverse, row 4 is zero
+    rng = np.random.Generator(np.random.PCG64(21))
+    X = rng.uniform(-1, 1, (5, 40)) * 2.0 ** -20 + 1j * rng.uniform(-1, 1, (5, 40)) * 2.0 ** 5
+    X[3] = X[3].imag * 2.0 ** -25 + 1j * X[3].real * 2.0 ** 25
+    X[4] = 0.0
+    E = orc.norm_exponents(X, True)
+    for i in range(5):
+        ss = sum(Fraction(v.real) ** 2 + Fraction(v.imag) ** 2 for v in X[i])
+        if ss == 0:
+            assert E[i] == 0
+            continue
+        assert Fraction(4) ** (int(E[i]) - 2) <= ss < Fraction(4) ** int(E[i])
+
+
 def test_complex_3m_norm(orc):
     rng = np.random.Generator(np.random.PCG64(13))
     A = rng.integers(-300, 301, (5, 30)) + 1j * rng.integers(-300, 301, (5, 30))
