@@ -107,9 +107,10 @@ MUTANTS = [
 RUNNER = r"""
 import importlib.util, inspect, itertools, os, sys, tempfile, pathlib
 root, lib, src = sys.argv[1:4]
+wrapper = sys.argv[4] if len(sys.argv) > 4 else os.path.join(root, "oracle", "__init__.py")
 sys.path[:0] = [root, os.path.join(root, "tests")]
 import pytest
-spec = importlib.util.spec_from_file_location("oracle_mutant", os.path.join(root, "oracle", "__init__.py"))
+spec = importlib.util.spec_from_file_location("oracle_mutant", wrapper)
 orc = importlib.util.module_from_spec(spec)
 spec.loader.exec_module(orc)
 orc._LIB_PATH, orc._SRC, orc._OUT_DIR = lib, src, os.path.dirname(lib)
@@ -213,6 +214,57 @@ def test_unmutated_copy_passes_every_pin(tmp_path):
     r = subprocess.run([sys.executable, "-c", RUNNER, ROOT, lib, src], capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "survived every pin" in r.stdout
+
+
+# The oracle's Python wrapper (oracle/__init__.py), which marshals operands
+# into the C code: the same check, with the wrapper's source mutated and the
+# C library as built.  Occurrences of the repeated marshalling line follow
+# the file: partials_I, emu_I, partials_F8, emu_F8, emu_II, dd_gemm.
+WRAPPER_SRC = os.path.join(ROOT, "oracle", "__init__.py")
+WRAPPER_MUTANTS = [
+    ("emu_I takes B untransposed", "A, Bt = _f64(A), _f64(np.asarray(B).T)", "A, Bt = _f64(A), _f64(np.asarray(B))", 1),
+    ("emu_II takes B untransposed", "A, Bt = _f64(A), _f64(np.asarray(B).T)", "A, Bt = _f64(A), _f64(np.asarray(B))", 4),
+    ("dd_gemm takes B untransposed", "A, Bt = _f64(A), _f64(np.asarray(B).T)", "A, Bt = _f64(A), _f64(np.asarray(B))", 5),
+    ("emu_Z3M conjugates B", "Bt = np.ascontiguousarray(np.asarray(B, dtype=np.complex128).T)",
+     "Bt = np.ascontiguousarray(np.asarray(B, dtype=np.complex128).conj().T)", 0),
+    ("dd_zgemm conjugates B", "Bt = np.ascontiguousarray(np.asarray(B, dtype=np.complex128).T)",
+     "Bt = np.ascontiguousarray(np.asarray(B, dtype=np.complex128).conj().T)", 2),
+    ("emu_Z3M conjugates alpha", "alpha, beta = complex(alpha), complex(beta)",
+     "alpha, beta = complex(alpha).conjugate(), complex(beta)", 0),
+    ("emu_Z4M_I conjugates beta", "alpha, beta = complex(alpha), complex(beta)",
+     "alpha, beta = complex(alpha), complex(beta).conjugate()", 1),
+    ("column exponents of the rows of B", "return row_exponents(np.ascontiguousarray(np.asarray(B, dtype=np.float64).T))",
+     "return row_exponents(np.ascontiguousarray(np.asarray(B, dtype=np.float64)))", None),
+    ("complex residues with real-part exponents", "        E = row_exponents_z(X)\n", "        E = row_exponents(X.real)\n", None),
+    ("error metric over |AB| instead of |A||B|", "den = np.abs(np.asarray(A)) @ np.abs(np.asarray(B))",
+     "den = np.abs(np.asarray(A) @ np.asarray(B))", None),
+]
+
+
+def run_wrapper_mutant(tmp, idx, name, old, new, which):
+    with open(WRAPPER_SRC) as fh:
+        text = fh.read()
+    wsrc = os.path.join(tmp, f"wrapper_m{idx}.py")
+    with open(wsrc, "w") as fh:
+        fh.write(mutate(text, old, new, which) if old is not None else text)
+    lib = oracle.build()
+    env = dict(os.environ, OMP_NUM_THREADS="2")
+    try:
+        r = subprocess.run([sys.executable, "-c", RUNNER, ROOT, lib, SRC, wsrc], capture_output=True, text=True,
+                           timeout=600, env=env)
+    except subprocess.TimeoutExpired:
+        return name, None, "timed out"
+    return name, r.returncode, (r.stdout.strip() or r.stderr.strip()).splitlines()[-1:] or [""]
+
+
+def test_every_wrapper_mutant_fails_a_pin(tmp_path):
+    with ThreadPoolExecutor(max_workers=4) as ex:
+        res = list(ex.map(lambda a: run_wrapper_mutant(str(tmp_path), *a),
+                          [(i,) + m for i, m in enumerate(WRAPPER_MUTANTS)]))
+    survivors = [(name, out) for name, rc, out in res if rc == 0 or rc is None]
+    assert not survivors, f"mutants no pin catches: {survivors}"
+    name, rc, out = run_wrapper_mutant(str(tmp_path), "orig", "unmutated", None, None, None)
+    assert rc == 0 and "survived" in out[0], out
 
 
 # The selector oracle (oracle/selector.py, numpy): the same check against its
