@@ -17,13 +17,17 @@
  *     A and B are scaled to integers, reduced modulo N pairwise-coprime
  *     moduli m_l <= 256 (256, 255, 253, 251, ...), multiplied with one
  *     integer GEMM per modulus, reduced modulo m_l and reconstructed by the
- *     Chinese Remainder Theorem (Eq. 8), all inside one kernel.  Complex
- *     input uses the 3M method (Eq. 16).  On sm_103a the per-modulus GEMMs
- *     run on the bf16 tensor cores (tcgen05): symmetric residues are exact
- *     bf16 values and FP32 sums of up to 960 of their products are exact
- *     integers, so each 960-deep K segment is reduced modulo m_l as it
- *     leaves the accumulator.  EMU_II_ENGINE=mma selects the INT8 mma.sync
- *     kernel instead (same results, k <= EMU_K_MAX_II).
+ *     Chinese Remainder Theorem (Eq. 8).  Complex input uses the 3M method
+ *     (Eq. 16).  On sm_103a the per-modulus GEMMs run by default on the bf16
+ *     tensor cores (tcgen05): symmetric residues are exact bf16 values and
+ *     FP32 sums of up to 960 of their products are exact integers, so each
+ *     960-deep K segment is reduced modulo m_l as it leaves the accumulator.
+ *     That engine uses two kernels, like the paper's Sec. IV design: the
+ *     residue GEMM writes one residue byte per output and modulus (Eq. 7),
+ *     and a second kernel forms the CRT sum, the inverse scaling and the
+ *     BLAS update.  EMU_II_ENGINE=mma selects the INT8 mma.sync kernel
+ *     instead, which keeps the residues on chip and does the CRT in the
+ *     same kernel (same results, k <= EMU_K_MAX_II).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -54,9 +58,9 @@
  *  - Environment (read once per process; results do not depend on it):
  *    EMU_II_ENGINE=mma runs Scheme II on the INT8 mma.sync kernel instead of
  *    the bf16 tcgen05 one; EMU_F8_ENGINE=mma runs E4M3 slices on the warp
- *    level instead of tcgen05; EMU_II_CLUSTER and EMU_TC_CLUSTER (1, 2, 4)
- *    set the CTAs per cluster that share operand chunks by TMA multicast in
- *    the two tcgen05 kernels (default 2); EMU_FAULT=alloc makes every
+ *    level instead of tcgen05; EMU_II_CLUSTER=2 runs the bf16 Scheme II
+ *    residue GEMM on CTA pairs (256 x 256 tiles, tcgen05.mma.cta_group::2)
+ *    instead of single CTAs (128 x 256 tiles); EMU_FAULT=alloc makes every
  *    library-owned workspace allocation fail (fault injection).
  */
 #ifndef EMUGEMM_H
@@ -228,11 +232,14 @@ emu_status_t emu_cgemm(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n
  * cudaMalloc, cudaFree or other allocating routine: its scratch is a fixed
  * file-scope device array of EMU_NOALLOC_SCRATCH_BYTES that every GPU which
  * loads the library holds until the process exits.
- *  - Runs on the current CUDA device.  The first call on a device looks up
- *    the array's device address (cudaGetSymbolAddress); make that first call
- *    before any stream capture on that device.
+ *  - Runs on the current CUDA device.  The first call in a CUDA context of
+ *    a device looks up the array's device address (cudaGetSymbolAddress) and
+ *    caches it with the context's unique ID; make that first call before any
+ *    stream capture on that device.  A call in a different context (for
+ *    example after cudaDeviceReset re-created the primary context) looks the
+ *    address up again, so that call, too, belongs outside a capture.
  *  - Products whose workspace (emu_workspace_size for Scheme I) exceeds
- *    EMU_NOALLOC_SCRATCH_BYTES - 256 are rejected with EMU_ERR_UNSUPPORTED
+ *    EMU_NOALLOC_SCRATCH_BYTES are rejected with EMU_ERR_UNSUPPORTED
  *    (e.g. m = n = k = 2048 fits for p <= 7).
  *  - All calls share the array and it keeps the last call's contents; each
  *    call clears what must start at zero.  Calls whose work overlaps on the

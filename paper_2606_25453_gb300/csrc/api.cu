@@ -485,9 +485,9 @@ Plan plan_II(int64_t m, int64_t n, int64_t k, int nm, int nsets, int es) {
   pl.off_accB = off; off += al256(16 * static_cast<size_t>(n > 0 ? n : 1));
   pl.off_nEA = off; off += al256(4 * static_cast<size_t>(m > 0 ? m : 1));
   pl.off_nEB = off; off += al256(4 * static_cast<size_t>(n > 0 ? n : 1));
-  // tcgen05 kernel: the residue planes (one byte per output and modulus; with
-  // clusters of up to 4 row tiles)
-  pl.off_scratch = off; off += es == 2 ? al256(gemm_II_tc_residue_bytes(m, n, nm, nsets == 3, 4)) : 0;
+  // tcgen05 kernel: the residue planes (one byte per output and modulus; row
+  // tiles rounded to whole CTA-pair tiles)
+  pl.off_scratch = off; off += es == 2 ? al256(gemm_II_tc_residue_bytes(m, n, nm, nsets == 3, 2)) : 0;
   pl.bytes = off;
   return pl;
 }
@@ -552,14 +552,12 @@ emu_status_t run_scheme_I(emu_handle_s* h, const View& v, int64_t k, int p, doub
   launch_split_I<T>(A, v.ldA, v.a_kcontig, v.M, k, p, maxA, hatA, EA, st, f8);
   launch_split_I<T>(B, v.ldB, v.b_kcontig, v.N, k, p, maxB, hatB, FB, st, f8);
   trace_end(h, PH_SPLIT, st, 2);
-  // E4M3 slices run on the tcgen05 kernel (A boxes of 128 B x 128 / cluster
-  // rows, multicast across the cluster); the INT8 engine uses the mma.sync
-  // kernel (32 B x 64 rows).
+  // E4M3 slices run on the tcgen05 kernel (A boxes of 128 B x 128 rows);
+  // the INT8 engine uses the mma.sync kernel (32 B x 64 rows).
   const bool tc = f8 && !f8_engine_mma();
-  const int cluster = tc ? gemm_f8tc_cluster() : 1;
   CUtensorMap ta, tb;
   if (!make_tmap_i8(&ta, hatA, static_cast<uint64_t>(pl.cols), static_cast<uint64_t>(pl.rows_a),
-                    tc ? static_cast<uint32_t>(128 / cluster) : 64, tc ? 128 : 32) ||
+                    tc ? 128u : 64u, tc ? 128 : 32) ||
       !make_tmap_i8(&tb, hatB, static_cast<uint64_t>(pl.cols), static_cast<uint64_t>(pl.rows_b), 32))
     return tmap_err();
   GemmIArgs a{};
@@ -578,7 +576,6 @@ emu_status_t run_scheme_I(emu_handle_s* h, const View& v, int64_t k, int p, doub
   a.partials = partials;
   a.status = h->status;
   a.num_sms = h->num_sms;
-  a.cluster = cluster;
   trace_begin(h, PH_GEMM, st);
   cudaError_t e = tc ? launch_gemm_f8tc(p, out_mode, a, st) : launch_gemm_I(p, out_mode, a, st, f8);
   trace_end(h, PH_GEMM, st, 1);
@@ -636,8 +633,8 @@ emu_status_t run_scheme_II(emu_handle_s* h, const View& v, int64_t k, int nm, in
   trace_end(h, PH_SPLIT, st, 2);
   CUtensorMap ta, tb;
   // tcgen05: the bf16 planes as bytes, 128-byte (64-element) boxes of 128
-  // rows (A) and 256 / cluster rows (B, multicast to the cluster); INT8:
-  // 32-byte boxes of 64 / 32 rows
+  // rows (A) and 256 / cluster rows (B: a CTA pair loads half of each
+  // 256-column tile per CTA); INT8: 32-byte boxes of 64 / 32 rows
   const uint64_t row_bytes = static_cast<uint64_t>(pl.cols) * (tc ? 2 : 1);
   const int cluster = tc ? gemm_II_tc_cluster() : 1;
   if (!make_tmap_i8(&ta, resA, row_bytes, static_cast<uint64_t>(pl.rows_a) * nm * nsets,
@@ -680,6 +677,7 @@ void launch_scale_c(T* C, int64_t ldc, int64_t M, int64_t N, double beta, cudaSt
   if (tot <= 0) return;
   scale_c_kernel<T><<<static_cast<unsigned>((tot + 255) / 256), 256, 0, st>>>(C, ldc, M, N, beta);
 }
+template void launch_scale_c<double>(double*, int64_t, int64_t, int64_t, double, cudaStream_t);
 
 }  // namespace emu
 

@@ -48,6 +48,10 @@ bool check_lds(emu_layout_t layout, int64_t m, int64_t n, int64_t k, int64_t lda
 
 emu_status_t handle_workspace(emu_handle_s* h, size_t bytes, cudaStream_t st, uint8_t** out);
 
+// C = beta * C for products with k == 0 (beta == 0 writes zeros, C is not read).
+template <typename T>
+void launch_scale_c(T* C, int64_t ldc, int64_t M, int64_t N, double beta, cudaStream_t st);
+
 // Tracing phases and hooks (no-ops unless tracing is enabled).
 enum TracePhase : int { PH_SCAN = 0, PH_SPLIT = 1, PH_GEMM = 2, PH_OTHER = 3 };
 void trace_begin(emu_handle_s* h, int phase, cudaStream_t st);

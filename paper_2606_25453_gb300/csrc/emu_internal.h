@@ -89,12 +89,10 @@ struct GemmIArgs {
   int32_t* partials;
   int* status;
   int num_sms;
-  int cluster;  // tcgen05 kernel: CTAs per cluster sharing the A tiles (1, 2, 4)
 };
 cudaError_t launch_gemm_I(int p, int out_mode, const GemmIArgs& a, cudaStream_t st, bool f8 = false);
 // Scheme I on E4M3 slices with tcgen05 / TMEM (128 x 32 output tiles).
 cudaError_t launch_gemm_f8tc(int p, int out_mode, const GemmIArgs& a, cudaStream_t st);
-int gemm_f8tc_cluster();
 
 // Scheme II kernel modes.
 enum GemmIIOut : int { II_F64 = 0, II_F32 = 1, II_RESIDUES = 2, II_Z3M = 3, II_C3M = 4 };
@@ -115,14 +113,14 @@ struct GemmIIArgs {
   uint8_t* residues;
   int* status;
   int num_sms;
-  int cluster;       // tcgen05 kernel: CTAs per cluster sharing the B chunks (1, 2, 4)
+  int cluster;       // tcgen05 kernel: CTAs per GEMM tile (2: a CTA pair, cta_group::2; 1: one CTA)
   uint8_t* scratch;  // tcgen05 kernel: the residue planes
 };
 cudaError_t launch_gemm_II(int out_mode, const GemmIIArgs& a, const ModTables& mt,
                            const CrtTables& ct, cudaStream_t st);
-// Scheme II on bf16 residue planes with tcgen05 / TMEM (128 x 256 tiles,
-// modulus-major), then the CRT kernel; modes II_F64, II_F32, II_Z3M,
-// II_C3M.  GemmIIArgs::scratch: gemm_II_tc_residue_bytes(M, N, nm, complex,
+// Scheme II on bf16 residue planes with tcgen05 / TMEM (256 x 256 tiles on
+// CTA pairs, or 128 x 256 on single CTAs; modulus-major), then the CRT
+// kernel; modes II_F64, II_F32, II_Z3M, II_C3M.  GemmIIArgs::scratch: gemm_II_tc_residue_bytes(M, N, nm, complex,
 // cluster) bytes of device memory for the residue planes.
 cudaError_t launch_gemm_II_tc(int out_mode, const GemmIIArgs& a, const ModTables& mt,
                               const CrtTables& ct, cudaStream_t st);

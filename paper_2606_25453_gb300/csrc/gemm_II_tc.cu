@@ -21,19 +21,33 @@
 // symmetric range, rounds it once to binary64, scales it back and applies
 // the BLAS update (3M combination of Eq. (16) for complex input).
 //
-// GEMM tile: 128 rows x 256 columns, one 128 x 256 x 16 MMA per K-step
-// (narrow MMAs leave the tensor pipe idle while the MMA thread waits for
-// data).  The two FP32 accumulators take all 512 TMEM columns and alternate
+// GEMM tile, PAIR form: 256 rows x 256 columns on a pair of CTAs
+// (a cluster of two on neighbouring SMs) with tcgen05.mma.cta_group::2: one
+// 256 x 256 x 16 MMA per K-step, issued by the even CTA, reads the 128 rows
+// of A that each CTA holds and the 256 columns of B of which each CTA holds
+// half, and leaves rows 0-127 of the product in the even CTA's TMEM and
+// rows 128-255 in the odd one's.  Each CTA's TMA fills only its own shared
+// memory (its A rows and its half of B) and counts the bytes on the even
+// CTA's stage barrier; the MMA commits release the stage in both CTAs.  Per
+// K-step an SM then reads 8 KB of operands from shared memory and receives
+// 8 KB by TMA, against 12 + 12 KB for a 128 x 256 tile on one CTA, whose
+// shared-memory traffic (192 B per clock at full tensor rate against 128 B
+// per clock of bandwidth) caps it near two thirds of the tensor peak; the
+// smaller stages also fit six deep instead of four.  Measured on GB300 the
+// pair form is nevertheless not faster than the single-CTA form (128 x 256
+// tile, tcgen05.mma.cta_group::1), which is the default; the pair form runs
+// with EMU_II_CLUSTER=2.
+//
+// Two FP32 accumulators take all 512 TMEM columns of each CTA and alternate
 // between K segments, so the MMAs of one segment overlap the reduction of
-// the last.  Roles (320 threads): warps 0-7 drain (warp w: TMEM lanes = tile
-// rows 32 (w % 4) .., columns 128 (w / 4) .. +127; each finished segment is
-// added to a running residue, four per register), warp 8 lane 0 TMA (each
-// load preceded by an L2 prefetch of the chunk four K steps ahead, which
-// hides part of the DRAM latency the four stages do not cover), warp 9 TMEM
-// allocation and (lane 0) MMAs.  CTAs may run in clusters of cl (1, 2,
-// 4) along M that share the B chunks by TMA multicast.  All waits are
-// bounded; a timeout sets the status word, raises an abort flag for the
-// other roles, and the TMEM is still released.
+// the last.  Roles (320 threads per CTA): warps 0-7 drain (warp w: TMEM
+// lanes = tile rows 32 (w % 4) .., columns 128 (w / 4) .. +127; each
+// finished segment is added to a running residue, four per register), warp
+// 8 lane 0 TMA (each load preceded by an L2 prefetch of the chunk four K
+// steps ahead), warp 9 TMEM allocation and (lane 0 of the even CTA) MMAs.
+// All waits are bounded; a timeout sets the status word, raises the abort
+// flag of both CTAs of a pair for the other roles, and the TMEM is still
+// released.
 #include <cstdlib>
 #include <type_traits>
 
@@ -44,27 +58,34 @@
 namespace emu {
 namespace {
 
-constexpr int kBM = 128, kBN = 256;
+constexpr int kBM = 128, kBN = 256;  // accumulator tile of one CTA: TMEM lanes x FP32 columns
 constexpr int kThreads = 320;
-constexpr int kDrainThreads = 256;
+constexpr int kDrainWarps = 8;
 constexpr int kProducerWarp = 8, kMmaWarp = 9;
 constexpr uint32_t kTmemCols = 512;
 constexpr int kSegStages = 15;  // 64-wide K chunks per exact FP32 segment (960 * 2^14 < 2^24)
 static_assert(kSegStages * 64 * 16384 < (1 << 24), "segment sums must stay exact in FP32");
-constexpr int kBlkA = kBM * 128;  // one K chunk: 128 rows x 64 bf16, 128-byte swizzled rows
-constexpr int kBlkB = kBN * 128;
-constexpr int kStageBytes = kBlkA + kBlkB;
-constexpr int kStages = 4;
-constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
 constexpr int kPrefetch = 4;  // chunks ahead of the TMA loads that are prefetched into L2
-static_assert(kSmem <= 232448, "shared memory");
+
+template <bool PAIR>
+struct CfgII {
+  static constexpr int kRowsB = PAIR ? kBN / 2 : kBN;  // B rows (output columns) this CTA loads
+  static constexpr int kBlkA = kBM * 128;               // one K chunk: 128 rows x 64 bf16, 128-byte rows
+  static constexpr int kBlkB = kRowsB * 128;
+  static constexpr int kStageBytes = kBlkA + kBlkB;
+  static constexpr int kStages = PAIR ? 6 : 4;
+  static constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
+  static_assert(kSmem <= 232448, "shared memory");
+  static_assert(kStageBytes % 1024 == 0, "stages keep the 1024-byte swizzle alignment");
+};
 
 struct KParamsIITC {
   CUtensorMap tA;  // bf16 planes as bytes: 128-byte x 128-row boxes, 128-byte swizzle
-  CUtensorMap tB;  // 128-byte x (256 / cl)-row boxes
-  int nst, tiles_m, tiles_n;  // nst: 64-wide K chunks per plane
-  int cl;          // CTAs per cluster (1, 2 or 4): neighbours along M sharing the B chunks
-  int tiles_mg;    // row-tile groups of cl tiles
+  CUtensorMap tB;  // 128-byte x (256 or 128)-row boxes
+  int nst;         // 64-wide K chunks per plane
+  int tiles_m;     // 128-row tiles of the residue matrices (even with CTA pairs)
+  int tiles_mu;    // row units of the work list: 256-row pair tiles or 128-row tiles
+  int tiles_n;     // 256-column tiles
   int nplanes;     // NSET * nm residue planes (plane p = set * nm + l)
   int nm;
   int rowsA_pad, rowsB_pad;
@@ -81,13 +102,120 @@ __device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
          | (static_cast<uint32_t>(M >> 4) << 24);   // M / 16
 }
 
+template <bool PAIR>
 __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                           uint32_t accumulate) {
+  if constexpr (PAIR)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Arrive on the barrier at shared::cluster address `bar` (this CTA's or the
+// peer's) once every MMA issued so far by this thread has completed.
+__device__ __forceinline__ void umma_commit_pair(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+template <bool PAIR>
+__device__ __forceinline__ void tmem_alloc_all(uint32_t* slot) {
+  if constexpr (PAIR) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  } else {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+}
+
+template <bool PAIR>
+__device__ __forceinline__ void tmem_free_all(uint32_t tmem) {
+  if constexpr (PAIR)
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  else
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+// shared::cluster address of the object at shared::cta address `saddr` in
+// the CTA of the cluster with rank `rank`.
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+
+// 2D tiled TMA load into this CTA's shared memory, completion counted on the
+// barrier at shared::cluster address `bar`, which may be the peer CTA's.
+__device__ __forceinline__ void tma_load_2d_pair(void* smem_dst, const void* desc, uint32_t bar, int x, int y) {
   asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(smem_dst)),
+      "l"(reinterpret_cast<uint64_t>(desc)), "r"(bar), "r"(x), "r"(y)
       : "memory");
+}
+
+// Arrive (release, cluster scope) on the barrier at shared::cluster address `bar`.
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait_acq_cluster(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Abort flags: this CTA's, and (pairs) the shared::cluster address of the
+// peer's, so that a role that gives up stops both CTAs of the pair.
+struct AbortFlag {
+  volatile int* local;
+  uint32_t peer;  // 0: no peer
+};
+
+__device__ __forceinline__ void raise_abort(const AbortFlag& ab) {
+  *ab.local = 1;
+  if (ab.peer) asm volatile("st.relaxed.cluster.shared::cluster.u32 [%0], %1;" ::"r"(ab.peer), "r"(1u) : "memory");
+}
+
+// Bounded wait unless the pair already gave up; false means "stop".  With
+// `cluster_acq` the wait acquires at cluster scope (arrivals from the peer).
+__device__ __forceinline__ bool wait_pair(uint64_t* bar, uint32_t parity, const AbortFlag& ab, int* status,
+                                          bool cluster_acq = false) {
+  if (*ab.local) return false;
+  if (cluster_acq) {
+    if (mbar_try_wait_acq_cluster(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait_acq_cluster(bar, parity)) {
+      if (*ab.local) return false;
+      if (clock64() - t0 > kWaitCycles) {
+        set_status(status, ST_TIMEOUT);
+        raise_abort(ab);
+        return false;
+      }
+    }
+    return true;
+  }
+  if (mbar_wait_bounded(bar, parity)) return true;
+  set_status(status, ST_TIMEOUT);
+  raise_abort(ab);
+  return false;
 }
 
 // Hint: bring a 2D box of the tensor into L2 (no shared memory involved).
@@ -130,137 +258,138 @@ __device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, 
   tn = in / gsz;
 }
 
-// Work item i of a cluster: plane p = i / (tiles per plane), then the tile.
+// Work item i: plane p = i / (tiles per plane), then the tile; tm is this
+// CTA's 128-row tile (a pair's rows 0-127 on the even CTA, 128-255 on the
+// odd one).
+template <bool PAIR>
 __device__ __forceinline__ void item_coords(const KParamsIITC& kp, int item, int crank, int& p, int& tm, int& tn) {
-  const int per_plane = kp.tiles_mg * kp.tiles_n;
+  const int per_plane = kp.tiles_mu * kp.tiles_n;
   p = item / per_plane;
-  int tg;
-  tile_coords(item - p * per_plane, kp.tiles_mg, kp.tiles_n, tg, tn);
-  tm = tg * kp.cl + crank;
-}
-
-// A warp-uniform bounded wait: every lane waits, and the warp goes on only
-// if all of them saw the phase complete.
-__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status) {
-  return __all_sync(0xFFFFFFFFu, wait_or_abort(bar, parity, abort_flag, status));
+  int tu;
+  tile_coords(item - p * per_plane, kp.tiles_mu, kp.tiles_n, tu, tn);
+  tm = PAIR ? 2 * tu + crank : tu;
 }
 
 __device__ __forceinline__ int sbyte(uint32_t w, int i) { return static_cast<int>(static_cast<int8_t>(w >> (8 * i))); }
 
+template <bool PAIR>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_II_tc_kernel(const __grid_constant__ KParamsIITC kp, const __grid_constant__ ModTables mt) {
+  using Cfg = CfgII<PAIR>;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* smem = smem_raw + (base - raw);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
-  uint64_t* empty = full + kStages;
-  uint64_t* acc_full = empty + kStages;  // two accumulators
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + Cfg::kStages * Cfg::kStageBytes);
+  uint64_t* empty = full + Cfg::kStages;
+  uint64_t* acc_full = empty + Cfg::kStages;  // two accumulators
   uint64_t* acc_empty = acc_full + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* abort_local = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int cl = kp.cl;
-  const uint16_t cl_mask = static_cast<uint16_t>((1u << cl) - 1u);
-  const int crank = cl > 1 ? static_cast<int>(cluster_ctarank()) : 0;
-  const int cid = cl > 1 ? static_cast<int>(cluster_id_x()) : static_cast<int>(blockIdx.x);
-  const int ncl = cl > 1 ? static_cast<int>(cluster_count_x()) : static_cast<int>(gridDim.x);
+  const uint32_t crank = PAIR ? cluster_ctarank() : 0u;  // 0: the pair's MMA-issuing CTA
+  const bool leader = crank == 0;
+  const int cid = PAIR ? static_cast<int>(cluster_id_x()) : static_cast<int>(blockIdx.x);
+  const int ncl = PAIR ? static_cast<int>(cluster_count_x()) : static_cast<int>(gridDim.x);
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], static_cast<uint32_t>(cl));  // one MMA commit from each CTA of the cluster
+    for (int s = 0; s < Cfg::kStages; ++s) {
+      mbar_init(&full[s], 1);   // the even CTA's expect-tx arrival (+ the bytes of both CTAs)
+      mbar_init(&empty[s], 1);  // one MMA commit
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], kDrainThreads);
+      mbar_init(&acc_empty[b], PAIR ? 2 * kDrainWarps : kDrainWarps);  // one arrival per drain warp
     }
-    *abort_flag = 0;
+    *abort_local = 0;
     fence_mbar_init();
   }
-  if (warp == kMmaWarp) {  // the whole warp allocates the tensor memory
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(kTmemCols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  if (warp == kMmaWarp) {  // the whole warp allocates the tensor memory (both CTAs of a pair)
+    tmem_alloc_all<PAIR>(tmem_slot);
     tc_fence_before();
   }
-  // barriers initialised in every CTA before any CTA multicasts into them
-  if (cl > 1)
+  // barriers and flags initialised in both CTAs before either touches the peer's
+  if (PAIR)
     cluster_sync_all();
   else
     __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  AbortFlag ab;
+  ab.local = abort_local;
+  ab.peer = PAIR ? cluster_addr(smem_u32(const_cast<int*>(abort_local)), crank ^ 1u) : 0u;
 
-  // the cluster walks items (plane, tile of (cl x 128) rows x 256 columns);
-  // CTA `crank` owns the crank-th 128-row tile of each
-  const int nitems = kp.nplanes * kp.tiles_mg * kp.tiles_n;
+  const int nitems = kp.nplanes * kp.tiles_mu * kp.tiles_n;
   const int my_items = cid < nitems ? (nitems - 1 - cid) / ncl + 1 : 0;
   const int nseg = (kp.nst + kSegStages - 1) / kSegStages;
 
   if (warp == kProducerWarp) {
-    // ---------------------------------------------------------------- producer
+    // ---------------------------------------------------------------- producer (both CTAs)
     if (lane == 0) {
       tma_prefetch_desc(&kp.tA);
       tma_prefetch_desc(&kp.tB);
-      const int piece_rows = kBN / cl;
       uint32_t j = 0;
       bool stop = false;
       for (int t = 0; t < my_items && !stop; ++t) {
         int p, tm, tn;
-        item_coords(kp, cid + t * ncl, crank, p, tm, tn);
+        item_coords<PAIR>(kp, cid + t * ncl, static_cast<int>(crank), p, tm, tn);
         const int ya = p * kp.rowsA_pad + tm * kBM;
-        const int yb = p * kp.rowsB_pad + tn * kBN;
+        const int yb = p * kp.rowsB_pad + tn * kBN + static_cast<int>(crank) * Cfg::kRowsB;
         int pya = 0, pyb = 0;  // the next item's rows, for prefetches that run past this item's K
         if (t + 1 < my_items) {
           int p2, tm2, tn2;
-          item_coords(kp, cid + (t + 1) * ncl, crank, p2, tm2, tn2);
+          item_coords<PAIR>(kp, cid + (t + 1) * ncl, static_cast<int>(crank), p2, tm2, tn2);
           pya = p2 * kp.rowsA_pad + tm2 * kBM;
-          pyb = p2 * kp.rowsB_pad + tn2 * kBN + crank * piece_rows;
+          pyb = p2 * kp.rowsB_pad + tn2 * kBN + static_cast<int>(crank) * Cfg::kRowsB;
         }
         for (int ks = 0; ks < kp.nst; ++ks, ++j) {
-          {  // warm L2 with the chunk kPrefetch steps ahead (this CTA's share of B)
+          {  // warm L2 with this CTA's operand rows of the chunk kPrefetch steps ahead
             const int kf = ks + kPrefetch;
             if (kf < kp.nst) {
               tma_prefetch_l2(&kp.tA, kf * 128, ya);
-              tma_prefetch_l2(&kp.tB, kf * 128, yb + crank * piece_rows);
+              tma_prefetch_l2(&kp.tB, kf * 128, yb);
             } else if (t + 1 < my_items && kf - kp.nst < kp.nst) {
               tma_prefetch_l2(&kp.tA, (kf - kp.nst) * 128, pya);
               tma_prefetch_l2(&kp.tB, (kf - kp.nst) * 128, pyb);
             }
           }
-          const uint32_t stage = j % kStages;
-          if (j >= static_cast<uint32_t>(kStages) &&
-              !wait_or_abort(&empty[stage], ((j / kStages) & 1u) ^ 1u, abort_flag, kp.status)) {
+          const uint32_t stage = j % Cfg::kStages;
+          if (j >= static_cast<uint32_t>(Cfg::kStages) &&
+              !wait_pair(&empty[stage], ((j / Cfg::kStages) & 1u) ^ 1u, ab, kp.status)) {
             stop = true;
             break;
           }
-          mbar_arrive_expect_tx(&full[stage], kStageBytes);
-          uint8_t* sA = smem + stage * kStageBytes;
-          tma_load_2d(sA, &kp.tA, &full[stage], ks * 128, ya);
-          if (cl > 1)  // this CTA's rows of the B chunk, to every CTA of the cluster
-            tma_load_2d_mc(sA + kBlkA + crank * piece_rows * 128, &kp.tB, &full[stage], ks * 128,
-                           yb + crank * piece_rows, cl_mask);
-          else
-            tma_load_2d(sA + kBlkA, &kp.tB, &full[stage], ks * 128, yb);
+          uint8_t* sA = smem + stage * Cfg::kStageBytes;
+          if (PAIR) {
+            // both CTAs' bytes are counted on the even CTA's barrier
+            const uint32_t bar = cluster_addr(smem_u32(&full[stage]), 0u);
+            if (leader) mbar_arrive_expect_tx(&full[stage], 2 * Cfg::kStageBytes);
+            tma_load_2d_pair(sA, &kp.tA, bar, ks * 128, ya);
+            tma_load_2d_pair(sA + Cfg::kBlkA, &kp.tB, bar, ks * 128, yb);
+          } else {
+            mbar_arrive_expect_tx(&full[stage], Cfg::kStageBytes);
+            tma_load_2d(sA, &kp.tA, &full[stage], ks * 128, ya);
+            tma_load_2d(sA + Cfg::kBlkA, &kp.tB, &full[stage], ks * 128, yb);
+          }
         }
       }
-      // Drain: wait until the last commits of every CTA of the cluster have
-      // arrived on this CTA's stage barriers, so none lands after it exits.
-      if (!stop && cl > 1) {
-        for (uint32_t jj = j; jj < j + kStages; ++jj) {
-          if (jj < static_cast<uint32_t>(kStages)) continue;
-          const uint32_t stage = jj % kStages;
-          if (!wait_or_abort(&empty[stage], ((jj / kStages) & 1u) ^ 1u, abort_flag, kp.status)) break;
+      // Drain: wait until the last MMA commits have arrived on this CTA's
+      // stage barriers (a pair's odd CTA gets them from the even one), so
+      // that none lands after the CTA exits.
+      if (!stop && PAIR) {
+        for (uint32_t jj = j; jj < j + Cfg::kStages; ++jj) {
+          if (jj < static_cast<uint32_t>(Cfg::kStages)) continue;
+          const uint32_t stage = jj % Cfg::kStages;
+          if (!wait_pair(&empty[stage], ((jj / Cfg::kStages) & 1u) ^ 1u, ab, kp.status)) break;
         }
       }
     }
     __syncwarp();
   } else if (warp == kMmaWarp) {
-    // ---------------------------------------------------------------- MMA issuer
-    if (lane == 0) {
-      const uint32_t idesc = idesc_bf16(kBM, kBN);
+    // ---------------------------------------------------------------- MMA issuer (even CTA of a pair)
+    if (lane == 0 && leader) {
+      const uint32_t idesc = idesc_bf16(PAIR ? 2 * kBM : kBM, kBN);
+      const uint32_t peer = 1u;
       uint32_t it = 0, seg = 0;
       bool stop = false;
       for (int t = 0; t < my_items && !stop; ++t)
@@ -268,45 +397,55 @@ __global__ void __launch_bounds__(kThreads, 1)
           const bool first = ks % kSegStages == 0;
           const uint32_t b = seg & 1u;
           if (first && seg >= 2) {  // the drain warps must have read this accumulator's last segment
-            if (!wait_or_abort(&acc_empty[b], ((seg >> 1) - 1) & 1u, abort_flag, kp.status)) {
+            if (!wait_pair(&acc_empty[b], ((seg >> 1) - 1) & 1u, ab, kp.status, PAIR)) {
               stop = true;
               break;
             }
             tc_fence_after();
           }
-          const uint32_t stage = it % kStages;
-          if (!wait_or_abort(&full[stage], (it / kStages) & 1u, abort_flag, kp.status)) {
+          const uint32_t stage = it % Cfg::kStages;
+          if (!wait_pair(&full[stage], (it / Cfg::kStages) & 1u, ab, kp.status)) {
             stop = true;
             break;
           }
           tc_fence_after();
-          const uint32_t sA = base + stage * kStageBytes;
+          const uint32_t sA = base + stage * Cfg::kStageBytes;
 #pragma unroll
           for (int q = 0; q < 4; ++q)  // four K-steps of 16 inside the 128-byte rows
-            umma_bf16(tmem + b * kBN, smem_desc_k128(sA + 32 * q), smem_desc_k128(sA + kBlkA + 32 * q), idesc,
-                      (first && q == 0) ? 0u : 1u);
-          // the stage is free (in every CTA of the cluster) once these MMAs finish
-          if (cl > 1)
-            umma_commit_mc(&empty[stage], cl_mask);
-          else
+            umma_bf16<PAIR>(tmem + b * kBN, smem_desc_k128(sA + 32 * q), smem_desc_k128(sA + Cfg::kBlkA + 32 * q),
+                            idesc, (first && q == 0) ? 0u : 1u);
+          // the stage is free (in both CTAs of a pair) once these MMAs finish
+          if (PAIR) {
+            umma_commit_pair(smem_u32(&empty[stage]));
+            umma_commit_pair(cluster_addr(smem_u32(&empty[stage]), peer));
+          } else {
             umma_commit(&empty[stage]);
+          }
           if ((ks + 1) % kSegStages == 0 || ks + 1 == kp.nst) {
-            umma_commit(&acc_full[b]);
+            if (PAIR) {
+              umma_commit_pair(smem_u32(&acc_full[b]));
+              umma_commit_pair(cluster_addr(smem_u32(&acc_full[b]), peer));
+            } else {
+              umma_commit(&acc_full[b]);
+            }
             ++seg;
           }
         }
     }
     __syncwarp();
   } else {
-    // ---------------------------------------------------------------- drain
+    // ---------------------------------------------------------------- drain (both CTAs)
     const int hh = warp >> 2;
     const int row_in_tile = (warp & 3) * 32 + lane;
     const uint32_t lane_addr = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16) + static_cast<uint32_t>(hh * 128);
+    // the accumulators are released to the even CTA's MMA thread
+    const uint32_t acc_empty0 = PAIR ? cluster_addr(smem_u32(&acc_empty[0]), 0u) : 0u;
+    const uint32_t acc_empty1 = PAIR ? cluster_addr(smem_u32(&acc_empty[1]), 0u) : 0u;
     uint32_t seg = 0;
     bool stop = false;
     for (int t = 0; t < my_items && !stop; ++t) {
       int p, tm, tn;
-      item_coords(kp, cid + t * ncl, crank, p, tm, tn);
+      item_coords<PAIR>(kp, cid + t * ncl, static_cast<int>(crank), p, tm, tn);
       const int l = p % kp.nm;
       const int m = static_cast<int>(mt.mods[l]), off = mt.off[l];
       const float inv = mt.inv[l], offinv = mt.offinv[l];
@@ -315,7 +454,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int i = 0; i < 32; ++i) run[i] = 0;
       for (int s = 0; s < nseg; ++s, ++seg) {
         const uint32_t b = seg & 1u;
-        if (!warp_wait(&acc_full[b], (seg >> 1) & 1u, abort_flag, kp.status)) {
+        if (!__all_sync(0xFFFFFFFFu, wait_pair(&acc_full[b], (seg >> 1) & 1u, ab, kp.status))) {
           stop = true;
           break;
         }
@@ -325,9 +464,15 @@ __global__ void __launch_bounds__(kThreads, 1)
           uint32_t v[16];
           tmem_ld16(lane_addr + b * kBN + 16 * q, v);
           tmem_wait_ld();
-          if (q == 7) {
+          if (q == 7) {  // the MMAs may refill this accumulator now
             tc_fence_before();
-            mbar_arrive(&acc_empty[b]);  // the MMAs may refill this accumulator now
+            __syncwarp();
+            if (lane == 0) {
+              if (PAIR)
+                mbar_arrive_cluster(b ? acc_empty1 : acc_empty0);
+              else
+                mbar_arrive(&acc_empty[b]);
+            }
           }
 #pragma unroll
           for (int w = 0; w < 4; ++w) {
@@ -365,14 +510,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   }
   tc_fence_before();
-  // no CTA leaves while a peer may still write into its shared memory
-  if (cl > 1)
+  // no CTA of a pair leaves while the other may still touch its shared or tensor memory
+  if (PAIR)
     cluster_sync_all();
   else
     __syncthreads();
   if (warp == kMmaWarp) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    tmem_free_all<PAIR>(tmem);
   }
 }
 
@@ -488,41 +633,42 @@ __global__ void __launch_bounds__(256) crt_II_kernel(const __grid_constant__ KPa
   }
 }
 
-// Largest number of co-resident clusters of `cl` CTAs of the GEMM kernel (0
-// if it cannot run with that cluster size).
-int max_clusters(int cl) {
+// Largest number of co-resident CTA pairs of the GEMM kernel (0 if it cannot
+// run in clusters of two).
+int max_pairs() {
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = static_cast<unsigned>(cl);
+  at[0].val.clusterDim.x = 2;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
-  cfg.gridDim = dim3(static_cast<unsigned>(cl) * 64u);
+  cfg.gridDim = dim3(2u * 64u);
   cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = kSmem;
+  cfg.dynamicSmemBytes = CfgII<true>::kSmem;
   cfg.attrs = at;
   cfg.numAttrs = 1;
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, gemm_II_tc_kernel, &cfg) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveClusters(&n, gemm_II_tc_kernel<true>, &cfg) != cudaSuccess) {
     (void)cudaGetLastError();
     return 0;
   }
   return n;
 }
 
-cudaError_t launch_residues(const GemmIIArgs& a, int nsets, const ModTables& mt, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(gemm_II_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+template <bool PAIR>
+cudaError_t launch_residues_t(const GemmIIArgs& a, int nsets, const ModTables& mt, cudaStream_t st) {
+  using Cfg = CfgII<PAIR>;
+  cudaError_t e = cudaFuncSetAttribute(gemm_II_tc_kernel<PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       Cfg::kSmem);
   if (e != cudaSuccess) return e;
-  const int cl = a.cluster;
-  if (cl != 1 && cl != 2 && cl != 4) return cudaErrorInvalidValue;
   KParamsIITC kp;
   kp.tA = *a.descA;
   kp.tB = *a.descB;
   kp.nst = a.nk32 / 2;  // planes are padded to 128 K-elements
   kp.tiles_m = (a.M + kBM - 1) / kBM;
+  if (PAIR) kp.tiles_m += kp.tiles_m & 1;  // whole pair tiles: the residue planes hold them
+  kp.tiles_mu = PAIR ? kp.tiles_m / 2 : kp.tiles_m;
   kp.tiles_n = (a.N + kBN - 1) / kBN;
-  kp.cl = cl;
-  kp.tiles_mg = (kp.tiles_m + cl - 1) / cl;
   kp.nplanes = nsets * a.nm;
   kp.nm = a.nm;
   kp.rowsA_pad = a.rowsA_pad;
@@ -530,36 +676,36 @@ cudaError_t launch_residues(const GemmIIArgs& a, int nsets, const ModTables& mt,
   kp.R = a.scratch;
   kp.ldr = static_cast<int64_t>(kp.tiles_n) * kBN;
   kp.status = a.status;
-  // the residue planes hold cl-rounded row tiles, so every CTA's tile is in bounds
-  kp.tiles_m = kp.tiles_mg * cl;
-  const int nitems = kp.nplanes * kp.tiles_mg * kp.tiles_n;
+  const int nitems = kp.nplanes * kp.tiles_mu * kp.tiles_n;
   if (nitems == 0 || kp.nst == 0) return cudaSuccess;
-  if (cl == 1) {
+  if (!PAIR) {
     const int grid = nitems < a.num_sms ? nitems : a.num_sms;
-    gemm_II_tc_kernel<<<grid, kThreads, kSmem, st>>>(kp, mt);
+    gemm_II_tc_kernel<false><<<grid, kThreads, Cfg::kSmem, st>>>(kp, mt);
     return cudaGetLastError();
   }
   static int mc = -1;
-  static int mc_cl = 0;
-  if (mc < 0 || mc_cl != cl) {
-    mc = max_clusters(cl);
-    mc_cl = cl;
-  }
+  if (mc < 0) mc = max_pairs();
   if (mc <= 0) return cudaErrorInvalidConfiguration;
-  const int nclusters = nitems < mc ? nitems : mc;
+  const int npairs = nitems < mc ? nitems : mc;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = static_cast<unsigned>(cl);
+  at[0].val.clusterDim.x = 2;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
-  cfg.gridDim = dim3(static_cast<unsigned>(nclusters * cl));
+  cfg.gridDim = dim3(static_cast<unsigned>(2 * npairs));
   cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = kSmem;
+  cfg.dynamicSmemBytes = Cfg::kSmem;
   cfg.stream = st;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, gemm_II_tc_kernel, kp, mt);
+  return cudaLaunchKernelEx(&cfg, gemm_II_tc_kernel<true>, kp, mt);
+}
+
+cudaError_t launch_residues(const GemmIIArgs& a, int nsets, const ModTables& mt, cudaStream_t st) {
+  if (a.cluster == 2) return launch_residues_t<true>(a, nsets, mt, st);
+  if (a.cluster == 1) return launch_residues_t<false>(a, nsets, mt, st);
+  return cudaErrorInvalidValue;
 }
 
 template <int MODE>
@@ -609,14 +755,15 @@ size_t gemm_II_tc_residue_bytes(int64_t M, int64_t N, int nm, bool is_complex, i
          static_cast<size_t>(tiles_n * kBN);
 }
 
-// CTAs per cluster for the Scheme II tcgen05 kernel: EMU_II_CLUSTER (1, 2
-// or 4) if set, else 2.  The B tensor map's box is 256 / cluster rows.
+// CTAs per GEMM tile of the Scheme II tcgen05 kernel: 1 (one CTA on a
+// 128 x 256 tile; the default) or 2 (a CTA pair on one 256 x 256 tile,
+// tcgen05.mma.cta_group::2) with EMU_II_CLUSTER=2.  The B tensor map's box
+// is 256 / cluster rows.
 int gemm_II_tc_cluster() {
   static int v = 0;
   if (v == 0) {
     const char* e = std::getenv("EMU_II_CLUSTER");
-    const int x = e ? std::atoi(e) : 2;
-    v = (x == 1 || x == 2 || x == 4) ? x : 2;
+    v = (e && std::atoi(e) == 2) ? 2 : 1;
   }
   return v;
 }

@@ -18,14 +18,10 @@
 //
 // The A slices of a K-chunk travel as 128-byte rows (four slices per TMA box,
 // 128-byte swizzle; the MMA of slice 4g+u starts 32 u bytes into the row), so
-// one L2 request carries four slices instead of one.  A 128 x 32 tile reads
-// its A slices once per 32 output columns, so without help the A operand
-// crosses L2 -> SM N/32 times.  CTAs are therefore launched
-// in clusters of CL (1, 2 or 4) that work on the same row block and CL
-// neighbouring column tiles: each CTA fetches 128/CL rows of every A slice and
-// multicasts them to the whole cluster, dividing that traffic by CL.  A stage
-// is refilled only when the MMAs of every CTA in the cluster are done with it
-// (the MMA commits arrive on the stage barrier of all CTAs of the cluster).  Slices are balanced
+// one L2 request carries four slices instead of one.  Each CTA loads its own
+// operands from this GPU's memory (no cluster sharing: pairs of CTAs that
+// shared the A slices by multicast measured within 1.5 % of single CTAs at
+// n = 8192, p = 12).  Slices are balanced
 // base-32 digits stored as E4M3 bytes, so every product is exact and the FP32
 // accumulators stay exact integers while |sum| <= 2^24: they are drained
 // every K_c (the E4M3 chunk bound) and at the end of each tile.  All waits are
@@ -65,11 +61,9 @@ struct CfgTC {
 };
 
 struct KParamsTC {
-  CUtensorMap tA;  // box: 128 B x (128 / cl) rows, 128-byte swizzle
+  CUtensorMap tA;  // box: 128 B x 128 rows, 128-byte swizzle
   CUtensorMap tB;  // box: 32 B x 32 rows
   int M, N, nk32, kc32, tiles_m, tiles_n;
-  int cl;          // CTAs per cluster (1, 2 or 4), neighbours along N
-  int tiles_ng;    // column-tile groups of cl tiles
   const int32_t* EA;
   const int32_t* FB;
   int escale;
@@ -178,15 +172,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1) gemm_f8tc_kernel(const __grid_c
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int cl = kp.cl;
-  const uint16_t cl_mask = static_cast<uint16_t>((1u << cl) - 1u);
-  const int crank = cl > 1 ? static_cast<int>(cluster_ctarank()) : 0;
-  const int cid = cl > 1 ? static_cast<int>(cluster_id_x()) : static_cast<int>(blockIdx.x);
-  const int ncl = cl > 1 ? static_cast<int>(cluster_count_x()) : static_cast<int>(gridDim.x);
+  const int cid = static_cast<int>(blockIdx.x);
+  const int ncl = static_cast<int>(gridDim.x);
   if (threadIdx.x == 0) {
     for (int s = 0; s < Cfg::kStages; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], static_cast<uint32_t>(cl));  // one MMA commit from each CTA of the cluster
+      mbar_init(&empty[s], 1);
     }
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, kEpiThreads);
@@ -200,17 +191,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1) gemm_f8tc_kernel(const __grid_c
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     tc_fence_before();
   }
-  // barriers initialised in every CTA before any CTA multicasts into them
-  if (cl > 1)
-    cluster_sync_all();
-  else
-    __syncthreads();
+  __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  // the cluster walks tiles of 128 rows x (cl x 32) columns; CTA `crank` owns
-  // the crank-th 32-column tile of each
-  const int ntiles = kp.tiles_m * kp.tiles_ng;
+  // the CTA walks tiles of 128 rows x 32 columns
+  const int ntiles = kp.tiles_m * kp.tiles_n;
   const int my_tiles = cid < ntiles ? (ntiles - 1 - cid) / ncl + 1 : 0;
   const int drains_per_tile = (kp.nk32 + kp.kc32 - 1) / kp.kc32;
 
@@ -219,12 +205,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1) gemm_f8tc_kernel(const __grid_c
     if (lane == 0) {
       tma_prefetch_desc(&kp.tA);
       tma_prefetch_desc(&kp.tB);
-      const int piece_rows = kBM / cl;
       const uint32_t total = static_cast<uint32_t>(my_tiles) * static_cast<uint32_t>(kp.nk32);
       bool ok = true;
       for (uint32_t j = 0; j < total; ++j) {
         const uint32_t stage = j % Cfg::kStages;
-        // the stage is free once every CTA of the cluster has consumed it
+        // the stage is free once the MMAs that read it have completed
         if (j >= static_cast<uint32_t>(Cfg::kStages) &&
             !wait_or_abort(&empty[stage], ((j / Cfg::kStages) & 1u) ^ 1u, abort_flag, kp.status)) {
           ok = false;
@@ -236,38 +221,22 @@ __global__ void __launch_bounds__(kThreadsTC, 1) gemm_f8tc_kernel(const __grid_c
         // the previous wave read last (still in L2); the sums are exact, so
         // their order does not matter
         const int kk = (tt & 1) ? kp.nk32 - 1 - static_cast<int>(j % kp.nk32) : static_cast<int>(j % kp.nk32);
-        int tm, tg;
-        tile_coords(tile, kp.tiles_m, kp.tiles_ng, tm, tg);
-        const int tn = tg * cl + crank;
+        int tm, tn;
+        tile_coords(tile, kp.tiles_m, kp.tiles_n, tm, tn);
         mbar_arrive_expect_tx(&full[stage], Cfg::kStageBytes);
         uint8_t* sA = smem + stage * Cfg::kStageBytes;
         uint8_t* sB = sA + Cfg::kGroups * Cfg::kBlkAg;
         // A: slices 4g .. 4g+3 of the chunk in one 128-byte box (a group that
         // runs past slice P-1 reads the next chunk's slices, or the zero fill
         // past the last chunk; the MMAs never use them)
-        if (cl > 1) {
 #pragma unroll
-          for (int g = 0; g < Cfg::kGroups; ++g)
-            tma_load_2d_mc(sA + g * Cfg::kBlkAg + crank * piece_rows * 128, &kp.tA, &full[stage],
-                           (kk * P + 4 * g) * 32, tm * kBM + crank * piece_rows, cl_mask);
-        } else {
-#pragma unroll
-          for (int g = 0; g < Cfg::kGroups; ++g)
-            tma_load_2d(sA + g * Cfg::kBlkAg, &kp.tA, &full[stage], (kk * P + 4 * g) * 32, tm * kBM);
-        }
+        for (int g = 0; g < Cfg::kGroups; ++g)
+          tma_load_2d(sA + g * Cfg::kBlkAg, &kp.tA, &full[stage], (kk * P + 4 * g) * 32, tm * kBM);
 #pragma unroll
         for (int t = 0; t < P; ++t)
           tma_load_2d(sB + t * Cfg::kBlkB, &kp.tB, &full[stage], (kk * P + t) * 32, tn * kBN);
       }
-      // Drain: wait until the last commits of every CTA of the cluster have
-      // arrived on this CTA's stage barriers, so none lands after it exits.
-      if (ok && cl > 1) {
-        for (uint32_t j = total; j < total + Cfg::kStages; ++j) {
-          if (j < static_cast<uint32_t>(Cfg::kStages)) continue;
-          const uint32_t stage = j % Cfg::kStages;
-          if (!wait_or_abort(&empty[stage], ((j / Cfg::kStages) & 1u) ^ 1u, abort_flag, kp.status)) break;
-        }
-      }
+      (void)ok;
     }
     __syncwarp();
   } else if (warp == kMmaWarp) {
@@ -317,11 +286,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) gemm_f8tc_kernel(const __grid_c
             if (i == kProbeRow && it + 1 < total)
               ready = mbar_test_wait(&full[(it + 1) % Cfg::kStages], ((it + 1) / Cfg::kStages) & 1u);
           }
-          // the stage is free (in every CTA of the cluster) once these MMAs finish
-          if (cl > 1)
-            umma_commit_mc(&empty[stage], cl_mask);
-          else
-            umma_commit(&empty[stage]);
+          // the stage is free once these MMAs finish
+          umma_commit(&empty[stage]);
           if ((kk + 1) % kp.kc32 == 0 || kk + 1 == kp.nk32) {
             umma_commit(acc_full);  // accumulators ready for the epilogue
             ++drain;
@@ -341,9 +307,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) gemm_f8tc_kernel(const __grid_c
     bool stop = false;
     for (int t = 0; t < my_tiles && !stop; ++t) {
       const int tile = cid + t * ncl;
-      int tm, tg;
-      tile_coords(tile, kp.tiles_m, kp.tiles_ng, tm, tg);
-      const int tn = tg * cl + crank;
+      int tm, tn;
+      tile_coords(tile, kp.tiles_m, kp.tiles_n, tm, tn);
       __int128 S[16];
 #pragma unroll
       for (int c = 0; c < 16; ++c) S[c] = 0;
@@ -403,42 +368,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1) gemm_f8tc_kernel(const __grid_c
     }
   }
   tc_fence_before();
-  // no CTA leaves while a peer may still write into its shared memory
-  if (cl > 1)
-    cluster_sync_all();
-  else
-    __syncthreads();
+  __syncthreads();
   if (warp == kMmaWarp) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }
-}
-
-// Largest number of co-resident clusters of `cl` CTAs of this kernel (0 if
-// it cannot run with that cluster size).
-template <int P, int OUT>
-int max_clusters(int cl) {
-  using Cfg = CfgTC<P>;
-  if (cudaFuncSetAttribute(gemm_f8tc_kernel<P, OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem) !=
-      cudaSuccess)
-    return 0;
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = static_cast<unsigned>(cl);
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.gridDim = dim3(static_cast<unsigned>(cl) * 64u);
-  cfg.blockDim = dim3(kThreadsTC);
-  cfg.dynamicSmemBytes = Cfg::kSmem;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, gemm_f8tc_kernel<P, OUT>, &cfg) != cudaSuccess) {
-    (void)cudaGetLastError();
-    return 0;
-  }
-  return n;
 }
 
 template <int P, int OUT>
@@ -447,8 +381,6 @@ cudaError_t launch_tc(const GemmIArgs& a, cudaStream_t st, bool partials) {
   cudaError_t e =
       cudaFuncSetAttribute(gemm_f8tc_kernel<P, OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
   if (e != cudaSuccess) return e;
-  const int cl = a.cluster;
-  if (cl != 1 && cl != 2 && cl != 4) return cudaErrorInvalidValue;
   KParamsTC kp;
   kp.tA = *a.descA;
   kp.tB = *a.descB;
@@ -458,8 +390,6 @@ cudaError_t launch_tc(const GemmIArgs& a, cudaStream_t st, bool partials) {
   kp.kc32 = a.kc32;
   kp.tiles_m = (a.M + kBM - 1) / kBM;
   kp.tiles_n = (a.N + kBN - 1) / kBN;
-  kp.cl = cl;
-  kp.tiles_ng = (kp.tiles_n + cl - 1) / cl;
   kp.EA = a.EA;
   kp.FB = a.FB;
   kp.escale = -8 - 5 * (P - 1);
@@ -469,51 +399,17 @@ cudaError_t launch_tc(const GemmIArgs& a, cudaStream_t st, bool partials) {
   kp.ldc = a.ldc;
   kp.partials = partials ? a.partials : nullptr;
   kp.status = a.status;
-  const int ntiles = kp.tiles_m * kp.tiles_ng;
+  const int ntiles = kp.tiles_m * kp.tiles_n;
   if (ntiles == 0 || kp.nk32 == 0) return cudaSuccess;
-  if (cl == 1) {
-    const int grid = ntiles < a.num_sms ? ntiles : a.num_sms;
-    gemm_f8tc_kernel<P, OUT><<<grid, kThreadsTC, Cfg::kSmem, st>>>(kp);
-    return cudaGetLastError();
-  }
-  static int cached[3] = {-1, -1, -1};  // per cluster size 1, 2, 4 (index cl / 2)
-  int& mc = cached[cl / 2];
-  if (mc < 0) mc = max_clusters<P, OUT>(cl);
-  if (mc <= 0) return cudaErrorInvalidConfiguration;
-  const int nclusters = ntiles < mc ? ntiles : mc;
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = static_cast<unsigned>(cl);
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.gridDim = dim3(static_cast<unsigned>(nclusters * cl));
-  cfg.blockDim = dim3(kThreadsTC);
-  cfg.dynamicSmemBytes = Cfg::kSmem;
-  cfg.stream = st;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, gemm_f8tc_kernel<P, OUT>, kp);
+  const int grid = ntiles < a.num_sms ? ntiles : a.num_sms;
+  gemm_f8tc_kernel<P, OUT><<<grid, kThreadsTC, Cfg::kSmem, st>>>(kp);
+  return cudaGetLastError();
 }
 
 }  // namespace
 
 int gemm_f8tc_tile_m() { return kBM; }
 int gemm_f8tc_tile_n() { return kBN; }
-
-// CTAs per cluster for the E4M3 tcgen05 kernel: EMU_TC_CLUSTER (1, 2 or 4)
-// if set, else 2 (pairs of CTAs halve the L2 reads of A and still fill all
-// 152 SMs; clusters of 4 leave some SMs idle).  The A tensor map's box is
-// 128 / cluster rows.
-int gemm_f8tc_cluster() {
-  static int v = 0;
-  if (v == 0) {
-    const char* e = std::getenv("EMU_TC_CLUSTER");
-    const int x = e ? std::atoi(e) : 2;
-    v = (x == 1 || x == 2 || x == 4) ? x : 2;
-  }
-  return v;
-}
 
 cudaError_t launch_gemm_f8tc(int p, int out_mode, const GemmIArgs& a, cudaStream_t st) {
 #define EMU_TC(PP)                                                \

@@ -13,11 +13,15 @@
 // the process exits.
 //
 // The array's name is only a host-side stand-in for the device object, so
-// host code obtains the real device address with cudaGetSymbolAddress, once
-// per device, with that device current, the first time this entry point runs
-// on it.  Every call shares the array and it keeps the last call's contents;
-// whatever must start at zero is cleared by each call.  Two calls whose work
-// overlaps on the GPU (different streams, not ordered) race on the array.
+// host code obtains the real device address with cudaGetSymbolAddress, with
+// the device current, the first time this entry point runs in a CUDA context
+// of that device.  The address is cached per device together with the
+// context's unique ID and looked up again whenever the current context's ID
+// differs (after cudaDeviceReset the primary context, and with it the
+// array, is created anew at another address).  Every call shares the array
+// and it keeps the last call's contents; whatever must start at zero is
+// cleared by each call.  Two calls whose work overlaps on the GPU (different
+// streams, not ordered) race on the array.
 #include <mutex>
 
 #include "emu_handle.h"
@@ -27,48 +31,83 @@ namespace emu {
 namespace {
 
 constexpr size_t kScratchBytes = static_cast<size_t>(EMU_NOALLOC_SCRATCH_BYTES);
-constexpr size_t kStatusBytes = 256;  // first 256 bytes: fallback status word
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) uint8_t g_scratch[kScratchBytes];
 
+// Driver entry points for the current context and its unique ID (CUDA 12.0+).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+struct DriverFns {
+  CtxGetCurrentFn get_current = nullptr;
+  CtxGetIdFn get_id = nullptr;
+};
+
+const DriverFns& driver_fns() {
+  static DriverFns f;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      f.get_current = reinterpret_cast<CtxGetCurrentFn>(p);
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      f.get_id = reinterpret_cast<CtxGetIdFn>(p);
+  });
+  return f;
+}
+
+// Unique ID of the current context (false if there is none yet).
+bool current_ctx_id(unsigned long long* id) {
+  const DriverFns& f = driver_fns();
+  if (!f.get_current || !f.get_id) return false;
+  CUcontext ctx = nullptr;
+  if (f.get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return false;
+  return f.get_id(ctx, id) == CUDA_SUCCESS;
+}
+
 struct DeviceSlot {
   bool ready = false;
+  unsigned long long ctx_id = 0;
   uint8_t* addr = nullptr;
   int num_sms = 0;
 };
 std::mutex g_mu;
 DeviceSlot g_slots[kMaxDevices];
 
-// Set-up for the current device: device address of g_scratch and SM count.
+// Set-up for the current device and context: device address of g_scratch
+// and SM count.
 emu_status_t scratch_for_current_device(uint8_t** addr, int* num_sms) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return EMU_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_mu);
   DeviceSlot& s = g_slots[dev];
-  if (!s.ready) {
+  unsigned long long id = 0;
+  const bool have_id = current_ctx_id(&id);
+  if (!s.ready || !have_id || id != s.ctx_id) {
+    // the runtime makes the device's primary context current here if no
+    // context is current yet
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || p == nullptr) {
       cudaGetLastError();
+      s.ready = false;
       return EMU_ERR_CUDA;
     }
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return EMU_ERR_CUDA;
+    if (!current_ctx_id(&id)) return EMU_ERR_CUDA;
     s.addr = static_cast<uint8_t*>(p);
     s.num_sms = sms;
+    s.ctx_id = id;
     s.ready = true;
   }
   *addr = s.addr;
   *num_sms = s.num_sms;
   return EMU_OK;
-}
-
-// C = beta * C for the k == 0 case (beta == 0 writes zeros; C is not read).
-__global__ void noalloc_scale_c(double* C, int64_t ldc, int64_t M, int64_t N, double beta) {
-  int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (idx >= M * N) return;
-  double* c = C + (idx / N) * ldc + idx % N;
-  *c = beta == 0.0 ? 0.0 : __dmul_rn(beta, *c);
 }
 
 }  // namespace
@@ -90,30 +129,28 @@ extern "C" emu_status_t emu_dgemm_noalloc(emu_layout_t layout, int64_t m, int64_
   View v;
   normalize(layout, m, n, A, lda, B, ldb, &v);
   if (v.M == 0 || v.N == 0) return EMU_OK;
-  if (k == 0) {
-    int64_t tot = v.M * v.N;
-    noalloc_scale_c<<<static_cast<unsigned>((tot + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        C, ldc, v.M, v.N, beta);
+  if (k == 0) {  // the same kernel as emu_dgemm's k == 0 path
+    launch_scale_c<double>(C, ldc, v.M, v.N, beta, static_cast<cudaStream_t>(stream));
     return cudaGetLastError() == cudaSuccess ? EMU_OK : EMU_ERR_CUDA;
   }
-  // the whole workspace of this product must fit after the status word
+  // the whole workspace of this product must fit in the array
   Plan pl = plan_I(v.M, v.N, k, p);
-  if (pl.bytes > kScratchBytes - kStatusBytes) return EMU_ERR_UNSUPPORTED;
+  if (pl.bytes > kScratchBytes) return EMU_ERR_UNSUPPORTED;
 
   uint8_t* scratch = nullptr;
   int num_sms = 0;
   emu_status_t s = scratch_for_current_device(&scratch, &num_sms);
   if (s != EMU_OK) return s;
   // A handle on the host stack (no allocation): no workspace, no tracing;
-  // device-detected errors go to the caller's status word, or to the
-  // fallback word at the start of the scratch array.
+  // device-detected errors go to the caller's status word (none if null:
+  // the kernels skip the flag update then).
   emu_handle_s hs;
   cudaGetDevice(&hs.device);
   hs.num_sms = num_sms;
-  hs.status = status_dev ? status_dev : reinterpret_cast<int*>(scratch);
+  hs.status = status_dev;
   hs.ws = nullptr;
   hs.ws_bytes = 0;
   hs.ws_user = true;
   return run_scheme_I<double>(&hs, v, k, p, alpha, beta, C, ldc, OUT_F64, nullptr,
-                              static_cast<cudaStream_t>(stream), scratch + kStatusBytes);
+                              static_cast<cudaStream_t>(stream), scratch);
 }

@@ -474,19 +474,35 @@ def test_dd_gemm_vs_exact_rationals(orc):
                 assert abs(Fraction(hi[i, j]) + Fraction(lo[i, j]) - ex) <= den * Fraction(2) ** -100
 
 
-def test_dd_zgemm_vs_exact_rationals(orc):
-    m, n, k = 3, 3, 6
-    A, B = synth.gemm_pair_complex(m, n, k, 2.0, 8)
+@pytest.mark.parametrize("seed,phi,cancel", [(8, 2.0, False), (9, 8.0, False), (10, 0.5, True), (11, 4.0, True)])
+def test_dd_zgemm_vs_exact_rationals(orc, seed, phi, cancel):
+    # k = 4 complex terms: 2k = 8 real products per part, so the compensated
+    # dot product errs by at most gamma_8^2 ~ 8^2 2^-106 = 2^-100 of the
+    # part's own sum of |products| (Ogita-Rump-Oishi Dot2, unevaluated hi + lo)
+    m, n, k = 3, 4, 4
+    A, B = synth.gemm_pair_complex(m, n, k, phi, seed)
+    if cancel:  # real and imaginary parts both cancel to small integers
+        A[0, :4] = [1e16 + 3j, 1.0 + 1e16j, -1e16 + 2j, 3.0 - 1e16j]
+        B[:4, 0] = [1.0 + 1.0j] * 4
+        A[1, :4] = [2.0 ** 60 + 1j, -1.0 + 2.0 ** 60 * 1j, -(2.0 ** 60) + 1j, 5.0 - 2.0 ** 60 * 1j]
+        B[:4, 1] = [1.0 - 1.0j, 1.0 + 1.0j, 1.0 - 1.0j, 1.0 + 1.0j]
     hi, lo = orc.dd_zgemm(A, B)
+    F = Fraction
+    tight = F(2) ** -100 * (1 + F(2) ** -40)
     for i in range(m):
         for j in range(n):
-            re = sum(Fraction(A[i, h].real) * Fraction(B[h, j].real) - Fraction(A[i, h].imag) * Fraction(B[h, j].imag)
-                     for h in range(k))
-            im = sum(Fraction(A[i, h].real) * Fraction(B[h, j].imag) + Fraction(A[i, h].imag) * Fraction(B[h, j].real)
-                     for h in range(k))
-            den = sum(abs(Fraction(A[i, h].real)) + abs(Fraction(A[i, h].imag)) for h in range(k)) * 4
-            assert abs(Fraction(hi[i, j].real) + Fraction(lo[i, j].real) - re) <= den * Fraction(2) ** -98 * 1000
-            assert abs(Fraction(hi[i, j].imag) + Fraction(lo[i, j].imag) - im) <= den * Fraction(2) ** -98 * 1000
+            ar = [F(A[i, h].real) for h in range(k)]
+            ai = [F(A[i, h].imag) for h in range(k)]
+            br = [F(B[h, j].real) for h in range(k)]
+            bi = [F(B[h, j].imag) for h in range(k)]
+            re = sum(ar[h] * br[h] - ai[h] * bi[h] for h in range(k))
+            im = sum(ar[h] * bi[h] + ai[h] * br[h] for h in range(k))
+            den_re = sum(abs(ar[h] * br[h]) + abs(ai[h] * bi[h]) for h in range(k))
+            den_im = sum(abs(ar[h] * bi[h]) + abs(ai[h] * br[h]) for h in range(k))
+            assert abs(F(hi[i, j].real) + F(lo[i, j].real) - re) <= den_re * tight
+            assert abs(F(hi[i, j].imag) + F(lo[i, j].imag) - im) <= den_im * tight
+    if cancel:
+        assert hi[0, 0] + lo[0, 0] == -1.0 + 9.0j
 
 
 def test_golden_gemm_counts():

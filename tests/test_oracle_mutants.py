@@ -75,6 +75,10 @@ MUTANTS = [
     # double-double reference
     ("dd ZGEMM real part adds Im*Im", "dot2(a, 1, b, 1, 2 * k, 1.0,", "dot2(a, 1, b, 1, 2 * k, 0.0,", None),
     ("dd dot drops the TwoSum error", "    c += err + e;\n  }\n  double t = s + c;", "    c += e;\n  }\n  double t = s + c;", None),
+    ("dd ZGEMM imaginary part drops the TwoSum error", "          c += err + e;\n        }\n      }",
+     "          c += e;\n        }\n      }", None),
+    ("dd ZGEMM imaginary part drops the product error", "          c += err + e;\n        }\n      }",
+     "          c += err;\n        }\n      }", None),
     # more of the integer and rounding machinery
     ("CRT rounding ignores the sticky bits", "if (guard && (sticky || (top & 1))) top += 1;",
      "if (guard && (top & 1)) top += 1;", None),

@@ -30,8 +30,18 @@ def _noalloc(A, B, C, p, alpha=1.0, beta=0.0, status=None):
     m, k = A.shape
     n = B.shape[1]
     stream = torch.cuda.current_stream().cuda_stream
-    return emu.emu_dgemm_noalloc(emu.EMU_ROW_MAJOR, m, n, k, alpha, A.data_ptr(), k, B.data_ptr(), n, beta,
-                                 C.data_ptr(), n, p, None if status is None else status.data_ptr(), stream)
+    return emu.emu_dgemm_noalloc(emu.EMU_ROW_MAJOR, m, n, k, alpha, A.data_ptr(), max(k, 1), B.data_ptr(),
+                                 max(n, 1), beta, C.data_ptr(), max(n, 1), p,
+                                 None if status is None else status.data_ptr(), stream)
+
+
+def _colmajor_padded(x, pad):
+    """The matrix x stored column-major with leading dimension rows + pad:
+    returns (storage tensor, leading dimension)."""
+    r, c = x.shape
+    buf = np.full((c, r + pad), np.nan)
+    buf[:, :r] = x.T
+    return torch.from_numpy(buf).cuda(), r + pad
 
 
 def test_noalloc_matches_emu_dgemm_twice():
@@ -71,4 +81,68 @@ def test_noalloc_alpha_beta_and_limits():
     big = torch.zeros((4096, 4096), dtype=torch.float64, device="cuda")
     out = torch.zeros((4096, 4096), dtype=torch.float64, device="cuda")
     assert _noalloc(big, big, out, 8) == 2  # EMU_ERR_UNSUPPORTED
+    h.close()
+
+
+def test_noalloc_against_oracle_colmajor_padded(orc):
+    # column-major A, B, C with leading dimensions larger than the minimum
+    # (the call maps the product onto the transposed row-major one)
+    h = emu.Handle(0)
+    m, n, k, p = 150, 97, 333, 7
+    A, B = synth.gemm_pair(m, n, k, 2.0, 21)
+    C0 = synth.test_matrix(m, n, 1.0, 22)
+    Ad, lda = _colmajor_padded(A, 5)
+    Bd, ldb = _colmajor_padded(B, 3)
+    want = orc.emu_I(A, B, p, alpha=1.5, beta=-0.25, C=C0)
+    stream = torch.cuda.current_stream().cuda_stream
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for _ in range(2):
+        Cd, ldc = _colmajor_padded(C0, 7)
+        assert emu.emu_dgemm_noalloc(emu.EMU_COL_MAJOR, m, n, k, 1.5, Ad.data_ptr(), lda, Bd.data_ptr(), ldb,
+                                     -0.25, Cd.data_ptr(), ldc, p, status.data_ptr(), stream) == 0
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0
+        got = Cd.cpu().numpy()
+        assert np.array_equal(got[:, :m].T, want)
+        assert np.all(np.isnan(got[:, m:]))  # the padding is not touched
+    # the same product through emu_dgemm (handle API), also column-major
+    Cref, _ = _colmajor_padded(C0, 7)
+    assert emu.emu_dgemm(h.h, emu.EMU_COL_MAJOR, m, n, k, 1.5, Ad.data_ptr(), lda, Bd.data_ptr(), ldb, -0.25,
+                         Cref.data_ptr(), ldc, emu.EMU_SCHEME_I, p, stream) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(Cref, Cd)
+    h.close()
+
+
+def test_noalloc_k_zero_and_nan_status(orc):
+    h = emu.Handle(0)
+    m, n = 70, 45
+    C0 = synth.test_matrix(m, n, 1.0, 31)
+    e = torch.zeros((m, 0), dtype=torch.float64, device="cuda")
+    f = torch.zeros((0, n), dtype=torch.float64, device="cuda")
+    for beta in (0.0, -3.0):
+        C = torch.from_numpy(C0).cuda()
+        ref = torch.from_numpy(C0).cuda()
+        emu.dgemm(e, f, ref, alpha=2.0, beta=beta, scheme="I", p=5, handle=h)
+        for _ in range(2):
+            C.copy_(torch.from_numpy(C0))
+            assert _noalloc(e, f, C, 5, alpha=2.0, beta=beta) == 0
+            torch.cuda.synchronize()
+            assert torch.equal(C, ref)
+            assert np.array_equal(C.cpu().numpy(), np.zeros_like(C0) if beta == 0.0 else beta * C0)
+    # a NaN in A: bit 1 (non-finite input) reaches the caller's status word
+    A, B = synth.gemm_pair(64, 64, 96, 1.0, 32)
+    A[5, 7] = np.nan
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    C = torch.zeros((64, 64), dtype=torch.float64, device="cuda")
+    assert _noalloc(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), C, 6, status=status) == 0
+    torch.cuda.synchronize()
+    assert int(status.item()) & 1
+    # and the next call, on finite input, is clean again
+    status.zero_()
+    A[5, 7] = 0.5
+    assert _noalloc(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), C, 6, status=status) == 0
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    assert np.array_equal(C.cpu().numpy(), orc.emu_I(A, B, 6))
     h.close()
