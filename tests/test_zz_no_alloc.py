@@ -110,7 +110,7 @@ def test_noalloc_against_oracle_colmajor_padded(orc):
     assert emu.emu_dgemm(h.h, emu.EMU_COL_MAJOR, m, n, k, 1.5, Ad.data_ptr(), lda, Bd.data_ptr(), ldb, -0.25,
                          Cref.data_ptr(), ldc, emu.EMU_SCHEME_I, p, stream) == 0
     torch.cuda.synchronize()
-    assert torch.equal(Cref, Cd)
+    assert torch.equal(Cref[:, :m], Cd[:, :m])  # the NaN padding compares unequal, so only C itself
     h.close()
 
 
