@@ -42,9 +42,9 @@
 // between K segments, so the MMAs of one segment overlap the reduction of
 // the last.  Roles (320 threads per CTA): warps 0-7 drain (warp w: TMEM
 // lanes = tile rows 32 (w % 4) .., columns 128 (w / 4) .. +127; each
-// finished segment is added to a running residue, four per register), warp
-// 8 lane 0 TMA (each load preceded by an L2 prefetch of the chunk four K
-// steps ahead), warp 9 TMEM allocation and (lane 0 of the even CTA) MMAs.
+// finished segment is added to a running residue, four per register, with
+// FP32 arithmetic only), warp 8 lane 0 TMA, warp 9 TMEM allocation and
+// (lane 0 of the even CTA) MMAs.
 // All waits are bounded; a timeout sets the status word, raises the abort
 // flag of both CTAs of a pair for the other roles, and the TMEM is still
 // released.
@@ -65,7 +65,6 @@ constexpr int kProducerWarp = 8, kMmaWarp = 9;
 constexpr uint32_t kTmemCols = 512;
 constexpr int kSegStages = 15;  // 64-wide K chunks per exact FP32 segment (960 * 2^14 < 2^24)
 static_assert(kSegStages * 64 * 16384 < (1 << 24), "segment sums must stay exact in FP32");
-constexpr int kPrefetch = 4;  // chunks ahead of the TMA loads that are prefetched into L2
 
 template <bool PAIR>
 struct CfgII {
@@ -198,9 +197,10 @@ __device__ __forceinline__ void raise_abort(const AbortFlag& ab) {
 // `cluster_acq` the wait acquires at cluster scope (arrivals from the peer).
 __device__ __forceinline__ bool wait_pair(uint64_t* bar, uint32_t parity, const AbortFlag& ab, int* status,
                                           bool cluster_acq = false) {
+  // fast path: the phase is already complete (no abort-flag load on the way)
+  if (cluster_acq ? mbar_try_wait_acq_cluster(bar, parity) : mbar_try_wait(bar, parity)) return true;
   if (*ab.local) return false;
   if (cluster_acq) {
-    if (mbar_try_wait_acq_cluster(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait_acq_cluster(bar, parity)) {
       if (*ab.local) return false;
@@ -212,18 +212,16 @@ __device__ __forceinline__ bool wait_pair(uint64_t* bar, uint32_t parity, const 
     }
     return true;
   }
-  if (mbar_wait_bounded(bar, parity)) return true;
-  set_status(status, ST_TIMEOUT);
-  raise_abort(ab);
-  return false;
-}
-
-// Hint: bring a 2D box of the tensor into L2 (no shared memory involved).
-__device__ __forceinline__ void tma_prefetch_l2(const void* desc, int x, int y) {
-  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
-                   reinterpret_cast<uint64_t>(desc)),
-               "r"(x), "r"(y)
-               : "memory");
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*ab.local) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      set_status(status, ST_TIMEOUT);
+      raise_abort(ab);
+      return false;
+    }
+  }
+  return true;
 }
 
 // 16 consecutive 32-bit TMEM columns of this thread's lane.
@@ -235,15 +233,19 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
       : "r"(taddr));
 }
 
-// t mod m_l in [-off, m - 1 - off] for |t| < 2^25: the quotient
-// floor(RN(RN(t) / m + off / m)) is floor((t + off) / m) or one off (the
-// roundings move a quotient below 2^18 by less than 0.05), and one
-// correction each way finishes.
-__device__ __forceinline__ int sym_mod(int t, int m, int off, float inv, float offinv) {
-  const int q = __float2int_rd(__fmaf_rn(__int2float_rn(t), inv, offinv));
-  int r = t - q * m;
-  if (r < -off) r += m;
-  if (r >= m - off) r -= m;
+// A multiple of m_l added to (or removed from) an exact int32 sum, keeping
+// its residue: x = hi 2^16 + lo -> hi (2^16 mod m) + lo, |result| < 2^22.1
+// (p16: the symmetric residue of 2^16 mod m, |p16| <= 128).
+__device__ __forceinline__ int fold16(int x, int p16) { return (x >> 16) * p16 + (x & 0xFFFF); }
+
+// x mod m in [0, m) for |x| < 2^23: the quotient estimate floor(RN(x) *
+// RN(1/m)) errs by at most one (|x / m| < 2^16, relative error < 2^-22),
+// and one correction each way finishes.
+__device__ __forceinline__ int mod_small(int x, int m, float inv) {
+  const int q = __float2int_rd(__fmul_rn(__int2float_rn(x), inv));
+  int r = x - q * m;
+  if (r < 0) r += m;
+  if (r >= m) r -= m;
   return r;
 }
 
@@ -269,8 +271,6 @@ __device__ __forceinline__ void item_coords(const KParamsIITC& kp, int item, int
   tile_coords(item - p * per_plane, kp.tiles_mu, kp.tiles_n, tu, tn);
   tm = PAIR ? 2 * tu + crank : tu;
 }
-
-__device__ __forceinline__ int sbyte(uint32_t w, int i) { return static_cast<int>(static_cast<int8_t>(w >> (8 * i))); }
 
 template <bool PAIR>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -335,24 +335,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         item_coords<PAIR>(kp, cid + t * ncl, static_cast<int>(crank), p, tm, tn);
         const int ya = p * kp.rowsA_pad + tm * kBM;
         const int yb = p * kp.rowsB_pad + tn * kBN + static_cast<int>(crank) * Cfg::kRowsB;
-        int pya = 0, pyb = 0;  // the next item's rows, for prefetches that run past this item's K
-        if (t + 1 < my_items) {
-          int p2, tm2, tn2;
-          item_coords<PAIR>(kp, cid + (t + 1) * ncl, static_cast<int>(crank), p2, tm2, tn2);
-          pya = p2 * kp.rowsA_pad + tm2 * kBM;
-          pyb = p2 * kp.rowsB_pad + tn2 * kBN + static_cast<int>(crank) * Cfg::kRowsB;
-        }
         for (int ks = 0; ks < kp.nst; ++ks, ++j) {
-          {  // warm L2 with this CTA's operand rows of the chunk kPrefetch steps ahead
-            const int kf = ks + kPrefetch;
-            if (kf < kp.nst) {
-              tma_prefetch_l2(&kp.tA, kf * 128, ya);
-              tma_prefetch_l2(&kp.tB, kf * 128, yb);
-            } else if (t + 1 < my_items && kf - kp.nst < kp.nst) {
-              tma_prefetch_l2(&kp.tA, (kf - kp.nst) * 128, pya);
-              tma_prefetch_l2(&kp.tB, (kf - kp.nst) * 128, pyb);
-            }
-          }
           const uint32_t stage = j % Cfg::kStages;
           if (j >= static_cast<uint32_t>(Cfg::kStages) &&
               !wait_pair(&empty[stage], ((j / Cfg::kStages) & 1u) ^ 1u, ab, kp.status)) {
@@ -390,8 +373,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0 && leader) {
       const uint32_t idesc = idesc_bf16(PAIR ? 2 * kBM : kBM, kBN);
       const uint32_t peer = 1u;
+      const uint32_t total = static_cast<uint32_t>(my_items) * static_cast<uint32_t>(kp.nst);
       uint32_t it = 0, seg = 0;
       bool stop = false;
+      bool ready = false;  // the probe after the previous stage's MMAs already saw this stage's data
       for (int t = 0; t < my_items && !stop; ++t)
         for (int ks = 0; ks < kp.nst; ++ks, ++it) {
           const bool first = ks % kSegStages == 0;
@@ -404,7 +389,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
           }
           const uint32_t stage = it % Cfg::kStages;
-          if (!wait_pair(&full[stage], (it / Cfg::kStages) & 1u, ab, kp.status)) {
+          if (!ready && !wait_pair(&full[stage], (it / Cfg::kStages) & 1u, ab, kp.status)) {
             stop = true;
             break;
           }
@@ -414,6 +399,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int q = 0; q < 4; ++q)  // four K-steps of 16 inside the 128-byte rows
             umma_bf16<PAIR>(tmem + b * kBN, smem_desc_k128(sA + 32 * q), smem_desc_k128(sA + Cfg::kBlkA + 32 * q),
                             idesc, (first && q == 0) ? 0u : 1u);
+          // Probe (without blocking) the next stage's data while these MMAs
+          // are queued: when it has arrived, the next MMAs follow at once
+          // instead of after a blocking wait, which would let the tensor
+          // pipe run dry.
+          ready = it + 1 < total &&
+                  mbar_test_wait(&full[(it + 1) % Cfg::kStages], ((it + 1) / Cfg::kStages) & 1u);
           // the stage is free (in both CTAs of a pair) once these MMAs finish
           if (PAIR) {
             umma_commit_pair(smem_u32(&empty[stage]));
@@ -447,14 +438,26 @@ __global__ void __launch_bounds__(kThreads, 1)
       int p, tm, tn;
       item_coords<PAIR>(kp, cid + t * ncl, static_cast<int>(crank), p, tm, tn);
       const int l = p % kp.nm;
-      const int m = static_cast<int>(mt.mods[l]), off = mt.off[l];
-      const float inv = mt.inv[l], offinv = mt.offinv[l];
-      uint32_t run[32];  // symmetric residues of this thread's 128 columns, four per word
+      const int m = static_cast<int>(mt.mods[l]);
+      const int p16 = mt.pow16[l][1];
+      const float inv = mt.inv[l];
+      // Exact integer sums of this thread's 128 columns over the segments so
+      // far: each segment adds one exact FP32 value per output, and only the
+      // final sum is reduced mod m -- two instructions per output and
+      // segment, because the drain competes for issue slots with the MMA
+      // thread, which must keep the tensor pipe fed.
+      int run[128];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) run[i] = 0;
+      for (int i = 0; i < 128; ++i) run[i] = 0;
       for (int s = 0; s < nseg; ++s, ++seg) {
         const uint32_t b = seg & 1u;
-        if (!__all_sync(0xFFFFFFFFu, wait_pair(&acc_full[b], (seg >> 1) & 1u, ab, kp.status))) {
+        // one lane per warp polls the barrier (256 polling threads slowed the
+        // other roles), the warp follows it
+        bool ok = true;
+        if (lane == 0) ok = wait_pair(&acc_full[b], (seg >> 1) & 1u, ab, kp.status);
+        ok = __shfl_sync(0xFFFFFFFFu, ok ? 1 : 0, 0) != 0;
+        __syncwarp();
+        if (!ok) {
           stop = true;
           break;
         }
@@ -475,16 +478,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
 #pragma unroll
-          for (int w = 0; w < 4; ++w) {
-            uint32_t o = 0;
+          for (int i = 0; i < 16; ++i) run[16 * q + i] += __float2int_rn(__uint_as_float(v[i]));
+        }
+        // |segment sum| <= 960 * 2^14 < 2^24: fold every 64 segments so that
+        // the int32 sums never overflow, whatever K is
+        if ((s & 63) == 63) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              const int x = sym_mod(sbyte(run[4 * q + w], i) + __float2int_rn(__uint_as_float(v[4 * w + i])), m,
-                                    off, inv, offinv);
-              o |= (static_cast<uint32_t>(x) & 0xFFu) << (8 * i);
-            }
-            run[4 * q + w] = o;
-          }
+          for (int i = 0; i < 128; ++i) run[i] = fold16(run[i], p16);
         }
       }
       if (stop) break;
@@ -498,11 +498,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int e = 0; e < 4; ++e) {
           uint32_t o = 0;
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            int x = sbyte(run[4 * i + e], k);
-            if (x < 0) x += m;
-            o |= static_cast<uint32_t>(x) << (8 * k);
-          }
+          for (int k = 0; k < 4; ++k)
+            o |= static_cast<uint32_t>(mod_small(fold16(run[16 * i + 4 * e + k], p16), m, inv)) << (8 * k);
           wv[e] = o;
         }
         dst[i] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
