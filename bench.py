@@ -58,7 +58,9 @@ def parse():
     ap.add_argument("--suite-md", default=None, nargs="+",
                     help="print the summary tables of --suite JSONL files (rows of later files replace the "
                          "matching rows of earlier ones)")
-    ap.add_argument("--suite-part", default="all", choices=["all", "ii", "scheme2"],
+    ap.add_argument("--selector-md", default=None,
+                    help="print the selector end-to-end summary of a --suite-part selector JSONL file")
+    ap.add_argument("--suite-part", default="all", choices=["all", "ii", "scheme2", "selector"],
                     help="ii: only the Scheme II DGEMM points (run in a child with EMU_II_ENGINE=mma by the full "
                          "suite); scheme2: every row of the bf16 tcgen05 Scheme II paths (DGEMM, SGEMM, norm "
                          "scaling, ZGEMM 3M, CGEMM 3M)")
@@ -254,6 +256,30 @@ def scheme_II_leg(emu, h, Ad, Bd, Cd, n, stream, ri, ci, hi, lo, den, cublas_tfl
     return out
 
 
+def probe_ref(emu, h, Ad, Bd, ri, ci, stream=None):
+    """Double-double reference of the sampled entries C[ri][:, ci] of A @ B and
+    sum_h |a_ih||b_hj| for each, from the library's probe kernel (emu_probe_dd:
+    error-free FP64 transformations on the GPU, checked against the CPU
+    oracle's double-double product in the tests).  A, B: row-major float64
+    CUDA tensors.  Returns (hi, lo, den) as numpy arrays of shape (len(ri), len(ci))."""
+    import torch
+    m, k = Ad.shape
+    n = Bd.shape[1]
+    pairs = np.array([[i, j] for i in ri for j in ci], dtype=np.int32).reshape(-1)
+    cnt = len(ri) * len(ci)
+    idx = torch.from_numpy(pairs).to(Ad.device)
+    ref = torch.empty(2 * cnt, dtype=torch.float64, device=Ad.device)
+    ab = torch.empty(cnt, dtype=torch.float64, device=Ad.device)
+    st = None if stream is None else stream.cuda_stream
+    emu.check(emu.emu_probe_dd(h.h, emu.EMU_ROW_MAJOR, m, n, k, Ad.data_ptr(), max(Ad.stride(0), 1), Bd.data_ptr(),
+                               max(Bd.stride(0), 1), cnt, idx.data_ptr(), ref.data_ptr(), ab.data_ptr(), st),
+              "emu_probe_dd")
+    torch.cuda.synchronize()
+    r = ref.cpu().numpy().reshape(cnt, 2)
+    shp = (len(ri), len(ci))
+    return r[:, 0].reshape(shp), r[:, 1].reshape(shp), ab.cpu().numpy().reshape(shp)
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -404,13 +430,11 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         cublas_tflops = 2 * flops / (s0.elapsed_time(s1) * 1e-3) / 1e12
         # accuracy on sampled entries against the double-double reference
-        import oracle
-        oracle.build()
+        # (the library's GPU probe kernel)
         rng = np.random.Generator(np.random.PCG64(1234))
         ri = np.sort(rng.choice(n, 8, replace=False))
         ci = np.sort(rng.choice(n, 64, replace=False))
-        hi, lo = oracle.dd_gemm(A[ri], B[:, ci])
-        den = np.abs(A[ri]) @ np.abs(B[:, ci])
+        hi, lo, den = probe_ref(emu, h, Ad, Bd, ri, ci, stream)
         ours_s = Cd[ri][:, ci].cpu().numpy()
         cub_s = ref[ri][:, ci].cpu().numpy()
         err_ours = float(np.max(np.abs((ours_s - hi) - lo) / den))
@@ -631,6 +655,123 @@ def suite_markdown(paths):
     return "\n".join(o)
 
 
+SEL_TOLS = (1e-8, 1e-12, 1e-15)
+
+
+def selector_products(count=12, seed=4242):
+    """Held-out products for the selector's end-to-end timing: square, n
+    log-uniform in [1024, 4096] (rounded to a multiple of 64), phi ~ U(0, 8)
+    (the selector's training range), seeds disjoint from its training data."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(count):
+        n = int(round(float(np.exp(rng.uniform(np.log(1024), np.log(4096)))) / 64)) * 64
+        out.append((n, float(rng.uniform(0.0, 8.0)), 7_000_000 + 2 * i))
+    return out
+
+
+def selector_points(emu, h, dev, emit, products=None, schemes=(("I", 12), ("II", 20)),
+                    tols=SEL_TOLS):
+    """emu_dgemm_auto / emu_dgemm_auto_II (committed selector weights; feature
+    scan, MLP, probe and every escalation inside the timed region) against
+    emu_dgemm at the fixed p (N) that passes every training product -- p = 12
+    for Scheme I, N = 20 for Scheme II with norm scaling -- on the same
+    products, CUDA-event time on the stream, one timed call each after a
+    warm-up at the largest size.  Pass = max |C - AB| / (|A||B|) <= tol on 256
+    sampled entries against the GPU double-double probe."""
+    import torch
+    from paper_2606_25453_gb300 import selector as sel
+    sel.install_default(h)
+    products = products or selector_products()
+    rng = np.random.Generator(np.random.PCG64(77))
+    stream = torch.cuda.current_stream(dev)
+    nmax = max(n for n, _, _ in products)
+    Aw = synth.test_matrix_torch(nmax, nmax, 1.0, 1, dev)
+    for sc, fixed in schemes:  # workspace at the largest size, and first-call costs, outside the timing
+        emu.dgemm(Aw, Aw, scheme="I" if sc == "I" else "II_NORM", p=fixed, handle=h)
+        emu.dgemm_auto(Aw, Aw, 1e-8, handle=h, scheme=sc)
+    del Aw
+    torch.cuda.synchronize()
+    rows = []
+    for n, phi, seed in products:
+        Ad = synth.test_matrix_torch(n, n, phi, seed, dev)
+        Bd = synth.test_matrix_torch(n, n, phi, seed + 1, dev)
+        Cf = torch.empty((n, n), dtype=torch.float64, device=dev)
+        ri = np.sort(rng.choice(n, 16, replace=False))
+        ci = np.sort(rng.choice(n, 16, replace=False))
+        hi, lo, den = probe_ref(emu, h, Ad, Bd, ri, ci)
+
+        def err(C):
+            return float(np.max(np.abs((C[ri][:, ci].cpu().numpy() - hi) - lo) / den))
+
+        for sc, fixed in schemes:
+            fixed_scheme = "I" if sc == "I" else "II_NORM"
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            emu.dgemm(Ad, Bd, Cf, scheme=fixed_scheme, p=fixed, handle=h)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_fixed = e0.elapsed_time(e1)
+            err_fixed = err(Cf)
+            for tol in tols:
+                e0.record(stream)
+                C, used, code = emu.dgemm_auto(Ad, Bd, tol, handle=h, scheme=sc)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms_auto = e0.elapsed_time(e1)
+                d = {"path": "selector_e2e", "scheme": sc, "n": n, "phi": phi, "tol": tol, "fixed": fixed,
+                     "used": used, "code": code, "ms_auto": ms_auto, "ms_fixed": ms_fixed,
+                     "err_auto": err(C), "err_fixed": err_fixed}
+                d["pass_auto"] = d["err_auto"] <= tol
+                d["pass_fixed"] = err_fixed <= tol
+                rows.append(d)
+                emit(d)
+                del C
+        del Ad, Bd, Cf
+    for sc, fixed in schemes:
+        for tol in tols:
+            r = [d for d in rows if d["scheme"] == sc and d["tol"] == tol]
+            ta, tf = sum(d["ms_auto"] for d in r), sum(d["ms_fixed"] for d in r)
+            emit({"path": "selector_e2e_summary", "scheme": sc, "tol": tol, "products": len(r), "fixed": fixed,
+                  "ms_auto_total": ta, "ms_fixed_total": tf, "speedup_vs_fixed": tf / ta,
+                  "pass_auto": float(np.mean([d["pass_auto"] for d in r])),
+                  "pass_fixed": float(np.mean([d["pass_fixed"] for d in r])),
+                  "mean_used": float(np.mean([d["used"] for d in r]))})
+    return rows
+
+
+def selector_markdown(path):
+    """The text of profiles/selector_e2e_gb300.md from a --suite-part selector file."""
+    rows = [json.loads(x) for x in open(path)]
+    pts = [d for d in rows if d.get("path") == "selector_e2e"]
+    summ = [d for d in rows if d.get("path") == "selector_e2e_summary"]
+    o = ["# Learned selector, end to end, on one GB300\n",
+         "Command: `python bench.py --suite selector.jsonl --suite-part selector`, then",
+         "`python bench.py --selector-md selector.jsonl > profiles/selector_e2e_gb300.md`.\n",
+         "Held-out products (square, n log-uniform in [1024, 4096], phi ~ U(0, 8), seeds outside the",
+         "training data; A and B drawn on the GPU by the Eq. 19 generator).  Timed with CUDA events on the",
+         "stream, one call each: `emu_dgemm_auto` / `emu_dgemm_auto_II` with the committed weights -- feature",
+         "scan, MLP, the 64-entry double-double probe and every escalation and recomputation inside the",
+         "timed region -- against `emu_dgemm` at the fixed p (N) that passes every training product (Scheme I",
+         "INT8 p = 12; Scheme II with norm scaling N = 20).  Pass: max |C - AB| / (|A||B|) <= tol on 256",
+         "other sampled entries against the GPU double-double probe.\n",
+         "| scheme | tol | products | fixed | mean chosen | auto pass | fixed pass | auto total ms | fixed total ms"
+         " | speed-up |",
+         "|---|---|---|---|---|---|---|---|---|---|"]
+    for d in summ:
+        o.append("| %s | %.0e | %d | %d | %.2f | %.0f %% | %.0f %% | %.1f | %.1f | %.2fx |" % (
+            d["scheme"], d["tol"], d["products"], d["fixed"], d["mean_used"], 100 * d["pass_auto"],
+            100 * d["pass_fixed"], d["ms_auto_total"], d["ms_fixed_total"], d["speedup_vs_fixed"]))
+    o.append("\nPer product (time in ms; chosen = the p or N of the returned result):\n")
+    o.append("| scheme | n | phi | tol | chosen | ms auto | ms fixed | err auto | err fixed |")
+    o.append("|---|---|---|---|---|---|---|---|---|")
+    for d in pts:
+        o.append("| %s | %d | %.2f | %.0e | %d | %.2f | %.2f | %.2e | %.2e |" % (
+            d["scheme"], d["n"], d["phi"], d["tol"], d["used"], d["ms_auto"], d["ms_fixed"], d["err_auto"],
+            d["err_fixed"]))
+    return "\n".join(o) + "\n"
+
+
 def run_suite(path, args):
     """Secondary measurements: every path of the library on one GPU, one JSON
     object per point (device-resident inputs, CUDA-event timing, 1 warm-up +
@@ -638,9 +779,7 @@ def run_suite(path, args):
     import torch
     import __graft_entry__
     __graft_entry__.build()
-    import oracle
     import paper_2606_25453_gb300 as emu
-    oracle.build()
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     h = emu.Handle(0)
@@ -665,13 +804,32 @@ def run_suite(path, args):
     rng = np.random.Generator(np.random.PCG64(99))
 
     def sampled_err(A, B, C, complex_=False):
+        """max |C - AB| / (|A||B|) over 8 x 64 sampled entries, AB from the GPU
+        double-double probe (complex: each part as a real dot product of the
+        sampled rows and columns over 2K terms; |.| the complex modulus)."""
         ri = np.sort(rng.choice(A.shape[0], 8, replace=False))
         ci = np.sort(rng.choice(B.shape[1], 64, replace=False))
-        if complex_:
-            hi, lo = oracle.dd_zgemm(A[ri], B[:, ci])
-        else:
-            hi, lo = oracle.dd_gemm(A[ri], B[:, ci])
-        return oracle.err_metric(C[ri][:, ci], (hi, lo), A[ri], B[:, ci])
+        As = torch.from_numpy(np.ascontiguousarray(A[ri])).to(dev)
+        Bs = torch.from_numpy(np.ascontiguousarray(B[:, ci])).to(dev)
+        rs, cs = np.arange(len(ri)), np.arange(len(ci))
+        if not complex_:
+            hi, lo, den = probe_ref(emu, h, As.double(), Bs.double(), rs, cs)
+            return float(np.max(np.abs((C[ri][:, ci] - hi) - lo) / den))
+        Ae = torch.cat([As.real.double(), As.imag.double()], dim=1).contiguous()
+        Bre = torch.cat([Bs.real.double(), -Bs.imag.double()], dim=0).contiguous()
+        Bim = torch.cat([Bs.imag.double(), Bs.real.double()], dim=0).contiguous()
+        hr, lr, _ = probe_ref(emu, h, Ae, Bre, rs, cs)
+        hm, lm, _ = probe_ref(emu, h, Ae, Bim, rs, cs)
+        den = (As.abs().double() @ Bs.abs().double()).cpu().numpy()
+        Cs = C[ri][:, ci]
+        d = np.hypot((Cs.real - hr) - lr, (Cs.imag - hm) - lm)
+        return float(np.max(d / den))
+
+    if args.suite_part == "selector":
+        selector_points(emu, h, dev, emit)
+        out.close()
+        h.close()
+        return
 
     cache = {}
 
@@ -871,6 +1029,9 @@ def run_suite(path, args):
 
 def main():
     args = parse()
+    if args.selector_md:
+        print(selector_markdown(args.selector_md), end="")
+        return
     if args.suite_md:
         print(suite_markdown(args.suite_md))
         return

@@ -29,6 +29,13 @@ struct SelState {
   bool loaded = false;
   float* params_II = nullptr;  // Scheme II, norm scaling: classes N = 6, 8, .., 20
   bool loaded_II = false;
+  // auto-precision buffers, grown on demand: device [feat 128 | prob 8 |
+  // probe idx | probe results], and a pinned host copy of the parts read
+  // back, so that each decision costs one device-to-host copy
+  uint8_t* dev = nullptr;
+  size_t dev_bytes = 0;
+  uint8_t* host = nullptr;
+  size_t host_bytes = 0;
 };
 SelState* sel_of(emu_handle_s* h) {
   if (!h->selector) h->selector = new SelState();
@@ -41,16 +48,33 @@ __device__ __forceinline__ int exp_bits(uint64_t ab) { return frexp_exp_bits(ab)
 
 // One block per sampled vector: 32-bin histogram of the exponent deficit
 // d = E_vec - e(x) in bins of 3 exponents (bin = min(d / 3, 31); x == 0 ->
-// bin 31), added to hist (uint32[32]).
+// bin 31), added to hist (uint32[32]).  E_vec, the exponent of the vector's
+// largest magnitude, is found by the block first (the vector is then read
+// a second time, from L2), so that no pass over the whole of A and B is
+// needed for 64 sampled vectors.
 __global__ void feat_hist_kernel(const double* __restrict__ X, int64_t ld, bool kcontig, int64_t rows, int64_t k,
-                                 int64_t stride, const unsigned long long* __restrict__ maxbits,
-                                 unsigned int* __restrict__ hist) {
+                                 int64_t stride, unsigned int* __restrict__ hist) {
   __shared__ unsigned int sh[32];
+  __shared__ unsigned long long shmax;
   if (threadIdx.x < 32) sh[threadIdx.x] = 0;
+  if (threadIdx.x == 0) shmax = 0;
   __syncthreads();
   int64_t r = static_cast<int64_t>(blockIdx.x) * stride;
   if (r < rows) {
-    uint64_t mb = maxbits[r];
+    unsigned long long mx = 0;  // largest |x| bit pattern (NaN > inf > finite)
+    for (int64_t h = threadIdx.x; h < k; h += blockDim.x) {
+      const unsigned long long ab = dbits(__ldg(kcontig ? X + r * ld + h : X + h * ld + r)) & 0x7FFFFFFFFFFFFFFFull;
+      mx = ab > mx ? ab : mx;
+    }
+    for (int o = 16; o; o >>= 1) {
+      const unsigned long long other = __shfl_xor_sync(0xffffffffu, mx, o);
+      mx = other > mx ? other : mx;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(&shmax, mx);
+  }
+  __syncthreads();
+  if (r < rows) {
+    const uint64_t mb = shmax;
     int E = mb >= 0x7FF0000000000000ull ? 0 : exp_bits(mb);
     for (int64_t h = threadIdx.x; h < k; h += blockDim.x) {
       uint64_t ab = dbits(__ldg(kcontig ? X + r * ld + h : X + h * ld + r)) & 0x7FFFFFFFFFFFFFFFull;
@@ -190,21 +214,29 @@ __device__ __forceinline__ DD dd_add(DD a, DD b) {
   return {t, __dsub_rn(e, __dsub_rn(t, s))};
 }
 
-// One warp per sampled entry (i, j): compensated dot product (TwoProduct by
-// fma, TwoSum accumulation) per lane, lanes combined by double-double adds.
-__global__ void probe_dd_kernel(const double* __restrict__ A, int64_t lda, bool a_kcontig, const double* __restrict__ B,
-                                int64_t ldb, bool b_kcontig, int64_t k, int count, const int32_t* __restrict__ idx,
-                                double* __restrict__ ref, double* __restrict__ absab) {
-  int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+// One block of kProbeThreads per sampled entry (i, j): compensated dot
+// product (TwoProduct by fma, TwoSum accumulation) per thread over a strided
+// share of K, threads combined by double-double adds (warp shuffles, then
+// the warps' partial results through shared memory).  A block per entry
+// keeps many independent loads in flight: one warp walking all of K waited
+// on one strided load per step.
+constexpr int kProbeThreads = 256;
+__global__ void __launch_bounds__(kProbeThreads) probe_dd_kernel(const double* __restrict__ A, int64_t lda,
+                                                                bool a_kcontig, const double* __restrict__ B,
+                                                                int64_t ldb, bool b_kcontig, int64_t k, int count,
+                                                                const int32_t* __restrict__ idx,
+                                                                double* __restrict__ ref, double* __restrict__ absab) {
+  __shared__ double sh[3][kProbeThreads / 32];
+  const int w = blockIdx.x, lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   if (w >= count) return;
-  int64_t i = idx[2 * w], j = idx[2 * w + 1];
+  const int64_t i = idx[2 * w], j = idx[2 * w + 1];
   DD acc{0.0, 0.0};
   double ab = 0.0;
-  for (int64_t h = lane; h < k; h += 32) {
-    double a = a_kcontig ? A[i * lda + h] : A[h * lda + i];
-    double b = b_kcontig ? B[j * ldb + h] : B[h * ldb + j];
-    double p = __dmul_rn(a, b);
-    double e = __fma_rn(a, b, -p);
+  for (int64_t h = threadIdx.x; h < k; h += kProbeThreads) {
+    const double a = a_kcontig ? A[i * lda + h] : A[h * lda + i];
+    const double b = b_kcontig ? B[j * ldb + h] : B[h * ldb + j];
+    const double p = __dmul_rn(a, b);
+    const double e = __fma_rn(a, b, -p);
     acc = dd_add(acc, DD{p, e});
     ab = __fma_rn(fabs(a), fabs(b), ab);
   }
@@ -214,9 +246,30 @@ __global__ void probe_dd_kernel(const double* __restrict__ A, int64_t lda, bool 
     ab = __dadd_rn(ab, __shfl_xor_sync(0xffffffffu, ab, o));
   }
   if (lane == 0) {
-    ref[2 * w] = acc.hi;
-    ref[2 * w + 1] = acc.lo;
-    absab[w] = ab;
+    sh[0][wp] = acc.hi;
+    sh[1][wp] = acc.lo;
+    sh[2][wp] = ab;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    DD t{sh[0][0], sh[1][0]};
+    double tab = sh[2][0];
+    for (int q = 1; q < kProbeThreads / 32; ++q) {
+      t = dd_add(t, DD{sh[0][q], sh[1][q]});
+      tab = __dadd_rn(tab, sh[2][q]);
+    }
+    ref[2 * w] = t.hi;
+    ref[2 * w + 1] = t.lo;
+    absab[w] = tab;
+  }
+}
+
+// idx pairs (i, j) -> (j, i), for gathering entries of a column-major C.
+__global__ void swap_pairs_kernel(const int32_t* __restrict__ idx, int count, int32_t* __restrict__ out) {
+  int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w < count) {
+    out[2 * w] = idx[2 * w + 1];
+    out[2 * w + 1] = idx[2 * w];
   }
 }
 
@@ -233,6 +286,8 @@ void selector_release(emu_handle_s* h) {
   if (!s) return;
   if (s->params) cudaFree(s->params);
   if (s->params_II) cudaFree(s->params_II);
+  if (s->dev) cudaFree(s->dev);
+  if (s->host) cudaFreeHost(s->host);
   delete s;
   h->selector = nullptr;
 }
@@ -247,11 +302,7 @@ namespace {
 // bytes of scratch (maxbits + histogram).
 emu_status_t features_impl(emu_handle_s* h, const View& v, int64_t k, double tol, int64_t sample, float* feat,
                            uint8_t* scratch, cudaStream_t st) {
-  auto* maxA = reinterpret_cast<unsigned long long*>(scratch);
-  auto* maxB = maxA + v.M;
-  auto* hist = reinterpret_cast<unsigned int*>(maxB + v.N);
-  launch_scan<double>(static_cast<const double*>(v.A), v.ldA, v.a_kcontig, v.M, k, 1, maxA, h->status, st);
-  launch_scan<double>(static_cast<const double*>(v.B), v.ldB, v.b_kcontig, v.N, k, 1, maxB, h->status, st);
+  auto* hist = reinterpret_cast<unsigned int*>(scratch);
   cudaMemsetAsync(hist, 0, 64 * sizeof(unsigned int), st);
   int64_t sa = sample > 0 ? std::max<int64_t>(1, v.M / sample) : 1;
   int64_t sb = sample > 0 ? std::max<int64_t>(1, v.N / sample) : 1;
@@ -261,14 +312,14 @@ emu_status_t features_impl(emu_handle_s* h, const View& v, int64_t k, double tol
     nb = std::min<int64_t>(nb, sample);
   }
   feat_hist_kernel<<<static_cast<unsigned>(na), 256, 0, st>>>(static_cast<const double*>(v.A), v.ldA, v.a_kcontig, v.M,
-                                                               k, sa, maxA, hist);
+                                                               k, sa, hist);
   feat_hist_kernel<<<static_cast<unsigned>(nb), 256, 0, st>>>(static_cast<const double*>(v.B), v.ldB, v.b_kcontig, v.N,
-                                                               k, sb, maxB, hist + 32);
+                                                               k, sb, hist + 32);
   feat_finalize_kernel<<<1, 96, 0, st>>>(hist, std::log2(static_cast<double>(k)), -std::log10(tol), feat);
   return cudaGetLastError() == cudaSuccess ? EMU_OK : EMU_ERR_CUDA;
 }
 
-size_t feat_scratch(const View& v) { return 8 * static_cast<size_t>(v.M + v.N) + 512; }
+size_t feat_scratch(const View&) { return 512; }
 
 bool valid_layout(emu_layout_t l) { return l == EMU_ROW_MAJOR || l == EMU_COL_MAJOR; }
 
@@ -419,8 +470,8 @@ emu_status_t emu_probe_dd(emu_handle_t h, emu_layout_t layout, int64_t m, int64_
   // entries are given in the caller's (i, j) of C; the kernel reads A rows
   // and B columns directly in the caller's layout
   bool a_k = layout == EMU_ROW_MAJOR, b_k = layout != EMU_ROW_MAJOR;
-  probe_dd_kernel<<<(count * 32 + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(
-      A, lda, a_k, B, ldb, b_k, k, count, idx, ref, absab);
+  probe_dd_kernel<<<count, kProbeThreads, 0, static_cast<cudaStream_t>(stream)>>>(A, lda, a_k, B, ldb, b_k, k,
+                                                                                 count, idx, ref, absab);
   return cudaGetLastError() == cudaSuccess ? EMU_OK : EMU_ERR_CUDA;
 }
 
@@ -450,23 +501,50 @@ emu_status_t auto_impl(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n
   SelState* ss = sel_of(h);
   View v;
   normalize(layout, m, n, A, lda, B, ldb, &v);
-  // small device scratch of the selector (features, probabilities, probe)
+  // selector buffers: features and probabilities (136 floats), then the
+  // probe's indices, its results [ref (hi, lo) | sum |a||b| | C entry], and
+  // the swapped index pairs of a column-major gather
   const int pc = std::max(probe, 1);
-  size_t need = feat_scratch(v) + 1024 + static_cast<size_t>(pc) * (8 + 16 + 8 + 8) + 256;
-  uint8_t* ws = nullptr;
-  emu_status_t s = handle_workspace(h, need, st, &ws);
-  if (s != EMU_OK) return s;
-  float* feat = reinterpret_cast<float*>(ws + feat_scratch(v));
+  const size_t off_idx = 1024, off_res = off_idx + (8 * static_cast<size_t>(pc) + 255) / 256 * 256;
+  const size_t dev_need = off_res + 40 * static_cast<size_t>(pc);
+  const size_t host_need = std::max<size_t>(1024, 32 * static_cast<size_t>(pc));
+  if (dev_need > ss->dev_bytes) {
+    if (ss->dev) cudaFree(ss->dev);
+    ss->dev = nullptr;
+    ss->dev_bytes = 0;
+    if (cudaMalloc(&ss->dev, dev_need) != cudaSuccess) {
+      cudaGetLastError();
+      return EMU_ERR_ALLOC;
+    }
+    ss->dev_bytes = dev_need;
+  }
+  if (host_need > ss->host_bytes) {
+    if (ss->host) cudaFreeHost(ss->host);
+    ss->host = nullptr;
+    ss->host_bytes = 0;
+    if (cudaMallocHost(&ss->host, host_need) != cudaSuccess) {
+      cudaGetLastError();
+      return EMU_ERR_ALLOC;
+    }
+    ss->host_bytes = host_need;
+  }
+  float* feat = reinterpret_cast<float*>(ss->dev);
   float* prob = feat + 128;
-  s = features_impl(h, v, k, tol, 64, feat, ws, st);
-  if (s != EMU_OK) return s;
-  float f[kIn], pr[kOut];
+  {  // the feature scan needs scratch for the row / column maxima and histograms
+    uint8_t* ws = nullptr;
+    emu_status_t s = handle_workspace(h, feat_scratch(v), st, &ws);
+    if (s != EMU_OK) return s;
+    s = features_impl(h, v, k, tol, 64, feat, ws, st);
+    if (s != EMU_OK) return s;
+  }
   const bool loaded = scheme_II ? ss->loaded_II : ss->loaded;
   if (loaded) mlp_forward_kernel<<<1, kHid, 0, st>>>(scheme_II ? ss->params_II : ss->params, feat, 1, prob, nullptr);
-  if (cudaMemcpyAsync(f, feat, sizeof(f), cudaMemcpyDeviceToHost, st) != cudaSuccess) return EMU_ERR_CUDA;
-  if (loaded && cudaMemcpyAsync(pr, prob, sizeof(pr), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+  // one copy back: features and (if a network is loaded) probabilities
+  if (cudaMemcpyAsync(ss->host, feat, sizeof(float) * (128 + kOut), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
     return EMU_ERR_CUDA;
-  if (cudaStreamSynchronize(st) != cudaSuccess) return EMU_ERR_CUDA;
+  const float* f = reinterpret_cast<const float*>(ss->host);
+  const float* pr = f + 128;
   // value of class c and the largest value: p = 3 + c up to EMU_P_MAX, or
   // N = 6 + 2c up to EMU_NM_MAX
   const int top = scheme_II ? EMU_NM_MAX : EMU_P_MAX;
@@ -487,53 +565,49 @@ emu_status_t auto_impl(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n
     // the top class is open-ended ("10 or more" / "20"): go to the largest value at once
     p = cls == kOut - 1 ? top : base_v + step * cls;
   }
-  // probe entries: a deterministic spread over C (caller's coordinates)
-  std::vector<int32_t> idx(2 * static_cast<size_t>(probe));
-  uint64_t x = 0x9E3779B97F4A7C15ull ^ static_cast<uint64_t>(m * 1315423911u + n * 2654435761u + k);
-  for (int q = 0; q < probe; ++q) {
-    x ^= x << 13;
-    x ^= x >> 7;
-    x ^= x << 17;
-    idx[2 * q] = static_cast<int32_t>(x % static_cast<uint64_t>(m));
-    x ^= x << 13;
-    x ^= x >> 7;
-    x ^= x << 17;
-    idx[2 * q + 1] = static_cast<int32_t>(x % static_cast<uint64_t>(n));
+  // probe entries: a deterministic spread over C (caller's coordinates),
+  // uploaded once for every attempt (row-major view: (i, j); column-major C:
+  // element (i, j) sits at row j, column i of the row-major view)
+  auto* d_idx = reinterpret_cast<int32_t*>(ss->dev + off_idx);
+  auto* d_ref = reinterpret_cast<double*>(ss->dev + off_res);
+  auto* d_ab = d_ref + 2 * pc;
+  auto* d_c = d_ab + pc;
+  auto* d_sw = reinterpret_cast<int32_t*>(d_c + pc);  // gather indices for column-major C
+  if (probe > 0) {
+    auto* hidx = reinterpret_cast<int32_t*>(ss->host);
+    uint64_t x = 0x9E3779B97F4A7C15ull ^ static_cast<uint64_t>(m * 1315423911u + n * 2654435761u + k);
+    for (int q = 0; q < probe; ++q) {
+      x ^= x << 13;
+      x ^= x >> 7;
+      x ^= x << 17;
+      hidx[2 * q] = static_cast<int32_t>(x % static_cast<uint64_t>(m));
+      x ^= x << 13;
+      x ^= x >> 7;
+      x ^= x << 17;
+      hidx[2 * q + 1] = static_cast<int32_t>(x % static_cast<uint64_t>(n));
+    }
+    if (cudaMemcpyAsync(d_idx, hidx, 8 * static_cast<size_t>(probe), cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return EMU_ERR_CUDA;
+    if (layout != EMU_ROW_MAJOR) swap_pairs_kernel<<<(probe + 127) / 128, 128, 0, st>>>(d_idx, probe, d_sw);
+    // (the host buffer is next written by the results' copy, which the
+    // stream orders after this one)
   }
   for (int attempt = 0; attempt < 3; ++attempt) {
-    s = emu_dgemm(h, layout, m, n, k, alpha, A, lda, B, ldb, 0.0, C, ldc,
-                  scheme_II ? EMU_SCHEME_II_NORM : EMU_SCHEME_I, p, stream);
+    emu_status_t s = emu_dgemm(h, layout, m, n, k, alpha, A, lda, B, ldb, 0.0, C, ldc,
+                               scheme_II ? EMU_SCHEME_II_NORM : EMU_SCHEME_I, p, stream);
     if (s != EMU_OK) return s;
     *p_used = p;
     if (probe == 0) return EMU_OK;
-    // workspace may have moved inside emu_dgemm: re-fetch the selector scratch
-    s = handle_workspace(h, need, st, &ws);
-    if (s != EMU_OK) return s;
-    auto* d_idx = reinterpret_cast<int32_t*>(ws + feat_scratch(v) + 1024);
-    auto* d_ref = reinterpret_cast<double*>(ws + feat_scratch(v) + 1024 + 8 * static_cast<size_t>(pc));
-    auto* d_ab = d_ref + 2 * pc;
-    auto* d_c = d_ab + pc;
-    if (cudaMemcpyAsync(d_idx, idx.data(), sizeof(int32_t) * idx.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
-      return EMU_ERR_CUDA;
     s = emu_probe_dd(h, layout, m, n, k, A, lda, B, ldb, probe, d_idx, d_ref, d_ab, stream);
     if (s != EMU_OK) return s;
-    if (layout == EMU_ROW_MAJOR) {
-      gather_kernel<<<(probe + 127) / 128, 128, 0, st>>>(C, ldc, probe, d_idx, d_c);
-    } else {  // column-major C: element (i, j) at C[i + j*ldc] = row-major view with (j, i)
-      std::vector<int32_t> sw(idx.size());
-      for (int q = 0; q < probe; ++q) {
-        sw[2 * q] = idx[2 * q + 1];
-        sw[2 * q + 1] = idx[2 * q];
-      }
-      auto* d_sw = reinterpret_cast<int32_t*>(d_c + pc);
-      cudaMemcpyAsync(d_sw, sw.data(), sizeof(int32_t) * sw.size(), cudaMemcpyHostToDevice, st);
-      gather_kernel<<<(probe + 127) / 128, 128, 0, st>>>(C, ldc, probe, d_sw, d_c);
-    }
-    std::vector<double> ref(2 * static_cast<size_t>(probe)), ab(probe), cv(probe);
-    cudaMemcpyAsync(ref.data(), d_ref, sizeof(double) * ref.size(), cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(ab.data(), d_ab, sizeof(double) * ab.size(), cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(cv.data(), d_c, sizeof(double) * cv.size(), cudaMemcpyDeviceToHost, st);
-    if (cudaStreamSynchronize(st) != cudaSuccess) return EMU_ERR_CUDA;
+    gather_kernel<<<(probe + 127) / 128, 128, 0, st>>>(C, ldc, probe, layout == EMU_ROW_MAJOR ? d_idx : d_sw, d_c);
+    // one copy back: [ref | ab | C entries]
+    if (cudaMemcpyAsync(ss->host, d_ref, 32 * static_cast<size_t>(probe), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return EMU_ERR_CUDA;
+    const double* ref = reinterpret_cast<const double*>(ss->host);
+    const double* ab = ref + 2 * probe;
+    const double* cv = ab + probe;
     double worst = 0.0;
     for (int q = 0; q < probe; ++q) {
       double d = std::fabs((cv[q] / alpha - ref[2 * q]) - ref[2 * q + 1]);

@@ -57,3 +57,16 @@ def grouped_shapes(count: int, seed: int, mn_range=(32, 1024), k_range=(64, 2048
         k = int(round(float(np.exp(rng.uniform(klo, khi)))))
         out.append((m, n, k))
     return out
+
+
+def test_matrix_torch(rows: int, cols: int, phi: float, seed: int, device):
+    """The same generator drawn on a torch device (u first, then g, each for
+    the whole matrix, from torch.Generator(device).manual_seed(seed)): for
+    benchmark-size operands, which the CPU would take seconds to draw.  The
+    values differ from test_matrix's (another random stream), the
+    distribution is the same."""
+    import torch
+    g = torch.Generator(device=device).manual_seed(int(seed))
+    u = torch.rand((rows, cols), generator=g, device=device, dtype=torch.float64)
+    gn = torch.randn((rows, cols), generator=g, device=device, dtype=torch.float64)
+    return (u - 0.5) * torch.exp(phi * gn)

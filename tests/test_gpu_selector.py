@@ -166,3 +166,59 @@ def test_training_II_beats_fixed_nm(h):
     A, B = synth.gemm_pair(256, 256, 512, 2.0, 78)
     C, nm, code = emu.dgemm_auto(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), 1e-8, handle=h, scheme="II")
     assert code == 0 and nm in sel.NM_CLASSES
+
+
+def test_committed_selector_end_to_end_gain_at_1e8():
+    """The committed Scheme I network, timed end to end through
+    emu_dgemm_auto -- feature scan, MLP, probe and every escalation inside
+    the CUDA-event interval -- against emu_dgemm at the fixed p = 12 (the
+    smallest p passing every training product) on held-out products: faster
+    in total at tol = 1e-8, and passing on exactly the products the fixed p
+    passes (checked on 256 sampled entries against the double-double probe)."""
+    hd = emu.Handle(0)
+    sel.install_default(hd)
+    dev = torch.device("cuda", 0)
+    rng = np.random.Generator(np.random.PCG64(31337))
+    prods = [(int(round(float(np.exp(rng.uniform(np.log(1024), np.log(2048)))) / 64)) * 64,
+              float(rng.uniform(0.0, 8.0)), 8_000_000 + 2 * i) for i in range(8)]
+    warm = synth.test_matrix_torch(2048, 2048, 1.0, 1, dev)
+    emu.dgemm(warm, warm, scheme="I", p=12, handle=hd)
+    emu.dgemm_auto(warm, warm, 1e-8, handle=hd)
+    del warm
+    t_auto = t_fixed = 0.0
+    pass_auto, pass_fixed = [], []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for n, phi, seed in prods:
+        A = synth.test_matrix_torch(n, n, phi, seed, dev)
+        B = synth.test_matrix_torch(n, n, phi, seed + 1, dev)
+        C = torch.empty((n, n), dtype=torch.float64, device=dev)
+        pairs = rng.integers(0, n, size=(256, 2)).astype(np.int32)
+        idx = torch.from_numpy(pairs.reshape(-1)).to(dev)
+        ref = torch.empty(512, dtype=torch.float64, device=dev)
+        ab = torch.empty(256, dtype=torch.float64, device=dev)
+        emu.check(emu.emu_probe_dd(hd.h, emu.EMU_ROW_MAJOR, n, n, n, A.data_ptr(), n, B.data_ptr(), n, 256,
+                                   idx.data_ptr(), ref.data_ptr(), ab.data_ptr(), None))
+        r = ref.cpu().numpy().reshape(256, 2)
+        den = ab.cpu().numpy()
+
+        def err(Cx):
+            c = Cx.cpu().numpy()[pairs[:, 0], pairs[:, 1]]
+            return float(np.max(np.abs((c - r[:, 0]) - r[:, 1]) / den))
+
+        torch.cuda.synchronize()
+        e0.record()
+        emu.dgemm(A, B, C, scheme="I", p=12, handle=hd)
+        e1.record()
+        torch.cuda.synchronize()
+        t_fixed += e0.elapsed_time(e1)
+        pass_fixed.append(err(C) <= 1e-8)
+        e0.record()
+        Ca, used, code = emu.dgemm_auto(A, B, 1e-8, handle=hd)
+        e1.record()
+        torch.cuda.synchronize()
+        t_auto += e0.elapsed_time(e1)
+        assert code == 0 and 3 <= used <= 12
+        pass_auto.append(err(Ca) <= 1e-8)
+    hd.close()
+    assert pass_auto == pass_fixed
+    assert t_fixed / t_auto >= 1.05, (t_fixed, t_auto)
