@@ -358,12 +358,15 @@ typedef struct {
 } emu_gemm_desc_t;
 
 /* `count` independent Scheme I products with p slices (row-major, the
- * descriptors are host memory).  One grouped split launch and one
- * persistent grouped GEMM launch over a (problem, tile) work list ordered
- * longest-first; the launch sequence is captured once into a CUDA graph and
- * replayed while the descriptors stay identical.  Tile shapes come from the
- * autotuner cache (emu_tune_grouped) or a default.  The paper has no
- * batched interface; the tile model follows Table I. */
+ * descriptors are host memory).  Each product falls into a shape bucket (p
+ * and log2 classes of sqrt(m n) and of k) and is cut into output tiles of
+ * that bucket's tuned shape (64 x 32, 32 x 32 or 32 x 64; 64 x 32 where the
+ * handle holds no tuning).  One grouped exponent scan, one grouped split,
+ * then one persistent grouped GEMM launch per tile shape in use over its
+ * (problem, tile) work list, balanced longest-first over the CTAs; the GEMM
+ * launches run on parallel branches of one CUDA graph, captured once and
+ * replayed while the descriptors and tunings stay identical.  The paper has
+ * no batched interface; the tile model follows Table I. */
 emu_status_t emu_dgemm_grouped(emu_handle_t h, int count, const emu_gemm_desc_t *descs_host, int p,
                                emu_stream_t stream);
 
@@ -371,11 +374,14 @@ emu_status_t emu_dgemm_grouped(emu_handle_t h, int count, const emu_gemm_desc_t 
 emu_status_t emu_dgemm_grouped_loop(emu_handle_t h, int count, const emu_gemm_desc_t *descs_host,
                                     int p, emu_stream_t stream);
 
-/* Autotune the grouped tile configuration for this problem list: times the
- * candidate configurations (Table I: tile M/N and pipeline depth) on the
- * given data and stores the fastest per shape bucket in the handle; writes
- * the chosen configuration index per bucket to the cache file `path` if
- * non-NULL.  Returns the number of configurations timed in *timed_host. */
+/* Autotune the tile shape per shape bucket on this problem list (data as
+ * given): coordinate descent on the time of the whole grouped call -- for
+ * each bucket in turn, the batch is timed (CUDA events, 5 graph replays)
+ * with that bucket's products in each other tile shape, and a change is
+ * kept if the batch gets at least 1 % faster.  The choices are stored per
+ * bucket in the handle and, if `path` is non-NULL, written to that cache
+ * file ("bucket": shape index lines).  *timed_host receives the number of
+ * batch configurations timed.  Synchronises `stream`. */
 emu_status_t emu_tune_grouped(emu_handle_t h, int count, const emu_gemm_desc_t *descs_host, int p,
                               const char *path, int *timed_host, emu_stream_t stream);
 

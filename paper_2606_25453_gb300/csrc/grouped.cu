@@ -1,13 +1,18 @@
 // grouped.cu -- many independent Scheme I products in one persistent launch.
 //
 // The paper has no batched interface; this follows its tile model (Table I):
-// the products' output tiles form one work list, balanced over the CTAs by a
+// each product is cut into output tiles of the shape its shape bucket was
+// tuned to (BM x BN: 64 x 32, 32 x 32 or 32 x 64, warps of 16 x 16); the
+// tiles of one shape form one work list, balanced over the CTAs by a
 // longest-processing-time assignment (tile cost = number of K chunks), and
-// one persistent kernel walks each CTA's list.  The exponent scan and the
-// split of all operands are one launch each.  The launch sequence (memset,
-// scan, split, GEMM) is captured once into a CUDA graph and replayed while
-// the product descriptors stay identical.  The tile shape (BM x BN, warps of
-// 16 x 16) is chosen per shape bucket by a timing autotuner.
+// one persistent kernel per shape in use walks each CTA's list.  The
+// exponent scan and the split of all operands are one launch each.  The
+// launch sequence (memset, scan, split, then the GEMM launches on parallel
+// branches, so that one shape's kernel fills the tail of another's) is
+// captured once into a CUDA graph and replayed while the product
+// descriptors stay identical.  A timing autotuner picks the shape per shape
+// bucket (log2 classes of sqrt(M N) and of K) by coordinate descent on the
+// time of the whole batch.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -253,7 +258,7 @@ __global__ void __launch_bounds__(CfgG<P, BM, BN>::kThreads, CfgG<P, BM, BN>::kO
     return;
   }
 
-  const int wm = warp / Cfg::kWN, wn = warp % Cfg::kWN;
+  const int wm = warp / Cfg::kWN, wn = warp % Cfg::kWN;  // this warp's 16 x 16 patch of the tile
   const uint32_t a_off = swz32(wm * 16 + (lane & 15), lane >> 4);
   const uint32_t b_off = swz32(wn * 16 + (lane & 7) + ((lane >> 4) << 3), (lane >> 3) & 1);
   uint32_t it = 0;
@@ -274,6 +279,9 @@ __global__ void __launch_bounds__(CfgG<P, BM, BN>::kThreads, CfgG<P, BM, BN>::kO
       for (int q = 0; q < 4; ++q) S[nt][q] = 0;
     int since = 0;
     const int nk32 = pr.nk32;
+    // a patch wholly outside the product (ragged last tiles) does no MMAs;
+    // its warp still takes part in the stage handshake
+    const bool live = tl.y * BM + wm * 16 < pr.M && tl.z * BN + wn * 16 < pr.N;
     for (int kk = 0; kk < nk32; ++kk, ++it) {
       const uint32_t stage = it % Cfg::kStages;
       const uint32_t par = (it / Cfg::kStages) & 1u;
@@ -281,19 +289,22 @@ __global__ void __launch_bounds__(CfgG<P, BM, BN>::kThreads, CfgG<P, BM, BN>::kO
         set_status(status, ST_TIMEOUT);
         return;
       }
-      const uint32_t sA = base + stage * Cfg::kStageBytes;
-      const uint32_t sB = sA + P * Cfg::kBlkA;
-      uint32_t af[P][4];
+      if (live) {
+        const uint32_t sA = base + stage * Cfg::kStageBytes;
+        const uint32_t sB = sA + P * Cfg::kBlkA;
+        uint32_t af[P][4];
 #pragma unroll
-      for (int i = 0; i < P; ++i) ldsm_x4(sA + i * Cfg::kBlkA + a_off, af[i][0], af[i][1], af[i][2], af[i][3]);
-      TriAll<P, Cfg::kBlkB, false>::run(acc, af, sB, b_off);
+        for (int i = 0; i < P; ++i) ldsm_x4(sA + i * Cfg::kBlkA + a_off, af[i][0], af[i][1], af[i][2], af[i][3]);
+        TriAll<P, Cfg::kBlkB, false>::run(acc, af, sB, b_off);
+      }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[stage]);
       if (++since == kc32) {
-        fold<P, false>(acc, S);
+        if (live) fold<P, false>(acc, S);
         since = 0;
       }
     }
+    if (!live) continue;
     fold<P, false>(acc, S);
     const int row0 = tl.y * BM + wm * 16 + (lane >> 2);
     const int col0 = tl.z * BN + wn * 16 + (lane & 3) * 2;
@@ -317,15 +328,23 @@ constexpr int kNumCfg = 3;
 constexpr int kCfgBM[kNumCfg] = {64, 32, 32};
 constexpr int kCfgBN[kNumCfg] = {32, 32, 64};
 
+// One GEMM launch of a plan: the tiles of every product whose bucket uses
+// tile configuration `cfg`.
+struct SubPlan {
+  int cfg = 0, grid = 0;
+  int4* d_tiles = nullptr;
+  int* d_cta = nullptr;
+};
+
 struct GroupPlan {
   std::vector<emu_gemm_desc_t> descs;
-  int p = 0, cfg = 0, grid = 0, count = 0;
+  std::vector<int> pcfg;  // tile configuration of each product
+  int p = 0, count = 0;
+  std::vector<SubPlan> subs;
   void* dev = nullptr;  // one device buffer: probs, maps, tiles, cta_ptr, starts, workspace
   size_t dev_bytes = 0;
   GProb* d_probs = nullptr;
   CUtensorMap* d_maps = nullptr;
-  int4* d_tiles = nullptr;
-  int* d_cta = nullptr;
   int* d_startA_scan = nullptr;
   int* d_startB_scan = nullptr;
   int* d_startA_split = nullptr;
@@ -341,6 +360,8 @@ struct GroupState {
   GroupPlan* plan = nullptr;
   std::map<std::string, int> tuned;  // shape bucket -> configuration index
   cudaStream_t capture = nullptr;
+  cudaStream_t side[kNumCfg] = {};   // branches of the captured graph
+  cudaEvent_t fork = nullptr, join[kNumCfg] = {};
 };
 
 void free_plan(GroupPlan* pl) {
@@ -356,63 +377,81 @@ GroupState* state_of(emu_handle_s* h) {
   return static_cast<GroupState*>(h->grouped);
 }
 
-bool same_descs(const std::vector<emu_gemm_desc_t>& a, const emu_gemm_desc_t* b, int count) {
-  if (static_cast<int>(a.size()) != count) return false;
-  return std::memcmp(a.data(), b, sizeof(emu_gemm_desc_t) * count) == 0;
+bool same_plan(const GroupPlan* pl, const emu_gemm_desc_t* b, int count, int p, const std::vector<int>& pcfg) {
+  if (!pl || pl->p != p || static_cast<int>(pl->descs.size()) != count || pl->pcfg != pcfg) return false;
+  return std::memcmp(pl->descs.data(), b, sizeof(emu_gemm_desc_t) * count) == 0;
 }
 
-// Shape bucket of a product list: p, and log2 buckets of the median output
-// side and of the median K.
-std::string bucket_of(int count, const emu_gemm_desc_t* d, int p) {
-  std::vector<double> side, kk;
-  for (int i = 0; i < count; ++i) {
-    side.push_back(std::sqrt(static_cast<double>(d[i].m) * static_cast<double>(d[i].n)));
-    kk.push_back(static_cast<double>(d[i].k));
-  }
-  std::nth_element(side.begin(), side.begin() + count / 2, side.end());
-  std::nth_element(kk.begin(), kk.begin() + count / 2, kk.end());
-  char buf[64];
-  std::snprintf(buf, sizeof(buf), "p%d_mn%d_k%d", p, static_cast<int>(std::floor(std::log2(side[count / 2] + 1))),
-                static_cast<int>(std::floor(std::log2(kk[count / 2] + 1))));
+// Shape bucket of one product: p, and log2 classes of its output side
+// sqrt(M N) (below 64, 128, 256, 512, and above) and of K (below 128, 256,
+// 512, 1024, and above).
+std::string bucket_of(const emu_gemm_desc_t& d, int p) {
+  const double side = std::sqrt(static_cast<double>(d.m) * static_cast<double>(d.n));
+  const int sc = std::min(4, std::max(0, static_cast<int>(std::floor(std::log2(side))) - 5));
+  const int kc = std::min(4, std::max(0, static_cast<int>(std::floor(std::log2(static_cast<double>(d.k)))) - 6));
+  char buf[48];
+  std::snprintf(buf, sizeof(buf), "p%d_s%d_k%d", p, sc, kc);
   return buf;
 }
 
+// Tile configuration of each product from the tuned map (0 where untuned).
+std::vector<int> configs_of(const GroupState* gs, int count, const emu_gemm_desc_t* d, int p) {
+  std::vector<int> c(count, 0);
+  for (int i = 0; i < count; ++i) {
+    auto it = gs->tuned.find(bucket_of(d[i], p));
+    if (it != gs->tuned.end()) c[i] = it->second;
+  }
+  return c;
+}
+
 template <int P, int BM, int BN>
-cudaError_t launch_gemm_grouped(const GroupPlan& pl, int* status, cudaStream_t st, bool attrs_only) {
+cudaError_t launch_gemm_grouped(const GroupPlan& pl, const SubPlan& sp, int* status, cudaStream_t st,
+                                bool attrs_only) {
   using Cfg = CfgG<P, BM, BN>;
   if (attrs_only)
     return cudaFuncSetAttribute(gemm_I_grouped_kernel<P, BM, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 Cfg::kSmem);
-  gemm_I_grouped_kernel<P, BM, BN><<<pl.grid, Cfg::kThreads, Cfg::kSmem, st>>>(
-      pl.d_probs, pl.d_maps, pl.d_tiles, pl.d_cta, static_cast<int>(host_chunk_len_I(P) / 32), -14 - 8 * (P - 1),
+  gemm_I_grouped_kernel<P, BM, BN><<<sp.grid, Cfg::kThreads, Cfg::kSmem, st>>>(
+      pl.d_probs, pl.d_maps, sp.d_tiles, sp.d_cta, static_cast<int>(host_chunk_len_I(P) / 32), -14 - 8 * (P - 1),
       status);
   return cudaGetLastError();
 }
 
 template <int P>
-cudaError_t launch_by_cfg(const GroupPlan& pl, int* status, cudaStream_t st, bool attrs_only) {
-  switch (pl.cfg) {
-    case 0: return launch_gemm_grouped<P, 64, 32>(pl, status, st, attrs_only);
-    case 1: return launch_gemm_grouped<P, 32, 32>(pl, status, st, attrs_only);
-    default: return launch_gemm_grouped<P, 32, 64>(pl, status, st, attrs_only);
+cudaError_t launch_by_cfg(const GroupPlan& pl, const SubPlan& sp, int* status, cudaStream_t st, bool attrs_only) {
+  switch (sp.cfg) {
+    case 0: return launch_gemm_grouped<P, 64, 32>(pl, sp, status, st, attrs_only);
+    case 1: return launch_gemm_grouped<P, 32, 32>(pl, sp, status, st, attrs_only);
+    default: return launch_gemm_grouped<P, 32, 64>(pl, sp, status, st, attrs_only);
   }
 }
 
-// Set the dynamic shared memory limit of the plan's GEMM instantiation
-// (done before capture: it is not stream work).
-cudaError_t prepare_attrs(const GroupPlan& pl) {
+cudaError_t launch_sub(const GroupPlan& pl, const SubPlan& sp, int* status, cudaStream_t st, bool attrs_only) {
   switch (pl.p) {
-#define EMU_GA(PP) case PP: return launch_by_cfg<PP>(pl, nullptr, nullptr, true);
-    EMU_GA(1) EMU_GA(2) EMU_GA(3) EMU_GA(4) EMU_GA(5) EMU_GA(6)
-    EMU_GA(7) EMU_GA(8) EMU_GA(9) EMU_GA(10) EMU_GA(11) EMU_GA(12)
-#undef EMU_GA
+#define EMU_GG(PP) case PP: return launch_by_cfg<PP>(pl, sp, status, st, attrs_only);
+    EMU_GG(1) EMU_GG(2) EMU_GG(3) EMU_GG(4) EMU_GG(5) EMU_GG(6)
+    EMU_GG(7) EMU_GG(8) EMU_GG(9) EMU_GG(10) EMU_GG(11) EMU_GG(12)
+#undef EMU_GG
     default: return cudaErrorInvalidValue;
   }
 }
 
+// Set the dynamic shared memory limit of the plan's GEMM instantiations
+// (done before capture: it is not stream work).
+cudaError_t prepare_attrs(const GroupPlan& pl) {
+  for (const SubPlan& sp : pl.subs) {
+    cudaError_t e = launch_sub(pl, sp, nullptr, nullptr, true);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 int occupancy_of(int cfg) { return (kCfgBM[cfg] / 16) * (kCfgBN[cfg] / 16) >= 8 ? 1 : 2; }
 
-cudaError_t launch_group(const GroupPlan& pl, int* status, cudaStream_t st) {
+// memset, scan, split on `st`; then one GEMM launch per tile configuration,
+// the first on `st`, the others on side branches that fork after the split
+// and join before the end.
+cudaError_t launch_group(const GroupPlan& pl, GroupState* gs, int* status, cudaStream_t st) {
   cudaMemsetAsync(pl.d_max, 0, pl.max_bytes, st);
   if (pl.scan_blocks)
     grouped_scan_kernel<<<pl.scan_blocks, 256, 0, st>>>(pl.d_probs, pl.count, pl.d_startA_scan, pl.d_startB_scan,
@@ -427,44 +466,40 @@ cudaError_t launch_group(const GroupPlan& pl, int* status, cudaStream_t st) {
       default: return cudaErrorInvalidValue;
     }
   }
-  switch (pl.p) {
-#define EMU_GG(PP) case PP: return launch_by_cfg<PP>(pl, status, st, false);
-    EMU_GG(1) EMU_GG(2) EMU_GG(3) EMU_GG(4) EMU_GG(5) EMU_GG(6)
-    EMU_GG(7) EMU_GG(8) EMU_GG(9) EMU_GG(10) EMU_GG(11) EMU_GG(12)
-#undef EMU_GG
-    default: return cudaErrorInvalidValue;
+  const size_t nsub = pl.subs.size();
+  if (nsub > 1 && cudaEventRecord(gs->fork, st) != cudaSuccess) return cudaErrorUnknown;
+  for (size_t i = 1; i < nsub; ++i) {
+    if (cudaStreamWaitEvent(gs->side[i], gs->fork, 0) != cudaSuccess) return cudaErrorUnknown;
+    cudaError_t e = launch_sub(pl, pl.subs[i], status, gs->side[i], false);
+    if (e != cudaSuccess) return e;
+    if (cudaEventRecord(gs->join[i], gs->side[i]) != cudaSuccess) return cudaErrorUnknown;
   }
+  if (nsub > 0) {
+    cudaError_t e = launch_sub(pl, pl.subs[0], status, st, false);
+    if (e != cudaSuccess) return e;
+  }
+  for (size_t i = 1; i < nsub; ++i)
+    if (cudaStreamWaitEvent(st, gs->join[i], 0) != cudaSuccess) return cudaErrorUnknown;
+  return cudaGetLastError();
 }
 
 static size_t al256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
-// Build a plan: device tables, workspace, tensor maps, LPT tile lists.
-emu_status_t build_plan(emu_handle_s* h, int count, const emu_gemm_desc_t* d, int p, int cfg, GroupPlan** out) {
-  auto* pl = new GroupPlan();
-  pl->descs.assign(d, d + count);
-  pl->p = p;
-  pl->cfg = cfg;
-  pl->count = count;
+// Tiles of the products in configuration `cfg`, longest-processing-time
+// assigned to `grid` CTA slots (cost = K chunks): flat list + CTA offsets.
+void lpt_tiles(int count, const emu_gemm_desc_t* d, const std::vector<int>& pcfg, int cfg, int grid_max,
+               std::vector<int4>* flat, std::vector<int>* cta, int* grid_out) {
   const int BM = kCfgBM[cfg], BN = kCfgBN[cfg];
-  pl->grid = h->num_sms * occupancy_of(cfg);
-
-  // sizes
-  std::vector<GProb> probs(count);
-  size_t off = 0;
-  size_t o_probs = off; off += al256(sizeof(GProb) * count);
-  size_t o_maps = off; off += al256(sizeof(CUtensorMap) * 2 * count);
-  // tile list
   std::vector<int4> tiles;
   for (int i = 0; i < count; ++i) {
+    if (pcfg[i] != cfg) continue;
     int tm = static_cast<int>((d[i].m + BM - 1) / BM), tn = static_cast<int>((d[i].n + BN - 1) / BN);
     for (int a = 0; a < tm; ++a)
       for (int b = 0; b < tn; ++b) tiles.push_back(make_int4(i, a, b, 0));
   }
-  // longest-processing-time assignment to grid slots (cost = K chunks)
   std::stable_sort(tiles.begin(), tiles.end(), [&](const int4& x, const int4& y) { return d[x.x].k > d[y.x].k; });
-  int grid = pl->grid;
+  int grid = grid_max;
   if (static_cast<int>(tiles.size()) < grid) grid = std::max<int>(1, static_cast<int>(tiles.size()));
-  pl->grid = grid;
   std::vector<std::vector<int4>> per(grid);
   using Slot = std::pair<int64_t, int>;
   std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> heap;
@@ -476,15 +511,48 @@ emu_status_t build_plan(emu_handle_s* h, int count, const emu_gemm_desc_t* d, in
     s.first += (d[t.x].k + 31) / 32;
     heap.push(s);
   }
-  std::vector<int4> flat;
-  std::vector<int> cta(grid + 1, 0);
+  flat->clear();
+  cta->assign(grid + 1, 0);
   for (int g = 0; g < grid; ++g) {
-    cta[g] = static_cast<int>(flat.size());
-    flat.insert(flat.end(), per[g].begin(), per[g].end());
+    (*cta)[g] = static_cast<int>(flat->size());
+    flat->insert(flat->end(), per[g].begin(), per[g].end());
   }
-  cta[grid] = static_cast<int>(flat.size());
-  size_t o_tiles = off; off += al256(sizeof(int4) * std::max<size_t>(flat.size(), 1));
-  size_t o_cta = off; off += al256(sizeof(int) * (grid + 1));
+  (*cta)[grid] = static_cast<int>(flat->size());
+  *grid_out = grid;
+}
+
+// Build a plan: device tables, workspace, tensor maps, LPT tile lists.
+emu_status_t build_plan(emu_handle_s* h, int count, const emu_gemm_desc_t* d, int p, const std::vector<int>& pcfg,
+                        GroupPlan** out) {
+  auto* pl = new GroupPlan();
+  pl->descs.assign(d, d + count);
+  pl->pcfg = pcfg;
+  pl->p = p;
+  pl->count = count;
+
+  std::vector<GProb> probs(count);
+  size_t off = 0;
+  size_t o_probs = off; off += al256(sizeof(GProb) * count);
+  size_t o_maps = off; off += al256(sizeof(CUtensorMap) * 2 * count);
+  // one tile list per configuration in use
+  std::vector<std::vector<int4>> flats;
+  std::vector<std::vector<int>> ctas;
+  std::vector<size_t> o_tiles, o_cta;
+  for (int cfg = 0; cfg < kNumCfg; ++cfg) {
+    if (std::find(pcfg.begin(), pcfg.end(), cfg) == pcfg.end()) continue;
+    SubPlan sp;
+    sp.cfg = cfg;
+    std::vector<int4> flat;
+    std::vector<int> cta;
+    lpt_tiles(count, d, pcfg, cfg, h->num_sms * occupancy_of(cfg), &flat, &cta, &sp.grid);
+    o_tiles.push_back(off);
+    off += al256(sizeof(int4) * std::max<size_t>(flat.size(), 1));
+    o_cta.push_back(off);
+    off += al256(sizeof(int) * cta.size());
+    flats.push_back(std::move(flat));
+    ctas.push_back(std::move(cta));
+    pl->subs.push_back(sp);
+  }
   // block prefix arrays
   std::vector<int> sA(count + 1), sB(count + 1), pA(count + 1), pB(count + 1);
   sA[0] = sB[0] = pA[0] = pB[0] = 0;
@@ -517,8 +585,10 @@ emu_status_t build_plan(emu_handle_s* h, int count, const emu_gemm_desc_t* d, in
   uint8_t* base = static_cast<uint8_t*>(pl->dev);
   pl->d_probs = reinterpret_cast<GProb*>(base + o_probs);
   pl->d_maps = reinterpret_cast<CUtensorMap*>(base + o_maps);
-  pl->d_tiles = reinterpret_cast<int4*>(base + o_tiles);
-  pl->d_cta = reinterpret_cast<int*>(base + o_cta);
+  for (size_t i = 0; i < pl->subs.size(); ++i) {
+    pl->subs[i].d_tiles = reinterpret_cast<int4*>(base + o_tiles[i]);
+    pl->subs[i].d_cta = reinterpret_cast<int*>(base + o_cta[i]);
+  }
   int* starts = reinterpret_cast<int*>(base + o_starts);
   pl->d_startA_scan = starts;
   pl->d_startB_scan = starts + (count + 1);
@@ -557,6 +627,8 @@ emu_status_t build_plan(emu_handle_s* h, int count, const emu_gemm_desc_t* d, in
     g.rows_a = w.rows_a;
     g.rows_b = w.rows_b;
     g.nchunks = (d[i].k + 31) / 32;
+    // TMA boxes of this product's tile configuration
+    const int BM = kCfgBM[pcfg[i]], BN = kCfgBN[pcfg[i]];
     if (!make_tmap_i8(&maps[2 * i], g.hatA, static_cast<uint64_t>(w.cols), static_cast<uint64_t>(w.rows_a), BM) ||
         !make_tmap_i8(&maps[2 * i + 1], g.hatB, static_cast<uint64_t>(w.cols), static_cast<uint64_t>(w.rows_b), BN)) {
       free_plan(pl);
@@ -570,9 +642,12 @@ emu_status_t build_plan(emu_handle_s* h, int count, const emu_gemm_desc_t* d, in
   st4.insert(st4.end(), pB.begin(), pB.end());
   bool ok = cudaMemcpy(pl->d_probs, probs.data(), sizeof(GProb) * count, cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(pl->d_maps, maps.data(), sizeof(CUtensorMap) * 2 * count, cudaMemcpyHostToDevice) == cudaSuccess &&
-            (flat.empty() || cudaMemcpy(pl->d_tiles, flat.data(), sizeof(int4) * flat.size(), cudaMemcpyHostToDevice) == cudaSuccess) &&
-            cudaMemcpy(pl->d_cta, cta.data(), sizeof(int) * (grid + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(starts, st4.data(), sizeof(int) * st4.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+  for (size_t i = 0; ok && i < pl->subs.size(); ++i)
+    ok = (flats[i].empty() || cudaMemcpy(pl->subs[i].d_tiles, flats[i].data(), sizeof(int4) * flats[i].size(),
+                                         cudaMemcpyHostToDevice) == cudaSuccess) &&
+         cudaMemcpy(pl->subs[i].d_cta, ctas[i].data(), sizeof(int) * ctas[i].size(), cudaMemcpyHostToDevice) ==
+             cudaSuccess;
   if (!ok) {
     free_plan(pl);
     return EMU_ERR_CUDA;
@@ -581,13 +656,21 @@ emu_status_t build_plan(emu_handle_s* h, int count, const emu_gemm_desc_t* d, in
   return EMU_OK;
 }
 
-// Capture the plan's launch sequence into a graph (on a private stream).
+// Capture the plan's launch sequence into a graph (on a private stream, with
+// private side streams for the parallel GEMM branches).
 emu_status_t capture_plan(emu_handle_s* h, GroupState* gs, GroupPlan* pl) {
   if (!gs->capture && cudaStreamCreateWithFlags(&gs->capture, cudaStreamNonBlocking) != cudaSuccess)
     return EMU_ERR_CUDA;
+  if (!gs->fork) {
+    if (cudaEventCreateWithFlags(&gs->fork, cudaEventDisableTiming) != cudaSuccess) return EMU_ERR_CUDA;
+    for (int i = 1; i < kNumCfg; ++i)
+      if (cudaStreamCreateWithFlags(&gs->side[i], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&gs->join[i], cudaEventDisableTiming) != cudaSuccess)
+        return EMU_ERR_CUDA;
+  }
   if (prepare_attrs(*pl) != cudaSuccess) return EMU_ERR_CUDA;
   if (cudaStreamBeginCapture(gs->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return EMU_ERR_CUDA;
-  cudaError_t le = launch_group(*pl, h->status, gs->capture);
+  cudaError_t le = launch_group(*pl, gs, h->status, gs->capture);
   cudaError_t ce = cudaStreamEndCapture(gs->capture, &pl->graph);
   if (le != cudaSuccess || ce != cudaSuccess) {
     cudaGetLastError();
@@ -609,17 +692,19 @@ emu_status_t validate(emu_handle_s* h, int count, const emu_gemm_desc_t* d, int 
   return EMU_OK;
 }
 
-// Run (building and capturing if the product list changed) with a given cfg.
-emu_status_t run_group(emu_handle_s* h, int count, const emu_gemm_desc_t* d, int p, int cfg, cudaStream_t st) {
+// Run (building and capturing if the product list or the configurations
+// changed) with a tile configuration per product.
+emu_status_t run_group(emu_handle_s* h, int count, const emu_gemm_desc_t* d, int p, const std::vector<int>& pcfg,
+                       cudaStream_t st) {
   GroupState* gs = state_of(h);
   GroupPlan* pl = gs->plan;
-  if (!pl || pl->p != p || pl->cfg != cfg || !same_descs(pl->descs, d, count)) {
+  if (!same_plan(pl, d, count, p, pcfg)) {
     if (pl) {
       cudaDeviceSynchronize();
       free_plan(pl);
       gs->plan = nullptr;
     }
-    emu_status_t s = build_plan(h, count, d, p, cfg, &pl);
+    emu_status_t s = build_plan(h, count, d, p, pcfg, &pl);
     if (s != EMU_OK) return s;
     s = capture_plan(h, gs, pl);
     if (s != EMU_OK) {
@@ -630,8 +715,23 @@ emu_status_t run_group(emu_handle_s* h, int count, const emu_gemm_desc_t* d, int
   }
   trace_begin(h, PH_GEMM, st);
   cudaError_t e = cudaGraphLaunch(pl->exec, st);
-  trace_end(h, PH_GEMM, st, 3);
+  trace_end(h, PH_GEMM, st, 3 + static_cast<int>(pl->subs.size()));
   return e == cudaSuccess ? EMU_OK : EMU_ERR_CUDA;
+}
+
+// Mean time of `reps` graph replays after a warm-up (ms).
+emu_status_t time_group(emu_handle_s* h, int count, const emu_gemm_desc_t* d, int p, const std::vector<int>& pcfg,
+                        cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, int reps, float* ms) {
+  emu_status_t s = run_group(h, count, d, p, pcfg, st);  // builds, captures and warms up
+  if (s != EMU_OK) return s;
+  run_group(h, count, d, p, pcfg, st);
+  cudaEventRecord(e0, st);
+  for (int r = 0; r < reps; ++r) run_group(h, count, d, p, pcfg, st);
+  cudaEventRecord(e1, st);
+  if (cudaEventSynchronize(e1) != cudaSuccess) return EMU_ERR_CUDA;
+  cudaEventElapsedTime(ms, e0, e1);
+  *ms /= static_cast<float>(reps);
+  return EMU_OK;
 }
 
 }  // namespace
@@ -641,6 +741,11 @@ void grouped_release(emu_handle_s* h) {
   auto* gs = static_cast<GroupState*>(h->grouped);
   free_plan(gs->plan);
   if (gs->capture) cudaStreamDestroy(gs->capture);
+  for (int i = 1; i < kNumCfg; ++i) {
+    if (gs->side[i]) cudaStreamDestroy(gs->side[i]);
+    if (gs->join[i]) cudaEventDestroy(gs->join[i]);
+  }
+  if (gs->fork) cudaEventDestroy(gs->fork);
   delete gs;
   h->grouped = nullptr;
 }
@@ -656,10 +761,7 @@ emu_status_t emu_dgemm_grouped(emu_handle_t h, int count, const emu_gemm_desc_t*
   if (s != EMU_OK || count == 0) return s;
   cudaSetDevice(h->device);
   GroupState* gs = state_of(h);
-  int cfg = 0;
-  auto it = gs->tuned.find(bucket_of(count, descs, p));
-  if (it != gs->tuned.end()) cfg = it->second;
-  return run_group(h, count, descs, p, cfg, static_cast<cudaStream_t>(stream));
+  return run_group(h, count, descs, p, configs_of(gs, count, descs, p), static_cast<cudaStream_t>(stream));
 }
 
 emu_status_t emu_dgemm_grouped_loop(emu_handle_t h, int count, const emu_gemm_desc_t* d, int p, emu_stream_t stream) {
@@ -673,38 +775,50 @@ emu_status_t emu_dgemm_grouped_loop(emu_handle_t h, int count, const emu_gemm_de
   return EMU_OK;
 }
 
+// Per-bucket tuning by coordinate descent on the whole batch: start from
+// the current choices (configuration 0 where untuned); for each bucket in
+// turn, time the batch with that bucket's products in each other
+// configuration and keep a change that makes the batch at least 1 % faster.
 emu_status_t emu_tune_grouped(emu_handle_t h, int count, const emu_gemm_desc_t* d, int p, const char* path,
                               int* timed, emu_stream_t stream) {
   emu_status_t s = validate(h, count, d, p);
   if (s != EMU_OK || count == 0) return s;
   cudaSetDevice(h->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  GroupState* gs = state_of(h);
+  std::map<std::string, std::vector<int>> members;
+  for (int i = 0; i < count; ++i) members[bucket_of(d[i], p)].push_back(i);
+  std::vector<int> cur = configs_of(gs, count, d, p);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  float best = 1e30f;
-  int best_cfg = 0, n_timed = 0;
-  for (int cfg = 0; cfg < kNumCfg; ++cfg) {
-    s = run_group(h, count, d, p, cfg, st);  // builds, captures and warms up
-    if (s != EMU_OK) break;
-    run_group(h, count, d, p, cfg, st);
-    cudaEventRecord(e0, st);
-    for (int r = 0; r < 3; ++r) run_group(h, count, d, p, cfg, st);
-    cudaEventRecord(e1, st);
-    cudaEventSynchronize(e1);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    ++n_timed;
-    if (ms < best) {
-      best = ms;
-      best_cfg = cfg;
+  constexpr int kReps = 5;
+  float best = 0.f;
+  int n_timed = 0;
+  s = time_group(h, count, d, p, cur, st, e0, e1, kReps, &best);
+  ++n_timed;
+  for (auto it = members.begin(); s == EMU_OK && it != members.end(); ++it) {
+    const int c0 = cur[it->second[0]];
+    int keep = c0;
+    for (int c = 0; c < kNumCfg; ++c) {
+      if (c == c0) continue;
+      std::vector<int> trial = cur;
+      for (int i : it->second) trial[i] = c;
+      float ms = 0.f;
+      s = time_group(h, count, d, p, trial, st, e0, e1, kReps, &ms);
+      if (s != EMU_OK) break;
+      ++n_timed;
+      if (ms < 0.99f * best) {
+        best = ms;
+        keep = c;
+      }
     }
+    for (int i : it->second) cur[i] = keep;
+    gs->tuned[it->first] = keep;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (s != EMU_OK) return s;
-  GroupState* gs = state_of(h);
-  gs->tuned[bucket_of(count, d, p)] = best_cfg;
   if (timed) *timed = n_timed;
   if (path) {
     std::ofstream f(path);

@@ -1,5 +1,6 @@
-"""Grouped emulated DGEMM (one persistent launch under a CUDA graph) against
-the oracle, the per-product loop, and the autotuner's interface."""
+"""Grouped emulated DGEMM (persistent launches per tile shape under one CUDA
+graph) against the oracle, the per-product loop, mixed tile shapes per
+shape bucket, and the autotuner's interface."""
 import json
 import os
 
@@ -79,9 +80,12 @@ def test_autotuner_and_cache(h, tmp_path):
     Cs = [torch.empty((m, n), dtype=torch.float64, device="cuda") for m, n, _ in shapes]
     d = emu.grouped_descs(As, Bs, Cs)
     path = str(tmp_path / "tune.json")
-    assert emu.tune_grouped(d, p, path=path, handle=h) == 3
+    timed = emu.tune_grouped(d, p, path=path, handle=h)
     cache = json.load(open(path))
-    assert len(cache) == 1 and list(cache.values())[0] in (0, 1, 2)
+    # one choice per shape bucket; the first timing plus two alternatives per bucket
+    assert len(cache) >= 2 and all(v in (0, 1, 2) for v in cache.values())
+    assert timed == 1 + 2 * len(cache)
+    assert all(k.startswith("p6_s") for k in cache)
     ref = [c.clone() for c in Cs]
     h2 = emu.Handle(0)
     emu.check(emu.emu_load_tuning(h2.h, path.encode()))
@@ -90,6 +94,34 @@ def test_autotuner_and_cache(h, tmp_path):
     for a, b in zip(Cs, ref):
         assert torch.equal(a, b)
     h2.close()
+
+
+def test_mixed_tile_shapes_bit_exact(orc, tmp_path):
+    """A tuning that gives the shape buckets different tile shapes: the
+    products run in three GEMM launches on parallel graph branches, each
+    bit-exact against the oracle (ragged edges exercise the patches that
+    lie wholly outside a product)."""
+    p = 5
+    shapes, mats = make_problems(60, 11, mn=(20, 700), kr=(60, 1500))
+    path = tmp_path / "mixed.json"
+    with open(path, "w") as fh:
+        fh.write("{\n" + ",\n".join('  "p5_s%d_k%d": %d' % (sc, kc, (sc + 2 * kc) % 3)
+                                      for sc in range(5) for kc in range(5)) + "\n}\n")
+    hd = emu.Handle(0)
+    emu.check(emu.emu_load_tuning(hd.h, str(path).encode()))
+    As = [torch.from_numpy(A).cuda() for A, _ in mats]
+    Bs = [torch.from_numpy(B).cuda() for _, B in mats]
+    Cs = [torch.full((m, n), np.nan, dtype=torch.float64, device="cuda") for m, n, _ in shapes]
+    d = emu.grouped_descs(As, Bs, Cs)
+    for _ in range(2):  # capture, then replay
+        emu.dgemm_grouped(d, p, handle=hd)
+        torch.cuda.synchronize()
+        assert hd.status() == 0
+        for (A, B), C in zip(mats, Cs):
+            assert np.array_equal(C.cpu().numpy(), orc.emu_I(A, B, p))
+        for C in Cs:
+            C.fill_(np.nan)
+    hd.close()
 
 
 def test_grouped_512_problems_sampled(orc, h):
