@@ -547,15 +547,21 @@ __global__ void __launch_bounds__(256) crt_II_kernel(const __grid_constant__ KPa
   const uint8_t* const p = kp.R + static_cast<int64_t>(row) * kp.ldr + c0;
   const int erow = kp.EA[row] + kp.escale;
   if constexpr (!CPLX) {
+    // all residue words first (independent, predicated loads in flight
+    // together), then the sums: a load per modulus waited on in turn left
+    // the kernel bound by memory latency
+    uint32_t wl[kMaxModuli];
+#pragma unroll
+    for (int l = 0; l < kMaxModuli; ++l)
+      wl[l] = l < kp.nm ? __ldg(reinterpret_cast<const uint32_t*>(p + static_cast<int64_t>(l) * kp.plane)) : 0u;
     CrtLazy acc[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) crt_lazy_init(acc[c]);
 #pragma unroll
     for (int l = 0; l < kMaxModuli; ++l) {
       if (l >= kp.nm) break;
-      const uint32_t w = *reinterpret_cast<const uint32_t*>(p + static_cast<int64_t>(l) * kp.plane);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) crt_lazy_acc(acc[c], ct, l, (w >> (8 * c)) & 0xFFu);
+      for (int c = 0; c < 4; ++c) crt_lazy_acc(acc[c], ct, l, (wl[l] >> (8 * c)) & 0xFFu);
     }
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -583,13 +589,21 @@ __global__ void __launch_bounds__(256) crt_II_kernel(const __grid_constant__ KPa
       crt_lazy_init(are[c]);
       crt_lazy_init(aim[c]);
     }
+    // the next modulus's three words are loaded while this one's are summed
+    const int64_t set = static_cast<int64_t>(kp.nm) * kp.plane;
+    uint32_t n1 = __ldg(reinterpret_cast<const uint32_t*>(p));
+    uint32_t n2 = __ldg(reinterpret_cast<const uint32_t*>(p + set));
+    uint32_t n3 = __ldg(reinterpret_cast<const uint32_t*>(p + 2 * set));
 #pragma unroll 1
     for (int l = 0; l < kp.nm; ++l) {
       const int m = static_cast<int>(mt.mods[l]);
-      const uint8_t* q = p + static_cast<int64_t>(l) * kp.plane;
-      const uint32_t w1 = *reinterpret_cast<const uint32_t*>(q);
-      const uint32_t w2 = *reinterpret_cast<const uint32_t*>(q + static_cast<int64_t>(kp.nm) * kp.plane);
-      const uint32_t w3 = *reinterpret_cast<const uint32_t*>(q + static_cast<int64_t>(2 * kp.nm) * kp.plane);
+      const uint32_t w1 = n1, w2 = n2, w3 = n3;
+      if (l + 1 < kp.nm) {
+        const uint8_t* q = p + static_cast<int64_t>(l + 1) * kp.plane;
+        n1 = __ldg(reinterpret_cast<const uint32_t*>(q));
+        n2 = __ldg(reinterpret_cast<const uint32_t*>(q + set));
+        n3 = __ldg(reinterpret_cast<const uint32_t*>(q + 2 * set));
+      }
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const int t1 = (w1 >> (8 * c)) & 0xFF, t2 = (w2 >> (8 * c)) & 0xFF, t3 = (w3 >> (8 * c)) & 0xFF;

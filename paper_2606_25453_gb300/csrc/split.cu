@@ -450,7 +450,9 @@ __device__ __forceinline__ int sym_residue(const int* d, const ModTables& mt, in
 template <int ND>
 __device__ __forceinline__ void digits14f(uint64_t bits, int shift, float* d) {
   const ScaledInt s = scaled_trunc_bits(bits, shift);
-  const uint32_t sg = static_cast<uint32_t>(bits >> 63) << 31;
+  // a' = 0 keeps its digits +0 (no sign), so that no residue below comes out
+  // as -0 (whose bf16 pattern is not that of the integer 0)
+  const uint32_t sg = s.mag != 0 ? static_cast<uint32_t>(bits >> 63) << 31 : 0u;
   uint32_t dg[ND];
   if constexpr (ND <= 4) {  // |a'| < 2^(14 ND) <= 2^56: one 64-bit word holds it
     const uint64_t v = s.lsh < 64 ? s.mag << s.lsh : 0ull;
@@ -473,6 +475,14 @@ __device__ __forceinline__ void digits14f(uint64_t bits, int shift, float* d) {
     d[j] = __uint_as_float(__float_as_uint(__uint_as_float(0x4B000000u | dg[j]) - 8388608.0f) | sg);
 }
 
+// With ND <= 4 digits |t| <= 16383 (1 + 3 * 128) < 2^22.6, and for every
+// modulus of the list (173 <= m <= 256) the estimate f = RN(t inv + offinv)
+// is within 0.38/m (from inv = RN(1/m)) + 2^-9 <= 0.5/m (the rounding of f,
+// |f| < 2^15.2) + 2^-25 < 1/m of (t + off) / m.  As t + off is an integer,
+// (t + off) / m = q + j/m with 0 <= j < m, so floor(f) is q, or q - 1 when
+// j = 0: r = t - floor(f) m is the symmetric residue or that plus m, and one
+// correction finishes.  Six digits (|t| < 2^23.3) keep both corrections.
+// No step produces -0 from the +0 digits of a' = 0.
 template <int ND>
 __device__ __forceinline__ float sym_residue_f(const float* d, const ModTables& mt, int l) {
   float t = d[0];
@@ -481,7 +491,7 @@ __device__ __forceinline__ float sym_residue_f(const float* d, const ModTables& 
   const float m = mt.mf[l], off = mt.offf[l];
   const float q = floorf(__fmaf_rn(t, mt.inv[l], mt.offinv[l]));
   float r = __fmaf_rn(-q, m, t);
-  if (r < -off) r += m;
+  if (ND > 4 && r < -off) r += m;
   if (r >= m - off) r -= m;
   return r;
 }
@@ -515,10 +525,10 @@ __device__ __forceinline__ void store4(int8_t* p, int r0, int r1, int r2, int r3
 // of the first element in plane 0, `plane` the plane stride in bytes.  The
 // modulus loop is unrolled so that the table entries are kernel-parameter
 // operands.
-// Four binary32 residues as bf16 (+ 0 turns a -0 into +0).
+// Four binary32 residues (integers |r| <= 128, never -0) as bf16.
 __device__ __forceinline__ void store4f(int8_t* p, float r0, float r1, float r2, float r3) {
-  const uint32_t f0 = __float_as_uint(r0 + 0.0f), f1 = __float_as_uint(r1 + 0.0f);
-  const uint32_t f2 = __float_as_uint(r2 + 0.0f), f3 = __float_as_uint(r3 + 0.0f);
+  const uint32_t f0 = __float_as_uint(r0), f1 = __float_as_uint(r1);
+  const uint32_t f2 = __float_as_uint(r2), f3 = __float_as_uint(r3);
   *reinterpret_cast<uint2*>(p) = make_uint2(__byte_perm(f0, f1, 0x7632u), __byte_perm(f2, f3, 0x7632u));
 }
 
