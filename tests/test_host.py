@@ -139,4 +139,24 @@ def test_suite_markdown_tables(tmp_path):
     md2 = bench.suite_markdown([str(path), str(later)])
     assert "| 8192 | 0.5 | 16 | 64.000 | 1023.0 | 56.0 |" in md2 and "| 8192 | 0.5 | 16 | 62.000 |" not in md2
     assert "| 8192 | 0.5 | 16 | 8.700 | 139.0 | 56.0 | 7.35x |" in md2  # against the replaced row
-    assert "| 8 | 116.00 | 24.0 | 1.66x |" in md2 and "--suite-part scheme2" in md2
+    assert "| 8 | 116.00 | 24.0 | 1.66x |" in md2 and "replace the rows of earlier files" in md2
+
+
+def test_selector_markdown(tmp_path):
+    # the end-to-end selector summary: per (scheme, tol) totals, speed-up and pass rates
+    import json
+
+    import bench
+    rows = [
+        {"path": "selector_e2e", "scheme": "I", "n": 2048, "phi": 1.0, "tol": 1e-8, "fixed": 12, "used": 7, "code": 0,
+         "ms_auto": 3.0, "ms_fixed": 8.0, "err_auto": 1e-10, "err_fixed": 1e-17, "pass_auto": True,
+         "pass_fixed": True},
+        {"path": "selector_e2e_summary", "scheme": "I", "tol": 1e-8, "products": 1, "fixed": 12,
+         "ms_auto_total": 3.0, "ms_fixed_total": 8.0, "speedup_vs_fixed": 8.0 / 3.0, "pass_auto": 1.0,
+         "pass_fixed": 1.0, "mean_used": 7.0},
+    ]
+    path = tmp_path / "sel.jsonl"
+    path.write_text("".join(json.dumps(r) + "\n" for r in rows))
+    md = bench.selector_markdown(str(path))
+    assert "| I | 1e-08 | 1 | 12 | 7.00 | 100 % | 100 % | 3.0 | 8.0 | 2.67x |" in md
+    assert "| I | 2048 | 1.00 | 1e-08 | 7 | 3.00 | 8.00 | 1.00e-10 | 1.00e-17 |" in md
