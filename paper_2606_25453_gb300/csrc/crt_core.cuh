@@ -129,10 +129,13 @@ __device__ __forceinline__ void crt_lazy_init(CrtLazy& a) {
   a.t = 0.0f;
 }
 
-// a += w_l r_l, r in [0, m_l).
+// a += w_l r_l, r in [0, m_l).  L: the number of 32-bit limbs of P (and so
+// of every w_l < P); the limbs above stay zero, their products are skipped.
+template <int L = kCrtLimbs>
 __device__ __forceinline__ void crt_lazy_acc(CrtLazy& a, const CrtTables& ct, int l, uint32_t r) {
+  static_assert(L >= 1 && L <= kCrtLimbs, "limb count");
 #pragma unroll
-  for (int i = 0; i < kCrtLimbs; ++i) a.s[i] += static_cast<uint64_t>(ct.w[l][i]) * r;
+  for (int i = 0; i < L; ++i) a.s[i] += static_cast<uint64_t>(ct.w[l][i]) * r;
   // r as binary32 without a conversion instruction: 2^23 + r has r in its low mantissa bits
   a.t = __fmaf_rn(__uint_as_float(0x4B000000u | r) - 8388608.0f, ct.wP[l], a.t);
 }

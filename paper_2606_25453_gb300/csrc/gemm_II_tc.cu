@@ -250,7 +250,7 @@ __device__ __forceinline__ int mod_small(int x, int m, float inv) {
 }
 
 __device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, int& tm, int& tn) {
-  constexpr int G = 8;
+  constexpr int G = 16;  // row tiles per group of the tile order (16: 1-2 % faster than 8 at n = 8192-16384)
   int per_group = G * tiles_n;
   int g = tile / per_group;
   int first = g * G;
@@ -535,7 +535,7 @@ struct KParamsCRT {
 // One thread per row and four consecutive columns: the CRT sums of Eq. (8)
 // from the residue planes (3M: Re = T1 - T2, Im = T3 - T1 - T2 mod m, Eq.
 // 16), S mod P with the symmetric lift, binary64, scaling and the update.
-template <int MODE>
+template <int MODE, int L>
 __global__ void __launch_bounds__(256) crt_II_kernel(const __grid_constant__ KParamsCRT kp,
                                                      const __grid_constant__ CrtTables ct,
                                                      const __grid_constant__ ModTables mt) {
@@ -561,7 +561,7 @@ __global__ void __launch_bounds__(256) crt_II_kernel(const __grid_constant__ KPa
     for (int l = 0; l < kMaxModuli; ++l) {
       if (l >= kp.nm) break;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) crt_lazy_acc(acc[c], ct, l, (wl[l] >> (8 * c)) & 0xFFu);
+      for (int c = 0; c < 4; ++c) crt_lazy_acc<L>(acc[c], ct, l, (wl[l] >> (8 * c)) & 0xFFu);
     }
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -612,8 +612,8 @@ __global__ void __launch_bounds__(256) crt_II_kernel(const __grid_constant__ KPa
         int im = t3 - t1 - t2;
         if (im < 0) im += m;
         if (im < 0) im += m;
-        crt_lazy_acc(are[c], ct, l, static_cast<uint32_t>(re));
-        crt_lazy_acc(aim[c], ct, l, static_cast<uint32_t>(im));
+        crt_lazy_acc<L>(are[c], ct, l, static_cast<uint32_t>(re));
+        crt_lazy_acc<L>(aim[c], ct, l, static_cast<uint32_t>(im));
       }
     }
 #pragma unroll
@@ -742,7 +742,14 @@ cudaError_t launch_crt(const GemmIIArgs& a, const ModTables& mt, const CrtTables
   kp.plain = a.alpha_re == 1.0 && a.alpha_im == 0.0 && a.beta_re == 0.0 && a.beta_im == 0.0;
   const int64_t threads = static_cast<int64_t>(a.M) * ((a.N + 3) / 4);
   if (threads == 0) return cudaSuccess;
-  crt_II_kernel<MODE><<<static_cast<unsigned>((threads + 255) / 256), 256, 0, st>>>(kp, ct, mt);
+  // limbs of P: 3 for up to 12 moduli (P < 2^96), 4 up to 16 (P < 2^128), else 5
+  const unsigned grid = static_cast<unsigned>((threads + 255) / 256);
+  if (ct.P[4] != 0)
+    crt_II_kernel<MODE, 5><<<grid, 256, 0, st>>>(kp, ct, mt);
+  else if (ct.P[3] != 0)
+    crt_II_kernel<MODE, 4><<<grid, 256, 0, st>>>(kp, ct, mt);
+  else
+    crt_II_kernel<MODE, 3><<<grid, 256, 0, st>>>(kp, ct, mt);
   return cudaGetLastError();
 }
 
