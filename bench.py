@@ -60,10 +60,11 @@ def parse():
                          "matching rows of earlier ones)")
     ap.add_argument("--selector-md", default=None,
                     help="print the selector end-to-end summary of a --suite-part selector JSONL file")
-    ap.add_argument("--suite-part", default="all", choices=["all", "ii", "scheme2", "selector"],
+    ap.add_argument("--suite-part", default="all", choices=["all", "ii", "scheme2", "selector", "grouped"],
                     help="ii: only the Scheme II DGEMM points (run in a child with EMU_II_ENGINE=mma by the full "
                          "suite); scheme2: every row of the bf16 tcgen05 Scheme II paths (DGEMM, SGEMM, norm "
-                         "scaling, ZGEMM 3M, CGEMM 3M)")
+                         "scaling, ZGEMM 3M, CGEMM 3M); selector: the selector's end-to-end points; grouped: the "
+                         "grouped-batch points")
     return ap.parse_args()
 
 
@@ -654,13 +655,54 @@ def suite_markdown(paths):
                 o.append(f"| {name} | {par} | {bits(d['err'])} | {d['tflops']:.2f} | {gb:.2f} |")
     except ImportError:
         pass
-    o.append("\n## Grouped: 512 uneven products (p = 6), one CUDA graph vs per-product loop\n")
+    o.append("\n## Grouped: 512 uneven products, one CUDA graph vs per-product loop\n")
     for d in rows:
         if d["path"] == "emu_dgemm_grouped":
-            o.append(f"graph (tuned tile) {d['ms_graph_tuned']:.2f} ms, default tile {d['ms_graph_default_tile']:.2f} ms, "
-                     f"loop {d['ms_loop']:.2f} ms: {d['speedup_graph_vs_loop']:.2f}x; {d['tflops_graph']:.2f} emulated "
-                     f"TFLOP/s, {d['int8_tops_graph']:.1f} INT8 TOP/s.")
+            o.append(f"p = {d['p']}: graph (tuned) {d['ms_graph_tuned']:.2f} ms, untuned (64 x 32, B-slice-major) "
+                     f"{d['ms_graph_default_tile']:.2f} ms, loop {d['ms_loop']:.2f} ms: "
+                     f"{d['speedup_graph_vs_loop']:.2f}x; {d['tflops_graph']:.2f} emulated TFLOP/s, "
+                     f"{d['int8_tops_graph']:.1f} INT8 TOP/s.")
+            if d.get("tuned"):
+                o.append("  Tuned configurations (bucket: tile, slice-pair order): " +
+                         ", ".join(f"{k} {v}" for k, v in d["tuned"].items()) + ".")
     return "\n".join(o)
+
+
+GROUPED_CFGS = ("64x32 B-major", "32x32 B-major", "32x64 B-major",
+                "64x32 A-major", "32x32 A-major", "32x64 A-major")
+
+
+def grouped_points(emu, h, dev, emit, timed):
+    """512 uneven products (M, N log-uniform in [32, 1024], K in [64, 2048]):
+    the grouped CUDA graph untuned and after the autotuner, against the
+    per-product loop, at p = 6 and p = 10."""
+    import tempfile
+
+    import torch
+    shapes = synth.grouped_shapes(512, 0)
+    As, Bs, Cs = [], [], []
+    for i, (m, nn, k) in enumerate(shapes):
+        A, B = synth.gemm_pair(m, nn, k, 1.0, 5000 + i)
+        As.append(torch.from_numpy(A).to(dev))
+        Bs.append(torch.from_numpy(B).to(dev))
+        Cs.append(torch.empty((m, nn), dtype=torch.float64, device=dev))
+    d = emu.grouped_descs(As, Bs, Cs)
+    flops = sum(2 * m * nn * k for m, nn, k in shapes)
+    for p in (6, 10):
+        ms_default = timed(lambda: emu.dgemm_grouped(d, p, handle=h), reps=5)
+        with tempfile.TemporaryDirectory() as td:
+            path = os.path.join(td, "tune.json")
+            ncfg = emu.tune_grouped(d, p, path=path, handle=h)
+            with open(path) as fh:
+                tuned = json.load(fh)
+        ms_tuned = timed(lambda: emu.dgemm_grouped(d, p, handle=h), reps=5)
+        ms_loop = timed(lambda: emu.dgemm_grouped(d, p, handle=h, loop=True), reps=2)
+        emit({"path": "emu_dgemm_grouped", "count": 512, "p": p, "ms_graph_default_tile": ms_default,
+              "ms_graph_tuned": ms_tuned, "configs_timed": ncfg, "ms_loop": ms_loop,
+              "tuned": {k: GROUPED_CFGS[v] for k, v in sorted(tuned.items())},
+              "tflops_graph": flops / ms_tuned / 1e9, "tflops_loop": flops / ms_loop / 1e9,
+              "int8_tops_graph": (p * (p + 1) // 2) * flops / ms_tuned / 1e9,
+              "speedup_graph_vs_loop": ms_loop / ms_tuned})
 
 
 SEL_TOLS = (1e-8, 1e-12, 1e-15)
@@ -833,8 +875,9 @@ def run_suite(path, args):
         d = np.hypot((Cs.real - hr) - lr, (Cs.imag - hm) - lm)
         return float(np.max(d / den))
 
-    if args.suite_part == "selector":
-        selector_points(emu, h, dev, emit)
+    if args.suite_part in ("selector", "grouped"):
+        (selector_points if args.suite_part == "selector" else
+         lambda *a: grouped_points(*a, timed))(emu, h, dev, emit)
         out.close()
         h.close()
         return
@@ -1013,24 +1056,7 @@ def run_suite(path, args):
         out.close()
         h.close()
         return
-    # grouped: 512 uneven products, graph vs per-product loop
-    shapes = synth.grouped_shapes(512, 0)
-    As, Bs, Cs = [], [], []
-    for i, (m, nn, k) in enumerate(shapes):
-        A, B = synth.gemm_pair(m, nn, k, 1.0, 5000 + i)
-        As.append(torch.from_numpy(A).to(dev))
-        Bs.append(torch.from_numpy(B).to(dev))
-        Cs.append(torch.empty((m, nn), dtype=torch.float64, device=dev))
-    d = emu.grouped_descs(As, Bs, Cs)
-    flops = sum(2 * m * nn * k for m, nn, k in shapes)
-    ms_default = timed(lambda: emu.dgemm_grouped(d, 6, handle=h), reps=5)
-    ncfg = emu.tune_grouped(d, 6, handle=h)
-    ms_tuned = timed(lambda: emu.dgemm_grouped(d, 6, handle=h), reps=5)
-    ms_loop = timed(lambda: emu.dgemm_grouped(d, 6, handle=h, loop=True), reps=2)
-    emit({"path": "emu_dgemm_grouped", "count": 512, "p": 6, "ms_graph_default_tile": ms_default,
-          "ms_graph_tuned": ms_tuned, "configs_timed": ncfg, "ms_loop": ms_loop,
-          "tflops_graph": flops / ms_tuned / 1e9, "tflops_loop": flops / ms_loop / 1e9,
-          "int8_tops_graph": 21 * flops / ms_tuned / 1e9, "speedup_graph_vs_loop": ms_loop / ms_tuned})
+    grouped_points(emu, h, dev, emit, timed)
     out.close()
     h.close()
 

@@ -359,10 +359,12 @@ typedef struct {
 
 /* `count` independent Scheme I products with p slices (row-major, the
  * descriptors are host memory).  Each product falls into a shape bucket (p
- * and log2 classes of sqrt(m n) and of k) and is cut into output tiles of
- * that bucket's tuned shape (64 x 32, 32 x 32 or 32 x 64; 64 x 32 where the
- * handle holds no tuning).  One grouped exponent scan, one grouped split,
- * then one persistent grouped GEMM launch per tile shape in use over its
+ * and log2 classes of sqrt(m n) and of k) and runs in that bucket's tuned
+ * configuration: output tiles of 64 x 32, 32 x 32 or 32 x 64 and the
+ * triangle's slice pairs B-slice-major or A-slice-major (64 x 32,
+ * B-slice-major where the handle holds no tuning).  One grouped exponent
+ * scan, one grouped split, then one persistent grouped GEMM launch per
+ * configuration in use over its
  * (problem, tile) work list, balanced longest-first over the CTAs; the GEMM
  * launches run on parallel branches of one CUDA graph, captured once and
  * replayed while the descriptors and tunings stay identical.  The paper has
@@ -374,14 +376,21 @@ emu_status_t emu_dgemm_grouped(emu_handle_t h, int count, const emu_gemm_desc_t 
 emu_status_t emu_dgemm_grouped_loop(emu_handle_t h, int count, const emu_gemm_desc_t *descs_host,
                                     int p, emu_stream_t stream);
 
-/* Autotune the tile shape per shape bucket on this problem list (data as
- * given): coordinate descent on the time of the whole grouped call -- for
- * each bucket in turn, the batch is timed (CUDA events, 5 graph replays)
- * with that bucket's products in each other tile shape, and a change is
- * kept if the batch gets at least 1 % faster.  The choices are stored per
- * bucket in the handle and, if `path` is non-NULL, written to that cache
- * file ("bucket": shape index lines).  *timed_host receives the number of
- * batch configurations timed.  Synchronises `stream`. */
+/* Autotune the configuration per shape bucket on this problem list (data
+ * as given).  A configuration is a tile shape (64 x 32, 32 x 32 or 32 x 64
+ * outputs per CTA) and a slice-pair order of the triangle of Eq. (2)
+ * (B-slice-major or A-slice-major): indices 0-2 are the three shapes in
+ * B-slice-major order, 3-5 the same shapes A-slice-major.  Each bucket's
+ * products are timed alone (CUDA events, 5 graph replays) in every
+ * configuration; the fastest is the bucket's candidate if it beats the
+ * current choice by 2 %.  The whole batch is then timed with all
+ * candidates and kept if it is faster than with the current choices; else
+ * the candidates are tried one bucket at a time on the whole batch (kept
+ * if the batch gets 0.5 % faster).  The choices are stored per bucket in
+ * the handle and, if `path` is non-NULL, written to that cache file
+ * ("bucket": configuration index lines).  *timed_host receives the number
+ * of (sub-)batch configurations timed.  Synchronises `stream`; the C
+ * arrays are written. */
 emu_status_t emu_tune_grouped(emu_handle_t h, int count, const emu_gemm_desc_t *descs_host, int p,
                               const char *path, int *timed_host, emu_stream_t stream);
 

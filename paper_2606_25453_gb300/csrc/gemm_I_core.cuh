@@ -1,7 +1,8 @@
 // gemm_I_core.cuh -- per-warp pieces of the fused Scheme I main loop shared
 // by the single-product and the grouped kernels: the triangular slice-pair
-// schedule of Eq. (2) on a 16 x 16 warp patch, and the exact drain of the p
-// accumulator sets into 128-bit integers (Eq. 3 without rounding).
+// schedule of Eq. (2) on a 16 x 16 warp patch (in two orders: B-slice-major
+// and A-slice-major), and the exact drain of the p accumulator sets into
+// 128-bit integers (Eq. 3 without rounding).
 //
 // Two slice engines share the code: INT8 slices (beta = 8, signed leading /
 // unsigned tail bytes, int32 accumulators, INT8 mma.sync) and E4M3 slices
@@ -58,6 +59,46 @@ struct TriAll {
       TriRow<P, F8, J>::run(acc, af, bf);
       TriAll<P, BLKB, F8, J + 1>::run(acc, af, sB, b_off);
     }
+  }
+};
+
+// The same triangle in A-slice-major order: the P B-slice fragments are
+// loaded first, then row i of the triangle (acc[i + j] += A'_i B'_j for
+// j < P - i) is issued as one run of MMAs.  More registers (4 P for the
+// fragments) against fewer shared-memory loads between MMAs of one slice
+// pair row; which order is faster depends on p and the tile, so the grouped
+// autotuner chooses.
+template <int P, bool F8, int I, int J = 0>
+struct TriRowA {
+  using Acc = typename Engine<F8>::Acc;
+  __device__ __forceinline__ static void run(Acc (*acc)[2][4], const uint32_t (*af)[4], const uint32_t (*bf)[4]) {
+    if constexpr (I + J < P) {
+      Engine<F8>::template mma<I, J>(acc[I + J][0], af[I], bf[J]);
+      Engine<F8>::template mma<I, J>(acc[I + J][1], af[I], bf[J] + 2);
+      TriRowA<P, F8, I, J + 1>::run(acc, af, bf);
+    }
+  }
+};
+
+template <int P, bool F8, int I = 0>
+struct TriRowsA {
+  using Acc = typename Engine<F8>::Acc;
+  __device__ __forceinline__ static void run(Acc (*acc)[2][4], const uint32_t (*af)[4], const uint32_t (*bf)[4]) {
+    if constexpr (I < P) {
+      TriRowA<P, F8, I>::run(acc, af, bf);
+      TriRowsA<P, F8, I + 1>::run(acc, af, bf);
+    }
+  }
+};
+
+template <int P, int BLKB, bool F8>
+struct TriAllByA {
+  using Acc = typename Engine<F8>::Acc;
+  __device__ __forceinline__ static void run(Acc (*acc)[2][4], const uint32_t (*af)[4], uint32_t sB, uint32_t b_off) {
+    uint32_t bf[P][4];
+#pragma unroll
+    for (int j = 0; j < P; ++j) ldsm_x4(sB + j * BLKB + b_off, bf[j][0], bf[j][1], bf[j][2], bf[j][3]);
+    TriRowsA<P, F8>::run(acc, af, bf);
   }
 };
 

@@ -1,18 +1,19 @@
 // grouped.cu -- many independent Scheme I products in one persistent launch.
 //
 // The paper has no batched interface; this follows its tile model (Table I):
-// each product is cut into output tiles of the shape its shape bucket was
-// tuned to (BM x BN: 64 x 32, 32 x 32 or 32 x 64, warps of 16 x 16); the
-// tiles of one shape form one work list, balanced over the CTAs by a
+// each product is cut into output tiles of the configuration its shape
+// bucket was tuned to -- a tile shape (BM x BN: 64 x 32, 32 x 32 or 32 x 64,
+// warps of 16 x 16) and a slice-pair schedule of the triangle (B-slice-major
+// or A-slice-major) --; the tiles of one configuration form one work list, balanced over the CTAs by a
 // longest-processing-time assignment (tile cost = number of K chunks), and
-// one persistent kernel per shape in use walks each CTA's list.  The
+// one persistent kernel per configuration in use walks each CTA's list.  The
 // exponent scan and the split of all operands are one launch each.  The
 // launch sequence (memset, scan, split, then the GEMM launches on parallel
-// branches, so that one shape's kernel fills the tail of another's) is
+// branches, so that one kernel fills the tail of another's) is
 // captured once into a CUDA graph and replayed while the product
-// descriptors stay identical.  A timing autotuner picks the shape per shape
-// bucket (log2 classes of sqrt(M N) and of K) by coordinate descent on the
-// time of the whole batch.
+// descriptors stay identical.  A timing autotuner picks the configuration
+// per shape bucket (log2 classes of sqrt(M N) and of K) by coordinate
+// descent on the time of the whole batch.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(256) grouped_split_kernel(const GProb* __restr
 }
 
 // ---------------------------------------------------------------- GEMM
-template <int P, int BM, int BN>
+template <int P, int BM, int BN, int SCHED>
 struct CfgG {
   static constexpr int kWM = BM / 16, kWN = BN / 16, kCW = kWM * kWN;
   static constexpr int kThreads = (kCW + 1) * 32;
@@ -207,12 +208,14 @@ struct CfgG {
   static constexpr int kOcc = kCW >= 8 ? 1 : 2;
 };
 
-template <int P, int BM, int BN>
-__global__ void __launch_bounds__(CfgG<P, BM, BN>::kThreads, CfgG<P, BM, BN>::kOcc)
+// SCHED: slice-pair order of the triangle, 0 = B-slice-major (TriAll),
+// 1 = A-slice-major (TriAllByA).
+template <int P, int BM, int BN, int SCHED>
+__global__ void __launch_bounds__(CfgG<P, BM, BN, SCHED>::kThreads, CfgG<P, BM, BN, SCHED>::kOcc)
     gemm_I_grouped_kernel(const GProb* __restrict__ probs, const CUtensorMap* __restrict__ maps,
                           const int4* __restrict__ tiles, const int* __restrict__ cta_ptr, int kc32, int escale,
                           int* status) {
-  using Cfg = CfgG<P, BM, BN>;
+  using Cfg = CfgG<P, BM, BN, SCHED>;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -295,7 +298,10 @@ __global__ void __launch_bounds__(CfgG<P, BM, BN>::kThreads, CfgG<P, BM, BN>::kO
         uint32_t af[P][4];
 #pragma unroll
         for (int i = 0; i < P; ++i) ldsm_x4(sA + i * Cfg::kBlkA + a_off, af[i][0], af[i][1], af[i][2], af[i][3]);
-        TriAll<P, Cfg::kBlkB, false>::run(acc, af, sB, b_off);
+        if constexpr (SCHED == 0)
+          TriAll<P, Cfg::kBlkB, false>::run(acc, af, sB, b_off);
+        else
+          TriAllByA<P, Cfg::kBlkB, false>::run(acc, af, sB, b_off);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[stage]);
@@ -324,9 +330,12 @@ __global__ void __launch_bounds__(CfgG<P, BM, BN>::kThreads, CfgG<P, BM, BN>::kO
 }
 
 // ---------------------------------------------------------------- host plan
-constexpr int kNumCfg = 3;
-constexpr int kCfgBM[kNumCfg] = {64, 32, 32};
-constexpr int kCfgBN[kNumCfg] = {32, 32, 64};
+// Candidate configurations: tile shape x slice-pair schedule (0-2
+// B-slice-major, 3-5 the same shapes A-slice-major; launch_by_cfg maps them
+// to kernel instantiations).
+constexpr int kNumCfg = 6;
+constexpr int kCfgBM[kNumCfg] = {64, 32, 32, 64, 32, 32};
+constexpr int kCfgBN[kNumCfg] = {32, 32, 64, 32, 32, 64};
 
 // One GEMM launch of a plan: the tiles of every product whose bucket uses
 // tile configuration `cfg`.
@@ -404,14 +413,14 @@ std::vector<int> configs_of(const GroupState* gs, int count, const emu_gemm_desc
   return c;
 }
 
-template <int P, int BM, int BN>
+template <int P, int BM, int BN, int SCHED>
 cudaError_t launch_gemm_grouped(const GroupPlan& pl, const SubPlan& sp, int* status, cudaStream_t st,
                                 bool attrs_only) {
-  using Cfg = CfgG<P, BM, BN>;
+  using Cfg = CfgG<P, BM, BN, SCHED>;
   if (attrs_only)
-    return cudaFuncSetAttribute(gemm_I_grouped_kernel<P, BM, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                Cfg::kSmem);
-  gemm_I_grouped_kernel<P, BM, BN><<<sp.grid, Cfg::kThreads, Cfg::kSmem, st>>>(
+    return cudaFuncSetAttribute(gemm_I_grouped_kernel<P, BM, BN, SCHED>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
+  gemm_I_grouped_kernel<P, BM, BN, SCHED><<<sp.grid, Cfg::kThreads, Cfg::kSmem, st>>>(
       pl.d_probs, pl.d_maps, sp.d_tiles, sp.d_cta, static_cast<int>(host_chunk_len_I(P) / 32), -14 - 8 * (P - 1),
       status);
   return cudaGetLastError();
@@ -420,9 +429,12 @@ cudaError_t launch_gemm_grouped(const GroupPlan& pl, const SubPlan& sp, int* sta
 template <int P>
 cudaError_t launch_by_cfg(const GroupPlan& pl, const SubPlan& sp, int* status, cudaStream_t st, bool attrs_only) {
   switch (sp.cfg) {
-    case 0: return launch_gemm_grouped<P, 64, 32>(pl, sp, status, st, attrs_only);
-    case 1: return launch_gemm_grouped<P, 32, 32>(pl, sp, status, st, attrs_only);
-    default: return launch_gemm_grouped<P, 32, 64>(pl, sp, status, st, attrs_only);
+    case 0: return launch_gemm_grouped<P, 64, 32, 0>(pl, sp, status, st, attrs_only);
+    case 1: return launch_gemm_grouped<P, 32, 32, 0>(pl, sp, status, st, attrs_only);
+    case 2: return launch_gemm_grouped<P, 32, 64, 0>(pl, sp, status, st, attrs_only);
+    case 3: return launch_gemm_grouped<P, 64, 32, 1>(pl, sp, status, st, attrs_only);
+    case 4: return launch_gemm_grouped<P, 32, 32, 1>(pl, sp, status, st, attrs_only);
+    default: return launch_gemm_grouped<P, 32, 64, 1>(pl, sp, status, st, attrs_only);
   }
 }
 
@@ -775,10 +787,16 @@ emu_status_t emu_dgemm_grouped_loop(emu_handle_t h, int count, const emu_gemm_de
   return EMU_OK;
 }
 
-// Per-bucket tuning by coordinate descent on the whole batch: start from
-// the current choices (configuration 0 where untuned); for each bucket in
-// turn, time the batch with that bucket's products in each other
-// configuration and keep a change that makes the batch at least 1 % faster.
+// Per-bucket tuning in two steps.  (1) Each bucket's products are timed
+// alone in every configuration; the fastest becomes the bucket's candidate
+// if it beats the bucket's current choice (configuration 0 where untuned) by
+// at least 2 %.  A bucket holds a few percent of a mixed batch, so its gain
+// is timed on its own products, where it is not lost in the noise of the
+// whole batch.  (2) The whole batch is timed with every candidate; if that
+// is not faster than with the current choices (the buckets' kernels run on
+// parallel graph branches and interact), the candidates are tried one
+// bucket at a time on the whole batch and each is kept only if the batch
+// gets at least 0.5 % faster.
 emu_status_t emu_tune_grouped(emu_handle_t h, int count, const emu_gemm_desc_t* d, int p, const char* path,
                               int* timed, emu_stream_t stream) {
   emu_status_t s = validate(h, count, d, p);
@@ -788,34 +806,62 @@ emu_status_t emu_tune_grouped(emu_handle_t h, int count, const emu_gemm_desc_t* 
   GroupState* gs = state_of(h);
   std::map<std::string, std::vector<int>> members;
   for (int i = 0; i < count; ++i) members[bucket_of(d[i], p)].push_back(i);
-  std::vector<int> cur = configs_of(gs, count, d, p);
+  const std::vector<int> cur = configs_of(gs, count, d, p);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   constexpr int kReps = 5;
-  float best = 0.f;
   int n_timed = 0;
-  s = time_group(h, count, d, p, cur, st, e0, e1, kReps, &best);
+  float base = 0.f;
+  s = time_group(h, count, d, p, cur, st, e0, e1, kReps, &base);
   ++n_timed;
+  std::map<std::string, int> cand;
   for (auto it = members.begin(); s == EMU_OK && it != members.end(); ++it) {
+    std::vector<emu_gemm_desc_t> sub;
+    for (int i : it->second) sub.push_back(d[i]);
+    const int nsub = static_cast<int>(sub.size());
     const int c0 = cur[it->second[0]];
+    float t0 = 0.f;
+    s = time_group(h, nsub, sub.data(), p, std::vector<int>(nsub, c0), st, e0, e1, kReps, &t0);
+    ++n_timed;
+    float best = t0;
     int keep = c0;
-    for (int c = 0; c < kNumCfg; ++c) {
+    for (int c = 0; s == EMU_OK && c < kNumCfg; ++c) {
       if (c == c0) continue;
-      std::vector<int> trial = cur;
-      for (int i : it->second) trial[i] = c;
       float ms = 0.f;
-      s = time_group(h, count, d, p, trial, st, e0, e1, kReps, &ms);
-      if (s != EMU_OK) break;
+      s = time_group(h, nsub, sub.data(), p, std::vector<int>(nsub, c), st, e0, e1, kReps, &ms);
       ++n_timed;
-      if (ms < 0.99f * best) {
+      if (ms < best) {
         best = ms;
         keep = c;
       }
     }
-    for (int i : it->second) cur[i] = keep;
-    gs->tuned[it->first] = keep;
+    cand[it->first] = best < 0.98f * t0 ? keep : c0;
   }
+  std::vector<int> next = cur;
+  for (int i = 0; i < count; ++i) next[i] = cand[bucket_of(d[i], p)];
+  if (s == EMU_OK && next != cur) {
+    float ms = 0.f;
+    s = time_group(h, count, d, p, next, st, e0, e1, kReps, &ms);
+    ++n_timed;
+    if (s == EMU_OK && !(ms < base)) {
+      next = cur;
+      for (auto it = members.begin(); s == EMU_OK && it != members.end(); ++it) {
+        const int c = cand[it->first];
+        if (c == cur[it->second[0]]) continue;
+        std::vector<int> trial = next;
+        for (int i : it->second) trial[i] = c;
+        s = time_group(h, count, d, p, trial, st, e0, e1, kReps, &ms);
+        ++n_timed;
+        if (s == EMU_OK && ms < 0.995f * base) {
+          base = ms;
+          next = trial;
+        }
+      }
+    }
+  }
+  if (s == EMU_OK)
+    for (auto& kv : members) gs->tuned[kv.first] = next[kv.second[0]];
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (s != EMU_OK) return s;

@@ -82,9 +82,11 @@ def test_autotuner_and_cache(h, tmp_path):
     path = str(tmp_path / "tune.json")
     timed = emu.tune_grouped(d, p, path=path, handle=h)
     cache = json.load(open(path))
-    # one choice per shape bucket; the first timing plus two alternatives per bucket
-    assert len(cache) >= 2 and all(v in (0, 1, 2) for v in cache.values())
-    assert timed == 1 + 2 * len(cache)
+    # one choice per shape bucket (3 tile shapes x 2 slice-pair orders): the
+    # whole batch, six timings of each bucket alone, then at most one whole
+    # batch with all candidates and one per changed bucket
+    assert len(cache) >= 2 and all(v in range(6) for v in cache.values())
+    assert 1 + 6 * len(cache) <= timed <= 2 + 7 * len(cache)
     assert all(k.startswith("p6_s") for k in cache)
     ref = [c.clone() for c in Cs]
     h2 = emu.Handle(0)
@@ -97,15 +99,15 @@ def test_autotuner_and_cache(h, tmp_path):
 
 
 def test_mixed_tile_shapes_bit_exact(orc, tmp_path):
-    """A tuning that gives the shape buckets different tile shapes: the
-    products run in three GEMM launches on parallel graph branches, each
-    bit-exact against the oracle (ragged edges exercise the patches that
-    lie wholly outside a product)."""
+    """A tuning that gives the shape buckets different configurations (tile
+    shape x slice-pair order): the products run in up to six GEMM launches
+    on parallel graph branches, each bit-exact against the oracle (ragged
+    edges exercise the patches that lie wholly outside a product)."""
     p = 5
     shapes, mats = make_problems(60, 11, mn=(20, 700), kr=(60, 1500))
     path = tmp_path / "mixed.json"
     with open(path, "w") as fh:
-        fh.write("{\n" + ",\n".join('  "p5_s%d_k%d": %d' % (sc, kc, (sc + 2 * kc) % 3)
+        fh.write("{\n" + ",\n".join('  "p5_s%d_k%d": %d' % (sc, kc, (sc + 2 * kc) % 6)
                                       for sc in range(5) for kc in range(5)) + "\n}\n")
     hd = emu.Handle(0)
     emu.check(emu.emu_load_tuning(hd.h, str(path).encode()))
