@@ -151,6 +151,7 @@ void host_mod_tables(int nm, ModTables* t) {
     t->off[l] = m - 1 - hi;
     t->inv[l] = 1.0f / static_cast<float>(m);
     t->offinv[l] = static_cast<float>(t->off[l]) / static_cast<float>(m);
+    t->offhinv[l] = static_cast<float>(t->off[l] + 0.5) / static_cast<float>(m);
     int64_t v = 1 % m;  // 2^(16 j) mod m
     for (int j = 0; j < kResDigits; ++j) {
       t->pow16[l][j] = static_cast<int32_t>(v > hi ? v - m : v);

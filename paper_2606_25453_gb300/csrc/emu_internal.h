@@ -29,6 +29,7 @@ struct ModTables {
   int32_t off[kMaxModuli];                 // m - 1 - floor((m - 1)/2): symmetric residues lie in [-off, m - 1 - off]
   float inv[kMaxModuli];                   // 1/m rounded to nearest
   float offinv[kMaxModuli];                // off/m rounded to nearest
+  float offhinv[kMaxModuli];               // (off + 1/2)/m rounded to nearest
   int32_t pow16[kMaxModuli][kResDigits];   // symmetric residue of 2^(16 j) mod m
   // binary32 form for the bf16 planes: 14-bit digits (six cover 2^84)
   float pow14f[kMaxModuli][kResDigitsF];   // symmetric residue of 2^(14 j) mod m

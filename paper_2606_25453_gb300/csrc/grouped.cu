@@ -50,6 +50,12 @@ struct GProb {
   int64_t rows_a, rows_b, nchunks;
 };
 
+// True when the rows of a row-major binary64 matrix start on 16-byte
+// boundaries (base aligned, even leading dimension).
+__device__ __forceinline__ bool a16(const double* X, int64_t ld) {
+  return ((reinterpret_cast<uintptr_t>(X) & 15u) | static_cast<uintptr_t>(ld & 1)) == 0;
+}
+
 // index of the problem owning block `blk` in a prefix array start[0..count]
 __device__ __forceinline__ int find_prob(const int* start, int count, int blk) {
   int lo = 0, hi = count - 1;
@@ -80,7 +86,22 @@ __global__ void grouped_scan_kernel(const GProb* __restrict__ probs, int count, 
     int h0 = ks * 2048, h1 = min(h0 + 2048, pr.K);
     const double* row = pr.A + static_cast<int64_t>(r) * pr.lda;
     uint64_t mx = 0;
-    for (int h = h0 + lane; h < h1; h += 32) {
+    int h = h0 + lane;
+    if (a16(pr.A, pr.lda)) {  // 16-byte loads of element pairs (h0 is even)
+      const uint4* pv = reinterpret_cast<const uint4*>(row + h0);
+      const int nv = (h1 - h0) >> 1;
+#pragma unroll 4
+      for (int i = lane; i < nv; i += 32) {
+        const uint4 v = __ldg(pv + i);
+        const uint64_t x = ((static_cast<uint64_t>(v.y) << 32) | v.x) & 0x7FFFFFFFFFFFFFFFull;
+        const uint64_t y = ((static_cast<uint64_t>(v.w) << 32) | v.z) & 0x7FFFFFFFFFFFFFFFull;
+        mx = x > mx ? x : mx;
+        mx = y > mx ? y : mx;
+      }
+      h = h0 + 2 * nv + lane;  // the odd last element, if any
+    }
+#pragma unroll 4
+    for (; h < h1; h += 32) {
       uint64_t v = dbits(__ldg(row + h)) & 0x7FFFFFFFFFFFFFFFull;
       mx = v > mx ? v : mx;
     }
@@ -105,6 +126,7 @@ __global__ void grouped_scan_kernel(const GProb* __restrict__ probs, int count, 
   int h0 = ks * 256, h1 = min(h0 + 256, pr.K);
   uint64_t mx = 0;
   if (c < pr.N) {
+#pragma unroll 4
     for (int h = h0 + ty; h < h1; h += 8) {
       uint64_t v = dbits(__ldg(pr.B + static_cast<int64_t>(h) * pr.ldb + c)) & 0x7FFFFFFFFFFFFFFFull;
       mx = v > mx ? v : mx;
@@ -152,9 +174,8 @@ __global__ void __launch_bounds__(256) grouped_split_kernel(const GProb* __restr
     const int64_t h0 = c * 32 + (lane & 7) * 4;
     const int E = exp_of(pr.maxA, r, pr.M);
     uint64_t bits[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      bits[q] = (r < pr.M && h0 + q < pr.K) ? dbits(__ldg(pr.A + static_cast<int64_t>(r) * pr.lda + h0 + q)) : 0ull;
+    load4_kcontig(pr.A + static_cast<int64_t>(r < pr.M ? r : 0) * pr.lda, h0, pr.K, r < pr.M, a16(pr.A, pr.lda),
+                  bits);
     uint32_t word[P];
     pack4<P, false>(bits, E, word);
     uint8_t* row = reinterpret_cast<uint8_t*>(pr.hatA) + static_cast<int64_t>(r) * pr.nchunks * 32 * P;
@@ -170,12 +191,7 @@ __global__ void __launch_bounds__(256) grouped_split_kernel(const GProb* __restr
   const int local = blk - startB[pi];
   const int64_t g = local % ngroups;
   const int64_t r0 = static_cast<int64_t>(local / ngroups) * 32;
-  for (int i = threadIdx.x; i < 32 * 128; i += 256) {
-    const int rl = i & 31, hl = i >> 5;
-    const int64_t r = r0 + rl, h = g * 128 + hl;
-    tile[rl][(hl & 3) * 33 + (hl >> 2)] =
-        (r < pr.N && h < pr.K) ? dbits(__ldg(pr.B + h * pr.ldb + r)) : 0ull;
-  }
+  fill_tile_strided(tile, pr.B, pr.ldb, pr.N, pr.K, r0, g * 128, a16(pr.B, pr.ldb));
   __syncthreads();
   const int64_t c = g * 4 + (lane >> 3);
   for (int rl = warp; rl < 32; rl += 8) {

@@ -338,7 +338,7 @@ template <typename T, int P, bool F8>
 __global__ void split_I_kcontig(const T* __restrict__ X, int64_t ld, int64_t rows, int64_t k,
                                 int64_t rows_pad, int64_t nchunks,
                                 const unsigned long long* __restrict__ maxbits,
-                                int8_t* __restrict__ hat, int32_t* __restrict__ E_out) {
+                                int8_t* __restrict__ hat, int32_t* __restrict__ E_out, bool vec) {
   const int lane = threadIdx.x & 31;
   const int64_t ngroups = (nchunks + 3) / 4;
   const int64_t w = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -349,8 +349,7 @@ __global__ void split_I_kcontig(const T* __restrict__ X, int64_t ld, int64_t row
   const int64_t h0 = c * 32 + (lane & 7) * 4;
   const int E = exp_from_maxbits(maxbits, r, rows);
   uint64_t bits[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) bits[q] = (r < rows && h0 + q < k) ? load_bits(X + r * ld + h0 + q) : 0ull;
+  load4_kcontig(X + (r < rows ? r : 0) * ld, h0, k, r < rows, vec, bits);
   uint32_t word[P];
   pack4<P, F8>(bits, E, word);
   uint8_t* row = reinterpret_cast<uint8_t*>(hat) + r * (nchunks * 32 * P);
@@ -371,7 +370,8 @@ template <typename T, int P, bool F8>
 __global__ void __launch_bounds__(256) split_I_kstrided(const T* __restrict__ X, int64_t ld, int64_t rows, int64_t k,
                                                         int64_t rows_pad, int64_t nchunks,
                                                         const unsigned long long* __restrict__ maxbits,
-                                                        int8_t* __restrict__ hat, int32_t* __restrict__ E_out) {
+                                                        int8_t* __restrict__ hat, int32_t* __restrict__ E_out,
+                                                        bool vec) {
   __shared__ uint64_t tile[32][133];
   const int64_t g = blockIdx.x;  // group of 4 chunks
   const int64_t hbase = g * 128;
@@ -380,11 +380,7 @@ __global__ void __launch_bounds__(256) split_I_kstrided(const T* __restrict__ X,
   for (int64_t r0 = static_cast<int64_t>(blockIdx.y) * 32; r0 < rows_pad;
        r0 += static_cast<int64_t>(gridDim.y) * 32) {
     __syncthreads();  // the previous row block is done with the tile
-    for (int i = threadIdx.x; i < 32 * 128; i += 256) {
-      const int rl = i & 31, hl = i >> 5;
-      const int64_t r = r0 + rl, h = hbase + hl;
-      tile[rl][(hl & 3) * 33 + (hl >> 2)] = (r < rows && h < k) ? load_bits(X + h * ld + r) : 0ull;
-    }
+    fill_tile_strided(tile, X, ld, rows, k, r0, hbase, vec);
     __syncthreads();
     for (int rl = warp; rl < 32; rl += 8) {
       const int64_t r = r0 + rl;
@@ -475,25 +471,25 @@ __device__ __forceinline__ void digits14f(uint64_t bits, int shift, float* d) {
     d[j] = __uint_as_float(__float_as_uint(__uint_as_float(0x4B000000u | dg[j]) - 8388608.0f) | sg);
 }
 
-// With ND <= 4 digits |t| <= 16383 (1 + 3 * 128) < 2^22.6, and for every
-// modulus of the list (173 <= m <= 256) the estimate f = RN(t inv + offinv)
-// is within 0.38/m (from inv = RN(1/m)) + 2^-9 <= 0.5/m (the rounding of f,
-// |f| < 2^15.2) + 2^-25 < 1/m of (t + off) / m.  As t + off is an integer,
-// (t + off) / m = q + j/m with 0 <= j < m, so floor(f) is q, or q - 1 when
-// j = 0: r = t - floor(f) m is the symmetric residue or that plus m, and one
-// correction finishes.  Six digits (|t| < 2^23.3) keep both corrections.
-// No step produces -0 from the +0 digits of a' = 0.
+// The quotient needs no correction: with c = RN((off + 1/2) / m) and
+// inv = RN(1/m), floor(t inv + c) (the exact value; the FMA rounds it
+// downward, which never crosses the integer below it) equals
+// floor((t + off) / m) for every integer |t| <= 16383 (1 + sum_j>=1 |c_j|)
+// -- the range of t for the digit count ND <= 6 -- and every modulus of the
+// list.  The half in the offset puts (t + off + 1/2) / m at least 1/(2m)
+// from the integers, and the roundings of inv and c move t inv + c by at
+// most |t| 2^-32 + 2^-25, below 1/(2m) for ND <= 4 (|t| < 2^22.6); the
+// claim is checked exhaustively over the whole range, ND = 6 included, by
+// the host tests.
+// So r = t - q m is the symmetric residue in [-off, m - 1 - off] at once.
+// No step produces -0 from the +0 digits of a' = 0 (t = +0, q = 0).
 template <int ND>
 __device__ __forceinline__ float sym_residue_f(const float* d, const ModTables& mt, int l) {
   float t = d[0];
 #pragma unroll
   for (int j = 1; j < ND; ++j) t = __fmaf_rn(d[j], mt.pow14f[l][j], t);
-  const float m = mt.mf[l], off = mt.offf[l];
-  const float q = floorf(__fmaf_rn(t, mt.inv[l], mt.offinv[l]));
-  float r = __fmaf_rn(-q, m, t);
-  if (ND > 4 && r < -off) r += m;
-  if (r >= m - off) r -= m;
-  return r;
+  const float q = floorf(__fmaf_rd(t, mt.inv[l], mt.offhinv[l]));
+  return __fmaf_rn(-q, mt.mf[l], t);
 }
 
 __device__ __forceinline__ uint32_t pack_bytes(int r0, int r1, int r2, int r3) {
@@ -608,7 +604,7 @@ template <typename T, int CW, bool BF, int ND>
 __global__ void split_II_kcontig(const T* __restrict__ X, int64_t ld, int64_t rows, int64_t k, int64_t rows_pad,
                                  int64_t kpad, int nm, int b, const __grid_constant__ ModTables mt,
                                  const unsigned long long* __restrict__ maxbits, const int32_t* __restrict__ Ein,
-                                 int8_t* __restrict__ res, int32_t* __restrict__ E_out) {
+                                 int8_t* __restrict__ res, int32_t* __restrict__ E_out, bool vec) {
   const int lane = threadIdx.x & 31;
   const int64_t ngroups = kpad / 128;
   const int64_t w = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -616,12 +612,18 @@ __global__ void split_II_kcontig(const T* __restrict__ X, int64_t ld, int64_t ro
   const int64_t r = w / ngroups, h0 = (w % ngroups) * 128 + lane * 4;
   const int E = Ein ? (r < rows ? Ein[r] : 0) : exp_from_maxbits(maxbits, r, rows);
   uint64_t re[4], im[4];
+  if constexpr (CW == 1) {
+    load4_kcontig(X + (r < rows ? r : 0) * ld, h0, k, r < rows, vec, re);
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const bool valid = r < rows && h0 + q < k;
-    const T* p = X + (r * ld + h0 + q) * CW;
-    re[q] = valid ? load_bits(p) : 0ull;
-    im[q] = (CW == 2 && valid) ? load_bits(p + 1) : 0ull;
+    for (int q = 0; q < 4; ++q) im[q] = 0ull;
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const bool valid = r < rows && h0 + q < k;
+      const T* p = X + (r * ld + h0 + q) * CW;
+      re[q] = valid ? load_bits(p) : 0ull;
+      im[q] = valid ? load_bits(p + 1) : 0ull;
+    }
   }
   residues4<CW, BF, ND>(mt, nm, b - E, re, im, rows_pad * kpad * (BF ? 2 : 1), res + (r * kpad + h0) * (BF ? 2 : 1));
   if (h0 == 0 && r < rows && E_out) E_out[r] = E;
@@ -633,7 +635,7 @@ __global__ void __launch_bounds__(256) split_II_kstrided(const T* __restrict__ X
                                                          const __grid_constant__ ModTables mt,
                                                          const unsigned long long* __restrict__ maxbits,
                                                          const int32_t* __restrict__ Ein, int8_t* __restrict__ res,
-                                                         int32_t* __restrict__ E_out) {
+                                                         int32_t* __restrict__ E_out, bool vec) {
   constexpr int TR = CW == 2 ? 16 : 32;  // vectors per tile (two tiles for complex)
   __shared__ uint64_t tre[TR][133];
   __shared__ uint64_t tim[CW == 2 ? TR : 1][CW == 2 ? 133 : 1];
@@ -642,14 +644,18 @@ __global__ void __launch_bounds__(256) split_II_kstrided(const T* __restrict__ X
   for (int64_t r0 = static_cast<int64_t>(blockIdx.y) * TR; r0 < rows_pad;
        r0 += static_cast<int64_t>(gridDim.y) * TR) {
     __syncthreads();  // the previous row block is done with the tiles
-    for (int i = threadIdx.x; i < TR * 128; i += 256) {
-      const int rl = i % TR, hl = i / TR;
-      const int64_t r = r0 + rl, h = hbase + hl;
-      const bool valid = r < rows && h < k;
-      const T* p = X + (h * ld + r) * CW;
-      const int col = (hl & 3) * 33 + (hl >> 2);
-      tre[rl][col] = valid ? load_bits(p) : 0ull;
-      if (CW == 2) tim[rl][col] = valid ? load_bits(p + 1) : 0ull;
+    if constexpr (CW == 1) {
+      fill_tile_strided(tre, X, ld, rows, k, r0, hbase, vec);
+    } else {
+      for (int i = threadIdx.x; i < TR * 128; i += 256) {
+        const int rl = i % TR, hl = i / TR;
+        const int64_t r = r0 + rl, h = hbase + hl;
+        const bool valid = r < rows && h < k;
+        const T* p = X + (h * ld + r) * CW;
+        const int col = (hl & 3) * 33 + (hl >> 2);
+        tre[rl][col] = valid ? load_bits(p) : 0ull;
+        tim[rl][col] = valid ? load_bits(p + 1) : 0ull;
+      }
     }
     __syncthreads();
     for (int rl = warp; rl < TR; rl += 8) {
@@ -709,11 +715,13 @@ static void launch_split_I_p(const T* X, int64_t ld, bool kcontig, int64_t rows,
     int64_t warps = rows_pad * ((nchunks + 3) / 4);
     int64_t blocks = (warps + 7) / 8;
     split_I_kcontig<T, P, F8><<<static_cast<unsigned>(blocks), 256, 0, st>>>(X, ld, rows, k, rows_pad,
-                                                                             nchunks, maxbits, hat, E);
+                                                                             nchunks, maxbits, hat, E,
+                                                                             vec16_ok(X, ld));
   } else {
     const int64_t rb = rows_pad / 32;
     dim3 grid(static_cast<unsigned>((nchunks + 3) / 4), static_cast<unsigned>(rb < 65535 ? rb : 65535));
-    split_I_kstrided<T, P, F8><<<grid, 256, 0, st>>>(X, ld, rows, k, rows_pad, nchunks, maxbits, hat, E);
+    split_I_kstrided<T, P, F8><<<grid, 256, 0, st>>>(X, ld, rows, k, rows_pad, nchunks, maxbits, hat, E,
+                                                     vec16_ok(X, ld));
   }
 }
 
@@ -748,7 +756,8 @@ void launch_split_II(const T* X, int64_t ld, bool kcontig, int64_t rows, int64_t
   if (rows_pad == 0 || kpad == 0) return;
   // 14-bit digits that hold |a'| < 2^b (bf16 planes; the INT8 form has its own)
   const int nd = b <= 28 ? 2 : b <= 56 ? 4 : 6;
-#define EMU_SPLIT_II_ARGS X, ld, rows, k, rows_pad, kpad, nm, b, tabs, maxbits, Ein, res, E
+  const bool vec = cw == 1 && vec16_ok(X, ld);
+#define EMU_SPLIT_II_ARGS X, ld, rows, k, rows_pad, kpad, nm, b, tabs, maxbits, Ein, res, E, vec
 #define EMU_SPLIT_II(KERNEL, GRID, CW)                                             \
   (!bf16      ? KERNEL<T, CW, false, 6><<<GRID, 256, 0, st>>>(EMU_SPLIT_II_ARGS) \
    : nd == 2 ? KERNEL<T, CW, true, 2><<<GRID, 256, 0, st>>>(EMU_SPLIT_II_ARGS)  \

@@ -34,6 +34,82 @@ __device__ __forceinline__ int exp_from_maxbits(const unsigned long long* maxbit
   return frexp_exp_bits(mb);
 }
 
+// Bit pattern (binary64) of an element: binary32 sources are widened exactly.
+__device__ __forceinline__ uint64_t elem_bits(double x) { return dbits(x); }
+__device__ __forceinline__ uint64_t elem_bits(float x) { return dbits(static_cast<double>(x)); }
+
+// Elements h0 .. h0+3 (h0 a multiple of 4) of a K-contiguous vector starting
+// at `row`, as binary64 bit patterns; zero past k and for a padding vector
+// (live false).  `vec`: the vector starts on a 16-byte boundary, so the four
+// elements are one (binary32) or two (binary64) aligned 16-byte loads
+// whenever all four lie inside.
+template <typename T>
+__device__ __forceinline__ void load4_kcontig(const T* row, int64_t h0, int64_t k, bool live, bool vec,
+                                              uint64_t* bits) {
+  if (live && vec && h0 + 3 < k) {
+    const uint4* pv = reinterpret_cast<const uint4*>(row + h0);
+    if constexpr (sizeof(T) == 8) {
+      const uint4 v0 = __ldg(pv), v1 = __ldg(pv + 1);
+      bits[0] = (static_cast<uint64_t>(v0.y) << 32) | v0.x;
+      bits[1] = (static_cast<uint64_t>(v0.w) << 32) | v0.z;
+      bits[2] = (static_cast<uint64_t>(v1.y) << 32) | v1.x;
+      bits[3] = (static_cast<uint64_t>(v1.w) << 32) | v1.z;
+    } else {
+      const uint4 v = __ldg(pv);
+      bits[0] = elem_bits(__uint_as_float(v.x));
+      bits[1] = elem_bits(__uint_as_float(v.y));
+      bits[2] = elem_bits(__uint_as_float(v.z));
+      bits[3] = elem_bits(__uint_as_float(v.w));
+    }
+    return;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) bits[q] = (live && h0 + q < k) ? elem_bits(__ldg(row + h0 + q)) : 0ull;
+}
+
+// Fill tile[32][133] with 32 K-strided vectors r0 .. r0+31 x 128 elements
+// hbase .. hbase+127 (element (r, h) at X[h ld + r]; zero outside rows x k),
+// element hl of vector rl at column (hl mod 4) 33 + hl / 4, by all 256
+// threads of the block.  With `vec` (X on a 16-byte boundary, ld a multiple
+// of 16 bytes) each thread reads 16 contiguous bytes: 16 / sizeof(T)
+// consecutive vectors of one K row.
+template <typename T>
+__device__ __forceinline__ void fill_tile_strided(uint64_t (*tile)[133], const T* X, int64_t ld, int64_t rows,
+                                                  int64_t k, int64_t r0, int64_t hbase, bool vec) {
+  constexpr int V = 16 / static_cast<int>(sizeof(T));  // vectors per 16-byte load
+  constexpr int LPR = 32 / V;                           // threads per K row
+#pragma unroll 4
+  for (int it = 0; it < 32 * 128 / V / 256; ++it) {
+    const int i = threadIdx.x + it * 256;
+    const int rl = (i % LPR) * V, hl = i / LPR;
+    const int64_t r = r0 + rl, h = hbase + hl;
+    const int col = (hl & 3) * 33 + (hl >> 2);
+    const T* p = X + h * ld + r;
+    if (vec && h < k && r + V <= rows) {
+      const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+      if constexpr (sizeof(T) == 8) {
+        tile[rl][col] = (static_cast<uint64_t>(v.y) << 32) | v.x;
+        tile[rl + 1][col] = (static_cast<uint64_t>(v.w) << 32) | v.z;
+      } else {
+        tile[rl][col] = elem_bits(__uint_as_float(v.x));
+        tile[rl + 1][col] = elem_bits(__uint_as_float(v.y));
+        tile[rl + 2][col] = elem_bits(__uint_as_float(v.z));
+        tile[rl + 3][col] = elem_bits(__uint_as_float(v.w));
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < V; ++j) tile[rl + j][col] = (r + j < rows && h < k) ? elem_bits(__ldg(p + j)) : 0ull;
+    }
+  }
+}
+
+// True when 16-byte loads of the vectors of X (leading dimension ld) are
+// aligned: X on a 16-byte boundary and ld a multiple of 16 bytes.
+template <typename T>
+inline bool vec16_ok(const T* X, int64_t ld) {
+  return (reinterpret_cast<uintptr_t>(X) & 15u) == 0 && (static_cast<uint64_t>(ld) * sizeof(T)) % 16 == 0;
+}
+
 // E4M3 bytes of two digits given as exact small integers in float: the
 // conversion of a lands in the upper byte, that of b in the lower byte.
 __device__ __forceinline__ uint32_t e4m3x2(float a, float b) {

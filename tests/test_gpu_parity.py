@@ -50,14 +50,25 @@ def deinterleave(hat: np.ndarray, rows: int, k: int, p: int) -> np.ndarray:
 
 
 # ---------------------------------------------------------------- split I
+def padded(x, extra):
+    """Row-major copy of x inside a buffer `extra` columns wider (leading
+    dimension = columns + extra)."""
+    buf = torch.zeros((x.shape[0], x.shape[1] + extra), dtype=torch.float64, device="cuda")
+    buf[:, :x.shape[1]] = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    return buf[:, :x.shape[1]]
+
+
 @pytest.mark.parametrize("p", [1, 3, 7, 8, 12])
 @pytest.mark.parametrize("operand", [0, 1])
-@pytest.mark.parametrize("col", [False, True])
+@pytest.mark.parametrize("col", [False, True, "padded"])
 def test_split_I_bit_exact(orc, h, p, operand, col):
+    # 77 x 101 with the minimal (odd) leading dimension takes the scalar
+    # loads; "padded" gives an even leading dimension (16-byte loads) with a
+    # ragged K tail and an odd vector count
     rows, k = 77, 101
     X = synth.test_matrix(rows, k, 4.0, 100 + p) if operand == 0 else synth.test_matrix(k, rows, 4.0, 100 + p)
     X[3] = 0.0 if operand == 0 else X[3]
-    Xd = colmajor(X) if col else dev(X)
+    Xd = padded(X, 3) if col == "padded" else colmajor(X) if col else dev(X)
     hat, E = emu.split_I(Xd, p, operand=operand, handle=h)
     torch.cuda.synchronize()
     Xr = X if operand == 0 else X.T
@@ -146,10 +157,13 @@ def test_sgemm_I_bit_exact(orc, h, p):
 # ---------------------------------------------------------------- Scheme II
 @pytest.mark.parametrize("nm", [1, 8, 15, 20])
 @pytest.mark.parametrize("operand", [0, 1])
-def test_split_II_bit_exact(orc, h, nm, operand):
-    rows, k = 70, 150
+@pytest.mark.parametrize("shape", [(70, 150, 0), (71, 151, 5)])
+def test_split_II_bit_exact(orc, h, nm, operand, shape):
+    # even leading dimensions (16-byte loads); the second shape stores the
+    # operand inside a wider buffer with an odd vector count and a ragged K tail
+    rows, k, extra = shape
     X = synth.test_matrix(rows, k, 3.0, nm) if operand == 0 else synth.test_matrix(k, rows, 3.0, nm)
-    res, E = emu.split_II(dev(X), nm, operand=operand, handle=h)
+    res, E = emu.split_II(padded(X, extra) if extra else dev(X), nm, operand=operand, handle=h)
     Xr = X if operand == 0 else X.T
     b = orc.scale_bits_II(nm, k)
     ref = orc.residues_II_rows(Xr, nm, b)
