@@ -663,7 +663,7 @@ def suite_markdown(paths):
                      f"{d['speedup_graph_vs_loop']:.2f}x; {d['tflops_graph']:.2f} emulated TFLOP/s, "
                      f"{d['int8_tops_graph']:.1f} INT8 TOP/s.")
             if d.get("tuned"):
-                o.append("  Tuned configurations (bucket: tile, slice-pair order): " +
+                o.append(f"  Tuned: {d.get('stages')} stage(s); configurations (bucket: tile, slice-pair order): " +
                          ", ".join(f"{k} {v}" for k, v in d["tuned"].items()) + ".")
     return "\n".join(o)
 
@@ -699,7 +699,8 @@ def grouped_points(emu, h, dev, emit, timed):
         ms_loop = timed(lambda: emu.dgemm_grouped(d, p, handle=h, loop=True), reps=2)
         emit({"path": "emu_dgemm_grouped", "count": 512, "p": p, "ms_graph_default_tile": ms_default,
               "ms_graph_tuned": ms_tuned, "configs_timed": ncfg, "ms_loop": ms_loop,
-              "tuned": {k: GROUPED_CFGS[v] for k, v in sorted(tuned.items())},
+              "tuned": {k: GROUPED_CFGS[v] for k, v in sorted(tuned.items()) if not k.endswith("_stages")},
+              "stages": tuned.get("p%d_stages" % p),
               "tflops_graph": flops / ms_tuned / 1e9, "tflops_loop": flops / ms_loop / 1e9,
               "int8_tops_graph": (p * (p + 1) // 2) * flops / ms_tuned / 1e9,
               "speedup_graph_vs_loop": ms_loop / ms_tuned})

@@ -362,13 +362,16 @@ typedef struct {
  * and log2 classes of sqrt(m n) and of k) and runs in that bucket's tuned
  * configuration: output tiles of 64 x 32, 32 x 32 or 32 x 64 and the
  * triangle's slice pairs B-slice-major or A-slice-major (64 x 32,
- * B-slice-major where the handle holds no tuning).  One grouped exponent
- * scan, one grouped split, then one persistent grouped GEMM launch per
- * configuration in use over its
- * (problem, tile) work list, balanced longest-first over the CTAs; the GEMM
- * launches run on parallel branches of one CUDA graph, captured once and
- * replayed while the descriptors and tunings stay identical.  The paper has
- * no batched interface; the tile model follows Table I. */
+ * B-slice-major where the handle holds no tuning).  The products are
+ * ordered by GEMM work per operand element and cut into up to three stages
+ * (at 15 % and 50 % of the batch's GEMM work; one stage below 8 products).
+ * Per stage: one grouped exponent scan, one grouped split, then one
+ * persistent grouped GEMM launch per configuration in use over its
+ * (problem, tile) work list, balanced longest-first over the CTAs.  Each
+ * stage's GEMM launches run on parallel branches of one CUDA graph beside
+ * the next stages' scan and split; the graph is captured once and replayed
+ * while the descriptors and tunings stay identical.  The paper has no
+ * batched interface; the tile model follows Table I. */
 emu_status_t emu_dgemm_grouped(emu_handle_t h, int count, const emu_gemm_desc_t *descs_host, int p,
                                emu_stream_t stream);
 
@@ -380,17 +383,19 @@ emu_status_t emu_dgemm_grouped_loop(emu_handle_t h, int count, const emu_gemm_de
  * as given).  A configuration is a tile shape (64 x 32, 32 x 32 or 32 x 64
  * outputs per CTA) and a slice-pair order of the triangle of Eq. (2)
  * (B-slice-major or A-slice-major): indices 0-2 are the three shapes in
- * B-slice-major order, 3-5 the same shapes A-slice-major.  Each bucket's
- * products are timed alone (CUDA events, 5 graph replays) in every
- * configuration; the fastest is the bucket's candidate if it beats the
- * current choice by 2 %.  The whole batch is then timed with all
- * candidates and kept if it is faster than with the current choices; else
- * the candidates are tried one bucket at a time on the whole batch (kept
- * if the batch gets 0.5 % faster).  The choices are stored per bucket in
- * the handle and, if `path` is non-NULL, written to that cache file
- * ("bucket": configuration index lines).  *timed_host receives the number
- * of (sub-)batch configurations timed.  Synchronises `stream`; the C
- * arrays are written. */
+ * B-slice-major order, 3-5 the same shapes A-slice-major.  Tuned twice,
+ * with the batch cut into three stages and as one stage, keeping the
+ * faster outcome and its stage setting.  Each time: the whole batch is
+ * timed (CUDA events, 5 graph replays) in each single configuration and in
+ * the current choices, the fastest being the starting point; each bucket's
+ * products are timed alone in every configuration, the fastest being the
+ * bucket's candidate; the whole batch with all candidates replaces the
+ * starting point if faster, else the candidates are tried one bucket at a
+ * time on the whole batch (kept if the batch gets 0.5 % faster).  The
+ * choices are stored in the handle and, if `path` is non-NULL, written to
+ * that cache file ("p<p>_s<i>_k<j>": configuration index per bucket,
+ * "p<p>_stages": 1 or 3).  *timed_host receives the number of (sub-)batch
+ * configurations timed.  Synchronises `stream`; the C arrays are written. */
 emu_status_t emu_tune_grouped(emu_handle_t h, int count, const emu_gemm_desc_t *descs_host, int p,
                               const char *path, int *timed_host, emu_stream_t stream);
 

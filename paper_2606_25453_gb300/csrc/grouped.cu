@@ -353,40 +353,59 @@ constexpr int kNumCfg = 6;
 constexpr int kCfgBM[kNumCfg] = {64, 32, 32, 64, 32, 32};
 constexpr int kCfgBN[kNumCfg] = {32, 32, 64, 32, 32, 64};
 
-// One GEMM launch of a plan: the tiles of every product whose bucket uses
-// tile configuration `cfg`.
+// Products are processed in up to three stages, in decreasing order of GEMM
+// work per operand byte: each stage's GEMM launches run while the scan and
+// split of the next stages proceed beside them.  Stage s ends where the
+// cumulative GEMM work reaches kStageEnd[s] of the batch's.
+constexpr int kMaxStages = 3;
+constexpr double kStageEnd[kMaxStages - 1] = {0.15, 0.5};
+
+// One GEMM launch of a plan: the tiles of every product of one stage whose
+// bucket uses configuration `cfg`.
 struct SubPlan {
-  int cfg = 0, grid = 0;
+  int cfg = 0, grid = 0, stage = 0;
   int4* d_tiles = nullptr;
   int* d_cta = nullptr;
 };
 
-struct GroupPlan {
-  std::vector<emu_gemm_desc_t> descs;
-  std::vector<int> pcfg;  // tile configuration of each product
-  int p = 0, count = 0;
-  std::vector<SubPlan> subs;
-  void* dev = nullptr;  // one device buffer: probs, maps, tiles, cta_ptr, starts, workspace
-  size_t dev_bytes = 0;
-  GProb* d_probs = nullptr;
-  CUtensorMap* d_maps = nullptr;
+// Scan and split launches of one stage: products [first, first + count) of
+// the plan's (stage-ordered) problem table, with block prefix arrays of
+// their own.
+struct StagePlan {
+  int first = 0, count = 0;
   int* d_startA_scan = nullptr;
   int* d_startB_scan = nullptr;
   int* d_startA_split = nullptr;
   int* d_startB_split = nullptr;
+  int scan_blocks = 0, split_blocks = 0;
+};
+
+struct GroupPlan {
+  std::vector<emu_gemm_desc_t> descs;
+  std::vector<int> pcfg;  // configuration of each product (caller's order)
+  int p = 0, count = 0;
+  int max_stages = kMaxStages;  // the setting the plan was built for
+  int nstages = 1;
+  StagePlan stages[kMaxStages];
+  std::vector<SubPlan> subs;
+  void* dev = nullptr;  // one device buffer: probs, maps, tiles, cta_ptr, starts, workspace
+  size_t dev_bytes = 0;
+  GProb* d_probs = nullptr;  // stage order
+  CUtensorMap* d_maps = nullptr;
   unsigned long long* d_max = nullptr;
   size_t max_bytes = 0;
-  int scan_blocks = 0, split_blocks = 0;
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
 };
+
+constexpr int kMaxSubs = kMaxStages * kNumCfg;
 
 struct GroupState {
   GroupPlan* plan = nullptr;
   std::map<std::string, int> tuned;  // shape bucket -> configuration index
   cudaStream_t capture = nullptr;
-  cudaStream_t side[kNumCfg] = {};   // branches of the captured graph
-  cudaEvent_t fork = nullptr, join[kNumCfg] = {};
+  cudaStream_t side[kMaxSubs] = {};  // branches of the captured graph
+  cudaEvent_t fork[kMaxStages] = {}, join[kMaxSubs] = {};
 };
 
 void free_plan(GroupPlan* pl) {
@@ -402,8 +421,11 @@ GroupState* state_of(emu_handle_s* h) {
   return static_cast<GroupState*>(h->grouped);
 }
 
-bool same_plan(const GroupPlan* pl, const emu_gemm_desc_t* b, int count, int p, const std::vector<int>& pcfg) {
-  if (!pl || pl->p != p || static_cast<int>(pl->descs.size()) != count || pl->pcfg != pcfg) return false;
+bool same_plan(const GroupPlan* pl, const emu_gemm_desc_t* b, int count, int p, const std::vector<int>& pcfg,
+               int stages) {
+  if (!pl || pl->p != p || pl->max_stages != stages || static_cast<int>(pl->descs.size()) != count ||
+      pl->pcfg != pcfg)
+    return false;
   return std::memcmp(pl->descs.data(), b, sizeof(emu_gemm_desc_t) * count) == 0;
 }
 
@@ -417,6 +439,20 @@ std::string bucket_of(const emu_gemm_desc_t& d, int p) {
   char buf[48];
   std::snprintf(buf, sizeof(buf), "p%d_s%d_k%d", p, sc, kc);
   return buf;
+}
+
+// Tuning-map key of the stage setting for slice count p.
+std::string stages_key(int p) {
+  char buf[32];
+  std::snprintf(buf, sizeof(buf), "p%d_stages", p);
+  return buf;
+}
+
+// Maximum stage count for slice count p from the tuned map (kMaxStages
+// where untuned).
+int stages_of(const GroupState* gs, int p) {
+  auto it = gs->tuned.find(stages_key(p));
+  return it != gs->tuned.end() ? it->second : kMaxStages;
 }
 
 // Tile configuration of each product from the tuned map (0 where untuned).
@@ -476,50 +512,55 @@ cudaError_t prepare_attrs(const GroupPlan& pl) {
 
 int occupancy_of(int cfg) { return (kCfgBM[cfg] / 16) * (kCfgBN[cfg] / 16) >= 8 ? 1 : 2; }
 
-// memset, scan, split on `st`; then one GEMM launch per tile configuration,
-// the first on `st`, the others on side branches that fork after the split
-// and join before the end.
+// memset on `st`; then per stage its scan and split on `st` and its GEMM
+// launches (one per configuration) on side branches that fork after that
+// split, so that stage 0's GEMMs overlap stage 1's scan and split; every
+// branch joins `st` before the end.
 cudaError_t launch_group(const GroupPlan& pl, GroupState* gs, int* status, cudaStream_t st) {
   cudaMemsetAsync(pl.d_max, 0, pl.max_bytes, st);
-  if (pl.scan_blocks)
-    grouped_scan_kernel<<<pl.scan_blocks, 256, 0, st>>>(pl.d_probs, pl.count, pl.d_startA_scan, pl.d_startB_scan,
-                                                         status);
-  if (pl.split_blocks) {
-    switch (pl.p) {
-#define EMU_GS(PP) \
-  case PP: grouped_split_kernel<PP><<<pl.split_blocks, 256, 0, st>>>(pl.d_probs, pl.count, pl.d_startA_split, pl.d_startB_split); break;
-      EMU_GS(1) EMU_GS(2) EMU_GS(3) EMU_GS(4) EMU_GS(5) EMU_GS(6)
-      EMU_GS(7) EMU_GS(8) EMU_GS(9) EMU_GS(10) EMU_GS(11) EMU_GS(12)
+  for (int s = 0; s < pl.nstages; ++s) {
+    const StagePlan& sg = pl.stages[s];
+    const GProb* probs = pl.d_probs + sg.first;
+    if (sg.scan_blocks)
+      grouped_scan_kernel<<<sg.scan_blocks, 256, 0, st>>>(probs, sg.count, sg.d_startA_scan, sg.d_startB_scan,
+                                                           status);
+    if (sg.split_blocks) {
+      switch (pl.p) {
+#define EMU_GS(PP)                                                                                  \
+  case PP:                                                                                          \
+    grouped_split_kernel<PP><<<sg.split_blocks, 256, 0, st>>>(probs, sg.count, sg.d_startA_split, \
+                                                               sg.d_startB_split);                 \
+    break;
+        EMU_GS(1) EMU_GS(2) EMU_GS(3) EMU_GS(4) EMU_GS(5) EMU_GS(6)
+        EMU_GS(7) EMU_GS(8) EMU_GS(9) EMU_GS(10) EMU_GS(11) EMU_GS(12)
 #undef EMU_GS
-      default: return cudaErrorInvalidValue;
+        default: return cudaErrorInvalidValue;
+      }
+    }
+    if (cudaEventRecord(gs->fork[s], st) != cudaSuccess) return cudaErrorUnknown;
+    for (size_t i = 0; i < pl.subs.size(); ++i) {
+      if (pl.subs[i].stage != s) continue;
+      if (cudaStreamWaitEvent(gs->side[i], gs->fork[s], 0) != cudaSuccess) return cudaErrorUnknown;
+      cudaError_t e = launch_sub(pl, pl.subs[i], status, gs->side[i], false);
+      if (e != cudaSuccess) return e;
+      if (cudaEventRecord(gs->join[i], gs->side[i]) != cudaSuccess) return cudaErrorUnknown;
     }
   }
-  const size_t nsub = pl.subs.size();
-  if (nsub > 1 && cudaEventRecord(gs->fork, st) != cudaSuccess) return cudaErrorUnknown;
-  for (size_t i = 1; i < nsub; ++i) {
-    if (cudaStreamWaitEvent(gs->side[i], gs->fork, 0) != cudaSuccess) return cudaErrorUnknown;
-    cudaError_t e = launch_sub(pl, pl.subs[i], status, gs->side[i], false);
-    if (e != cudaSuccess) return e;
-    if (cudaEventRecord(gs->join[i], gs->side[i]) != cudaSuccess) return cudaErrorUnknown;
-  }
-  if (nsub > 0) {
-    cudaError_t e = launch_sub(pl, pl.subs[0], status, st, false);
-    if (e != cudaSuccess) return e;
-  }
-  for (size_t i = 1; i < nsub; ++i)
+  for (size_t i = 0; i < pl.subs.size(); ++i)
     if (cudaStreamWaitEvent(st, gs->join[i], 0) != cudaSuccess) return cudaErrorUnknown;
   return cudaGetLastError();
 }
 
 static size_t al256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
-// Tiles of the products in configuration `cfg`, longest-processing-time
-// assigned to `grid` CTA slots (cost = K chunks): flat list + CTA offsets.
-void lpt_tiles(int count, const emu_gemm_desc_t* d, const std::vector<int>& pcfg, int cfg, int grid_max,
+// Tiles of the products lo .. hi-1 in configuration `cfg`,
+// longest-processing-time assigned to `grid` CTA slots (cost = K chunks):
+// flat list + CTA offsets.
+void lpt_tiles(int lo, int hi, const emu_gemm_desc_t* d, const std::vector<int>& pcfg, int cfg, int grid_max,
                std::vector<int4>* flat, std::vector<int>* cta, int* grid_out) {
   const int BM = kCfgBM[cfg], BN = kCfgBN[cfg];
   std::vector<int4> tiles;
-  for (int i = 0; i < count; ++i) {
+  for (int i = lo; i < hi; ++i) {
     if (pcfg[i] != cfg) continue;
     int tm = static_cast<int>((d[i].m + BM - 1) / BM), tn = static_cast<int>((d[i].n + BN - 1) / BN);
     for (int a = 0; a < tm; ++a)
@@ -549,50 +590,112 @@ void lpt_tiles(int count, const emu_gemm_desc_t* d, const std::vector<int>& pcfg
   *grid_out = grid;
 }
 
+// Stage order of a batch: products sorted by GEMM work per operand element
+// (M N K / ((M + N) K)), cut where the cumulative work reaches the
+// kStageEnd fractions (one stage for fewer than 8 products or when
+// max_stages is 1; no empty stage).  Returns the permutation and the stage
+// sizes (*nstages of them).
+std::vector<int> stage_order(int count, const emu_gemm_desc_t* d, int max_stages, int* sizes, int* nstages) {
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  *nstages = 1;
+  sizes[0] = count;
+  if (count < 8 || max_stages < 2) return order;
+  auto dens = [&](int i) { return static_cast<double>(d[i].m) * d[i].n / static_cast<double>(d[i].m + d[i].n); };
+  auto work = [&](int i) { return static_cast<double>(d[i].m) * d[i].n * d[i].k; };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return dens(a) > dens(b); });
+  double total = 0.0;
+  for (int i = 0; i < count; ++i) total += work(i);
+  double acc = 0.0;
+  int n = 0, ns = 0, start = 0;
+  for (int s = 0; s < kMaxStages - 1; ++s) {
+    while (n < count - 1 && acc < kStageEnd[s] * total) acc += work(order[n++]);
+    if (n > start) {
+      sizes[ns++] = n - start;
+      start = n;
+    }
+  }
+  sizes[ns++] = count - start;
+  *nstages = ns;
+  return order;
+}
+
 // Build a plan: device tables, workspace, tensor maps, LPT tile lists.
-emu_status_t build_plan(emu_handle_s* h, int count, const emu_gemm_desc_t* d, int p, const std::vector<int>& pcfg,
-                        GroupPlan** out) {
+emu_status_t build_plan(emu_handle_s* h, int count, const emu_gemm_desc_t* d_in, int p,
+                        const std::vector<int>& pcfg_in, int stages, GroupPlan** out) {
   auto* pl = new GroupPlan();
-  pl->descs.assign(d, d + count);
-  pl->pcfg = pcfg;
+  pl->descs.assign(d_in, d_in + count);
+  pl->pcfg = pcfg_in;
   pl->p = p;
   pl->count = count;
+  pl->max_stages = stages;
+  // the problem table in stage order
+  int sizes[kMaxStages] = {};
+  const std::vector<int> order = stage_order(count, d_in, stages, sizes, &pl->nstages);
+  std::vector<emu_gemm_desc_t> dv(count);
+  std::vector<int> pcfg(count);
+  for (int i = 0; i < count; ++i) {
+    dv[i] = d_in[order[i]];
+    pcfg[i] = pcfg_in[order[i]];
+  }
+  const emu_gemm_desc_t* d = dv.data();
+  for (int s = 0, first = 0; s < pl->nstages; first += sizes[s++]) {
+    pl->stages[s].first = first;
+    pl->stages[s].count = sizes[s];
+  }
 
   std::vector<GProb> probs(count);
   size_t off = 0;
   size_t o_probs = off; off += al256(sizeof(GProb) * count);
   size_t o_maps = off; off += al256(sizeof(CUtensorMap) * 2 * count);
-  // one tile list per configuration in use
+  // one tile list per stage and configuration in use
   std::vector<std::vector<int4>> flats;
   std::vector<std::vector<int>> ctas;
   std::vector<size_t> o_tiles, o_cta;
-  for (int cfg = 0; cfg < kNumCfg; ++cfg) {
-    if (std::find(pcfg.begin(), pcfg.end(), cfg) == pcfg.end()) continue;
-    SubPlan sp;
-    sp.cfg = cfg;
-    std::vector<int4> flat;
-    std::vector<int> cta;
-    lpt_tiles(count, d, pcfg, cfg, h->num_sms * occupancy_of(cfg), &flat, &cta, &sp.grid);
-    o_tiles.push_back(off);
-    off += al256(sizeof(int4) * std::max<size_t>(flat.size(), 1));
-    o_cta.push_back(off);
-    off += al256(sizeof(int) * cta.size());
-    flats.push_back(std::move(flat));
-    ctas.push_back(std::move(cta));
-    pl->subs.push_back(sp);
+  for (int s = 0; s < pl->nstages; ++s) {
+    const int lo = pl->stages[s].first, hi = lo + pl->stages[s].count;
+    for (int cfg = 0; cfg < kNumCfg; ++cfg) {
+      if (std::find(pcfg.begin() + lo, pcfg.begin() + hi, cfg) == pcfg.begin() + hi) continue;
+      SubPlan sp;
+      sp.cfg = cfg;
+      sp.stage = s;
+      std::vector<int4> flat;
+      std::vector<int> cta;
+      lpt_tiles(lo, hi, d, pcfg, cfg, h->num_sms * occupancy_of(cfg), &flat, &cta, &sp.grid);
+      o_tiles.push_back(off);
+      off += al256(sizeof(int4) * std::max<size_t>(flat.size(), 1));
+      o_cta.push_back(off);
+      off += al256(sizeof(int) * cta.size());
+      flats.push_back(std::move(flat));
+      ctas.push_back(std::move(cta));
+      pl->subs.push_back(sp);
+    }
   }
-  // block prefix arrays
-  std::vector<int> sA(count + 1), sB(count + 1), pA(count + 1), pB(count + 1);
-  sA[0] = sB[0] = pA[0] = pB[0] = 0;
-  for (int i = 0; i < count; ++i) {
-    int64_t M = d[i].m, N = d[i].n, K = d[i].k;
-    int64_t rows_a = split_rows(M), rows_b = split_rows(N), nch = (K + 31) / 32;
-    sA[i + 1] = sA[i] + static_cast<int>(((M + 7) / 8) * ((K + 2047) / 2048));
-    sB[i + 1] = sB[i] + static_cast<int>(((N + 31) / 32) * ((K + 255) / 256));
-    pA[i + 1] = pA[i] + static_cast<int>((rows_a * ((nch + 3) / 4) + 7) / 8);
-    pB[i + 1] = pB[i] + static_cast<int>((rows_b / 32) * ((nch + 3) / 4));
+  // block prefix arrays, per stage: [sA | sB | pA | pB], each count_s + 1 long
+  std::vector<int> st4;
+  std::vector<size_t> st4_off(pl->nstages);
+  for (int s = 0; s < pl->nstages; ++s) {
+    StagePlan& sg = pl->stages[s];
+    const int c = sg.count;
+    std::vector<int> sA(c + 1, 0), sB(c + 1, 0), pA(c + 1, 0), pB(c + 1, 0);
+    for (int j = 0; j < c; ++j) {
+      const emu_gemm_desc_t& dj = d[sg.first + j];
+      int64_t M = dj.m, N = dj.n, K = dj.k;
+      int64_t rows_a = split_rows(M), rows_b = split_rows(N), nch = (K + 31) / 32;
+      sA[j + 1] = sA[j] + static_cast<int>(((M + 7) / 8) * ((K + 2047) / 2048));
+      sB[j + 1] = sB[j] + static_cast<int>(((N + 31) / 32) * ((K + 255) / 256));
+      pA[j + 1] = pA[j] + static_cast<int>((rows_a * ((nch + 3) / 4) + 7) / 8);
+      pB[j + 1] = pB[j] + static_cast<int>((rows_b / 32) * ((nch + 3) / 4));
+    }
+    sg.scan_blocks = sA[c] + sB[c];
+    sg.split_blocks = pA[c] + pB[c];
+    st4_off[s] = st4.size();
+    st4.insert(st4.end(), sA.begin(), sA.end());
+    st4.insert(st4.end(), sB.begin(), sB.end());
+    st4.insert(st4.end(), pA.begin(), pA.end());
+    st4.insert(st4.end(), pB.begin(), pB.end());
   }
-  size_t o_starts = off; off += al256(sizeof(int) * 4 * (count + 1));
+  size_t o_starts = off; off += al256(sizeof(int) * st4.size());
   // per-problem workspace
   size_t o_max = off;
   size_t max_bytes = 0;
@@ -618,14 +721,16 @@ emu_status_t build_plan(emu_handle_s* h, int count, const emu_gemm_desc_t* d, in
     pl->subs[i].d_cta = reinterpret_cast<int*>(base + o_cta[i]);
   }
   int* starts = reinterpret_cast<int*>(base + o_starts);
-  pl->d_startA_scan = starts;
-  pl->d_startB_scan = starts + (count + 1);
-  pl->d_startA_split = starts + 2 * (count + 1);
-  pl->d_startB_split = starts + 3 * (count + 1);
+  for (int s = 0; s < pl->nstages; ++s) {
+    StagePlan& sg = pl->stages[s];
+    int* st = starts + st4_off[s];
+    sg.d_startA_scan = st;
+    sg.d_startB_scan = st + (sg.count + 1);
+    sg.d_startA_split = st + 2 * (sg.count + 1);
+    sg.d_startB_split = st + 3 * (sg.count + 1);
+  }
   pl->d_max = reinterpret_cast<unsigned long long*>(base + o_max);
   pl->max_bytes = max_bytes;
-  pl->scan_blocks = sA[count] + sB[count];
-  pl->split_blocks = pA[count] + pB[count];
   std::vector<CUtensorMap> maps(2 * count);
   size_t moff = 0;
   for (int i = 0; i < count; ++i) {
@@ -663,11 +768,6 @@ emu_status_t build_plan(emu_handle_s* h, int count, const emu_gemm_desc_t* d, in
       return EMU_ERR_CUDA;
     }
   }
-  std::vector<int> st4;
-  st4.insert(st4.end(), sA.begin(), sA.end());
-  st4.insert(st4.end(), sB.begin(), sB.end());
-  st4.insert(st4.end(), pA.begin(), pA.end());
-  st4.insert(st4.end(), pB.begin(), pB.end());
   bool ok = cudaMemcpy(pl->d_probs, probs.data(), sizeof(GProb) * count, cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(pl->d_maps, maps.data(), sizeof(CUtensorMap) * 2 * count, cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(starts, st4.data(), sizeof(int) * st4.size(), cudaMemcpyHostToDevice) == cudaSuccess;
@@ -689,9 +789,10 @@ emu_status_t build_plan(emu_handle_s* h, int count, const emu_gemm_desc_t* d, in
 emu_status_t capture_plan(emu_handle_s* h, GroupState* gs, GroupPlan* pl) {
   if (!gs->capture && cudaStreamCreateWithFlags(&gs->capture, cudaStreamNonBlocking) != cudaSuccess)
     return EMU_ERR_CUDA;
-  if (!gs->fork) {
-    if (cudaEventCreateWithFlags(&gs->fork, cudaEventDisableTiming) != cudaSuccess) return EMU_ERR_CUDA;
-    for (int i = 1; i < kNumCfg; ++i)
+  if (!gs->fork[0]) {
+    for (int s = 0; s < kMaxStages; ++s)
+      if (cudaEventCreateWithFlags(&gs->fork[s], cudaEventDisableTiming) != cudaSuccess) return EMU_ERR_CUDA;
+    for (int i = 0; i < kMaxSubs; ++i)
       if (cudaStreamCreateWithFlags(&gs->side[i], cudaStreamNonBlocking) != cudaSuccess ||
           cudaEventCreateWithFlags(&gs->join[i], cudaEventDisableTiming) != cudaSuccess)
         return EMU_ERR_CUDA;
@@ -723,16 +824,16 @@ emu_status_t validate(emu_handle_s* h, int count, const emu_gemm_desc_t* d, int 
 // Run (building and capturing if the product list or the configurations
 // changed) with a tile configuration per product.
 emu_status_t run_group(emu_handle_s* h, int count, const emu_gemm_desc_t* d, int p, const std::vector<int>& pcfg,
-                       cudaStream_t st) {
+                       int stages, cudaStream_t st) {
   GroupState* gs = state_of(h);
   GroupPlan* pl = gs->plan;
-  if (!same_plan(pl, d, count, p, pcfg)) {
+  if (!same_plan(pl, d, count, p, pcfg, stages)) {
     if (pl) {
       cudaDeviceSynchronize();
       free_plan(pl);
       gs->plan = nullptr;
     }
-    emu_status_t s = build_plan(h, count, d, p, pcfg, &pl);
+    emu_status_t s = build_plan(h, count, d, p, pcfg, stages, &pl);
     if (s != EMU_OK) return s;
     s = capture_plan(h, gs, pl);
     if (s != EMU_OK) {
@@ -743,23 +844,107 @@ emu_status_t run_group(emu_handle_s* h, int count, const emu_gemm_desc_t* d, int
   }
   trace_begin(h, PH_GEMM, st);
   cudaError_t e = cudaGraphLaunch(pl->exec, st);
-  trace_end(h, PH_GEMM, st, 3 + static_cast<int>(pl->subs.size()));
+  trace_end(h, PH_GEMM, st, 1 + 2 * pl->nstages + static_cast<int>(pl->subs.size()));
   return e == cudaSuccess ? EMU_OK : EMU_ERR_CUDA;
 }
 
 // Mean time of `reps` graph replays after a warm-up (ms).
 emu_status_t time_group(emu_handle_s* h, int count, const emu_gemm_desc_t* d, int p, const std::vector<int>& pcfg,
-                        cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, int reps, float* ms) {
-  emu_status_t s = run_group(h, count, d, p, pcfg, st);  // builds, captures and warms up
+                        int stages, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, int reps, float* ms) {
+  emu_status_t s = run_group(h, count, d, p, pcfg, stages, st);  // builds, captures and warms up
   if (s != EMU_OK) return s;
-  run_group(h, count, d, p, pcfg, st);
+  run_group(h, count, d, p, pcfg, stages, st);
   cudaEventRecord(e0, st);
-  for (int r = 0; r < reps; ++r) run_group(h, count, d, p, pcfg, st);
+  for (int r = 0; r < reps; ++r) run_group(h, count, d, p, pcfg, stages, st);
   cudaEventRecord(e1, st);
   if (cudaEventSynchronize(e1) != cudaSuccess) return EMU_ERR_CUDA;
   cudaEventElapsedTime(ms, e0, e1);
   *ms /= static_cast<float>(reps);
   return EMU_OK;
+}
+
+// Tuning, all timed with CUDA events over graph replays, done once with
+// the batch cut into stages (kMaxStages) and once as a single stage; the
+// faster outcome is kept, with its stage setting.  For each setting:
+// (1) The whole batch in each single configuration (and in the current
+// choices): the fastest is the starting point.  (2) Each bucket's products
+// alone in every configuration: the fastest is the bucket's candidate (a
+// bucket holds a few percent of a mixed batch, so its gain is timed on its
+// own products, where it is not lost in the noise of the whole batch).
+// (3) The whole batch with every candidate; if that beats the starting
+// point it is kept, else each bucket whose choice differs from the
+// candidate's is tried on the whole batch and switched if the batch gets at
+// least 0.5 % faster.  The buckets' kernels share the GPU (parallel graph
+// branches, stages), which is why every decision is confirmed on the whole
+// batch.
+emu_status_t tune_setting(emu_handle_s* h, int count, const emu_gemm_desc_t* d, int p, int stages,
+                          const std::map<std::string, std::vector<int>>& members, cudaStream_t st, cudaEvent_t e0,
+                          cudaEvent_t e1, std::vector<int>* out, float* out_ms, int* n_timed) {
+  constexpr int kReps = 5;
+  GroupState* gs = state_of(h);
+  // (1) starting point
+  std::vector<int> next = configs_of(gs, count, d, p);
+  float base = 0.f;
+  emu_status_t s = time_group(h, count, d, p, next, stages, st, e0, e1, kReps, &base);
+  ++*n_timed;
+  for (int c = 0; s == EMU_OK && c < kNumCfg; ++c) {
+    const std::vector<int> uni(count, c);
+    if (uni == next) continue;
+    float ms = 0.f;
+    s = time_group(h, count, d, p, uni, stages, st, e0, e1, kReps, &ms);
+    ++*n_timed;
+    if (s == EMU_OK && ms < base) {
+      base = ms;
+      next = uni;
+    }
+  }
+  // (2) per-bucket candidates
+  std::map<std::string, int> cand;
+  for (auto it = members.begin(); s == EMU_OK && it != members.end(); ++it) {
+    std::vector<emu_gemm_desc_t> sub;
+    for (int i : it->second) sub.push_back(d[i]);
+    const int nsub = static_cast<int>(sub.size());
+    float best = 0.f;
+    int keep = 0;
+    for (int c = 0; s == EMU_OK && c < kNumCfg; ++c) {
+      float ms = 0.f;
+      s = time_group(h, nsub, sub.data(), p, std::vector<int>(nsub, c), stages, st, e0, e1, kReps, &ms);
+      ++*n_timed;
+      if (c == 0 || ms < best) {
+        best = ms;
+        keep = c;
+      }
+    }
+    cand[it->first] = keep;
+  }
+  // (3) candidates on the whole batch
+  std::vector<int> mix(count);
+  for (int i = 0; i < count; ++i) mix[i] = cand[bucket_of(d[i], p)];
+  if (s == EMU_OK && mix != next) {
+    float ms = 0.f;
+    s = time_group(h, count, d, p, mix, stages, st, e0, e1, kReps, &ms);
+    ++*n_timed;
+    if (s == EMU_OK && ms < base) {
+      base = ms;
+      next = mix;
+    } else {
+      for (auto it = members.begin(); s == EMU_OK && it != members.end(); ++it) {
+        const int c = cand[it->first];
+        if (c == next[it->second[0]]) continue;
+        std::vector<int> trial = next;
+        for (int i : it->second) trial[i] = c;
+        s = time_group(h, count, d, p, trial, stages, st, e0, e1, kReps, &ms);
+        ++*n_timed;
+        if (s == EMU_OK && ms < 0.995f * base) {
+          base = ms;
+          next = trial;
+        }
+      }
+    }
+  }
+  *out = next;
+  *out_ms = base;
+  return s;
 }
 
 }  // namespace
@@ -769,11 +954,12 @@ void grouped_release(emu_handle_s* h) {
   auto* gs = static_cast<GroupState*>(h->grouped);
   free_plan(gs->plan);
   if (gs->capture) cudaStreamDestroy(gs->capture);
-  for (int i = 1; i < kNumCfg; ++i) {
+  for (int i = 0; i < kMaxSubs; ++i) {
     if (gs->side[i]) cudaStreamDestroy(gs->side[i]);
     if (gs->join[i]) cudaEventDestroy(gs->join[i]);
   }
-  if (gs->fork) cudaEventDestroy(gs->fork);
+  for (int s = 0; s < kMaxStages; ++s)
+    if (gs->fork[s]) cudaEventDestroy(gs->fork[s]);
   delete gs;
   h->grouped = nullptr;
 }
@@ -789,7 +975,8 @@ emu_status_t emu_dgemm_grouped(emu_handle_t h, int count, const emu_gemm_desc_t*
   if (s != EMU_OK || count == 0) return s;
   cudaSetDevice(h->device);
   GroupState* gs = state_of(h);
-  return run_group(h, count, descs, p, configs_of(gs, count, descs, p), static_cast<cudaStream_t>(stream));
+  return run_group(h, count, descs, p, configs_of(gs, count, descs, p), stages_of(gs, p),
+                   static_cast<cudaStream_t>(stream));
 }
 
 emu_status_t emu_dgemm_grouped_loop(emu_handle_t h, int count, const emu_gemm_desc_t* d, int p, emu_stream_t stream) {
@@ -803,16 +990,6 @@ emu_status_t emu_dgemm_grouped_loop(emu_handle_t h, int count, const emu_gemm_de
   return EMU_OK;
 }
 
-// Per-bucket tuning in two steps.  (1) Each bucket's products are timed
-// alone in every configuration; the fastest becomes the bucket's candidate
-// if it beats the bucket's current choice (configuration 0 where untuned) by
-// at least 2 %.  A bucket holds a few percent of a mixed batch, so its gain
-// is timed on its own products, where it is not lost in the noise of the
-// whole batch.  (2) The whole batch is timed with every candidate; if that
-// is not faster than with the current choices (the buckets' kernels run on
-// parallel graph branches and interact), the candidates are tried one
-// bucket at a time on the whole batch and each is kept only if the batch
-// gets at least 0.5 % faster.
 emu_status_t emu_tune_grouped(emu_handle_t h, int count, const emu_gemm_desc_t* d, int p, const char* path,
                               int* timed, emu_stream_t stream) {
   emu_status_t s = validate(h, count, d, p);
@@ -822,60 +999,20 @@ emu_status_t emu_tune_grouped(emu_handle_t h, int count, const emu_gemm_desc_t* 
   GroupState* gs = state_of(h);
   std::map<std::string, std::vector<int>> members;
   for (int i = 0; i < count; ++i) members[bucket_of(d[i], p)].push_back(i);
-  const std::vector<int> cur = configs_of(gs, count, d, p);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  constexpr int kReps = 5;
   int n_timed = 0;
-  float base = 0.f;
-  s = time_group(h, count, d, p, cur, st, e0, e1, kReps, &base);
-  ++n_timed;
-  std::map<std::string, int> cand;
-  for (auto it = members.begin(); s == EMU_OK && it != members.end(); ++it) {
-    std::vector<emu_gemm_desc_t> sub;
-    for (int i : it->second) sub.push_back(d[i]);
-    const int nsub = static_cast<int>(sub.size());
-    const int c0 = cur[it->second[0]];
-    float t0 = 0.f;
-    s = time_group(h, nsub, sub.data(), p, std::vector<int>(nsub, c0), st, e0, e1, kReps, &t0);
-    ++n_timed;
-    float best = t0;
-    int keep = c0;
-    for (int c = 0; s == EMU_OK && c < kNumCfg; ++c) {
-      if (c == c0) continue;
-      float ms = 0.f;
-      s = time_group(h, nsub, sub.data(), p, std::vector<int>(nsub, c), st, e0, e1, kReps, &ms);
-      ++n_timed;
-      if (ms < best) {
-        best = ms;
-        keep = c;
-      }
-    }
-    cand[it->first] = best < 0.98f * t0 ? keep : c0;
+  std::vector<int> next, single;
+  float ms_staged = 0.f, ms_single = 0.f;
+  s = tune_setting(h, count, d, p, kMaxStages, members, st, e0, e1, &next, &ms_staged, &n_timed);
+  if (s == EMU_OK) s = tune_setting(h, count, d, p, 1, members, st, e0, e1, &single, &ms_single, &n_timed);
+  int stages = kMaxStages;
+  if (s == EMU_OK && ms_single < ms_staged) {
+    next = single;
+    stages = 1;
   }
-  std::vector<int> next = cur;
-  for (int i = 0; i < count; ++i) next[i] = cand[bucket_of(d[i], p)];
-  if (s == EMU_OK && next != cur) {
-    float ms = 0.f;
-    s = time_group(h, count, d, p, next, st, e0, e1, kReps, &ms);
-    ++n_timed;
-    if (s == EMU_OK && !(ms < base)) {
-      next = cur;
-      for (auto it = members.begin(); s == EMU_OK && it != members.end(); ++it) {
-        const int c = cand[it->first];
-        if (c == cur[it->second[0]]) continue;
-        std::vector<int> trial = next;
-        for (int i : it->second) trial[i] = c;
-        s = time_group(h, count, d, p, trial, st, e0, e1, kReps, &ms);
-        ++n_timed;
-        if (s == EMU_OK && ms < 0.995f * base) {
-          base = ms;
-          next = trial;
-        }
-      }
-    }
-  }
+  if (s == EMU_OK) gs->tuned[stages_key(p)] = stages;
   if (s == EMU_OK)
     for (auto& kv : members) gs->tuned[kv.first] = next[kv.second[0]];
   cudaEventDestroy(e0);
@@ -904,8 +1041,10 @@ emu_status_t emu_load_tuning(emu_handle_t h, const char* path) {
     size_t q1 = line.find('"'), q2 = line.find('"', q1 + 1), c = line.find(':', q2 + 1);
     if (q1 == std::string::npos || q2 == std::string::npos || c == std::string::npos) continue;
     int v = std::atoi(line.c_str() + c + 1);
-    if (v < 0 || v >= kNumCfg) return EMU_ERR_INVALID_ARG;
-    gs->tuned[line.substr(q1 + 1, q2 - q1 - 1)] = v;
+    const std::string key = line.substr(q1 + 1, q2 - q1 - 1);
+    const bool stages = key.size() > 7 && key.compare(key.size() - 7, 7, "_stages") == 0;
+    if (stages ? (v < 1 || v > kMaxStages) : (v < 0 || v >= kNumCfg)) return EMU_ERR_INVALID_ARG;
+    gs->tuned[key] = v;
   }
   return EMU_OK;
 }

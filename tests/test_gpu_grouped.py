@@ -82,12 +82,16 @@ def test_autotuner_and_cache(h, tmp_path):
     path = str(tmp_path / "tune.json")
     timed = emu.tune_grouped(d, p, path=path, handle=h)
     cache = json.load(open(path))
-    # one choice per shape bucket (3 tile shapes x 2 slice-pair orders): the
-    # whole batch, six timings of each bucket alone, then at most one whole
-    # batch with all candidates and one per changed bucket
-    assert len(cache) >= 2 and all(v in range(6) for v in cache.values())
-    assert 1 + 6 * len(cache) <= timed <= 2 + 7 * len(cache)
+    # one choice per shape bucket (3 tile shapes x 2 slice-pair orders) and
+    # the stage setting; for each of the two settings (three stages, one):
+    # the whole batch in the current choices and the five other single
+    # configurations, six timings of each bucket alone, then at most one
+    # whole batch with all candidates and one per changed bucket
+    assert cache.pop("p6_stages") in (1, 3)
+    nb = len(cache)
+    assert nb >= 2 and all(v in range(6) for v in cache.values())
     assert all(k.startswith("p6_s") for k in cache)
+    assert 2 * (6 + 6 * nb) <= timed <= 2 * (7 + 7 * nb)
     ref = [c.clone() for c in Cs]
     h2 = emu.Handle(0)
     emu.check(emu.emu_load_tuning(h2.h, path.encode()))
