@@ -102,17 +102,21 @@ def test_autotuner_and_cache(h, tmp_path):
     h2.close()
 
 
-def test_mixed_tile_shapes_bit_exact(orc, tmp_path):
+@pytest.mark.parametrize("stages", [None, 1])
+def test_mixed_tile_shapes_bit_exact(orc, tmp_path, stages):
     """A tuning that gives the shape buckets different configurations (tile
     shape x slice-pair order): the products run in up to six GEMM launches
-    on parallel graph branches, each bit-exact against the oracle (ragged
-    edges exercise the patches that lie wholly outside a product)."""
+    per stage on parallel graph branches (three stages by default, one with
+    "p5_stages": 1), each bit-exact against the oracle (ragged edges
+    exercise the patches that lie wholly outside a product)."""
     p = 5
     shapes, mats = make_problems(60, 11, mn=(20, 700), kr=(60, 1500))
     path = tmp_path / "mixed.json"
+    lines = ['  "p5_s%d_k%d": %d' % (sc, kc, (sc + 2 * kc) % 6) for sc in range(5) for kc in range(5)]
+    if stages is not None:
+        lines.append('  "p5_stages": %d' % stages)
     with open(path, "w") as fh:
-        fh.write("{\n" + ",\n".join('  "p5_s%d_k%d": %d' % (sc, kc, (sc + 2 * kc) % 6)
-                                      for sc in range(5) for kc in range(5)) + "\n}\n")
+        fh.write("{\n" + ",\n".join(lines) + "\n}\n")
     hd = emu.Handle(0)
     emu.check(emu.emu_load_tuning(hd.h, str(path).encode()))
     As = [torch.from_numpy(A).cuda() for A, _ in mats]
