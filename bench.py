@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--suite-md", default=None, nargs="+",
                     help="print the summary tables of --suite JSONL files (rows of later files replace the "
                          "matching rows of earlier ones)")
+    ap.add_argument("--grouped-run", action="store_true",
+                    help="run the 512-product grouped batch (p = --p) --warmup + --steps times with the handle's "
+                         "default configuration (no tuning) and print its time; for profiling launch lists")
     ap.add_argument("--selector-md", default=None,
                     help="print the selector end-to-end summary of a --suite-part selector JSONL file")
     ap.add_argument("--suite-part", default="all", choices=["all", "ii", "scheme2", "selector", "grouped"],
@@ -222,8 +225,9 @@ def fp8_engine_leg(emu, h, Ad, Bd, Cd, n, stream, ri, ci, A, B, hi, lo, den, cub
 
 def scheme_II_leg(emu, h, Ad, Bd, Cd, n, stream, ri, ci, hi, lo, den, cublas_tflops):
     """Scheme II (16 and 20 moduli) on the same inputs with the default engine
-    (bf16 tcgen05): TFLOP/s, GEMM-kernel bf16 TFLOP/s against the measured bf16
-    peak, and sampled error, with the same CUDA-event timing."""
+    (bf16 tcgen05): TFLOP/s, residue-GEMM bf16 TFLOP/s against the measured
+    bf16 peak (alone and with the CRT kernel's time), and sampled error, with
+    the same CUDA-event timing."""
     import torch
     out = {}
     bf16 = measured_peaks().get("bf16_tflops") or 1900.0
@@ -248,9 +252,12 @@ def scheme_II_leg(emu, h, Ad, Bd, Cd, n, stream, ri, ci, hi, lo, den, cublas_tfl
         got = Cd[ri][:, ci].cpu().numpy()
         err = float(np.max(np.abs((got - hi) - lo) / den))
         gms = tr["ms_gemm"] / max(tr["gemm_launches"], 1)
+        cms = tr["ms_other"] / max(tr["gemm_launches"], 1)
         tc = 2.0 * nm * n ** 3 / (gms * 1e-3) / 1e12
         out["nm%d" % nm] = {"tflops": 2.0 * n ** 3 / (ms * 1e-3) / 1e12, "ms_per_step": ms, "gemm_ms": gms,
-                            "gemm_bf16_tflops": tc, "frac_of_bf16_peak": tc / bf16, "bf16_peak_tflops": bf16,
+                            "crt_ms": cms, "gemm_bf16_tflops": tc, "frac_of_bf16_peak": tc / bf16,
+                            "frac_of_bf16_peak_with_crt": 2.0 * nm * n ** 3 / ((gms + cms) * 1e-3) / 1e12 / bf16,
+                            "bf16_peak_tflops": bf16,
                             "err_max_rel_absAB": err,
                             "speedup_vs_cublas_dgemm": 2.0 * n ** 3 / (ms * 1e-3) / 1e12 / cublas_tflops,
                             "kernel": "gemm_II_tc_kernel (tcgen05 bf16, 128 x 256 tiles)"}
@@ -483,7 +490,7 @@ def run_ours(args, rank, world, local_rank):
         traffic = (load_traffic("gemm_I", "p%d_n%d" % (p, n)) if args.scheme == "I" else
                    load_traffic("gemm_f8tc", "p%d_n%d" % (p, n)) if args.scheme == "I_F8" else
                    load_traffic("gemm_II_tc", "nm%d_n%d" % (p, n)) if ii_tc else None)
-        kname = ("gemm_II_tc_kernel + crt_II_kernel (tcgen05 bf16 residue GEMM, then CRT)" if ii_tc else "gemm_II_kernel (mma.sync INT8)" if args.scheme == "II" else
+        kname = ("gemm_II_tc_kernel (tcgen05 bf16 residue GEMM; the CRT kernel is timed apart)" if ii_tc else "gemm_II_kernel (mma.sync INT8)" if args.scheme == "II" else
                  "gemm_f8tc_kernel<%d, OUT_F64> (tcgen05)" % p if args.scheme == "I_F8" else
                  "gemm_I_kernel<%d, OUT_F64> (mma.sync INT8)" % p)
         ops_desc = ("bf16 tensor ops 2 N_m M N K (residue products)" if ii_tc else
@@ -663,8 +670,12 @@ def suite_markdown(paths):
                      f"{d['speedup_graph_vs_loop']:.2f}x; {d['tflops_graph']:.2f} emulated TFLOP/s, "
                      f"{d['int8_tops_graph']:.1f} INT8 TOP/s.")
             if d.get("tuned"):
-                o.append(f"  Tuned: {d.get('stages')} stage(s); configurations (bucket: tile, slice-pair order): " +
-                         ", ".join(f"{k} {v}" for k, v in d["tuned"].items()) + ".")
+                hist = {}
+                for v in d["tuned"].values():
+                    hist[v] = hist.get(v, 0) + 1
+                o.append(f"  Tuned: {d.get('stages')} stage(s); shape buckets per configuration (tile, slice-pair "
+                         "order): " + ", ".join(f"{v} {c}" for v, c in sorted(hist.items(), key=lambda x: -x[1])) +
+                         ".")
     return "\n".join(o)
 
 
@@ -699,11 +710,48 @@ def grouped_points(emu, h, dev, emit, timed):
         ms_loop = timed(lambda: emu.dgemm_grouped(d, p, handle=h, loop=True), reps=2)
         emit({"path": "emu_dgemm_grouped", "count": 512, "p": p, "ms_graph_default_tile": ms_default,
               "ms_graph_tuned": ms_tuned, "configs_timed": ncfg, "ms_loop": ms_loop,
-              "tuned": {k: GROUPED_CFGS[v] for k, v in sorted(tuned.items()) if not k.endswith("_stages")},
+              "tuned": {k: GROUPED_CFGS[v] for k, v in sorted(tuned.items())
+                        if k.startswith("p%d_s" % p) and not k.endswith("_stages")},
               "stages": tuned.get("p%d_stages" % p),
               "tflops_graph": flops / ms_tuned / 1e9, "tflops_loop": flops / ms_loop / 1e9,
               "int8_tops_graph": (p * (p + 1) // 2) * flops / ms_tuned / 1e9,
               "speedup_graph_vs_loop": ms_loop / ms_tuned})
+
+
+def grouped_run(args):
+    """The 512-product grouped batch (the grouped_points shapes) at p = args.p,
+    untuned: args.warmup + args.steps graph launches, CUDA-event time of the
+    timed ones."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2606_25453_gb300 as emu
+    dev = torch.device("cuda", 0)
+    shapes = synth.grouped_shapes(512, 0)
+    As, Bs, Cs = [], [], []
+    for i, (m, nn, k) in enumerate(shapes):
+        A, B = synth.gemm_pair(m, nn, k, 1.0, 5000 + i)
+        As.append(torch.from_numpy(A).to(dev))
+        Bs.append(torch.from_numpy(B).to(dev))
+        Cs.append(torch.empty((m, nn), dtype=torch.float64, device=dev))
+    h = emu.Handle(0)
+    d = emu.grouped_descs(As, Bs, Cs)
+    for _ in range(args.warmup):
+        emu.dgemm_grouped(d, args.p, handle=h)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        emu.dgemm_grouped(d, args.p, handle=h)
+    e1.record()
+    torch.cuda.synchronize()
+    if h.status() != 0:
+        raise RuntimeError("device status %d" % h.status())
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    flops = sum(2 * m * nn * k for m, nn, k in shapes)
+    print(json.dumps({"path": "emu_dgemm_grouped", "count": 512, "p": args.p, "ms": ms,
+                      "tflops": flops / ms / 1e9, "int8_tops": args.p * (args.p + 1) // 2 * flops / ms / 1e9}))
+    h.close()
 
 
 SEL_TOLS = (1e-8, 1e-12, 1e-15)
@@ -1072,6 +1120,9 @@ def main():
         return
     if args.suite:
         run_suite(args.suite, args)
+        return
+    if args.grouped_run:
+        grouped_run(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

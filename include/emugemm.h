@@ -162,7 +162,8 @@ emu_status_t emu_set_workspace(emu_handle_t h, void *workspace_dev, size_t bytes
  * each kernel phase (exponent scan, split, fused GEMM, other) and counts the
  * kernels it launches.  emu_trace_read synchronises the recorded events and
  * returns the accumulated device milliseconds per phase (ms_host[4]: scan,
- * split, gemm, other), the number of fused-GEMM launches and of all kernel
+ * split, gemm, other -- on the bf16 Scheme II engine "gemm" is the residue
+ * GEMM and "other" the CRT kernel), the number of GEMM launches and of all kernel
  * launches since the last read, then clears the counters.  Not available
  * while a stream is being captured into a CUDA graph. */
 emu_status_t emu_trace_enable(emu_handle_t h, int enable);

@@ -666,9 +666,20 @@ emu_status_t run_scheme_II(emu_handle_s* h, const View& v, int64_t k, int nm, in
   a.num_sms = h->num_sms;
   a.cluster = cluster;
   a.scratch = ws + pl.off_scratch;
+  if (!tc) {
+    trace_begin(h, PH_GEMM, st);
+    cudaError_t e = launch_gemm_II(out_mode, a, mt, ct, st);
+    trace_end(h, PH_GEMM, st, 1);
+    return cuda_err(e);
+  }
+  // the residue GEMM is the traced GEMM phase, the CRT kernel "other"
   trace_begin(h, PH_GEMM, st);
-  cudaError_t e = tc ? launch_gemm_II_tc(out_mode, a, mt, ct, st) : launch_gemm_II(out_mode, a, mt, ct, st);
+  cudaError_t e = launch_gemm_II_tc(out_mode, a, mt, ct, st, 1);
   trace_end(h, PH_GEMM, st, 1);
+  if (e != cudaSuccess) return cuda_err(e);
+  trace_begin(h, PH_OTHER, st);
+  e = launch_gemm_II_tc(out_mode, a, mt, ct, st, 2);
+  trace_end(h, PH_OTHER, st, 1);
   return cuda_err(e);
 }
 

@@ -122,9 +122,11 @@ cudaError_t launch_gemm_II(int out_mode, const GemmIIArgs& a, const ModTables& m
 // Scheme II on bf16 residue planes with tcgen05 / TMEM (256 x 256 tiles on
 // CTA pairs, or 128 x 256 on single CTAs; modulus-major), then the CRT
 // kernel; modes II_F64, II_F32, II_Z3M, II_C3M.  GemmIIArgs::scratch: gemm_II_tc_residue_bytes(M, N, nm, complex,
-// cluster) bytes of device memory for the residue planes.
+// cluster) bytes of device memory for the residue planes.  part: 1 launches
+// the residue GEMM, 2 the CRT kernel (after the residue GEMM on the same
+// stream), 3 both.
 cudaError_t launch_gemm_II_tc(int out_mode, const GemmIIArgs& a, const ModTables& mt,
-                              const CrtTables& ct, cudaStream_t st);
+                              const CrtTables& ct, cudaStream_t st, int part = 3);
 int gemm_II_tc_tile_m();
 int gemm_II_tc_tile_n();
 size_t gemm_II_tc_residue_bytes(int64_t M, int64_t N, int nm, bool is_complex, int cluster);

@@ -753,12 +753,15 @@ cudaError_t launch_crt(const GemmIIArgs& a, const ModTables& mt, const CrtTables
   return cudaGetLastError();
 }
 
+// part: 1 = the residue GEMM, 2 = the CRT kernel, 3 = both.
 template <int MODE>
-cudaError_t launch_mode(const GemmIIArgs& a, const ModTables& mt, const CrtTables& ct, cudaStream_t st) {
+cudaError_t launch_mode(const GemmIIArgs& a, const ModTables& mt, const CrtTables& ct, cudaStream_t st, int part) {
   constexpr int NSET = (MODE == II_Z3M || MODE == II_C3M) ? 3 : 1;
-  cudaError_t e = launch_residues(a, NSET, mt, st);
-  if (e != cudaSuccess) return e;
-  return launch_crt<MODE>(a, mt, ct, st);
+  if (part & 1) {
+    cudaError_t e = launch_residues(a, NSET, mt, st);
+    if (e != cudaSuccess) return e;
+  }
+  return (part & 2) ? launch_crt<MODE>(a, mt, ct, st) : cudaSuccess;
 }
 
 }  // namespace
@@ -787,16 +790,16 @@ int gemm_II_tc_cluster() {
 }
 
 cudaError_t launch_gemm_II_tc(int out_mode, const GemmIIArgs& a, const ModTables& mt, const CrtTables& ct,
-                              cudaStream_t st) {
+                              cudaStream_t st, int part) {
   switch (out_mode) {
     case II_F64:
-      return launch_mode<II_F64>(a, mt, ct, st);
+      return launch_mode<II_F64>(a, mt, ct, st, part);
     case II_F32:
-      return launch_mode<II_F32>(a, mt, ct, st);
+      return launch_mode<II_F32>(a, mt, ct, st, part);
     case II_Z3M:
-      return launch_mode<II_Z3M>(a, mt, ct, st);
+      return launch_mode<II_Z3M>(a, mt, ct, st, part);
     case II_C3M:
-      return launch_mode<II_C3M>(a, mt, ct, st);
+      return launch_mode<II_C3M>(a, mt, ct, st, part);
     default:
       return cudaErrorInvalidValue;
   }

@@ -172,3 +172,20 @@ def test_zgemm_3m_sampled_rows_n4096(orc, h):
     assert h.status() == 0
     rows = [1, 3000]
     assert np.array_equal(C[rows].cpu().numpy(), orc.emu_Z3M(A[rows], B, nm))
+
+
+def test_trace_splits_residue_gemm_and_crt(h):
+    # the traced "gemm" phase of the bf16 engine is the residue GEMM alone;
+    # the CRT kernel is recorded as "other"
+    A, B = synth.gemm_pair(512, 512, 1000, 1.0, 61)
+    Ad, Bd = dev(A), dev(B)
+    emu.dgemm(Ad, Bd, scheme="II", p=16, handle=h)
+    torch.cuda.synchronize()
+    h.trace(True)
+    h.trace_read()
+    emu.dgemm(Ad, Bd, scheme="II", p=16, handle=h)
+    tr = h.trace_read()
+    h.trace(False)
+    assert tr["gemm_launches"] == 1
+    assert tr["kernel_launches"] == 6  # two scans, two splits, residue GEMM, CRT
+    assert tr["ms_gemm"] > 0 and tr["ms_other"] > 0 and tr["ms_scan"] > 0 and tr["ms_split"] > 0
