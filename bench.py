@@ -776,7 +776,8 @@ def selector_points(emu, h, dev, emit, products=None, schemes=(("I", 12), ("II",
     emu_dgemm at the fixed p (N) that passes every training product -- p = 12
     for Scheme I, N = 20 for Scheme II with norm scaling -- on the same
     products, CUDA-event time on the stream, one timed call each after a
-    warm-up at the largest size.  Pass = max |C - AB| / (|A||B|) <= tol on 256
+    warm-up at the largest size (both outputs preallocated outside the
+    timing).  Pass = max |C - AB| / (|A||B|) <= tol on 256
     sampled entries against the GPU double-double probe."""
     import torch
     from paper_2606_25453_gb300 import selector as sel
@@ -796,6 +797,7 @@ def selector_points(emu, h, dev, emit, products=None, schemes=(("I", 12), ("II",
         Ad = synth.test_matrix_torch(n, n, phi, seed, dev)
         Bd = synth.test_matrix_torch(n, n, phi, seed + 1, dev)
         Cf = torch.empty((n, n), dtype=torch.float64, device=dev)
+        Ca = torch.empty((n, n), dtype=torch.float64, device=dev)
         ri = np.sort(rng.choice(n, 16, replace=False))
         ci = np.sort(rng.choice(n, 16, replace=False))
         hi, lo, den = probe_ref(emu, h, Ad, Bd, ri, ci)
@@ -814,7 +816,7 @@ def selector_points(emu, h, dev, emit, products=None, schemes=(("I", 12), ("II",
             err_fixed = err(Cf)
             for tol in tols:
                 e0.record(stream)
-                C, used, code = emu.dgemm_auto(Ad, Bd, tol, handle=h, scheme=sc)
+                C, used, code = emu.dgemm_auto(Ad, Bd, tol, handle=h, scheme=sc, C=Ca)
                 e1.record(stream)
                 torch.cuda.synchronize()
                 ms_auto = e0.elapsed_time(e1)
@@ -825,8 +827,7 @@ def selector_points(emu, h, dev, emit, products=None, schemes=(("I", 12), ("II",
                 d["pass_fixed"] = err_fixed <= tol
                 rows.append(d)
                 emit(d)
-                del C
-        del Ad, Bd, Cf
+        del Ad, Bd, Cf, Ca
     for sc, fixed in schemes:
         for tol in tols:
             r = [d for d in rows if d["scheme"] == sc and d["tol"] == tol]
@@ -849,7 +850,8 @@ def selector_markdown(path):
          "`python bench.py --selector-md selector.jsonl > profiles/selector_e2e_gb300.md`.\n",
          "Held-out products (square, n log-uniform in [1024, 4096], phi ~ U(0, 8), seeds outside the",
          "training data; A and B drawn on the GPU by the Eq. 19 generator).  Timed with CUDA events on the",
-         "stream, one call each: `emu_dgemm_auto` / `emu_dgemm_auto_II` with the committed weights -- feature",
+         "stream, one call each into preallocated outputs: `emu_dgemm_auto` / `emu_dgemm_auto_II` with the",
+         "committed weights -- feature",
          "scan, MLP, the 64-entry double-double probe and every escalation and recomputation inside the",
          "timed region -- against `emu_dgemm` at the fixed p (N) that passes every training product (Scheme I",
          "INT8 p = 12; Scheme II with norm scaling N = 20).  Pass: max |C - AB| / (|A||B|) <= tol on 256",

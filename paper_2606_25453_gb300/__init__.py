@@ -379,15 +379,17 @@ def tune_grouped(descs, p: int = 6, path: str | None = None, handle=None, stream
     return timed.value
 
 
-def dgemm_auto(A, B, tol: float, alpha: float = 1.0, probe: int = 64, handle=None, stream=None, scheme="I"):
+def dgemm_auto(A, B, tol: float, alpha: float = 1.0, probe: int = 64, handle=None, stream=None, scheme="I",
+               C=None):
     """C = alpha*A@B with the p (scheme="I") or the N moduli (scheme="II":
     Scheme II with norm scaling) chosen by the selector -- the bound if no
     weights are loaded -- checked on `probe` sampled entries; returns
-    (C, p or N, status code)."""
+    (C, p or N, status code).  C: optional output tensor (allocated if None)."""
     import torch
     m, k = A.shape
     n = B.shape[1]
-    C = torch.empty((m, n), dtype=torch.float64, device=A.device)
+    if C is None:
+        C = torch.empty((m, n), dtype=torch.float64, device=A.device)
     layout, lda, ldb, ldc = _layout_of(A, B, C)
     h = handle or default_handle(A.device.index or 0)
     p = _i32()

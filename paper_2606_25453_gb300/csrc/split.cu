@@ -47,16 +47,16 @@ __device__ __forceinline__ uint64_t load_bits<float>(const float* p) {
 // ------------------------------------------------------------------ scan
 // Vector r, element h of operand X: kcontig -> X[(r*ld + h)*cw + part],
 // else X[(h*ld + r)*cw + part]; cw = 2 for complex (both parts scanned).
+// seg: elements of a vector per block row (K segment), chosen by the launcher.
 template <typename T, bool KCONTIG>
-__global__ void scan_kernel(const T* __restrict__ X, int64_t ld, int64_t rows, int64_t k, int cw,
+__global__ void scan_kernel(const T* __restrict__ X, int64_t ld, int64_t rows, int64_t k, int cw, int64_t seg,
                             unsigned long long* __restrict__ maxbits, int* status) {
   if (KCONTIG) {
-    // one warp per (row, K segment of 32*64 elements)
+    // one warp per (row, K segment)
     int lane = threadIdx.x & 31;
     int64_t r = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (r >= rows) return;
     int64_t len = k * cw;
-    int64_t seg = 2048;
     int64_t h0 = static_cast<int64_t>(blockIdx.y) * seg;
     int64_t h1 = h0 + seg < len ? h0 + seg : len;
     const T* row = X + r * ld * cw;
@@ -76,7 +76,6 @@ __global__ void scan_kernel(const T* __restrict__ X, int64_t ld, int64_t rows, i
   } else {
     // block 32 x 8: lanes over vectors (coalesced), 8 row-groups over K
     int64_t r = static_cast<int64_t>(blockIdx.x) * 32 + threadIdx.x;
-    int64_t seg = 256;
     int64_t h0 = static_cast<int64_t>(blockIdx.y) * seg;
     int64_t h1 = h0 + seg < k ? h0 + seg : k;
     uint64_t mx = 0;
@@ -141,16 +140,16 @@ __device__ __forceinline__ uint64_t scalar_absbits(T x) {
 }
 
 template <typename T, bool KCONTIG>
-__global__ void scan_vec_kernel(const T* __restrict__ X, int64_t ld, int64_t rows, int64_t k, int cw,
+__global__ void scan_vec_kernel(const T* __restrict__ X, int64_t ld, int64_t rows, int64_t k, int cw, int64_t seg,
                                 unsigned long long* __restrict__ maxbits, int* status) {
   constexpr int S = 16 / static_cast<int>(sizeof(T));
   if (KCONTIG) {
-    // one warp per (row, segment of 2048 scalars); lane l loads uint4 l, l + 32, ...
+    // one warp per (row, segment of seg scalars); lane l loads uint4 l, l + 32, ...
     const int lane = threadIdx.x & 31;
     const int64_t r = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (r >= rows) return;
-    const int64_t len = k * cw, h0 = static_cast<int64_t>(blockIdx.y) * 2048;
-    const int64_t h1 = h0 + 2048 < len ? h0 + 2048 : len;
+    const int64_t len = k * cw, h0 = static_cast<int64_t>(blockIdx.y) * seg;
+    const int64_t h1 = h0 + seg < len ? h0 + seg : len;
     const T* row = X + r * ld * cw;
     const int64_t nv = (h1 - h0) / S;
     const uint4* pv = reinterpret_cast<const uint4*>(row + h0);
@@ -180,12 +179,12 @@ __global__ void scan_vec_kernel(const T* __restrict__ X, int64_t ld, int64_t row
   } else {
     // block 32 x 8: lane x loads the CV vectors x*CV .. x*CV + CV - 1 of a
     // block of 32*CV vectors (512 contiguous bytes per warp and K row);
-    // the 8 row-groups split a K segment of 256
+    // the 8 row-groups split a K segment of seg
     const int cv = S / cw;
     const int64_t rb = static_cast<int64_t>(blockIdx.x) * 32 * cv;
     const int64_t r = rb + static_cast<int64_t>(threadIdx.x) * cv;
-    const int64_t h0 = static_cast<int64_t>(blockIdx.y) * 256;
-    const int64_t h1 = h0 + 256 < k ? h0 + 256 : k;
+    const int64_t h0 = static_cast<int64_t>(blockIdx.y) * seg;
+    const int64_t h1 = h0 + seg < k ? h0 + seg : k;
     uint64_t mx[4] = {0, 0, 0, 0};
     if (r + cv <= rows) {
 #pragma unroll 4
@@ -238,7 +237,10 @@ __global__ void scan_vec_kernel(const T* __restrict__ X, int64_t ld, int64_t row
 // frexp exponent of the row maximum and y = x 2^-E (|y| < 1), every square
 // is rounded UP to an integer number of units 2^-64, the integers are summed
 // (order-free, 128 bits), and e = E + ceil((bitlen(S) - 64) / 2).
-__device__ __forceinline__ unsigned __int128 sq_ceil64(uint64_t bits, int Emax) {
+// The value is below 2^64 (y^2 < 1): M^2 (106 bits at most) shifted right
+// by s = -sh >= 1 with a sticky round-up, in 64-bit halves; a left shift
+// (sh >= 0) only occurs for rows of subnormal numbers.
+__device__ __forceinline__ uint64_t sq_ceil64(uint64_t bits, int Emax) {
   const uint64_t ab = bits & 0x7FFFFFFFFFFFFFFFull;
   if (ab == 0) return 0;
   const int ef = static_cast<int>(ab >> 52);
@@ -250,13 +252,21 @@ __device__ __forceinline__ unsigned __int128 sq_ceil64(uint64_t bits, int Emax) 
     M |= uint64_t{1} << 52;
     q = ef - 1075;
   }
-  const unsigned __int128 M2 = static_cast<unsigned __int128>(M) * M;
+  const uint64_t lo = M * M, hi = __umul64hi(M, M);
   const int sh = 2 * (q - Emax) + 64;
-  if (sh >= 0) return M2 << sh;  // y^2 2^64 < 2^64
-  if (-sh >= 128) return 1;
-  unsigned __int128 r = M2 >> (-sh);
-  if ((r << (-sh)) != M2) r += 1;
-  return r;
+  if (sh >= 0) return lo << sh;  // then M^2 2^sh < 2^64, so hi = 0 and lo << sh is exact
+  const int s = -sh;
+  if (s >= 128) return 1;
+  uint64_t r, sticky;
+  if (s >= 64) {
+    const int t = s - 64;
+    r = hi >> t;
+    sticky = lo | (t ? (hi << (64 - t)) : 0ull);
+  } else {
+    r = (hi << (64 - s)) | (lo >> s);
+    sticky = lo << (64 - s);
+  }
+  return r + (sticky != 0 ? 1ull : 0ull);
 }
 
 // Exact 128-bit atomic add on (lo, hi) words.
@@ -278,7 +288,7 @@ __device__ __forceinline__ unsigned __int128 shfl_add_u128(unsigned __int128 v) 
 
 // Same launch shapes as scan_kernel; acc: 2 words per row, zeroed first.
 template <typename T, bool KCONTIG>
-__global__ void norm_kernel(const T* __restrict__ X, int64_t ld, int64_t rows, int64_t k, int cw,
+__global__ void norm_kernel(const T* __restrict__ X, int64_t ld, int64_t rows, int64_t k, int cw, int64_t seg,
                             const unsigned long long* __restrict__ maxbits, unsigned long long* __restrict__ acc) {
   if (KCONTIG) {
     const int lane = threadIdx.x & 31;
@@ -287,17 +297,17 @@ __global__ void norm_kernel(const T* __restrict__ X, int64_t ld, int64_t rows, i
     const uint64_t mb = maxbits[r];
     if (mb == 0 || mb >= 0x7FF0000000000000ull) return;  // zero row / non-finite (flagged by the scan)
     const int Emax = frexp_exp_bits(mb);
-    const int64_t len = k * cw, seg = 2048;
+    const int64_t len = k * cw;
     const int64_t h0 = static_cast<int64_t>(blockIdx.y) * seg;
     const int64_t h1 = h0 + seg < len ? h0 + seg : len;
     const T* row = X + r * ld * cw;
     unsigned __int128 sum = 0;
+#pragma unroll 4
     for (int64_t h = h0 + lane; h < h1; h += 32) sum += sq_ceil64(load_bits(row + h), Emax);
     sum = shfl_add_u128(sum);
     if (lane == 0 && sum) atomic_add_u128(acc + 2 * r, sum);
   } else {
     const int64_t r = static_cast<int64_t>(blockIdx.x) * 32 + threadIdx.x;
-    const int64_t seg = 256;
     const int64_t h0 = static_cast<int64_t>(blockIdx.y) * seg;
     const int64_t h1 = h0 + seg < k ? h0 + seg : k;
     if (r >= rows) return;
@@ -305,6 +315,7 @@ __global__ void norm_kernel(const T* __restrict__ X, int64_t ld, int64_t rows, i
     if (mb == 0 || mb >= 0x7FF0000000000000ull) return;
     const int Emax = frexp_exp_bits(mb);
     unsigned __int128 sum = 0;
+#pragma unroll 4
     for (int64_t h = h0 + threadIdx.y; h < h1; h += blockDim.y) {
       const T* p = X + (h * ld + r) * cw;
       sum += sq_ceil64(load_bits(p), Emax);
@@ -676,6 +687,21 @@ __global__ void __launch_bounds__(256) split_II_kstrided(const T* __restrict__ X
 }
 
 // ------------------------------------------------------------------ launchers
+// K segment (elements of a vector per block) of the scan and norm kernels:
+// `seg0` (2048 along K-contiguous rows, 256 down strided columns), halved
+// while the grid would hold fewer than four blocks per SM -- small operands
+// then still have enough loads in flight -- down to `seg_min`, and doubled
+// while the segment count exceeds the grid's y limit.
+static int64_t scan_seg(int64_t vec_blocks, int64_t len, int64_t seg0, int64_t seg_min) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t seg = seg0;
+  while (seg > seg_min && vec_blocks * ((len + seg - 1) / seg) < 4 * static_cast<int64_t>(sms)) seg >>= 1;
+  while ((len + seg - 1) / seg > 65535) seg <<= 1;
+  return seg;
+}
+
 template <typename T>
 void launch_scan(const T* X, int64_t ld, bool kcontig, int64_t rows, int64_t k, int cw,
                  unsigned long long* maxbits, int* status, cudaStream_t st) {
@@ -685,19 +711,21 @@ void launch_scan(const T* X, int64_t ld, bool kcontig, int64_t rows, int64_t k, 
   const bool vec = (reinterpret_cast<uintptr_t>(X) & 15u) == 0 &&
                    (static_cast<uint64_t>(ld) * cw * sizeof(T)) % 16 == 0;
   if (kcontig) {
-    int64_t len = k * cw;
-    dim3 grid(static_cast<unsigned>((rows + 7) / 8), static_cast<unsigned>((len + 2047) / 2048));
+    const int64_t len = k * cw, rb = (rows + 7) / 8, seg = scan_seg(rb, len, 2048, 256);
+    dim3 grid(static_cast<unsigned>(rb), static_cast<unsigned>((len + seg - 1) / seg));
     if (vec)
-      scan_vec_kernel<T, true><<<grid, 256, 0, st>>>(X, ld, rows, k, cw, maxbits, status);
+      scan_vec_kernel<T, true><<<grid, 256, 0, st>>>(X, ld, rows, k, cw, seg, maxbits, status);
     else
-      scan_kernel<T, true><<<grid, 256, 0, st>>>(X, ld, rows, k, cw, maxbits, status);
+      scan_kernel<T, true><<<grid, 256, 0, st>>>(X, ld, rows, k, cw, seg, maxbits, status);
   } else if (vec) {
     const int64_t per_block = 32 * static_cast<int64_t>(16 / sizeof(T)) / cw;
-    dim3 grid(static_cast<unsigned>((rows + per_block - 1) / per_block), static_cast<unsigned>((k + 255) / 256));
-    scan_vec_kernel<T, false><<<grid, dim3(32, 8), 0, st>>>(X, ld, rows, k, cw, maxbits, status);
+    const int64_t rb = (rows + per_block - 1) / per_block, seg = scan_seg(rb, k, 256, 32);
+    dim3 grid(static_cast<unsigned>(rb), static_cast<unsigned>((k + seg - 1) / seg));
+    scan_vec_kernel<T, false><<<grid, dim3(32, 8), 0, st>>>(X, ld, rows, k, cw, seg, maxbits, status);
   } else {
-    dim3 grid(static_cast<unsigned>((rows + 31) / 32), static_cast<unsigned>((k + 255) / 256));
-    scan_kernel<T, false><<<grid, dim3(32, 8), 0, st>>>(X, ld, rows, k, cw, maxbits, status);
+    const int64_t rb = (rows + 31) / 32, seg = scan_seg(rb, k, 256, 32);
+    dim3 grid(static_cast<unsigned>(rb), static_cast<unsigned>((k + seg - 1) / seg));
+    scan_kernel<T, false><<<grid, dim3(32, 8), 0, st>>>(X, ld, rows, k, cw, seg, maxbits, status);
   }
 }
 template void launch_scan<double>(const double*, int64_t, bool, int64_t, int64_t, int,
@@ -789,12 +817,13 @@ void launch_norm(const T* X, int64_t ld, bool kcontig, int64_t rows, int64_t k, 
   cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * 2 * rows, st);
   if (k > 0) {
     if (kcontig) {
-      int64_t len = k * cw;
-      dim3 grid(static_cast<unsigned>((rows + 7) / 8), static_cast<unsigned>((len + 2047) / 2048));
-      norm_kernel<T, true><<<grid, 256, 0, st>>>(X, ld, rows, k, cw, maxbits, acc);
+      const int64_t len = k * cw, rb = (rows + 7) / 8, seg = scan_seg(rb, len, 2048, 256);
+      dim3 grid(static_cast<unsigned>(rb), static_cast<unsigned>((len + seg - 1) / seg));
+      norm_kernel<T, true><<<grid, 256, 0, st>>>(X, ld, rows, k, cw, seg, maxbits, acc);
     } else {
-      dim3 grid(static_cast<unsigned>((rows + 31) / 32), static_cast<unsigned>((k + 255) / 256));
-      norm_kernel<T, false><<<grid, dim3(32, 8), 0, st>>>(X, ld, rows, k, cw, maxbits, acc);
+      const int64_t rb = (rows + 31) / 32, seg = scan_seg(rb, k, 256, 32);
+      dim3 grid(static_cast<unsigned>(rb), static_cast<unsigned>((k + seg - 1) / seg));
+      norm_kernel<T, false><<<grid, dim3(32, 8), 0, st>>>(X, ld, rows, k, cw, seg, maxbits, acc);
     }
   }
   norm_finish_kernel<<<static_cast<unsigned>((rows + 255) / 256), 256, 0, st>>>(rows, maxbits, acc, E);

@@ -192,6 +192,7 @@ def test_committed_selector_end_to_end_gain_at_1e8():
         A = synth.test_matrix_torch(n, n, phi, seed, dev)
         B = synth.test_matrix_torch(n, n, phi, seed + 1, dev)
         C = torch.empty((n, n), dtype=torch.float64, device=dev)
+        Ca = torch.empty((n, n), dtype=torch.float64, device=dev)
         pairs = rng.integers(0, n, size=(256, 2)).astype(np.int32)
         idx = torch.from_numpy(pairs.reshape(-1)).to(dev)
         ref = torch.empty(512, dtype=torch.float64, device=dev)
@@ -213,7 +214,7 @@ def test_committed_selector_end_to_end_gain_at_1e8():
         t_fixed += e0.elapsed_time(e1)
         pass_fixed.append(err(C) <= 1e-8)
         e0.record()
-        Ca, used, code = emu.dgemm_auto(A, B, 1e-8, handle=hd)
+        Ca, used, code = emu.dgemm_auto(A, B, 1e-8, handle=hd, C=Ca)
         e1.record()
         torch.cuda.synchronize()
         t_auto += e0.elapsed_time(e1)
