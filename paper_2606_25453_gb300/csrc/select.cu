@@ -36,6 +36,10 @@ struct SelState {
   size_t dev_bytes = 0;
   uint8_t* host = nullptr;
   size_t host_bytes = 0;
+  // side stream for the probe's reference sums (they depend on A and B
+  // only, so they run beside the feature pass and the product)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_probe = nullptr;
 };
 SelState* sel_of(emu_handle_s* h) {
   if (!h->selector) h->selector = new SelState();
@@ -52,14 +56,28 @@ __device__ __forceinline__ int exp_bits(uint64_t ab) { return frexp_exp_bits(ab)
 // largest magnitude, is found by the block first (the vector is then read
 // a second time, from L2), so that no pass over the whole of A and B is
 // needed for 64 sampled vectors.
-__global__ void feat_hist_kernel(const double* __restrict__ X, int64_t ld, bool kcontig, int64_t rows, int64_t k,
-                                 int64_t stride, unsigned int* __restrict__ hist) {
+// One launch serves both operands: blocks [0, nblk_a) sample A (histogram
+// hist[0..31]), the rest sample B (hist[32..63]).
+struct FeatOperand {
+  const double* X;
+  int64_t ld;
+  bool kcontig;
+  int64_t rows, stride;
+};
+__global__ void feat_hist_kernel(FeatOperand oa, FeatOperand ob, int nblk_a, int64_t k,
+                                 unsigned int* __restrict__ hist_all) {
   __shared__ unsigned int sh[32];
   __shared__ unsigned long long shmax;
   if (threadIdx.x < 32) sh[threadIdx.x] = 0;
   if (threadIdx.x == 0) shmax = 0;
   __syncthreads();
-  int64_t r = static_cast<int64_t>(blockIdx.x) * stride;
+  const bool is_a = static_cast<int>(blockIdx.x) < nblk_a;
+  const FeatOperand& op = is_a ? oa : ob;
+  const double* __restrict__ X = op.X;
+  const int64_t ld = op.ld, rows = op.rows;
+  const bool kcontig = op.kcontig;
+  unsigned int* __restrict__ hist = hist_all + (is_a ? 0 : 32);
+  int64_t r = static_cast<int64_t>(is_a ? blockIdx.x : blockIdx.x - nblk_a) * op.stride;
   if (r < rows) {
     unsigned long long mx = 0;  // largest |x| bit pattern (NaN > inf > finite)
     for (int64_t h = threadIdx.x; h < k; h += blockDim.x) {
@@ -288,6 +306,9 @@ void selector_release(emu_handle_s* h) {
   if (s->params_II) cudaFree(s->params_II);
   if (s->dev) cudaFree(s->dev);
   if (s->host) cudaFreeHost(s->host);
+  if (s->side) cudaStreamDestroy(s->side);
+  if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+  if (s->ev_probe) cudaEventDestroy(s->ev_probe);
   delete s;
   h->selector = nullptr;
 }
@@ -311,10 +332,9 @@ emu_status_t features_impl(emu_handle_s* h, const View& v, int64_t k, double tol
     na = std::min<int64_t>(na, sample);
     nb = std::min<int64_t>(nb, sample);
   }
-  feat_hist_kernel<<<static_cast<unsigned>(na), 256, 0, st>>>(static_cast<const double*>(v.A), v.ldA, v.a_kcontig, v.M,
-                                                               k, sa, hist);
-  feat_hist_kernel<<<static_cast<unsigned>(nb), 256, 0, st>>>(static_cast<const double*>(v.B), v.ldB, v.b_kcontig, v.N,
-                                                               k, sb, hist + 32);
+  const FeatOperand oa{static_cast<const double*>(v.A), v.ldA, v.a_kcontig, v.M, sa};
+  const FeatOperand ob{static_cast<const double*>(v.B), v.ldB, v.b_kcontig, v.N, sb};
+  feat_hist_kernel<<<static_cast<unsigned>(na + nb), 256, 0, st>>>(oa, ob, static_cast<int>(na), k, hist);
   feat_finalize_kernel<<<1, 96, 0, st>>>(hist, std::log2(static_cast<double>(k)), -std::log10(tol), feat);
   return cudaGetLastError() == cudaSuccess ? EMU_OK : EMU_ERR_CUDA;
 }
@@ -530,6 +550,44 @@ emu_status_t auto_impl(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n
   }
   float* feat = reinterpret_cast<float*>(ss->dev);
   float* prob = feat + 128;
+  // probe entries: a deterministic spread over C (caller's coordinates),
+  // uploaded once for every attempt (row-major view: (i, j); column-major C:
+  // element (i, j) sits at row j, column i of the row-major view); their
+  // double-double reference sums depend on A and B only, so they run on a
+  // side stream beside the feature pass and the product
+  auto* d_idx = reinterpret_cast<int32_t*>(ss->dev + off_idx);
+  auto* d_ref = reinterpret_cast<double*>(ss->dev + off_res);
+  auto* d_ab = d_ref + 2 * pc;
+  auto* d_c = d_ab + pc;
+  auto* d_sw = reinterpret_cast<int32_t*>(d_c + pc);  // gather indices for column-major C
+  if (probe > 0) {
+    if (!ss->side && (cudaStreamCreateWithFlags(&ss->side, cudaStreamNonBlocking) != cudaSuccess ||
+                      cudaEventCreateWithFlags(&ss->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                      cudaEventCreateWithFlags(&ss->ev_probe, cudaEventDisableTiming) != cudaSuccess))
+      return EMU_ERR_CUDA;
+    auto* hidx = reinterpret_cast<int32_t*>(ss->host);
+    uint64_t x = 0x9E3779B97F4A7C15ull ^ static_cast<uint64_t>(m * 1315423911u + n * 2654435761u + k);
+    for (int q = 0; q < probe; ++q) {
+      x ^= x << 13;
+      x ^= x >> 7;
+      x ^= x << 17;
+      hidx[2 * q] = static_cast<int32_t>(x % static_cast<uint64_t>(m));
+      x ^= x << 13;
+      x ^= x >> 7;
+      x ^= x << 17;
+      hidx[2 * q + 1] = static_cast<int32_t>(x % static_cast<uint64_t>(n));
+    }
+    // (the host buffer is next written by the features' copy, which the
+    // stream orders after this one)
+    if (cudaMemcpyAsync(d_idx, hidx, 8 * static_cast<size_t>(probe), cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return EMU_ERR_CUDA;
+    if (layout != EMU_ROW_MAJOR) swap_pairs_kernel<<<(probe + 127) / 128, 128, 0, st>>>(d_idx, probe, d_sw);
+    if (cudaEventRecord(ss->ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(ss->side, ss->ev_fork, 0) != cudaSuccess)
+      return EMU_ERR_CUDA;
+    emu_status_t s = emu_probe_dd(h, layout, m, n, k, A, lda, B, ldb, probe, d_idx, d_ref, d_ab, ss->side);
+    if (s != EMU_OK) return s;
+    if (cudaEventRecord(ss->ev_probe, ss->side) != cudaSuccess) return EMU_ERR_CUDA;
+  }
   {  // the feature scan needs scratch for the row / column maxima and histograms
     uint8_t* ws = nullptr;
     emu_status_t s = handle_workspace(h, feat_scratch(v), st, &ws);
@@ -565,41 +623,13 @@ emu_status_t auto_impl(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n
     // the top class is open-ended ("10 or more" / "20"): go to the largest value at once
     p = cls == kOut - 1 ? top : base_v + step * cls;
   }
-  // probe entries: a deterministic spread over C (caller's coordinates),
-  // uploaded once for every attempt (row-major view: (i, j); column-major C:
-  // element (i, j) sits at row j, column i of the row-major view)
-  auto* d_idx = reinterpret_cast<int32_t*>(ss->dev + off_idx);
-  auto* d_ref = reinterpret_cast<double*>(ss->dev + off_res);
-  auto* d_ab = d_ref + 2 * pc;
-  auto* d_c = d_ab + pc;
-  auto* d_sw = reinterpret_cast<int32_t*>(d_c + pc);  // gather indices for column-major C
-  if (probe > 0) {
-    auto* hidx = reinterpret_cast<int32_t*>(ss->host);
-    uint64_t x = 0x9E3779B97F4A7C15ull ^ static_cast<uint64_t>(m * 1315423911u + n * 2654435761u + k);
-    for (int q = 0; q < probe; ++q) {
-      x ^= x << 13;
-      x ^= x >> 7;
-      x ^= x << 17;
-      hidx[2 * q] = static_cast<int32_t>(x % static_cast<uint64_t>(m));
-      x ^= x << 13;
-      x ^= x >> 7;
-      x ^= x << 17;
-      hidx[2 * q + 1] = static_cast<int32_t>(x % static_cast<uint64_t>(n));
-    }
-    if (cudaMemcpyAsync(d_idx, hidx, 8 * static_cast<size_t>(probe), cudaMemcpyHostToDevice, st) != cudaSuccess)
-      return EMU_ERR_CUDA;
-    if (layout != EMU_ROW_MAJOR) swap_pairs_kernel<<<(probe + 127) / 128, 128, 0, st>>>(d_idx, probe, d_sw);
-    // (the host buffer is next written by the results' copy, which the
-    // stream orders after this one)
-  }
   for (int attempt = 0; attempt < 3; ++attempt) {
     emu_status_t s = emu_dgemm(h, layout, m, n, k, alpha, A, lda, B, ldb, 0.0, C, ldc,
                                scheme_II ? EMU_SCHEME_II_NORM : EMU_SCHEME_I, p, stream);
     if (s != EMU_OK) return s;
     *p_used = p;
     if (probe == 0) return EMU_OK;
-    s = emu_probe_dd(h, layout, m, n, k, A, lda, B, ldb, probe, d_idx, d_ref, d_ab, stream);
-    if (s != EMU_OK) return s;
+    if (attempt == 0 && cudaStreamWaitEvent(st, ss->ev_probe, 0) != cudaSuccess) return EMU_ERR_CUDA;
     gather_kernel<<<(probe + 127) / 128, 128, 0, st>>>(C, ldc, probe, layout == EMU_ROW_MAJOR ? d_idx : d_sw, d_c);
     // one copy back: [ref | ab | C entries]
     if (cudaMemcpyAsync(ss->host, d_ref, 32 * static_cast<size_t>(probe), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
