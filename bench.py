@@ -212,10 +212,12 @@ def fp8_engine_leg(emu, h, Ad, Bd, Cd, n, stream, ri, ci, A, B, hi, lo, den, cub
         gms = tr["ms_gemm"] / max(tr["gemm_launches"], 1)
         f8_tops = p * (p + 1) * n ** 3 / (gms * 1e-3) / 1e12
         bf16 = measured_peaks().get("bf16_tflops") or 1900.0
+        bf16s = measured_peaks().get("bf16_tflops_sustained")
         out["p%d" % p] = {"tflops": 2.0 * n ** 3 / (ms * 1e-3) / 1e12, "ms_per_step": ms,
                           "gemm_8bit_tops": f8_tops, "gemm_ms": gms,
                           "frac_of_fp8_peak": f8_tops / (2.0 * bf16),
                           "fp8_peak_tflops": 2.0 * bf16,
+                          "frac_of_fp8_peak_sustained": (f8_tops / (2.0 * bf16s)) if bf16s else None,
                           "algorithmic_bytes": p * 2 * n * n + 8 * n * n,
                           "dram_traffic_bytes": load_traffic("gemm_f8tc", "p%d_n%d" % (p, n)),
                           "err_max_rel_absAB": err, "speedup_vs_cublas_dgemm": 2.0 * n ** 3 / (ms * 1e-3) / 1e12 / cublas_tflops,
@@ -231,6 +233,7 @@ def scheme_II_leg(emu, h, Ad, Bd, Cd, n, stream, ri, ci, hi, lo, den, cublas_tfl
     import torch
     out = {}
     bf16 = measured_peaks().get("bf16_tflops") or 1900.0
+    bf16s = measured_peaks().get("bf16_tflops_sustained")
     for nm in (16, 20):
         def call():
             emu.check(emu.emu_dgemm(h.h, emu.EMU_ROW_MAJOR, n, n, n, 1.0, Ad.data_ptr(), n, Bd.data_ptr(), n, 0.0,
@@ -257,6 +260,7 @@ def scheme_II_leg(emu, h, Ad, Bd, Cd, n, stream, ri, ci, hi, lo, den, cublas_tfl
         out["nm%d" % nm] = {"tflops": 2.0 * n ** 3 / (ms * 1e-3) / 1e12, "ms_per_step": ms, "gemm_ms": gms,
                             "crt_ms": cms, "gemm_bf16_tflops": tc, "frac_of_bf16_peak": tc / bf16,
                             "frac_of_bf16_peak_with_crt": 2.0 * nm * n ** 3 / ((gms + cms) * 1e-3) / 1e12 / bf16,
+                            "frac_of_bf16_peak_sustained": (tc / bf16s) if bf16s else None,
                             "bf16_peak_tflops": bf16,
                             "err_max_rel_absAB": err,
                             "speedup_vs_cublas_dgemm": 2.0 * n ** 3 / (ms * 1e-3) / 1e12 / cublas_tflops,
@@ -398,10 +402,11 @@ def run_ours(args, rank, world, local_rank):
     e3 = torch.cuda.Event(enable_timing=True)
 
     def e2e_step():
-        Ad.copy_(A_pin, non_blocking=True)
-        Bd.copy_(B_pin, non_blocking=True)
-        step()
-        C_pin.copy_(Cd, non_blocking=True)
+        # the public host-buffer entry point: it copies A and B in, computes
+        # (Scheme I in row chunks whose copies overlap the GEMM) and returns
+        # once C is back in C_pin
+        emu.check(emu.emu_dgemm_host(h.h, emu.EMU_ROW_MAJOR, n, n, n, 1.0, A_pin.data_ptr(), n, B_pin.data_ptr(), n,
+                                     0.0, C_pin.data_ptr(), n, scheme_code, p, stream.cuda_stream), "emu_dgemm_host")
 
     # untimed warm-up: the first transfers from freshly pinned buffers pay a
     # one-time mapping cost (tens of ms per step when spread over the steps)
@@ -416,6 +421,9 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     ms_e2e = max_over_ranks(e2.elapsed_time(e3), dist, dev)
     e2e_value = aggregate_tflops(world, flops, args.steps, ms_e2e)
+    # the host-buffer result is the device result, bit for bit (sampled)
+    if not torch.equal(C_pin[::997, ::991], Cd[::997, ::991].cpu()):
+        raise RuntimeError("emu_dgemm_host result differs from emu_dgemm")
 
     extras = {}
     int8_peak = None

@@ -223,6 +223,27 @@ emu_status_t emu_cgemm(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n
                        int64_t ldb, const float *beta_host, float *C, int64_t ldc,
                        emu_scheme_t scheme, int p_or_nm, emu_stream_t stream);
 
+/* emu_dgemm on host-resident matrices: A_host, B_host, C_host are host
+ * memory (pinned, for the copies to overlap the computation; pageable
+ * memory works, but then each copy completes before the next step is
+ * queued).  Scheme I (EMU_SCHEME_I, EMU_SCHEME_I_F8) scales per row of A and
+ * per column of B (Sec. III-A), so the product is cut along the rows of C
+ * (of the row-major view: columns of C for EMU_COL_MAJOR) into up to four
+ * chunks of at least 1024 rows: B is copied to the device, scanned and
+ * split once, then each chunk's rows of A (and of C when beta != 0) are
+ * copied on a copy stream while the compute stream scans, splits and
+ * multiplies the chunk before and the copy stream returns the finished rows
+ * of C -- the result is bit-identical to emu_dgemm on device copies.  Other
+ * schemes copy the operands whole around emu_dgemm.  The handle owns the
+ * device staging (8 (m k + k n + m n) bytes, grown on demand by cudaMalloc)
+ * and the copy stream, so calls on one handle must not overlap.  The call
+ * returns once C_host holds the result (it synchronises `stream`).
+ * Arguments, layouts and return codes otherwise as emu_dgemm. */
+emu_status_t emu_dgemm_host(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k,
+                            double alpha, const double *A_host, int64_t lda, const double *B_host,
+                            int64_t ldb, double beta, double *C_host, int64_t ldc,
+                            emu_scheme_t scheme, int p_or_nm, emu_stream_t stream);
+
 /* Allocation-free Scheme I DGEMM.  The paper has no counterpart: this entry
  * point exists for callers that may not allocate device memory while they
  * run -- programs that reserve all device memory up front in their own pool,

@@ -55,6 +55,8 @@ _SIGS = {
     "emu_set_workspace": (_i32, [_vp, _vp, _sz]),
     "emu_dgemm": (_i32, [_vp, _i32, _i64, _i64, _i64, _dbl, _vp, _i64, _vp, _i64, _dbl, _vp, _i64, _i32,
                          _i32, _vp]),
+    "emu_dgemm_host": (_i32, [_vp, _i32, _i64, _i64, _i64, _dbl, _vp, _i64, _vp, _i64, _dbl, _vp, _i64, _i32,
+                              _i32, _vp]),
     "emu_sgemm": (_i32, [_vp, _i32, _i64, _i64, _i64, _flt, _vp, _i64, _vp, _i64, _flt, _vp, _i64, _i32,
                          _i32, _vp]),
     "emu_zgemm": (_i32, [_vp, _i32, _i64, _i64, _i64, _vp, _vp, _i64, _vp, _i64, _vp, _vp, _i64, _i32, _i32,
@@ -208,6 +210,43 @@ def dgemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, scheme="I", p: in
     h = handle or default_handle(A.device.index or 0)
     check(emu_dgemm(h.h, layout, m, n, k, alpha, _ptr(A), lda, _ptr(B), ldb, beta, _ptr(C), ldc,
                     _scheme(scheme), p, _stream_ptr(stream)), "emu_dgemm")
+    return C
+
+
+def dgemm_host(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, scheme="I", p: int = 7, handle=None,
+               stream=None):
+    """C = alpha*A@B + beta*C for float64 host matrices (numpy arrays or CPU
+    tensors; pinned CPU tensors let the copies overlap the computation)
+    through emu_dgemm_host; all three row-major (C-contiguous rows with any
+    leading dimension) or all column-major.  Returns C (a new numpy array if
+    C is None)."""
+    import numpy as np
+
+    def lay(x):
+        """(strides in elements, data pointer, number of elements)"""
+        if isinstance(x, np.ndarray):
+            return [v // x.itemsize for v in x.strides], x.ctypes.data, x.size
+        return list(x.stride()), x.data_ptr(), x.numel()
+
+    m, k = A.shape
+    n = B.shape[1]
+    if C is None:
+        C = np.empty((m, n), dtype=np.float64)
+        beta = 0.0
+    ops = [(lay(t), t.shape) for t in (A, B, C)]
+    pa, pb, pc = (o[0][1] for o in ops)
+    # an empty matrix fits either layout (its strides are arbitrary)
+    if all(st[1] == 1 or sh[1] <= 1 or sz == 0 for (st, _, sz), sh in ops):
+        layout = EMU_ROW_MAJOR
+        lds = [max(st[0] if sz else 0, sh[1], 1) for (st, _, sz), sh in ops]
+    elif all(st[0] == 1 or sh[0] <= 1 or sz == 0 for (st, _, sz), sh in ops):
+        layout = EMU_COL_MAJOR
+        lds = [max(st[1] if sz else 0, sh[0], 1) for (st, _, sz), sh in ops]
+    else:
+        raise ValueError("A, B and C must all be row-major or all column-major")
+    h = handle or default_handle(0)
+    check(emu_dgemm_host(h.h, layout, m, n, k, alpha, pa, lds[0], pb, lds[1], beta, pc, lds[2], _scheme(scheme), p,
+                         _stream_ptr(stream)), "emu_dgemm_host")
     return C
 
 

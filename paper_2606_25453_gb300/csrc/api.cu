@@ -553,19 +553,31 @@ emu_status_t run_scheme_I(emu_handle_s* h, const View& v, int64_t k, int p, doub
   launch_split_I<T>(A, v.ldA, v.a_kcontig, v.M, k, p, maxA, hatA, EA, st, f8);
   launch_split_I<T>(B, v.ldB, v.b_kcontig, v.N, k, p, maxB, hatB, FB, st, f8);
   trace_end(h, PH_SPLIT, st, 2);
+  return scheme_I_gemm(h, hatA, pl.rows_a, hatB, pl.rows_b, pl.cols, v.M, v.N, k, p, EA, FB, alpha, beta, C, ldc,
+                       out_mode, partials, st, f8);
+}
+
+// The fused Scheme I GEMM on split operands: hatA (rows_a padded rows) and
+// hatB (rows_b) in the interleaved slice layout, `cols` bytes per row; C
+// (M x N, leading dimension ldc) from the exact slice sums scaled by EA (M)
+// and FB (N).
+emu_status_t scheme_I_gemm(emu_handle_s* h, const int8_t* hatA, int64_t rows_a, const int8_t* hatB, int64_t rows_b,
+                           int64_t cols, int64_t M, int64_t N, int64_t k, int p, const int32_t* EA,
+                           const int32_t* FB, double alpha, double beta, void* C, int64_t ldc, int out_mode,
+                           int32_t* partials, cudaStream_t st, bool f8) {
   // E4M3 slices run on the tcgen05 kernel (A boxes of 128 B x 128 rows);
   // the INT8 engine uses the mma.sync kernel (32 B x 64 rows).
   const bool tc = f8 && !f8_engine_mma();
   CUtensorMap ta, tb;
-  if (!make_tmap_i8(&ta, hatA, static_cast<uint64_t>(pl.cols), static_cast<uint64_t>(pl.rows_a),
+  if (!make_tmap_i8(&ta, hatA, static_cast<uint64_t>(cols), static_cast<uint64_t>(rows_a),
                     tc ? 128u : 64u, tc ? 128 : 32) ||
-      !make_tmap_i8(&tb, hatB, static_cast<uint64_t>(pl.cols), static_cast<uint64_t>(pl.rows_b), 32))
+      !make_tmap_i8(&tb, hatB, static_cast<uint64_t>(cols), static_cast<uint64_t>(rows_b), 32))
     return tmap_err();
   GemmIArgs a{};
   a.descA = &ta;
   a.descB = &tb;
-  a.M = static_cast<int>(v.M);
-  a.N = static_cast<int>(v.N);
+  a.M = static_cast<int>(M);
+  a.N = static_cast<int>(N);
   a.nk32 = static_cast<int>((k + 31) / 32);
   a.kc32 = static_cast<int>((f8 ? host_chunk_len_F8(p) : host_chunk_len_I(p)) / 32);
   a.EA = EA;
@@ -714,7 +726,7 @@ emu_status_t emu_workspace_size(emu_scheme_t scheme, int64_t m, int64_t n, int64
 
 }  // extern "C"
 
-static emu_status_t gemm_common(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k,
+emu_status_t emu::gemm_common(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k,
                                 const void* A, int64_t lda, const void* B, int64_t ldb, const void* C,
                                 int64_t ldc, emu_scheme_t scheme, int p_or_nm) {
   if (!h) return EMU_ERR_INVALID_ARG;

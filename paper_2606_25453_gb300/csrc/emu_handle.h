@@ -17,6 +17,7 @@ struct emu_handle_s {
   void* grouped = nullptr;   // grouped-GEMM plan cache (grouped.cu)
   void* selector = nullptr;  // selector state (select.cu)
   void* trace = nullptr;     // per-phase timing state (trace.cu), null when off
+  void* hostio = nullptr;    // host-buffer entry point's staging and copy stream (host_api.cu)
 };
 
 namespace emu {
@@ -47,6 +48,18 @@ void normalize(emu_layout_t layout, int64_t m, int64_t n, const void* A, int64_t
 bool check_lds(emu_layout_t layout, int64_t m, int64_t n, int64_t k, int64_t lda, int64_t ldb, int64_t ldc);
 
 emu_status_t handle_workspace(emu_handle_s* h, size_t bytes, cudaStream_t st, uint8_t** out);
+
+// Argument checks shared by the emulated GEMM entry points; sets the
+// handle's device (api.cu).
+emu_status_t gemm_common(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n, int64_t k, const void* A,
+                         int64_t lda, const void* B, int64_t ldb, const void* C, int64_t ldc, emu_scheme_t scheme,
+                         int p_or_nm);
+
+// The fused Scheme I GEMM on operands already split (api.cu).
+emu_status_t scheme_I_gemm(emu_handle_s* h, const int8_t* hatA, int64_t rows_a, const int8_t* hatB, int64_t rows_b,
+                           int64_t cols, int64_t M, int64_t N, int64_t k, int p, const int32_t* EA,
+                           const int32_t* FB, double alpha, double beta, void* C, int64_t ldc, int out_mode,
+                           int32_t* partials, cudaStream_t st, bool f8);
 
 // C = beta * C for products with k == 0 (beta == 0 writes zeros, C is not read).
 template <typename T>
