@@ -32,8 +32,21 @@ HostIO* hostio_of(emu_handle_s* h) {
   return static_cast<HostIO*>(h->hostio);
 }
 
+void hostio_free_sync(HostIO* io) {
+  if (io->copy) cudaStreamDestroy(io->copy);
+  for (cudaEvent_t e : {io->ev_start, io->ev_b, io->ev_done})
+    if (e) cudaEventDestroy(e);
+  for (int c = 0; c < kMaxChunks; ++c) {
+    if (io->ev_a[c]) cudaEventDestroy(io->ev_a[c]);
+    if (io->ev_c[c]) cudaEventDestroy(io->ev_c[c]);
+  }
+  io->copy = nullptr;
+  io->ev_start = io->ev_b = io->ev_done = nullptr;
+  for (int c = 0; c < kMaxChunks; ++c) io->ev_a[c] = io->ev_c[c] = nullptr;
+}
+
 emu_status_t hostio_setup(HostIO* io, size_t bytes) {
-  if (!io->copy) {
+  if (!io->copy) {  // all or nothing: a partial set is released again
     bool ok = cudaStreamCreateWithFlags(&io->copy, cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&io->ev_start, cudaEventDisableTiming) == cudaSuccess &&
               cudaEventCreateWithFlags(&io->ev_b, cudaEventDisableTiming) == cudaSuccess &&
@@ -41,7 +54,11 @@ emu_status_t hostio_setup(HostIO* io, size_t bytes) {
     for (int c = 0; ok && c < kMaxChunks; ++c)
       ok = cudaEventCreateWithFlags(&io->ev_a[c], cudaEventDisableTiming) == cudaSuccess &&
            cudaEventCreateWithFlags(&io->ev_c[c], cudaEventDisableTiming) == cudaSuccess;
-    if (!ok) return EMU_ERR_CUDA;
+    if (!ok) {
+      cudaGetLastError();
+      hostio_free_sync(io);
+      return EMU_ERR_CUDA;
+    }
   }
   if (bytes > io->dev_bytes) {
     if (io->dev) {
@@ -75,13 +92,7 @@ void hostio_release(emu_handle_s* h) {
   auto* io = static_cast<HostIO*>(h->hostio);
   if (!io) return;
   if (io->dev) cudaFree(io->dev);
-  if (io->copy) cudaStreamDestroy(io->copy);
-  for (cudaEvent_t e : {io->ev_start, io->ev_b, io->ev_done})
-    if (e) cudaEventDestroy(e);
-  for (int c = 0; c < kMaxChunks; ++c) {
-    if (io->ev_a[c]) cudaEventDestroy(io->ev_a[c]);
-    if (io->ev_c[c]) cudaEventDestroy(io->ev_c[c]);
-  }
+  hostio_free_sync(io);
   delete io;
   h->hostio = nullptr;
 }
