@@ -611,17 +611,18 @@ def suite_markdown(paths):
             o.append(f"| {d['nm']} | {d['tflops']:.2f} | {bits(d['err'])} | {d['tflops'] / csg[8192]['tflops']:.2f}x |" if 8192 in csg else f"| {d['nm']} | {d['tflops']:.2f} | {bits(d['err'])} | - |")
     o.append("\n## Scheme II on the INT8 mma.sync engine (EMU_II_ENGINE=mma), same inputs\n")
     o.append("| n | phi | N_m | TFLOP/s | INT8 TOP/s | bits | bf16 tcgen05 speedup |\n|---|---|---|---|---|---|---|")
-    tc = {(d["phi"], d["nm"]): d["ms"] for d in rows if d["path"] == "emu_dgemm_II"}
+    tc = {(d["n"], d["phi"], d["nm"]): d["ms"] for d in rows if d["path"] == "emu_dgemm_II"}
     for d in rows:
         if d["path"] == "emu_dgemm_II_int8":
-            sp = d["ms"] / tc[(d["phi"], d["nm"])] if (d["phi"], d["nm"]) in tc else float("nan")
+            key = (d["n"], d["phi"], d["nm"])
+            sp = d["ms"] / tc[key] if key in tc else float("nan")
             o.append(f"| {d['n']} | {d['phi']:g} | {d['nm']} | {d['tflops']:.3f} | {d['tensor_tops']:.1f} | {bits(d['err'])} | {sp:.2f}x |")
     o.append("\n## Scheme II with norm-based scaling (EMU_SCHEME_II_NORM)\n")
     o.append("| n | phi | N_m | TFLOP/s | tensor TOP/s | bits | bits, worst-case scaling |\n|---|---|---|---|---|---|---|")
-    worst = {(d["phi"], d["nm"]): d["err"] for d in rows if d["path"] == "emu_dgemm_II"}
+    worst = {(d["n"], d["phi"], d["nm"]): d["err"] for d in rows if d["path"] == "emu_dgemm_II"}
     for d in rows:
         if d["path"] == "emu_dgemm_II_norm":
-            w = worst.get((d["phi"], d["nm"]))
+            w = worst.get((d["n"], d["phi"], d["nm"]))
             o.append(f"| {d['n']} | {d['phi']:g} | {d['nm']} | {d['tflops']:.3f} | {d['tensor_tops']:.1f} | {bits(d['err'])} | {bits(w) if w is not None else '-'} |")
     o.append("\n## Complex: ZGEMM (3M Scheme II, 4M Scheme I) and CGEMM, n = 8192, phi = 1\n")
     o.append("| path | scheme | p / N_m | TFLOP/s (8MNK) | bits |\n|---|---|---|---|---|")
@@ -954,19 +955,23 @@ def run_suite(path, args):
         return cache[key]
 
     def scheme_II_points():
-        """Scheme II DGEMM at n = 8192 with the engine of this process (the
-        default bf16 tcgen05 one, or INT8 mma.sync under EMU_II_ENGINE=mma)."""
+        """Scheme II DGEMM with the engine of this process (the default bf16
+        tcgen05 one, or INT8 mma.sync under EMU_II_ENGINE=mma): n = 8192 at
+        two phi and N_m = 8..20, and (default engine only) n = 4096 and 16384
+        at phi = 0.5 and N_m = 12, 16, 20."""
         engine = "int8 mma.sync" if os.environ.get("EMU_II_ENGINE") == "mma" else "bf16 tcgen05"
-        for phi in (0.5, 4.0):
-            if args.suite_part == "ii" and phi != 0.5:
-                continue
-            A, B, Ad, Bd = pair(8192, phi)
-            Cd = torch.empty((8192, 8192), dtype=torch.float64, device=dev)
-            for nm in ((12, 16, 20) if args.suite_part == "ii" else (8, 10, 12, 14, 16, 18, 20)):
-                ms = timed(lambda: emu.dgemm(Ad, Bd, Cd, scheme="II", p=nm, handle=h))
-                emit({"path": "emu_dgemm_II", "n": 8192, "phi": phi, "nm": nm, "tflops": 2 * 8192 ** 3 / ms / 1e9,
-                      "engine": engine, "tensor_tops": 2 * nm * 8192 ** 3 / ms / 1e9, "ms": ms,
+        pts = [(8192, 0.5, (12, 16, 20) if args.suite_part == "ii" else (8, 10, 12, 14, 16, 18, 20))]
+        if args.suite_part != "ii":
+            pts += [(8192, 4.0, (8, 10, 12, 14, 16, 18, 20)), (4096, 0.5, (12, 16, 20)), (16384, 0.5, (12, 16, 20))]
+        for n2, phi, nms in pts:
+            A, B, Ad, Bd = pair(n2, phi)
+            Cd = torch.empty((n2, n2), dtype=torch.float64, device=dev)
+            for nm in nms:
+                ms = timed(lambda: emu.dgemm(Ad, Bd, Cd, scheme="II", p=nm, handle=h), reps=1 if n2 > 8192 else 3)
+                emit({"path": "emu_dgemm_II", "n": n2, "phi": phi, "nm": nm, "tflops": 2 * n2 ** 3 / ms / 1e9,
+                      "engine": engine, "tensor_tops": 2 * nm * n2 ** 3 / ms / 1e9, "ms": ms,
                       "err": sampled_err(A, B, Cd.cpu().numpy())})
+            del Cd
 
     if args.suite_part == "ii":
         scheme_II_points()
