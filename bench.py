@@ -505,7 +505,10 @@ def run_ours(args, rank, world, local_rank):
                     "INT8 ops 2 N_m M N K" if args.scheme == "II" else
                     "exact E4M3 products p(p+1) M N K (multiply+add = 2)" if args.scheme == "I_F8" else
                     "INT8 ops p(p+1) M N K (multiply+add = 2)")
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        metric = METRIC if args.scheme == "I" else (
+            "emulated FP64 TFLOP/s (Scheme II DGEMM on %s tensor cores)" % ("bf16" if ii_tc else "INT8")
+            if args.scheme == "II" else "emulated FP64 TFLOP/s (Scheme I DGEMM on E4M3 tensor cores)")
+        line = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": ("e4m3->fp32 (f64 in/out)" if args.scheme == "I_F8" else
