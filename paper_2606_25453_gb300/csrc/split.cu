@@ -451,9 +451,8 @@ __device__ __forceinline__ int sym_residue(const int* d, const ModTables& mt, in
 // |a'|, negated for a negative element (|a'| < 2^b, so ND = ceil(b / 14),
 // rounded up to 2, 4 or 6, covers it; six cover 2^84).  Every partial sum of
 // t = sum_j d_j c_j is an integer with |t| <= 16383 (1 + 5 * 128) < 2^24, so
-// the FMA chain is exact; q = floor(RN(t / m + off / m)) is floor((t + off)
-// / m) or one off, r = t - q m is exact (|r| < 2^24), and one correction each
-// way gives the symmetric residue -- all on the FP32 pipe.
+// the FMA chain is exact, and sym_residue_f below takes the symmetric
+// residue of t on the FP32 pipe without a correction step.
 template <int ND>
 __device__ __forceinline__ void digits14f(uint64_t bits, int shift, float* d) {
   const ScaledInt s = scaled_trunc_bits(bits, shift);
