@@ -116,8 +116,10 @@ __device__ __forceinline__ double crt_finish(const uint32_t* S, const CrtTables&
 
 // ---------------------------------------------------------------- lazy form
 // S = sum_l w_l r_l kept as one 64-bit sum per 32-bit limb of w (each below
-// nm * 255 * 2^32 < 2^45, so no carries until the end), next to the binary32
-// estimate t = sum_l r_l (w_l / P) of S / P.
+// nm * 3 * 256 * 2^32 < 2^46 for residues r_l < 3 m_l, so no carries until
+// the end), next to the binary32 estimate t = sum_l r_l (w_l / P) of S / P.
+// Residues may exceed m_l (the complex modes add m_l or 2 m_l instead of
+// reducing): w_l m_l is a multiple of P, so S mod P is unchanged.
 struct CrtLazy {
   uint64_t s[kCrtLimbs];
   float t;
@@ -129,7 +131,7 @@ __device__ __forceinline__ void crt_lazy_init(CrtLazy& a) {
   a.t = 0.0f;
 }
 
-// a += w_l r_l, r in [0, m_l).  L: the number of 32-bit limbs of P (and so
+// a += w_l r_l, r in [0, 3 m_l).  L: the number of 32-bit limbs of P (and so
 // of every w_l < P); the limbs above stay zero, their products are skipped.
 template <int L = kCrtLimbs>
 __device__ __forceinline__ void crt_lazy_acc(CrtLazy& a, const CrtTables& ct, int l, uint32_t r) {
@@ -177,13 +179,14 @@ __device__ __forceinline__ void mul6(const uint32_t* P, uint32_t k, uint32_t* d)
       : "r"(P[0]), "r"(P[1]), "r"(P[2]), "r"(P[3]), "r"(P[4]), "r"(k));
 }
 
-// Eq. (8) finish from the lazy form: x = S - kP with k = rint(t), which is
-// round(S / P) or one off (t errs by less than 0.02 for up to 20 moduli), then
+// Eq. (8) finish from the lazy form: x = S - kP with k = rint(t) (below
+// 3 * 20 * 256), which is round(S / P) or one off (t errs by less than 0.02
+// for up to 20 moduli), then
 // one exact correction each way into the symmetric range (-P/2, P/2] (the
 // lift of S mod P: above floor(P/2) it becomes negative), rounded once to
 // binary64.  All limb arithmetic is exact; only the choice of k is estimated.
 __device__ __forceinline__ double crt_finish_lazy(const CrtLazy& a, const CrtTables& ct) {
-  // S in six 32-bit limbs: the 64-bit lazy sums (each < 2^45) overlap by 32 bits
+  // S in six 32-bit limbs: the 64-bit lazy sums (each < 2^46) overlap by 32 bits
   uint32_t S[kSL];
   {
     uint32_t l[kCrtLimbs], h[kCrtLimbs];

@@ -532,18 +532,24 @@ struct KParamsCRT {
   int plain;  // alpha = 1, beta = 0: C = the result (no FP64 update arithmetic)
 };
 
-// One thread per row and four consecutive columns: the CRT sums of Eq. (8)
-// from the residue planes (3M: Re = T1 - T2, Im = T3 - T1 - T2 mod m, Eq.
-// 16), S mod P with the symmetric lift, binary64, scaling and the update.
+// Output columns per thread of the CRT kernel: four in the real modes (one
+// 32-bit word per residue plane), two in the complex ones (three planes per
+// modulus in 16-bit words, so that every residue is loaded up front).
+constexpr int crt_cols(int mode) { return (mode == II_Z3M || mode == II_C3M) ? 2 : 4; }
+
+// One thread per row and crt_cols consecutive columns: the CRT sums of Eq.
+// (8) from the residue planes (3M: Re = T1 - T2, Im = T3 - T1 - T2 mod m,
+// Eq. 16), S mod P with the symmetric lift, binary64, scaling and the update.
 template <int MODE, int L>
 __global__ void __launch_bounds__(256) crt_II_kernel(const __grid_constant__ KParamsCRT kp,
                                                      const __grid_constant__ CrtTables ct,
                                                      const __grid_constant__ ModTables mt) {
   constexpr bool CPLX = MODE == II_Z3M || MODE == II_C3M;
+  constexpr int kCols = crt_cols(MODE);
   const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int ncq = (kp.N + 3) / 4;
+  const int ncq = (kp.N + kCols - 1) / kCols;
   if (idx >= static_cast<int64_t>(kp.M) * ncq) return;
-  const int row = static_cast<int>(idx / ncq), c0 = static_cast<int>(idx % ncq) * 4;
+  const int row = static_cast<int>(idx / ncq), c0 = static_cast<int>(idx % ncq) * kCols;
   const uint8_t* const p = kp.R + static_cast<int64_t>(row) * kp.ldr + c0;
   const int erow = kp.EA[row] + kp.escale;
   if constexpr (!CPLX) {
@@ -583,41 +589,42 @@ __global__ void __launch_bounds__(256) crt_II_kernel(const __grid_constant__ KPa
       }
     }
   } else {
-    CrtLazy are[4], aim[4];
+    // two columns per thread: all 3 N_m residue pairs (16-bit words) first,
+    // then the sums with every table index a compile-time constant
+    const int64_t set = static_cast<int64_t>(kp.nm) * kp.plane;
+    uint32_t v1[kMaxModuli], v2[kMaxModuli], v3[kMaxModuli];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int l = 0; l < kMaxModuli; ++l) {
+      const bool on = l < kp.nm;
+      const uint8_t* q = p + static_cast<int64_t>(l) * kp.plane;
+      v1[l] = on ? __ldg(reinterpret_cast<const unsigned short*>(q)) : 0u;
+      v2[l] = on ? __ldg(reinterpret_cast<const unsigned short*>(q + set)) : 0u;
+      v3[l] = on ? __ldg(reinterpret_cast<const unsigned short*>(q + 2 * set)) : 0u;
+    }
+    CrtLazy are[kCols], aim[kCols];
+#pragma unroll
+    for (int c = 0; c < kCols; ++c) {
       crt_lazy_init(are[c]);
       crt_lazy_init(aim[c]);
     }
-    // the next modulus's three words are loaded while this one's are summed
-    const int64_t set = static_cast<int64_t>(kp.nm) * kp.plane;
-    uint32_t n1 = __ldg(reinterpret_cast<const uint32_t*>(p));
-    uint32_t n2 = __ldg(reinterpret_cast<const uint32_t*>(p + set));
-    uint32_t n3 = __ldg(reinterpret_cast<const uint32_t*>(p + 2 * set));
-#pragma unroll 1
-    for (int l = 0; l < kp.nm; ++l) {
-      const int m = static_cast<int>(mt.mods[l]);
-      const uint32_t w1 = n1, w2 = n2, w3 = n3;
-      if (l + 1 < kp.nm) {
-        const uint8_t* q = p + static_cast<int64_t>(l + 1) * kp.plane;
-        n1 = __ldg(reinterpret_cast<const uint32_t*>(q));
-        n2 = __ldg(reinterpret_cast<const uint32_t*>(q + set));
-        n3 = __ldg(reinterpret_cast<const uint32_t*>(q + 2 * set));
-      }
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int t1 = (w1 >> (8 * c)) & 0xFF, t2 = (w2 >> (8 * c)) & 0xFF, t3 = (w3 >> (8 * c)) & 0xFF;
-        int re = t1 - t2;
-        if (re < 0) re += m;
-        int im = t3 - t1 - t2;
-        if (im < 0) im += m;
-        if (im < 0) im += m;
+    for (int l = 0; l < kMaxModuli; ++l) {
+      if (l >= kp.nm) break;
+      const int m = static_cast<int>(mt.mods[l]);
+#pragma unroll
+      for (int c = 0; c < kCols; ++c) {
+        // T1 - T2 and T3 - T1 - T2 modulo m, kept non-negative by adding m
+        // and 2m instead of reducing: w_l m_l is a multiple of P, so the
+        // offsets leave S mod P unchanged (residues below 3 m)
+        const int t1 = (v1[l] >> (8 * c)) & 0xFF, t2 = (v2[l] >> (8 * c)) & 0xFF, t3 = (v3[l] >> (8 * c)) & 0xFF;
+        const int re = t1 - t2 + m;
+        const int im = t3 - t1 - t2 + 2 * m;
         crt_lazy_acc<L>(are[c], ct, l, static_cast<uint32_t>(re));
         crt_lazy_acc<L>(aim[c], ct, l, static_cast<uint32_t>(im));
       }
     }
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < kCols; ++c) {
       const int cidx = c0 + c;
       if (cidx >= kp.N) break;
       const int sc = erow + kp.FB[cidx];
@@ -740,7 +747,7 @@ cudaError_t launch_crt(const GemmIIArgs& a, const ModTables& mt, const CrtTables
   kp.C = a.C;
   kp.ldc = a.ldc;
   kp.plain = a.alpha_re == 1.0 && a.alpha_im == 0.0 && a.beta_re == 0.0 && a.beta_im == 0.0;
-  const int64_t threads = static_cast<int64_t>(a.M) * ((a.N + 3) / 4);
+  const int64_t threads = static_cast<int64_t>(a.M) * ((a.N + crt_cols(MODE) - 1) / crt_cols(MODE));
   if (threads == 0) return cudaSuccess;
   // limbs of P: 3 for up to 12 moduli (P < 2^96), 4 up to 16 (P < 2^128), else 5
   const unsigned grid = static_cast<unsigned>((threads + 255) / 256);
