@@ -533,8 +533,9 @@ struct KParamsCRT {
 };
 
 // Output columns per thread of the CRT kernel: four in the real modes (one
-// 32-bit word per residue plane), two in the complex ones (three planes per
-// modulus in 16-bit words, so that every residue is loaded up front).
+// 32-bit word per residue plane; two measured no faster), two in the complex
+// ones (three planes per modulus in 16-bit words, so that every residue is
+// loaded up front).
 constexpr int crt_cols(int mode) { return (mode == II_Z3M || mode == II_C3M) ? 2 : 4; }
 
 // One thread per row and crt_cols consecutive columns: the CRT sums of Eq.
@@ -558,19 +559,24 @@ __global__ void __launch_bounds__(256) crt_II_kernel(const __grid_constant__ KPa
     // the kernel bound by memory latency
     uint32_t wl[kMaxModuli];
 #pragma unroll
-    for (int l = 0; l < kMaxModuli; ++l)
-      wl[l] = l < kp.nm ? __ldg(reinterpret_cast<const uint32_t*>(p + static_cast<int64_t>(l) * kp.plane)) : 0u;
-    CrtLazy acc[4];
+    for (int l = 0; l < kMaxModuli; ++l) {
+      const uint8_t* q = p + static_cast<int64_t>(l) * kp.plane;
+      if constexpr (kCols == 4)
+        wl[l] = l < kp.nm ? __ldg(reinterpret_cast<const uint32_t*>(q)) : 0u;
+      else
+        wl[l] = l < kp.nm ? __ldg(reinterpret_cast<const unsigned short*>(q)) : 0u;
+    }
+    CrtLazy acc[kCols];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) crt_lazy_init(acc[c]);
+    for (int c = 0; c < kCols; ++c) crt_lazy_init(acc[c]);
 #pragma unroll
     for (int l = 0; l < kMaxModuli; ++l) {
       if (l >= kp.nm) break;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) crt_lazy_acc<L>(acc[c], ct, l, (wl[l] >> (8 * c)) & 0xFFu);
+      for (int c = 0; c < kCols; ++c) crt_lazy_acc<L>(acc[c], ct, l, (wl[l] >> (8 * c)) & 0xFFu);
     }
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < kCols; ++c) {
       const int cidx = c0 + c;
       if (cidx >= kp.N) break;
       const double xr = scale2_fast(crt_finish_lazy(acc[c], ct), erow + kp.FB[cidx]);
