@@ -233,8 +233,12 @@ emu_status_t emu_cgemm(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t n
  * split once, then each chunk's rows of A (and of C when beta != 0) are
  * copied on a copy stream while the compute stream scans, splits and
  * multiplies the chunk before and the copy stream returns the finished rows
- * of C -- the result is bit-identical to emu_dgemm on device copies.  Other
- * schemes copy the operands whole around emu_dgemm.  The handle owns the
+ * of C -- the result is bit-identical to emu_dgemm on device copies.
+ * Scheme II (EMU_SCHEME_II, EMU_SCHEME_II_NORM) scales per row and column
+ * as well and runs the same way on the default bf16 tcgen05 engine (B's
+ * residues once, then each chunk of A through the residue GEMM and the
+ * CRT); the INT8 Scheme II engine and k = 0 copy the operands whole around
+ * emu_dgemm.  The handle owns the
  * device staging (8 (m k + k n + m n) bytes, grown on demand by cudaMalloc)
  * and the copy stream, so calls on one handle must not overlap.  The call
  * returns once C_host holds the result (it synchronises `stream`).

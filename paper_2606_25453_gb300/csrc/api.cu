@@ -600,15 +600,18 @@ template emu_status_t run_scheme_I<float>(emu_handle_s*, const View&, int64_t, i
                                           void*, int64_t, int, int32_t*, cudaStream_t, uint8_t*, bool);
 
 template <typename T>
+// Phases (declared in emu_handle.h): B's split once, then A in row chunks
+// (per-row scaling makes the chunks independent).
 emu_status_t run_scheme_II(emu_handle_s* h, const View& v, int64_t k, int nm, int cw, double ar,
                            double ai, double br, double bi, void* C, int64_t ldc, int out_mode,
-                           uint8_t* residues, cudaStream_t st, bool norm = false) {
+                           uint8_t* residues, cudaStream_t st, bool norm, int phase, int64_t plan_rows) {
   const int nsets = cw == 2 ? 3 : 1;
   // the tcgen05 kernel takes bf16 residue planes; the INT8 kernel sums a
   // modulus's products over the whole K in INT32 (|sum| <= k 2^14)
   const bool tc = out_mode != II_RESIDUES && ii_engine_tc();
   if (!tc && k > EMU_K_MAX_II) return EMU_ERR_UNSUPPORTED;
-  Plan pl = plan_II(v.M, v.N, k, nm, nsets, tc ? 2 : 1);
+  Plan pl = plan_II(plan_rows > 0 ? plan_rows : v.M, v.N, k, nm, nsets, tc ? 2 : 1);
+  pl.rows_a = split_rows(v.M);  // A's planes are laid out for this call's rows
   uint8_t* ws = nullptr;
   emu_status_t s = handle_workspace(h, pl.bytes, st, &ws);
   if (s != EMU_OK) return s;
@@ -630,20 +633,24 @@ emu_status_t run_scheme_II(emu_handle_s* h, const View& v, int64_t k, int nm, in
   host_mod_tables(nm, &mt);
   CrtTables ct;
   host_crt_tables(nm, &ct);
+  const bool do_a = phase != 1, do_b = phase != 2;
   trace_begin(h, PH_SCAN, st);
-  launch_scan<T>(A, v.ldA, v.a_kcontig, v.M, k, cw, maxA, h->status, st);
-  launch_scan<T>(B, v.ldB, v.b_kcontig, v.N, k, cw, maxB, h->status, st);
-  if (norm) {
+  if (do_a) launch_scan<T>(A, v.ldA, v.a_kcontig, v.M, k, cw, maxA, h->status, st);
+  if (do_b) launch_scan<T>(B, v.ldB, v.b_kcontig, v.N, k, cw, maxB, h->status, st);
+  if (norm && do_a)
     launch_norm<T>(A, v.ldA, v.a_kcontig, v.M, k, cw, maxA, reinterpret_cast<unsigned long long*>(ws + pl.off_accA),
                    nEA, st);
+  if (norm && do_b)
     launch_norm<T>(B, v.ldB, v.b_kcontig, v.N, k, cw, maxB, reinterpret_cast<unsigned long long*>(ws + pl.off_accB),
                    nEB, st);
-  }
-  trace_end(h, PH_SCAN, st, norm ? 6 : 2);
+  trace_end(h, PH_SCAN, st, (do_a + do_b) * (norm ? 3 : 1));
   trace_begin(h, PH_SPLIT, st);
-  launch_split_II<T>(A, v.ldA, v.a_kcontig, v.M, k, nm, bA, cw, mt, maxA, resA, EA, st, norm ? nEA : nullptr, tc);
-  launch_split_II<T>(B, v.ldB, v.b_kcontig, v.N, k, nm, bB, cw, mt, maxB, resB, FB, st, norm ? nEB : nullptr, tc);
-  trace_end(h, PH_SPLIT, st, 2);
+  if (do_a)
+    launch_split_II<T>(A, v.ldA, v.a_kcontig, v.M, k, nm, bA, cw, mt, maxA, resA, EA, st, norm ? nEA : nullptr, tc);
+  if (do_b)
+    launch_split_II<T>(B, v.ldB, v.b_kcontig, v.N, k, nm, bB, cw, mt, maxB, resB, FB, st, norm ? nEB : nullptr, tc);
+  trace_end(h, PH_SPLIT, st, do_a + do_b);
+  if (phase == 1) return cuda_err(cudaGetLastError());
   CUtensorMap ta, tb;
   // tcgen05: the bf16 planes as bytes, 128-byte (64-element) boxes of 128
   // rows (A) and 256 / cluster rows (B: a CTA pair loads half of each
@@ -694,6 +701,11 @@ emu_status_t run_scheme_II(emu_handle_s* h, const View& v, int64_t k, int nm, in
   trace_end(h, PH_OTHER, st, 1);
   return cuda_err(e);
 }
+
+template emu_status_t run_scheme_II<double>(emu_handle_s*, const View&, int64_t, int, int, double, double, double,
+                                            double, void*, int64_t, int, uint8_t*, cudaStream_t, bool, int, int64_t);
+template emu_status_t run_scheme_II<float>(emu_handle_s*, const View&, int64_t, int, int, double, double, double,
+                                           double, void*, int64_t, int, uint8_t*, cudaStream_t, bool, int, int64_t);
 
 template <typename T>
 void launch_scale_c(T* C, int64_t ldc, int64_t M, int64_t N, double beta, cudaStream_t st) {

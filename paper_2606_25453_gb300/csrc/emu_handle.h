@@ -55,6 +55,16 @@ emu_status_t gemm_common(emu_handle_t h, emu_layout_t layout, int64_t m, int64_t
                          int64_t lda, const void* B, int64_t ldb, const void* C, int64_t ldc, emu_scheme_t scheme,
                          int p_or_nm);
 
+// Scheme II on the row-major view (api.cu).  phase: 0 the whole product;
+// 1 only B's scan and split; 2 the rest, with B's split from an earlier
+// phase-1 call on the same workspace.  plan_rows: the rows of A the
+// workspace is laid out for (at least v.M; 0 means v.M), the same in the
+// phase-1 and phase-2 calls of one product.
+template <typename T>
+emu_status_t run_scheme_II(emu_handle_s* h, const View& v, int64_t k, int nm, int cw, double ar, double ai,
+                           double br, double bi, void* C, int64_t ldc, int out_mode, uint8_t* residues,
+                           cudaStream_t st, bool norm = false, int phase = 0, int64_t plan_rows = 0);
+
 // The fused Scheme I GEMM on operands already split (api.cu).
 emu_status_t scheme_I_gemm(emu_handle_s* h, const int8_t* hatA, int64_t rows_a, const int8_t* hatB, int64_t rows_b,
                            int64_t cols, int64_t M, int64_t N, int64_t k, int p, const int32_t* EA,

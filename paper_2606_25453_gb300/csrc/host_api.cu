@@ -7,8 +7,11 @@
 // view) is copied, scanned and split once; the rows of A then go in chunks,
 // each chunk's copy to the device, exponent scan, split and fused GEMM
 // running on the compute stream while a copy stream brings in the next
-// chunks and takes the finished rows of C back.  Scheme II, k = 0 and small
-// products copy the operands whole around emu_dgemm.
+// chunks and takes the finished rows of C back.  Scheme II scales per row
+// of A and per column of B as well, and runs the same way on the bf16
+// tcgen05 engine (B split once, then each chunk of A through the residue
+// GEMM and the CRT); k = 0, the INT8 Scheme II engine and products below
+// 2048 rows copy the operands whole around emu_dgemm.
 #include <algorithm>
 
 #include "emu_handle.h"
@@ -118,7 +121,10 @@ emu_status_t host_gemm(emu_handle_s* h, HostIO* io, const View& v, int64_t k, do
   if (cudaEventRecord(io->ev_start, st) != cudaSuccess || cudaStreamWaitEvent(cs, io->ev_start, 0) != cudaSuccess)
     return EMU_ERR_CUDA;
   const bool sI = (scheme == EMU_SCHEME_I || scheme == EMU_SCHEME_I_F8) && k > 0;
-  const int nch = sI ? static_cast<int>(std::min<int64_t>(kMaxChunks, std::max<int64_t>(1, M / 1024))) : 1;
+  // Scheme II in chunks on the bf16 tcgen05 engine (the INT8 engine takes
+  // the whole product)
+  const bool sII = (scheme == EMU_SCHEME_II || scheme == EMU_SCHEME_II_NORM) && k > 0 && ii_engine_tc();
+  const int nch = (sI || sII) ? static_cast<int>(std::min<int64_t>(kMaxChunks, std::max<int64_t>(1, M / 1024))) : 1;
   // chunk rows: a multiple of the split's row padding, so that each chunk's
   // slices start on a padded row of the whole split
   const int64_t R = split_rows((M + nch - 1) / nch);
@@ -132,7 +138,26 @@ emu_status_t host_gemm(emu_handle_s* h, HostIO* io, const View& v, int64_t k, do
   }
   if (!ok) return EMU_ERR_CUDA;
   emu_status_t s = EMU_OK;
-  if (!sI) {
+  if (sII) {
+    // B's scan and split once (phase 1), then each chunk of A through the
+    // rest of the product (phase 2) on a workspace laid out for R rows
+    const bool norm = scheme == EMU_SCHEME_II_NORM;
+    View vb{R, N, dA, std::max<int64_t>(k, 1), true, dB, N, false};
+    if (cudaStreamWaitEvent(st, io->ev_b, 0) != cudaSuccess) return EMU_ERR_CUDA;
+    s = run_scheme_II<double>(h, vb, k, p, 1, alpha, 0.0, beta, 0.0, dC, N, II_F64, nullptr, st, norm, 1, R);
+    if (s != EMU_OK) return s;
+    for (int c = 0; c < nch; ++c) {
+      const int64_t r0 = c * R, rows = std::min(R, M - r0);
+      View vc{rows, N, dA + r0 * k, k, true, dB, N, false};
+      if (cudaStreamWaitEvent(st, io->ev_a[c], 0) != cudaSuccess) return EMU_ERR_CUDA;
+      s = run_scheme_II<double>(h, vc, k, p, 1, alpha, 0.0, beta, 0.0, dC + r0 * N, N, II_F64, nullptr, st, norm, 2,
+                                R);
+      if (s != EMU_OK) return s;
+      if (cudaEventRecord(io->ev_c[c], st) != cudaSuccess || cudaStreamWaitEvent(cs, io->ev_c[c], 0) != cudaSuccess ||
+          copy_rows(C_host, ldc, dC, N, r0, rows, N, cudaMemcpyDeviceToHost, cs) != cudaSuccess)
+        return EMU_ERR_CUDA;
+    }
+  } else if (!sI) {
     // whole operands around emu_dgemm on the row-major view
     if (cudaStreamWaitEvent(st, io->ev_a[0], 0) != cudaSuccess) return EMU_ERR_CUDA;
     s = emu_dgemm(h, EMU_ROW_MAJOR, M, N, k, alpha, dA, std::max<int64_t>(k, 1), dB, N, beta, dC, N, scheme, p, st);

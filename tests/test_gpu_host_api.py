@@ -1,9 +1,10 @@
-"""emu_dgemm_host (host-resident A, B, C; Scheme I in row chunks whose copies
-overlap the computation, other schemes whole) against emu_dgemm on device
-copies of the same matrices, bit for bit, and against the oracle: several
-chunks with a ragged last one, both layouts with padded leading dimensions,
-beta != 0, pinned and pageable host memory, Scheme II, k = 0, and a
-product below the chunk size."""
+"""emu_dgemm_host (host-resident A, B, C; Scheme I and the bf16 Scheme II
+engine in row chunks whose copies overlap the computation) against
+emu_dgemm on device copies of the same matrices, bit for bit, and against
+the oracle: several chunks with a ragged last one, both layouts with padded
+leading dimensions, beta != 0, pinned and pageable host memory, Scheme II
+with worst-case and norm scaling, k = 0, and a product below the chunk
+size."""
 import numpy as np
 import pytest
 
@@ -69,12 +70,22 @@ def test_column_major_four_chunks(h):
 
 
 @pytest.mark.parametrize("scheme,p", [("II", 14), ("II_NORM", 12)])
-def test_scheme_II_whole(h, scheme, p):
-    m, n, k = 1100, 300, 2000
+@pytest.mark.parametrize("m", [1100, 2100])
+def test_scheme_II_chunks(orc, h, scheme, p, m):
+    # 1100 rows: one chunk through the split-B-then-A phases; 2100: two
+    # chunks (1152 and 948 rows) sharing B's split, beta != 0
+    n, k = 300, 2000
     A, B = synth.gemm_pair(m, n, k, 1.0, 84)
-    C = emu.dgemm_host(A, B, scheme=scheme, p=p, handle=h)
-    Cd = emu.dgemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), scheme=scheme, p=p, handle=h)
-    assert np.array_equal(C, Cd.cpu().numpy())
+    C0 = synth.test_matrix(m, n, 1.0, 87)
+    Ch = padded_host(C0, 2, True)
+    emu.dgemm_host(padded_host(A, 1, True), B, Ch, alpha=1.5, beta=0.25, scheme=scheme, p=p, handle=h)
+    Cd = torch.from_numpy(C0).cuda()
+    emu.dgemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), Cd, alpha=1.5, beta=0.25, scheme=scheme, p=p,
+              handle=h)
+    torch.cuda.synchronize()
+    assert h.status() == 0
+    assert np.array_equal(Ch.numpy(), Cd.cpu().numpy())
+    assert np.array_equal(Ch.numpy(), orc.emu_II(A, B, p, alpha=1.5, beta=0.25, C=C0, norm=scheme == "II_NORM"))
 
 
 def test_small_and_k0(orc, h):
