@@ -80,3 +80,37 @@ def test_random_case(orc, h, i):
         Bh = np.array(B, order="F" if layout == "col" else "C")
         emu.dgemm_host(Ah, Bh, Ch, alpha=alpha, beta=beta, scheme=scheme, p=p, handle=h)
         assert np.array_equal(Ch, ref), case(i)
+
+
+def zcase(i):
+    rng = np.random.Generator(np.random.PCG64(19000 + i))
+    m, n, k = (int(rng.choice(SIZES)) for _ in range(3))
+    scheme = ["II", "I", "I_F8", "II_NORM"][i % 4]
+    p = int(rng.integers(4, 21)) if scheme.startswith("II") else int(rng.integers(3, 9)) if scheme == "I" else \
+        int(rng.integers(6, 13))
+    alpha = complex(rng.choice([1.0, -0.5])) + 1j * float(rng.choice([0.0, 0.75]))
+    beta = complex(rng.choice([0.0, 0.0, 1.0])) + 1j * float(rng.choice([0.0, -0.25]))
+    f32 = rng.random() < 0.3
+    return m, n, k, scheme, p, alpha, beta, f32
+
+
+@pytest.mark.parametrize("i", range(32))
+def test_random_complex_case(orc, h, i):
+    m, n, k, scheme, p, alpha, beta, f32 = zcase(i)
+    A, B = synth.gemm_pair_complex(m, n, k, 1.0, 19500 + i)
+    C0 = synth.test_matrix_complex(m, n, 1.0, 19600 + i)
+    if f32:  # CGEMM (complex64): the oracle takes the rounded inputs as given
+        A, B, C0 = A.astype(np.complex64), B.astype(np.complex64), C0.astype(np.complex64)
+    Cd = torch.from_numpy(np.ascontiguousarray(C0)).cuda()
+    Ad, Bd = torch.from_numpy(np.ascontiguousarray(A)).cuda(), torch.from_numpy(np.ascontiguousarray(B)).cuda()
+    if f32:
+        emu.cgemm(Ad, Bd, Cd, alpha=alpha, beta=beta, p=p, scheme=scheme, handle=h)
+    else:
+        emu.zgemm(Ad, Bd, Cd, alpha=alpha, beta=beta, nm=p, scheme=scheme, p=p, handle=h)
+    torch.cuda.synchronize()
+    assert h.status() == 0, zcase(i)
+    if scheme.startswith("II"):
+        ref = orc.emu_Z3M(A, B, p, alpha=alpha, beta=beta, C=C0, out_f32=f32, norm=scheme == "II_NORM")
+    else:
+        ref = orc.emu_Z4M_I(A, B, p, f8=scheme == "I_F8", alpha=alpha, beta=beta, C=C0, out_f32=f32)
+    assert np.array_equal(Cd.cpu().numpy(), ref), zcase(i)
