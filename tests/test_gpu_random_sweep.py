@@ -114,3 +114,35 @@ def test_random_complex_case(orc, h, i):
     else:
         ref = orc.emu_Z4M_I(A, B, p, f8=scheme == "I_F8", alpha=alpha, beta=beta, C=C0, out_f32=f32)
     assert np.array_equal(Cd.cpu().numpy(), ref), zcase(i)
+
+
+@pytest.mark.parametrize("count", [1, 7, 8, 9, 40])
+def test_random_grouped_batch(orc, tmp_path, count):
+    # batch sizes around the staging threshold (one stage below 8 products),
+    # random shapes with padded leading dimensions, alpha/beta per product,
+    # random configurations per shape bucket from a tuning file
+    rng = np.random.Generator(np.random.PCG64(29000 + count))
+    p = int(rng.integers(3, 9))
+    lines = ['  "p%d_s%d_k%d": %d' % (p, sc, kc, int(rng.integers(0, 6))) for sc in range(5) for kc in range(5)]
+    path = tmp_path / "tune.json"
+    path.write_text("{\n" + ",\n".join(lines) + "\n}\n")
+    hd = emu.Handle(0)
+    emu.check(emu.emu_load_tuning(hd.h, str(path).encode()))
+    mats, As, Bs, Cs, C0s, al, be = [], [], [], [], [], [], []
+    for i in range(count):
+        m, n, k = (int(rng.choice(SIZES)) for _ in range(3))
+        A, B = synth.gemm_pair(m, n, k, float(rng.choice([0.5, 2.0])), 29100 + 50 * count + i)
+        C0 = synth.test_matrix(m, n, 1.0, 29200 + 50 * count + i)
+        mats.append((A, B))
+        As.append(on_device(A, "row", int(rng.integers(0, 3))))
+        Bs.append(on_device(B, "row", int(rng.integers(0, 3))))
+        Cs.append(on_device(C0, "row", int(rng.integers(0, 3))))
+        C0s.append(C0)
+        al.append(float(rng.choice([1.0, -2.0])))
+        be.append(float(rng.choice([0.0, 0.5])))
+    emu.dgemm_grouped(emu.grouped_descs(As, Bs, Cs, al, be), p, handle=hd)
+    torch.cuda.synchronize()
+    assert hd.status() == 0
+    for (A, B), C, C0, a, b in zip(mats, Cs, C0s, al, be):
+        assert np.array_equal(C.cpu().numpy(), orc.emu_I(A, B, p, alpha=a, beta=b, C=C0))
+    hd.close()
