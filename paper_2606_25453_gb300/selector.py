@@ -154,15 +154,66 @@ def init_params(seed=0):
     return theta
 
 
-def train(X, y, epochs=60, batch=512, lr=2e-3, seed=0, log=None):
+CKPT_VERSION = 1
+
+
+def save_checkpoint(path, params, m, v, step, epoch, rng_state, hist, seed, lr):
+    """Training state after `epoch` finished epochs: the parameters, Adam's
+    moment estimates and step count, the state of the shuffling generator
+    and the loss history, written atomically (a temporary file, then a
+    rename), so that an interrupted run leaves the last complete state."""
+    meta = {"version": CKPT_VERSION, "n_param": int(SEL_NPARAM), "step": int(step), "epoch": int(epoch),
+            "rng": rng_state, "hist": [float(x) for x in hist], "seed": int(seed), "lr": float(lr)}
+    tmp = "%s.tmp.%d" % (path, os.getpid())
+    try:
+        with open(tmp, "wb") as fh:
+            np.savez(fh, params=np.asarray(params, dtype=np.float32), m=np.asarray(m, dtype=np.float32),
+                     v=np.asarray(v, dtype=np.float32), meta=np.frombuffer(json.dumps(meta).encode(), dtype=np.uint8))
+        os.replace(tmp, path)
+    except BaseException:
+        if os.path.exists(tmp):
+            os.remove(tmp)
+        raise
+
+
+def load_checkpoint(path):
+    """The state save_checkpoint wrote: dict with params, m, v (float32
+    arrays) and step, epoch, rng, hist, seed, lr; ValueError for another
+    format version or network size."""
+    with np.load(path) as z:
+        meta = json.loads(bytes(z["meta"]).decode())
+        if meta.get("version") != CKPT_VERSION or meta.get("n_param") != SEL_NPARAM:
+            raise ValueError("selector checkpoint %s: version %s, %s parameters (expected %d, %d)" %
+                             (path, meta.get("version"), meta.get("n_param"), CKPT_VERSION, SEL_NPARAM))
+        out = {k: np.array(z[k], dtype=np.float32) for k in ("params", "m", "v")}
+    out.update({k: meta[k] for k in ("step", "epoch", "rng", "hist", "seed", "lr")})
+    return out
+
+
+def train(X, y, epochs=60, batch=512, lr=2e-3, seed=0, log=None, checkpoint=None, resume=False):
     """Adam on the mean cross-entropy with the library's kernels; returns
-    (params float32 [8968], loss history)."""
+    (params float32 [8968], loss history).  checkpoint: a file that receives
+    the training state after every epoch; resume: continue from it (same
+    data, seed and learning rate) up to `epochs` epochs in total."""
     torch = _torch()
     h = default_handle(0)
     dev = torch.device("cuda")
-    prm = torch.from_numpy(init_params(seed)).to(dev)
-    m = torch.zeros_like(prm)
-    v = torch.zeros_like(prm)
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    step, start, hist = 0, 0, []
+    if resume and checkpoint and os.path.exists(checkpoint):
+        ck = load_checkpoint(checkpoint)
+        if ck["seed"] != seed or ck["lr"] != lr:
+            raise ValueError("selector checkpoint %s was written with seed %d, lr %g" %
+                             (checkpoint, ck["seed"], ck["lr"]))
+        prm, m, v = (torch.from_numpy(ck[k]).to(dev) for k in ("params", "m", "v"))
+        step, start, hist = ck["step"], ck["epoch"], list(ck["hist"])
+        rng.bit_generator.state = ck["rng"]
+        if log:
+            log("resumed from %s after epoch %d (step %d)" % (checkpoint, start, step))
+    else:
+        prm = torch.from_numpy(init_params(seed)).to(dev)
+        m = torch.zeros_like(prm)
+        v = torch.zeros_like(prm)
     grad = torch.zeros_like(prm)
     lossd = torch.zeros(1, dtype=torch.float32, device=dev)
     Xd = torch.from_numpy(X).to(dev)
@@ -170,11 +221,8 @@ def train(X, y, epochs=60, batch=512, lr=2e-3, seed=0, log=None):
     n = len(y)
     P = torch.empty((batch, 8), dtype=torch.float32, device=dev)
     act = torch.empty((batch, 128), dtype=torch.float32, device=dev)
-    rng = np.random.Generator(np.random.PCG64(seed + 1))
     sp = _stream_ptr(None)
-    step = 0
-    hist = []
-    for ep in range(epochs):
+    for ep in range(start, epochs):
         perm = torch.from_numpy(rng.permutation(n)).to(dev)
         tot = 0.0
         nb = 0
@@ -192,6 +240,9 @@ def train(X, y, epochs=60, batch=512, lr=2e-3, seed=0, log=None):
             tot += float(lossd.item())
             nb += 1
         hist.append(tot / max(nb, 1))
+        if checkpoint:
+            save_checkpoint(checkpoint, prm.cpu().numpy(), m.cpu().numpy(), v.cpu().numpy(), step, ep + 1,
+                            rng.bit_generator.state, hist, seed, lr)
         if log and (ep % 10 == 0 or ep == epochs - 1):
             log("epoch %d loss %.4f" % (ep, hist[-1]))
     return prm.cpu().numpy(), hist
@@ -432,6 +483,8 @@ def main(argv=None):
     ap.add_argument("--report", default=None)
     ap.add_argument("--scheme", default="I", choices=["I", "II"],
                     help="I: slices p = 3..10; II: moduli N = 6..20 of Scheme II with norm scaling")
+    ap.add_argument("--checkpoint", default=None, help="file for the training state after every epoch")
+    ap.add_argument("--resume", action="store_true", help="continue the training from --checkpoint")
     a = ap.parse_args(argv)
     if a.scheme == "II" and a.out == WEIGHTS:
         a.out = WEIGHTS_II
@@ -443,7 +496,7 @@ def main(argv=None):
     t_data = time.time() - t0
     X, y, _ = expand(ftr, etr)
     t1 = time.time()
-    params, hist = train(X, y, epochs=a.epochs, log=log)
+    params, hist = train(X, y, epochs=a.epochs, log=log, checkpoint=a.checkpoint, resume=a.resume)
     t_train = time.time() - t1
     res = (evaluate_II if a.scheme == "II" else evaluate)(params, fev, eev, kev, etr)
     meta = {"scheme": a.scheme, "n_train": a.n_train, "n_eval": a.n_eval, "epochs": a.epochs, "final_loss": hist[-1],

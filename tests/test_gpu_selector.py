@@ -1,7 +1,7 @@
 """Learned slice-count selector on the GPU: the feature, MLP forward/backward,
 Adam and double-double probe kernels against the CPU oracle, the auto-
-precision entry point, and a small training run that must beat the fixed
-choice of p at the same tolerance."""
+precision entry point, a small training run that must beat the fixed
+choice of p at the same tolerance, and training resumed from a checkpoint."""
 import ctypes
 import math
 
@@ -129,6 +129,25 @@ def test_training_beats_fixed_p(h):
     A, B = synth.gemm_pair(256, 256, 512, 2.0, 77)
     C, p, code = emu.dgemm_auto(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), 1e-8, handle=h)
     assert code == 0 and 3 <= p <= emu.EMU_P_MAX
+
+
+def test_training_resumes_from_checkpoint(tmp_path):
+    """A run stopped after 3 of 6 epochs and resumed from its checkpoint ends
+    where the uninterrupted run ends: the same shuffles and Adam state, so the
+    same loss curve and parameters up to the order of the gradient atomics."""
+    ftr, etr, _, _ = sel.build_dataset(256, 21)
+    X, y, _ = sel.expand(ftr, etr)
+    full, hist_full = sel.train(X, y, epochs=6, batch=256, lr=3e-3, seed=4)
+    ck = str(tmp_path / "sel.ckpt")
+    _, hist_a = sel.train(X, y, epochs=3, batch=256, lr=3e-3, seed=4, checkpoint=ck)
+    assert sel.load_checkpoint(ck)["epoch"] == 3
+    resumed, hist_b = sel.train(X, y, epochs=6, batch=256, lr=3e-3, seed=4, checkpoint=ck, resume=True)
+    assert len(hist_b) == 6 and hist_b[:3] == hist_a
+    assert np.allclose(hist_b, hist_full, rtol=1e-3)
+    assert np.allclose(resumed, full, rtol=1e-2, atol=1e-3)
+    assert sel.load_checkpoint(ck)["epoch"] == 6
+    with pytest.raises(ValueError):  # another learning rate is refused
+        sel.train(X, y, epochs=8, batch=256, lr=1e-3, seed=4, checkpoint=ck, resume=True)
 
 
 def test_auto_II_bound_and_escalation(h):
