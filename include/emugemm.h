@@ -165,7 +165,9 @@ emu_status_t emu_set_workspace(emu_handle_t h, void *workspace_dev, size_t bytes
  * split, gemm, other -- on the bf16 Scheme II engine "gemm" is the residue
  * GEMM and "other" the CRT kernel), the number of GEMM launches and of all kernel
  * launches since the last read, then clears the counters.  Not available
- * while a stream is being captured into a CUDA graph. */
+ * while a stream is being captured into a CUDA graph.  Independently of
+ * this switch, the host-side launches of each phase sit in an NVTX range
+ * named emu.scan, emu.split, emu.gemm or emu.other (for profilers). */
 emu_status_t emu_trace_enable(emu_handle_t h, int enable);
 emu_status_t emu_trace_read(emu_handle_t h, double *ms_host, int64_t *gemm_launches_host,
                             int64_t *kernel_launches_host);
