@@ -155,7 +155,14 @@ emu_status_t emu_workspace_size(emu_scheme_t scheme, int64_t m, int64_t n, int64
 /* Give the handle a caller-owned workspace (device pointer, 256-byte
  * aligned).  Calls that need more than `bytes` return EMU_ERR_ALLOC instead
  * of allocating.  Passing NULL returns to library-owned workspace, which is
- * grown with cudaMallocAsync on the call's stream when needed. */
+ * grown with cudaMallocAsync on the call's stream when needed.
+ * CUDA graphs: emu_dgemm, emu_sgemm, emu_zgemm, emu_cgemm and the step
+ * entry points may be captured on their stream once the workspace is large
+ * enough for the call (after an uncaptured call of the same shape, or with
+ * a caller-owned workspace); a call that would have to grow the
+ * library-owned workspace while its stream is capturing returns
+ * EMU_ERR_ALLOC and enqueues nothing.  emu_dgemm_host, emu_dgemm_auto(_II)
+ * and emu_get_status synchronise and cannot be captured. */
 emu_status_t emu_set_workspace(emu_handle_t h, void *workspace_dev, size_t bytes);
 
 /* Tracing: when enabled, every call records CUDA events on its stream around

@@ -307,6 +307,13 @@ emu_status_t handle_workspace(emu_handle_s* h, size_t bytes, cudaStream_t st, ui
     return EMU_OK;
   }
   if (bytes > h->ws_bytes) {
+    // no growth inside a stream capture: the memory would belong to the
+    // graph, and the handle would keep using it after the capture
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+      cudaGetLastError();
+      return EMU_ERR_ALLOC;
+    }
     if (h->ws) cudaFreeAsync(h->ws, st);
     h->ws = nullptr;
     h->ws_bytes = 0;
