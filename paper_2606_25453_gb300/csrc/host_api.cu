@@ -64,10 +64,9 @@ emu_status_t hostio_setup(HostIO* io, size_t bytes) {
     }
   }
   if (bytes > io->dev_bytes) {
-    if (io->dev) {
-      cudaDeviceSynchronize();
-      cudaFree(io->dev);
-    }
+    // every earlier call waited for its copies and kernels before returning,
+    // so nothing in flight still uses the old staging buffer
+    if (io->dev) cudaFree(io->dev);
     io->dev = nullptr;
     io->dev_bytes = 0;
     if (cudaMalloc(&io->dev, bytes) != cudaSuccess) {
