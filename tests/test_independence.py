@@ -1,8 +1,9 @@
 """The oracle and the CUDA path stay independent: no source of the library
 package imports or includes anything of the oracle, no oracle source
 refers to the package, its kernels or its header, the shared input module
-imports neither side, and outside tests/ only the build/smoke entry points
-and the benchmark's CPU legs import the oracle."""
+imports neither side, outside tests/ only the build/smoke entry points
+and the benchmark's CPU legs import the oracle, and the package refuses to
+import without its CUDA library (no fallback)."""
 import os
 import re
 import subprocess
@@ -61,3 +62,25 @@ def test_only_allowed_modules_import_the_oracle():
             continue
         if PY_IMPORT_ORACLE.search(read(rel)):
             assert rel in allowed, rel
+
+
+def test_package_import_fails_loudly_without_the_library():
+    # the binding has no fallback: with its shared library missing, the
+    # import itself raises
+    code = (
+        "import importlib.util, sys\n"
+        "spec = importlib.util.spec_from_file_location('paper_2606_25453_gb300.build', %r)\n"
+        "mod = importlib.util.module_from_spec(spec)\n"
+        "spec.loader.exec_module(mod)\n"
+        "mod.LIB = '/nonexistent/libemugemm.so'\n"
+        "sys.modules['paper_2606_25453_gb300.build'] = mod\n"
+        "try:\n"
+        "    import paper_2606_25453_gb300\n"
+        "except ImportError as e:\n"
+        "    print('raised:', e)\n"
+        "    sys.exit(0)\n"
+        "sys.exit(3)\n" % os.path.join(ROOT, "paper_2606_25453_gb300", "build.py"))
+    import sys
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "not built" in r.stdout
