@@ -1,7 +1,8 @@
 """Host-side checks that need no GPU: the library loads and exports every
 entry point declared in include/emugemm.h, its method constants agree with
-the oracle's independent derivations, argument validation, and the
-multi-rank aggregation of bench.py over a 2-rank gloo process group."""
+the oracle's independent derivations, argument validation, the
+multi-rank aggregation of bench.py over a 2-rank gloo process group, and
+the JSON line of the benchmark's reference arm (the oracle on the host)."""
 import ctypes
 import os
 import re
@@ -160,3 +161,26 @@ def test_selector_markdown(tmp_path):
     md = bench.selector_markdown(str(path))
     assert "| I | 1e-08 | 1 | 12 | 7.00 | 100 % | 100 % | 3.0 | 8.0 | 2.67x |" in md
     assert "| I | 2048 | 1.00 | 1e-08 | 7 | 3.00 | 8.00 | 1.00e-10 | 1.00e-17 |" in md
+
+
+def test_reference_arm_json_line():
+    # the reference arm (the oracle, timed on the host's cores) prints the
+    # benchmark's JSON line: same metric, unit and config keys as our arm,
+    # plus impl, cpu_baseline and a zero-copy e2e
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--n", "512", "--cpu-rows", "8",
+                        "--steps", "2", "--warmup", "1"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["steps"] == 2 and line["warmup"] == 1
+    assert line["higher_is_better"] is True and line["value"] > 0 and line["unit"] == "TFLOP/s"
+    assert line["config"]["n"] == 512 and "workload" in line["config"]
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and "rows" in cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
