@@ -61,7 +61,9 @@
  *    level instead of tcgen05; EMU_II_CLUSTER=2 runs the bf16 Scheme II
  *    residue GEMM on CTA pairs (256 x 256 tiles, tcgen05.mma.cta_group::2)
  *    instead of single CTAs (128 x 256 tiles); EMU_FAULT=alloc makes every
- *    library-owned workspace allocation fail (fault injection).
+ *    library-owned workspace allocation fail and EMU_FAULT=launch every
+ *    fused GEMM launch of a product fail with EMU_ERR_CUDA (host-side fault
+ *    injection; nothing is run on the device in its place).
  */
 #ifndef EMUGEMM_H
 #define EMUGEMM_H
@@ -135,7 +137,10 @@ emu_status_t emu_get_status(emu_handle_t h, emu_stream_t stream);
  * status word and returns, leaving the context usable.  emu_get_status then
  * reports EMU_ERR_TIMEOUT.  (The library's own waits give up after ~1 s.)
  * Host-side fault injection: with the environment variable EMU_FAULT=alloc
- * every library-owned workspace allocation fails with EMU_ERR_ALLOC. */
+ * every library-owned workspace allocation fails with EMU_ERR_ALLOC; with
+ * EMU_FAULT=launch the fused GEMM launch of every emu_dgemm / emu_sgemm /
+ * emu_zgemm / emu_cgemm call fails with EMU_ERR_CUDA ("unspecified launch
+ * failure") after the scan and split were enqueued, and C is not written. */
 emu_status_t emu_selftest_wait(emu_handle_t h, int64_t limit_cycles, emu_stream_t stream);
 
 /* Human-readable name of a status code (static string). */

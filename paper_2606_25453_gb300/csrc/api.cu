@@ -288,15 +288,21 @@ static emu_status_t tmap_err() {
 }
 
 namespace emu {
-// EMU_FAULT=alloc: host-side fault injection for the allocation failure path.
-static bool fault_alloc() {
+// EMU_FAULT=alloc / EMU_FAULT=launch: host-side fault injection (read once).
+static int fault_mode() {
   static int v = -1;
   if (v < 0) {
     const char* e = std::getenv("EMU_FAULT");
-    v = (e && std::strcmp(e, "alloc") == 0) ? 1 : 0;
+    v = !e ? 0 : std::strcmp(e, "alloc") == 0 ? 1 : std::strcmp(e, "launch") == 0 ? 2 : 0;
   }
-  return v == 1;
+  return v;
 }
+// alloc: every library-owned workspace allocation fails.
+static bool fault_alloc() { return fault_mode() == 1; }
+// launch: the fused GEMM launch of every product fails as a launch would
+// (cudaErrorLaunchFailure, after the scan and split were enqueued); nothing
+// runs on the device that could fault.
+static cudaError_t fault_launch() { return fault_mode() == 2 ? cudaErrorLaunchFailure : cudaSuccess; }
 
 emu_status_t handle_workspace(emu_handle_s* h, size_t bytes, cudaStream_t st, uint8_t** out) {
   if (bytes == 0) bytes = 256;
@@ -597,7 +603,8 @@ emu_status_t scheme_I_gemm(emu_handle_s* h, const int8_t* hatA, int64_t rows_a, 
   a.status = h->status;
   a.num_sms = h->num_sms;
   trace_begin(h, PH_GEMM, st);
-  cudaError_t e = tc ? launch_gemm_f8tc(p, out_mode, a, st) : launch_gemm_I(p, out_mode, a, st, f8);
+  cudaError_t e = fault_launch();
+  if (e == cudaSuccess) e = tc ? launch_gemm_f8tc(p, out_mode, a, st) : launch_gemm_I(p, out_mode, a, st, f8);
   trace_end(h, PH_GEMM, st, 1);
   return cuda_err(e);
 }
@@ -694,13 +701,15 @@ emu_status_t run_scheme_II(emu_handle_s* h, const View& v, int64_t k, int nm, in
   a.scratch = ws + pl.off_scratch;
   if (!tc) {
     trace_begin(h, PH_GEMM, st);
-    cudaError_t e = launch_gemm_II(out_mode, a, mt, ct, st);
+    cudaError_t e = fault_launch();
+    if (e == cudaSuccess) e = launch_gemm_II(out_mode, a, mt, ct, st);
     trace_end(h, PH_GEMM, st, 1);
     return cuda_err(e);
   }
   // the residue GEMM is the traced GEMM phase, the CRT kernel "other"
   trace_begin(h, PH_GEMM, st);
-  cudaError_t e = launch_gemm_II_tc(out_mode, a, mt, ct, st, 1);
+  cudaError_t e = fault_launch();
+  if (e == cudaSuccess) e = launch_gemm_II_tc(out_mode, a, mt, ct, st, 1);
   trace_end(h, PH_GEMM, st, 1);
   if (e != cudaSuccess) return cuda_err(e);
   trace_begin(h, PH_OTHER, st);

@@ -1,8 +1,9 @@
 """Failure detection without faulting the GPU: a bounded device wait that is
 made to run out reports EMU_ERR_TIMEOUT through the status word and leaves
-the context usable; host-side fault injection (EMU_FAULT=alloc) turns
+the context usable; host-side fault injection: EMU_FAULT=alloc turns
 workspace allocation into EMU_ERR_ALLOC while a caller-owned workspace still
-works."""
+works, and EMU_FAULT=launch makes every fused GEMM launch fail on the host
+(EMU_ERR_CUDA, C untouched, context intact)."""
 import os
 import subprocess
 import sys
@@ -61,3 +62,41 @@ def test_alloc_fault_injection():
     assert r.returncode == 0, r.stderr
     assert "code 5" in r.stdout  # EMU_ERR_ALLOC
     assert "user-ws 64.0" in r.stdout
+
+
+CHILD_LAUNCH = r"""
+import sys, torch
+sys.path.insert(0, %r)
+import paper_2606_25453_gb300 as emu
+h = emu.Handle(0)
+A = torch.ones((64, 64), dtype=torch.float64, device="cuda")
+for scheme, p in (("I", 4), ("I_F8", 8), ("II", 10)):
+    C = torch.full((64, 64), 7.0, dtype=torch.float64, device="cuda")
+    try:
+        emu.dgemm(A, A, C, scheme=scheme, p=p, handle=h)
+        print(scheme, "no-error")
+    except emu.EmuError as e:
+        torch.cuda.synchronize()
+        print(scheme, "code", e.code, "untouched", bool((C == 7.0).all()), "|", str(e))
+try:
+    emu.zgemm(A.to(torch.complex128), A.to(torch.complex128), nm=8, handle=h)
+except emu.EmuError as e:
+    print("Z code", e.code)
+print("status", h.status(), "ctx", float((A @ A)[0, 0]))
+"""
+
+
+def test_launch_fault_injection():
+    # EMU_FAULT=launch: each fused GEMM launch fails on the host side after
+    # the scan and split were enqueued; the caller gets EMU_ERR_CUDA with
+    # the runtime's text, C is not written, nothing faults on the device,
+    # and the context stays usable
+    env = dict(os.environ, EMU_FAULT="launch")
+    r = subprocess.run([sys.executable, "-c", CHILD_LAUNCH % ROOT], env=env, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr
+    for scheme in ("I", "I_F8", "II"):
+        assert "%s code 4 untouched True" % scheme in r.stdout, r.stdout
+    assert "unspecified launch failure" in r.stdout
+    assert "Z code 4" in r.stdout
+    assert "status 0 ctx 64.0" in r.stdout
