@@ -161,7 +161,9 @@ __device__ __forceinline__ uint32_t sub6(const uint32_t* a, const uint32_t* b, u
   return br & 1u;
 }
 
-// d = k * P for a five-limb P and k < 2^32 (six limbs).
+// d = k * P for a five-limb P and k < 2^32 (six limbs).  h0..h3 are scratch
+// outputs of the multiply chain (hence the front-end note suppressed here).
+#pragma nv_diag_suppress 550
 __device__ __forceinline__ void mul6(const uint32_t* P, uint32_t k, uint32_t* d) {
   uint32_t h0, h1, h2, h3;
   asm("mul.lo.u32 %0, %10, %15;\n\t"
@@ -178,6 +180,7 @@ __device__ __forceinline__ void mul6(const uint32_t* P, uint32_t k, uint32_t* d)
         "=&r"(h2), "=&r"(h3)
       : "r"(P[0]), "r"(P[1]), "r"(P[2]), "r"(P[3]), "r"(P[4]), "r"(k));
 }
+#pragma nv_diag_default 550
 
 // Eq. (8) finish from the lazy form: x = S - kP with k = rint(t) (below
 // 3 * 20 * 256), which is round(S / P) or one off (t errs by less than 0.02
